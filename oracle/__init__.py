@@ -1,0 +1,188 @@
+"""ctypes binding of the FP64 CPU oracle (``rts_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the
+benchmark's CPU-baseline leg use it; the product path never does.  It shares
+no code with the CUDA library.  All arrays are numpy complex128 / float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rts_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_i32 = ctypes.c_int32
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (plain C11, OpenMP, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "rts_oracle.h"))):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-D_GNU_SOURCE", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            L.orc_n_baselines.restype = ctypes.c_int64
+            L.orc_n_baselines.argtypes = [_i32]
+            L.orc_baseline_index.restype = ctypes.c_int64
+            L.orc_baseline_index.argtypes = [_i32, _i32, _i32]
+            L.orc_baseline_antennas.argtypes = [_i32, _ip, _ip]
+            L.orc_delay_m.restype = ctypes.c_double
+            L.orc_delay_m.argtypes = [_dp, _i32, _i32, _i32, _i32, ctypes.c_double, ctypes.c_double]
+            L.orc_phase_turns.restype = ctypes.c_double
+            L.orc_phase_turns.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_predict.argtypes = [_i32, _i32, _i32, _dp, _dp, _i32, _dp, _dp, _dp, _i32]
+            L.orc_rotate_average.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp,
+                                             ctypes.c_double, ctypes.c_double, _dp]
+            L.orc_als.restype = _i32
+            L.orc_als.argtypes = [_i32, _dp, ctypes.c_double, _i32, _dp, _dp]
+            L.orc_subtract.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _dp]
+            L.orc_peel.restype = _i32
+            L.orc_peel.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _ip, _dp]
+            L.orc_loss_grad.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _dp,
+                                        _dp, _dp, _dp, _dp, _dp]
+            L.orc_num_threads.restype = _i32
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def n_baselines(n_ant: int) -> int:
+    return int(lib().orc_n_baselines(n_ant))
+
+
+def baseline_index(n_ant: int, i: int, j: int) -> int:
+    return int(lib().orc_baseline_index(n_ant, i, j))
+
+
+def baseline_antennas(n_ant: int):
+    nb = n_baselines(n_ant)
+    ai = np.zeros(max(nb, 1), np.int32)
+    aj = np.zeros(max(nb, 1), np.int32)
+    lib().orc_baseline_antennas(n_ant, ai.ctypes.data_as(_ip), aj.ctypes.data_as(_ip))
+    return ai[:nb], aj[:nb]
+
+
+def delay_m(uvw, t, i, j, l, m) -> float:
+    uvw = _f64(uvw)
+    return float(lib().orc_delay_m(_d(uvw), uvw.shape[1], t, i, j, l, m))
+
+
+def phase_turns(tau_m, freq_hz) -> float:
+    return float(lib().orc_phase_turns(tau_m, freq_hz))
+
+
+def predict(uvw, freq, lmS, jones, vis=None):
+    """[n_time][n_bl][n_chan][4] complex128 model visibilities (+= vis if given)."""
+    uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
+    jones = _f64(jones, np.complex128)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    n_chan, n_src = freq.shape[0], lmS.shape[0]
+    nb = n_ant * (n_ant - 1) // 2
+    acc = vis is not None
+    out = _f64(vis, np.complex128).copy() if acc else np.zeros((n_time, nb, n_chan, 4), np.complex128)
+    lib().orc_predict(n_ant, n_chan, n_time, _d(uvw), _d(freq), n_src, _d(lmS),
+                      _d(jones), _d(out), int(acc))
+    return out
+
+
+def rotate_average(uvw, freq, vis, l, m):
+    uvw, freq = _f64(uvw), _f64(freq)
+    vis = _f64(vis, np.complex128)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    nb = n_ant * (n_ant - 1) // 2
+    avg = np.zeros((nb, 4), np.complex128)
+    lib().orc_rotate_average(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(vis),
+                             float(l), float(m), _d(avg))
+    return avg
+
+
+def als(avg, S, n_ant, n_iter=20):
+    """Jones [n_ant][4] from one source's averaged visibilities; (J, status, rel)."""
+    avg = _f64(avg, np.complex128)
+    J = np.zeros((n_ant, 4), np.complex128)
+    rel = ctypes.c_double(0.0)
+    st = lib().orc_als(n_ant, _d(avg), float(S), n_iter, _d(J), ctypes.byref(rel))
+    return J, int(st), rel.value
+
+
+def subtract(uvw, freq, vis, l, m, S, jones_k):
+    uvw, freq = _f64(uvw), _f64(freq)
+    out = _f64(vis, np.complex128).copy()
+    J = _f64(jones_k, np.complex128)
+    lib().orc_subtract(uvw.shape[1], freq.shape[0], uvw.shape[0], _d(uvw), _d(freq),
+                       _d(out), float(l), float(m), float(S), _d(J))
+    return out
+
+
+def peel(uvw, freq, vis, lmS, n_iter=20, keep_avg=False):
+    """Sequential peel.  Returns (residual, jones [n_src][n_ant][4], status[, avg])."""
+    uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
+    R = _f64(vis, np.complex128).copy()
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    n_src = lmS.shape[0]
+    nb = n_ant * (n_ant - 1) // 2
+    J = np.zeros((n_src, n_ant, 4), np.complex128)
+    st = np.zeros(max(n_src, 1), np.int32)
+    avg = np.zeros((n_src, nb, 4), np.complex128) if keep_avg else None
+    lib().orc_peel(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(R), n_src, _d(lmS),
+                   n_iter, _d(J), st.ctypes.data_as(_ip), _d(avg) if keep_avg else None)
+    return (R, J, st[:n_src], avg) if keep_avg else (R, J, st[:n_src])
+
+
+def loss_grad(uvw, freq, vis, lmS, jones):
+    """(loss, dL/dJ [n_src][n_ant][4] complex, dL/dl, dL/dm, dL/dS)."""
+    uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
+    vis = _f64(vis, np.complex128)
+    jones = _f64(jones, np.complex128)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    n_src = lmS.shape[0]
+    loss = ctypes.c_double(0.0)
+    gJ = np.zeros((n_src, n_ant, 4), np.complex128)
+    gl, gm, gS = (np.zeros(max(n_src, 1)) for _ in range(3))
+    lib().orc_loss_grad(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(vis), n_src,
+                        _d(lmS), _d(jones), ctypes.byref(loss), _d(gJ), _d(gl), _d(gm), _d(gS))
+    return loss.value, gJ, gl[:n_src], gm[:n_src], gS[:n_src]
+
+
+def simulate(cad, noise=True, sources=None, jones=None):
+    """Visibility cube of a synthetic cadence: oracle prediction + generator noise."""
+    src = cad.sources() if sources is None else sources
+    J = cad.jones() if jones is None else jones
+    V = predict(cad.uvw(), cad.freqs(), src, J)
+    if noise and cad.noise_sigma > 0:
+        V += cad.noise().reshape(V.shape)
+    return V

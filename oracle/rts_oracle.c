@@ -1,0 +1,386 @@
+/* FP64 CPU oracle of the MWA calibrate-and-peel loop.
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the tests, the package's smoke check and
+ * the benchmark's CPU-baseline leg, never by the product path.  Plain loops,
+ * double precision throughout, libm sin/cos.  Shares no code with the CUDA
+ * library.
+ *
+ * What it follows.  Section 3 of the paper (the Calibration-Measurement Loop
+ * paragraph) states the method only in words: the CML steps sequentially
+ * through a list of calibrator sources, reduces calibration to linear
+ * equations per source, and fits a 2x2 Jones matrix per tile in the direction
+ * of each calibrator.  Section 2 describes visibilities as Fourier samples of
+ * the sky for each pair of receptors.  The paper prints no equation for the
+ * loop, so the steps below are the standard measurement-equation reading,
+ * each listed as a reading in the design notes:
+ *
+ *   model   V_ij(t,c) = sum_k  S_k J_i^k J_j^kH exp(-2 pi i phi_k)        (R1, R2)
+ *   phase   phi_k = (u l + v m + w (n-1)) nu_c / c_light  [turns],
+ *           n = sqrt(1 - l^2 - m^2), uvw_ij = uvw_i - uvw_j                 (R1)
+ *   peel, for each source k in list order:                                  (R4)
+ *     rotate + average   A_k(bl) = mean_{t,c} R(t,bl,c) exp(+2 pi i phi_k)  (R5)
+ *     solve              per antenna p, Z_pq = S_k J_q^H,
+ *                        J_p <- [sum_q A_pq Z_pq^H] [sum_q Z_pq Z_pq^H]^-1,
+ *                        A_qp = A_pq^H; Jacobi sweep from J = I; on every
+ *                        second sweep J <- (J_new + J_old)/2; fixed n_iter (R6)
+ *     subtract           R(t,bl,c) -= S_k J_p J_q^H exp(-2 pi i phi_k)
+ *   loss    L = sum ||V - sum_k S_k J_i J_j^H exp(-2 pi i phi_k)||_F^2 and its
+ *           gradient w.r.t. (J, l, m, S) in the PyTorch convention
+ *           dL/dRe + i dL/dIm (hand-derived adjoint, checked by differences).
+ *
+ * Parallelism: baselines are independent in every streaming step; each
+ * baseline's sums run serially in (t, c) order, and sums across baselines are
+ * taken serially in baseline order afterwards, so results do not depend on
+ * the thread count.
+ */
+#include "rts_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define C_LIGHT 299792458.0
+#define TWO_PI 6.283185307179586476925286766559
+
+typedef double complex cplx;
+typedef struct { cplx e[4]; } mat2;      /* [0 1; 2 3] */
+
+static mat2 m_load(const double* p) {
+  mat2 r;
+  for (int k = 0; k < 4; ++k) r.e[k] = p[2 * k] + I * p[2 * k + 1];
+  return r;
+}
+static void m_store(double* p, mat2 a) {
+  for (int k = 0; k < 4; ++k) { p[2 * k] = creal(a.e[k]); p[2 * k + 1] = cimag(a.e[k]); }
+}
+static mat2 m_zero(void) { mat2 r; for (int k = 0; k < 4; ++k) r.e[k] = 0; return r; }
+static mat2 m_eye(void) { mat2 r = m_zero(); r.e[0] = 1; r.e[3] = 1; return r; }
+static mat2 m_mul(mat2 a, mat2 b) {
+  mat2 r;
+  r.e[0] = a.e[0] * b.e[0] + a.e[1] * b.e[2];
+  r.e[1] = a.e[0] * b.e[1] + a.e[1] * b.e[3];
+  r.e[2] = a.e[2] * b.e[0] + a.e[3] * b.e[2];
+  r.e[3] = a.e[2] * b.e[1] + a.e[3] * b.e[3];
+  return r;
+}
+static mat2 m_herm(mat2 a) {
+  mat2 r;
+  r.e[0] = conj(a.e[0]); r.e[1] = conj(a.e[2]);
+  r.e[2] = conj(a.e[1]); r.e[3] = conj(a.e[3]);
+  return r;
+}
+static mat2 m_add(mat2 a, mat2 b) { for (int k = 0; k < 4; ++k) a.e[k] += b.e[k]; return a; }
+static mat2 m_sub(mat2 a, mat2 b) { for (int k = 0; k < 4; ++k) a.e[k] -= b.e[k]; return a; }
+static mat2 m_scale(mat2 a, cplx s) { for (int k = 0; k < 4; ++k) a.e[k] *= s; return a; }
+static cplx m_trace(mat2 a) { return a.e[0] + a.e[3]; }
+static double m_norm2(mat2 a) {
+  double s = 0;
+  for (int k = 0; k < 4; ++k) s += creal(a.e[k]) * creal(a.e[k]) + cimag(a.e[k]) * cimag(a.e[k]);
+  return s;
+}
+/* closed-form 2x2 inverse: [d -b; -c a] / (ad - bc) */
+static mat2 m_inv(mat2 a) {
+  cplx det = a.e[0] * a.e[3] - a.e[1] * a.e[2];
+  mat2 r;
+  r.e[0] = a.e[3] / det; r.e[1] = -a.e[1] / det;
+  r.e[2] = -a.e[2] / det; r.e[3] = a.e[0] / det;
+  return r;
+}
+static int m_finite(mat2 a) {
+  for (int k = 0; k < 4; ++k)
+    if (!isfinite(creal(a.e[k])) || !isfinite(cimag(a.e[k]))) return 0;
+  return 1;
+}
+
+int32_t orc_num_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ---- baselines ---------------------------------------------------------- */
+
+int64_t orc_n_baselines(int32_t n_ant) { return (int64_t)n_ant * (n_ant - 1) / 2; }
+
+int64_t orc_baseline_index(int32_t n_ant, int32_t i, int32_t j) {
+  return (int64_t)i * n_ant - (int64_t)i * (i + 1) / 2 + (j - i - 1);
+}
+
+/* inverse map by enumeration: rows i = 0.., columns j = i+1.. */
+void orc_baseline_antennas(int32_t n_ant, int32_t* ant_i, int32_t* ant_j) {
+  int64_t b = 0;
+  for (int32_t i = 0; i < n_ant; ++i)
+    for (int32_t j = i + 1; j < n_ant; ++j) { ant_i[b] = i; ant_j[b] = j; ++b; }
+}
+
+/* ---- geometry and phase (reading R1) ------------------------------------ */
+
+double orc_delay_m(const double* uvw, int32_t n_ant, int32_t t, int32_t i, int32_t j,
+                   double l, double m) {
+  const double* a = uvw + ((int64_t)t * n_ant + i) * 3;
+  const double* b = uvw + ((int64_t)t * n_ant + j) * 3;
+  double u = a[0] - b[0], v = a[1] - b[1], w = a[2] - b[2];
+  double n = sqrt(1.0 - l * l - m * m);
+  return u * l + v * m + w * (n - 1.0);
+}
+
+/* phase in turns, reduced to [-1/2, 1/2] by x - round(x) */
+double orc_phase_turns(double tau_m, double freq_hz) {
+  double x = tau_m * freq_hz / C_LIGHT;
+  return x - nearbyint(x);
+}
+
+static cplx phasor(double turns, double sign) {       /* exp(sign * 2 pi i turns) */
+  double a = TWO_PI * turns;
+  return cos(a) + I * sign * sin(a);
+}
+
+static int32_t* g_ai;
+static int32_t* g_aj;
+static int32_t g_map_n = -1;
+static void antenna_map(int32_t n_ant, int32_t** ai, int32_t** aj) {
+  if (g_map_n != n_ant) {
+    int64_t nb = orc_n_baselines(n_ant);
+    free(g_ai); free(g_aj);
+    g_ai = (int32_t*)malloc(sizeof(int32_t) * (nb > 0 ? nb : 1));
+    g_aj = (int32_t*)malloc(sizeof(int32_t) * (nb > 0 ? nb : 1));
+    orc_baseline_antennas(n_ant, g_ai, g_aj);
+    g_map_n = n_ant;
+  }
+  *ai = g_ai; *aj = g_aj;
+}
+
+static double* vis_at(double* vis, int64_t n_bl, int32_t n_chan, int32_t t, int64_t bl, int32_t c) {
+  return vis + (((int64_t)t * n_bl + bl) * n_chan + c) * 8;
+}
+
+/* ---- predict: V += sum_k S_k J_i J_j^H exp(-2 pi i phi_k) (R1, R2) ------- */
+
+void orc_predict(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                 const double* freq, int32_t n_src, const double* lmS, const double* jones,
+                 double* vis, int32_t accumulate) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    int32_t i = ai[bl], j = aj[bl];
+    for (int32_t t = 0; t < n_time; ++t)
+      for (int32_t c = 0; c < n_chan; ++c) {
+        double* out = vis_at(vis, n_bl, n_chan, t, bl, c);
+        mat2 v = accumulate ? m_load(out) : m_zero();
+        for (int32_t k = 0; k < n_src; ++k) {
+          double l = lmS[3 * k], m = lmS[3 * k + 1], S = lmS[3 * k + 2];
+          mat2 Ji = m_load(jones + ((int64_t)k * n_ant + i) * 8);
+          mat2 Jj = m_load(jones + ((int64_t)k * n_ant + j) * 8);
+          mat2 M = m_scale(m_mul(Ji, m_herm(Jj)), S);
+          double phi = orc_phase_turns(orc_delay_m(uvw, n_ant, t, i, j, l, m), freq[c]);
+          v = m_add(v, m_scale(M, phasor(phi, -1.0)));
+        }
+        m_store(out, v);
+      }
+  }
+}
+
+/* ---- rotate + average (R5): A(bl) = mean_{t,c} V exp(+2 pi i phi) -------- */
+
+void orc_rotate_average(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                        const double* freq, const double* vis, double l, double m,
+                        double* avg) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  double inv_n = 1.0 / ((double)n_time * n_chan);
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    int32_t i = ai[bl], j = aj[bl];
+    mat2 acc = m_zero();
+    for (int32_t t = 0; t < n_time; ++t) {
+      double tau = orc_delay_m(uvw, n_ant, t, i, j, l, m);
+      for (int32_t c = 0; c < n_chan; ++c) {
+        mat2 v = m_load(vis_at((double*)vis, n_bl, n_chan, t, bl, c));
+        acc = m_add(acc, m_scale(v, phasor(orc_phase_turns(tau, freq[c]), +1.0)));
+      }
+    }
+    m_store(avg + bl * 8, m_scale(acc, inv_n));
+  }
+}
+
+/* ---- ALS solve for one source (R6) --------------------------------------
+ * Returns 0 when the last relative change ||J_new - J_old||_F / ||J_new||_F
+ * is <= 1e-6, 1 when it is larger, -4 when a non-finite value appears.    */
+
+int32_t orc_als(int32_t n_ant, const double* avg, double S, int32_t n_iter,
+                double* jones, double* rel_change) {
+  mat2* J = (mat2*)malloc(sizeof(mat2) * n_ant);
+  mat2* Jn = (mat2*)malloc(sizeof(mat2) * n_ant);
+  for (int32_t p = 0; p < n_ant; ++p) J[p] = m_eye();
+  double rel = 0.0;
+  int finite = 1;
+  for (int32_t it = 1; it <= n_iter; ++it) {
+    for (int32_t p = 0; p < n_ant; ++p) {
+      mat2 A = m_zero(), C = m_zero();
+      for (int32_t q = 0; q < n_ant; ++q) {
+        if (q == p) continue;
+        mat2 Vpq = p < q ? m_load(avg + orc_baseline_index(n_ant, p, q) * 8)
+                         : m_herm(m_load(avg + orc_baseline_index(n_ant, q, p) * 8));
+        mat2 Z = m_scale(m_herm(J[q]), S);          /* Z_pq = B J_q^H, B = S I */
+        A = m_add(A, m_mul(Vpq, m_herm(Z)));
+        C = m_add(C, m_mul(Z, m_herm(Z)));
+      }
+      Jn[p] = m_mul(A, m_inv(C));
+    }
+    if (it % 2 == 0)
+      for (int32_t p = 0; p < n_ant; ++p) Jn[p] = m_scale(m_add(Jn[p], J[p]), 0.5);
+    double dn = 0.0, nn = 0.0;
+    for (int32_t p = 0; p < n_ant; ++p) {
+      dn += m_norm2(m_sub(Jn[p], J[p]));
+      nn += m_norm2(Jn[p]);
+      if (!m_finite(Jn[p])) finite = 0;
+    }
+    rel = sqrt(dn / nn);
+    mat2* tmp = J; J = Jn; Jn = tmp;
+  }
+  for (int32_t p = 0; p < n_ant; ++p) m_store(jones + (int64_t)p * 8, J[p]);
+  free(J); free(Jn);
+  if (rel_change) *rel_change = rel;
+  if (!finite || !isfinite(rel)) return -4;
+  return rel > 1e-6 ? 1 : 0;
+}
+
+/* ---- subtract one source: R -= S J_i J_j^H exp(-2 pi i phi) -------------- */
+
+void orc_subtract(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                  const double* freq, double* vis, double l, double m, double S,
+                  const double* jones) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    int32_t i = ai[bl], j = aj[bl];
+    mat2 M = m_scale(m_mul(m_load(jones + (int64_t)i * 8), m_herm(m_load(jones + (int64_t)j * 8))), S);
+    for (int32_t t = 0; t < n_time; ++t) {
+      double tau = orc_delay_m(uvw, n_ant, t, i, j, l, m);
+      for (int32_t c = 0; c < n_chan; ++c) {
+        double* p = vis_at(vis, n_bl, n_chan, t, bl, c);
+        m_store(p, m_sub(m_load(p), m_scale(M, phasor(orc_phase_turns(tau, freq[c]), -1.0))));
+      }
+    }
+  }
+}
+
+/* ---- the peel: average, solve, subtract for each source in list order ---- */
+
+int32_t orc_peel(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                 const double* freq, double* vis, int32_t n_src, const double* lmS,
+                 int32_t n_iter, double* jones, int32_t* status, double* avg_per_src) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  double* avg = (double*)malloc(sizeof(double) * 8 * (n_bl > 0 ? n_bl : 1));
+  int32_t worst = 0;
+  for (int32_t k = 0; k < n_src; ++k) {
+    double l = lmS[3 * k], m = lmS[3 * k + 1], S = lmS[3 * k + 2];
+    double* Jk = jones + (int64_t)k * n_ant * 8;
+    orc_rotate_average(n_ant, n_chan, n_time, uvw, freq, vis, l, m, avg);
+    if (avg_per_src) memcpy(avg_per_src + (int64_t)k * n_bl * 8, avg, sizeof(double) * 8 * n_bl);
+    int32_t st = orc_als(n_ant, avg, S, n_iter, Jk, NULL);
+    if (status) status[k] = st;
+    if (st < 0) worst = st;
+    orc_subtract(n_ant, n_chan, n_time, uvw, freq, vis, l, m, S, Jk);
+  }
+  free(avg);
+  return worst;
+}
+
+/* ---- loss and its gradient ------------------------------------------------
+ * R = V - sum_k M_k exp(-2 pi i phi_k), M_k = S_k J_i J_j^H,  L = sum ||R||^2.
+ * With G_k = sum_{t,c} R exp(+2 pi i phi_k) and
+ *      H_k^l = sum_{t,c} R exp(+2 pi i phi_k) d(phi_k)/dl,
+ *      d(phi)/dl = (u - w l/n) nu / c_light  (turns per unit l), same for m:
+ *   dL/dJ_i  += -2 S_k G_k J_j          dL/dJ_j += -2 S_k G_k^H J_i
+ *   dL/dS_k  += -2 Re tr(G_k^H J_i J_j^H)
+ *   dL/dl_k  += -4 pi Im tr(H_k^lH M_k)  (and m likewise).                  */
+
+void orc_loss_grad(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                   const double* freq, const double* vis, int32_t n_src, const double* lmS,
+                   const double* jones, double* loss, double* g_jones, double* g_l,
+                   double* g_m, double* g_S) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  int64_t nkb = (int64_t)n_src * n_bl;
+  mat2* G = (mat2*)calloc((size_t)(nkb > 0 ? nkb : 1), sizeof(mat2));
+  mat2* Hl = (mat2*)calloc((size_t)(nkb > 0 ? nkb : 1), sizeof(mat2));
+  mat2* Hm = (mat2*)calloc((size_t)(nkb > 0 ? nkb : 1), sizeof(mat2));
+  double* bl_loss = (double*)calloc((size_t)(n_bl > 0 ? n_bl : 1), sizeof(double));
+  mat2* Mk = (mat2*)malloc(sizeof(mat2) * (nkb > 0 ? nkb : 1));
+  for (int32_t k = 0; k < n_src; ++k)
+    for (int64_t bl = 0; bl < n_bl; ++bl) {
+      mat2 Ji = m_load(jones + ((int64_t)k * n_ant + ai[bl]) * 8);
+      mat2 Jj = m_load(jones + ((int64_t)k * n_ant + aj[bl]) * 8);
+      Mk[k * n_bl + bl] = m_scale(m_mul(Ji, m_herm(Jj)), lmS[3 * k + 2]);
+    }
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    int32_t i = ai[bl], j = aj[bl];
+    double* phi = (double*)malloc(sizeof(double) * (n_src > 0 ? n_src : 1));
+    for (int32_t t = 0; t < n_time; ++t) {
+      const double* a = uvw + ((int64_t)t * n_ant + i) * 3;
+      const double* b = uvw + ((int64_t)t * n_ant + j) * 3;
+      double u = a[0] - b[0], w = a[2] - b[2], v = a[1] - b[1];
+      for (int32_t c = 0; c < n_chan; ++c) {
+        mat2 R = m_load(vis_at((double*)vis, n_bl, n_chan, t, bl, c));
+        for (int32_t k = 0; k < n_src; ++k) {
+          phi[k] = orc_phase_turns(orc_delay_m(uvw, n_ant, t, i, j, lmS[3 * k], lmS[3 * k + 1]), freq[c]);
+          R = m_sub(R, m_scale(Mk[k * n_bl + bl], phasor(phi[k], -1.0)));
+        }
+        bl_loss[bl] += m_norm2(R);
+        for (int32_t k = 0; k < n_src; ++k) {
+          double l = lmS[3 * k], m = lmS[3 * k + 1];
+          double n = sqrt(1.0 - l * l - m * m);
+          double dphi_dl = (u - w * l / n) * freq[c] / C_LIGHT;
+          double dphi_dm = (v - w * m / n) * freq[c] / C_LIGHT;
+          mat2 Rr = m_scale(R, phasor(phi[k], +1.0));
+          G[k * n_bl + bl] = m_add(G[k * n_bl + bl], Rr);
+          Hl[k * n_bl + bl] = m_add(Hl[k * n_bl + bl], m_scale(Rr, dphi_dl));
+          Hm[k * n_bl + bl] = m_add(Hm[k * n_bl + bl], m_scale(Rr, dphi_dm));
+        }
+      }
+    }
+    free(phi);
+  }
+  double L = 0.0;
+  for (int64_t bl = 0; bl < n_bl; ++bl) L += bl_loss[bl];
+  *loss = L;
+  if (g_jones) memset(g_jones, 0, sizeof(double) * 8 * n_src * (size_t)n_ant);
+  for (int32_t k = 0; k < n_src; ++k) {
+    double S = lmS[3 * k + 2];
+    double gl = 0.0, gm = 0.0, gS = 0.0;
+    for (int64_t bl = 0; bl < n_bl; ++bl) {
+      int32_t i = ai[bl], j = aj[bl];
+      mat2 Ji = m_load(jones + ((int64_t)k * n_ant + i) * 8);
+      mat2 Jj = m_load(jones + ((int64_t)k * n_ant + j) * 8);
+      mat2 Gk = G[k * n_bl + bl];
+      mat2 M = Mk[k * n_bl + bl];
+      if (g_jones) {
+        double* gi = g_jones + ((int64_t)k * n_ant + i) * 8;
+        double* gj = g_jones + ((int64_t)k * n_ant + j) * 8;
+        m_store(gi, m_add(m_load(gi), m_scale(m_mul(Gk, Jj), -2.0 * S)));
+        m_store(gj, m_add(m_load(gj), m_scale(m_mul(m_herm(Gk), Ji), -2.0 * S)));
+      }
+      gS += -2.0 * creal(m_trace(m_mul(m_herm(Gk), m_mul(Ji, m_herm(Jj)))));
+      gl += -4.0 * M_PI * cimag(m_trace(m_mul(m_herm(Hl[k * n_bl + bl]), M)));
+      gm += -4.0 * M_PI * cimag(m_trace(m_mul(m_herm(Hm[k * n_bl + bl]), M)));
+    }
+    if (g_l) g_l[k] = gl;
+    if (g_m) g_m[k] = gm;
+    if (g_S) g_S[k] = gS;
+  }
+  free(G); free(Hl); free(Hm); free(bl_loss); free(Mk);
+}
