@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Benchmark of the calibrate-and-peel cadence on GB300.
+
+Workload (a synthetic MWA cadence with the shape of the paper's Table 1):
+512 antennas (130816 baselines), 768 channels x 40 kHz from 167 MHz, 8 times x
+1 s, 4 polarisations, complex64 (25.7 GB cube), 1000 sources peeled with 20 ALS
+sweeps each.  The cube is the library's own prediction of the 1000 sources with
+their true Jones matrices plus Gaussian noise (sigma = 0.01 Jy), resident in HBM
+before timing.  One step = one rts_peel_cadence call over that cube (out of
+place: the input stays intact, the residual goes to a second cube).
+
+Metric: source x visibility peel updates per second = K N_bl N_chan N_t / time.
+Extra legs in the same run: end to end through rts_peel_cadence_host (pinned
+host buffers, copies timed), the plain FP64 GPU path on the same input for a
+bounded number of sources, the adjoint step (config with 300 sources,
+perturbed positions; mixed and FP64 paths), and the FP64 CPU oracle on a
+bounded sample (the CPU baseline).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "source×visibility peel updates/s (512 ant, 768 ch); adjoint step ms vs FP64 path"
+UNIT = "updates/s"
+BYTES_PER_UPDATE = 64          # complex64 2x2 read + write per source x visibility
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload_config(cad, n_src, n_iter):
+    return {
+        "workload": (f"MWA cadence {cad.n_ant} ant ({cad.n_bl} baselines) x {cad.n_chan} ch x "
+                     f"{cad.n_time} t x 4 pol complex64, {n_src} sources peeled, {n_iter} ALS sweeps"),
+        "n_ant": cad.n_ant, "n_baselines": cad.n_bl, "n_chan": cad.n_chan, "n_time": cad.n_time,
+        "n_sources": n_src, "n_iter": n_iter,
+        "cube_bytes": cad.n_vis * 32,
+        "l2": "inputs larger than L2 (25.7 GB cube vs 129 MB L2); no flush needed",
+        "precision": "mixed: FP32 streaming, FP64 phase argument and normal-equation sums",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks (nvidia-smi sampled during the timed region)
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("common.cuh", "stream_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1003_5575_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the kernel source."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+        e = t[kernel]
+        if e.get("source_hash") == kernel_source_hash():
+            return e["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+
+def oracle_sample(n_chan=16, n_src=4):
+    """A bounded sample of the same workload for the FP64 CPU oracle: the full
+    512-antenna geometry and 8 times, the first n_chan channels, n_src sources."""
+    import numpy as np
+    import oracle
+    from synth import config
+    cad = config(3).with_(n_chan=n_chan, n_src=n_src)
+    V = oracle.simulate(cad)
+    V = V.astype(np.complex64).astype(np.complex128)
+    return cad, V
+
+
+def time_oracle(cad, V, reps=1):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.peel(cad.uvw(), cad.freqs(), V, cad.sources(), n_iter=20)
+    dt = (time.perf_counter() - t0) / reps
+    return cad.n_src * cad.n_vis / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from synth import config
+    oracle.build()
+    cad, V = oracle_sample(n_chan=8, n_src=2)
+    for _ in range(args.warmup):
+        time_oracle(cad, V)
+    times = []
+    for _ in range(args.steps):
+        _, dt = time_oracle(cad, V)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = cad.n_src * cad.n_vis / (ms / 1e3)
+    sample = (f"512 ant, 8 t, first {cad.n_chan} of 768 channels, {cad.n_src} sources per step "
+              "(FP64 C oracle, OpenMP over baselines)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(config(3), 1000, 20),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU legs
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sources", type=int, default=1000, help="sources peeled per cadence")
+    ap.add_argument("--n-iter", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / adjoint / CPU legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1003_5575_gb300 import Peeler, _abi
+    from synth import config
+
+    cad = config(3).with_(n_src=args.sources, seed=config(3).seed + 1000 * rank)
+    src = cad.sources()
+    K = cad.n_src
+    log(f"[rank {rank}] building cadence: {cad.n_ant} ant, {cad.n_chan} ch, {cad.n_time} t, {K} sources")
+    p = Peeler(cad.uvw(), cad.freqs(), n_iter=args.n_iter, precision="mixed", max_sources=K)
+    J_true = torch.from_numpy(cad.jones().astype(np.complex64)).cuda()
+    stream = torch.cuda.current_stream()
+    d_vis = p.predict(src, J_true)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cad.seed)
+    noise = torch.randn(d_vis.shape + (2,), generator=gen, device="cuda", dtype=torch.float32)
+    d_vis.view(torch.float32).view(noise.shape).add_(noise, alpha=cad.noise_sigma)
+    del noise
+    d_resid = p.empty_cube()
+    d_jones = torch.empty((K, cad.n_ant, 4), dtype=torch.complex64, device="cuda")
+    torch.cuda.synchronize()
+    updates_per_step = K * cad.n_vis
+
+    for _ in range(args.warmup):
+        p.cadence(d_vis, src, resid=d_resid, jones=d_jones, status=False)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    _abi.rts_peel_timing(p.h, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        p.cadence(d_vis, src, resid=d_resid, jones=d_jones, status=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    _abi.rts_peel_timing(p.h, 0)
+    ktimes = _abi.rts_peel_timing_read(p.h)
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    value = world * updates_per_step * args.steps / (ms_total / 1e3)
+    launches = sum(v[2] for v in ktimes.values())
+
+    # results of the timed cadence: statuses (untimed re-run with status)
+    _, _, st = p.cadence(d_vis, src, resid=d_resid, jones=d_jones, status=True)
+    n_nonconv = int(np.sum(st == 1))
+
+    # roofline of the dominant kernel (subtract k + average k+1)
+    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ms_k3, n_k3, _ = ktimes["sub_average"]
+    per_launch_s = (ms_k3 / n_k3) / 1e3 if n_k3 else float("nan")
+    alg_bytes = cad.n_vis * BYTES_PER_UPDATE
+    achieved = alg_bytes / per_launch_s / 1e9
+    shares = {k: round(v[0] / max(1e-9, sum(x[0] for x in ktimes.values())), 4) for k, v in ktimes.items()
+              if v[2]}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": ncu_traffic("k_stream_mixed<true,true>"),
+                "kernel": "k_stream_mixed<SUB,ACC> (subtract source k + rotate/average source k+1)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": per_launch_s * 1e3,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
+                "device_time_share": shares}
+    log(f"[rank {rank}] {ms_step:.1f} ms/step, {value:.3e} updates/s, K3 {achieved:.0f} GB/s")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MWA-shaped cadence, library-predicted sky + noise)",
+        "config": dict(workload_config(cad, K, args.n_iter), parallelism=f"replicas{world}"),
+        "clocks": clk, "gpu_launches": int(launches), "roofline": roofline,
+        "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items() if v[2]},
+        "status": {"not_converged": n_nonconv, "sources": K},
+    }
+
+    # ---- end to end through the host-buffer C-ABI call ---------------------
+    if not args.no_e2e:
+        cube_bytes = cad.n_vis * 32
+        h_in = _abi.rts_host_alloc(cube_bytes)
+        h_out = _abi.rts_host_alloc(cube_bytes)
+        try:
+            import ctypes
+            arr = np.ctypeslib.as_array((ctypes.c_float * (cad.n_vis * 8)).from_address(h_in))
+            torch.from_numpy(arr).copy_(d_vis.view(torch.float32).reshape(-1))
+            h_vis = torch.from_numpy(arr).view(torch.complex64).view(p.cube_shape)
+            arr_o = np.ctypeslib.as_array((ctypes.c_float * (cad.n_vis * 8)).from_address(h_out))
+            h_res = torch.from_numpy(arr_o).view(torch.complex64).view(p.cube_shape)
+            p.cadence_host(h_vis, src, d_work=d_resid, h_resid=h_res)
+            n_e2e = max(1, min(args.steps, 2))
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                p.cadence_host(h_vis, src, d_work=d_resid, h_resid=h_res)
+            dt = max_over_ranks((time.perf_counter() - t0) / n_e2e)
+            line["e2e"] = {"value": world * updates_per_step / dt, "unit": UNIT,
+                           "h2d_bytes_per_step": cube_bytes + K * 24,
+                           "d2h_bytes_per_step": cube_bytes + K * cad.n_ant * 32 + K * 4,
+                           "ms_per_step": dt * 1e3, "steps": n_e2e,
+                           "api": "rts_peel_cadence_host (pinned host buffers from rts_host_alloc)"}
+        finally:
+            _abi.rts_host_free(h_in)
+            _abi.rts_host_free(h_out)
+
+    if not args.no_extra:
+        line.update(extra_legs(args, p, cad, d_vis, d_resid, src, rank))
+
+    p.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def extra_legs(args, p, cad, d_vis, d_resid, src, rank):
+    """FP64-path comparison, adjoint step, CPU baseline (rank 0 at N=1 only)."""
+    import numpy as np
+    import torch
+    from paper_1003_5575_gb300 import Peeler
+    from synth import config
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # plain FP64 GPU path on the same input, first k64 sources, vs the mixed path on the same sources
+    k64 = 4
+    d_jm = torch.empty((k64, cad.n_ant, 4), dtype=torch.complex64, device="cuda")
+    a, b = ev(), ev()
+    p.cadence(d_vis, src[:k64], resid=d_resid, jones=d_jm, status=False)
+    a.record()
+    p.cadence(d_vis, src[:k64], resid=d_resid, jones=d_jm, status=False)
+    b.record()
+    torch.cuda.synchronize()
+    ms_mixed = a.elapsed_time(b)
+    R_mixed_sample = d_resid[:, :64].cpu().numpy()
+    J_mixed = d_jm.cpu().numpy()
+    p64 = Peeler(cad.uvw(), cad.freqs(), n_iter=args.n_iter, precision="fp64", max_sources=k64)
+    v64 = d_vis.to(torch.complex128)
+    d_j64 = torch.empty((k64, cad.n_ant, 4), dtype=torch.complex128, device="cuda")
+    r64 = torch.empty_like(v64)
+    p64.cadence(v64, src[:1], resid=r64, jones=d_j64[:1], status=False)     # warm
+    a, b = ev(), ev()
+    a.record()
+    p64.cadence(v64, src[:k64], resid=r64, jones=d_j64, status=False)
+    b.record()
+    torch.cuda.synchronize()
+    ms_64 = a.elapsed_time(b)
+    R64 = r64[:, :64].cpu().numpy()
+    J64 = d_j64.cpu().numpy()
+    rms = float(torch.sqrt(torch.mean(d_vis.view(torch.float32).double() ** 2)).item())
+    out["fp64_path"] = {
+        "sources": k64, "ms_mixed": ms_mixed, "ms_fp64": ms_64, "speedup_mixed_vs_fp64": ms_64 / ms_mixed,
+        "updates_per_s_fp64": k64 * cad.n_vis / (ms_64 / 1e3),
+        "mixed_vs_fp64_max_resid_err_x_rms": float(np.abs(R_mixed_sample - R64).max() / rms),
+        "mixed_vs_fp64_jones_rel": float(max(np.linalg.norm(J_mixed[k] - J64[k]) / np.linalg.norm(J64[k])
+                                             for k in range(k64))),
+        "note": "same input cube; residual error sampled on the first 64 baselines",
+    }
+    del v64, r64
+    p64.close()
+    torch.cuda.empty_cache()
+
+    # adjoint step at the config-5 shape (300 sources, positions perturbed by 1 arcmin)
+    c5 = config(5)
+    pa = Peeler(c5.uvw(), c5.freqs(), n_iter=args.n_iter, precision="mixed", max_sources=c5.n_src)
+    Jt = torch.from_numpy(c5.jones().astype(np.complex64)).cuda()
+    pa.predict(c5.sources(), Jt, out=d_resid)
+    s_fit = torch.from_numpy(c5.perturbed_sources()).cuda()
+    J_fit = Jt.clone()
+    for _ in range(2):
+        pa.grad(d_resid, J_fit, s_fit)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 3)
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(steps):
+        loss, gJ, gs = pa.grad(d_resid, J_fit, s_fit)
+    b.record()
+    torch.cuda.synchronize()
+    ms_adj = a.elapsed_time(b) / steps
+    # the FP64 adjoint on a bounded number of sources, per source x visibility
+    k_adj64 = 8
+    pa64 = Peeler(c5.uvw(), c5.freqs(), n_iter=args.n_iter, precision="fp64", max_sources=k_adj64)
+    v64 = d_resid.to(torch.complex128)
+    J64 = Jt[:k_adj64].to(torch.complex128)
+    pa64.grad(v64, J64, s_fit[:k_adj64])
+    a, b = ev(), ev()
+    a.record()
+    pa64.grad(v64, J64, s_fit[:k_adj64])
+    b.record()
+    torch.cuda.synchronize()
+    ms_adj64 = a.elapsed_time(b)
+    per_upd_mixed = ms_adj / (c5.n_src * c5.n_vis)
+    per_upd_64 = ms_adj64 / (k_adj64 * c5.n_vis)
+    out["adjoint"] = {
+        "workload": "512 ant x 768 ch x 8 t, 300 sources, positions perturbed N(0, 1 arcmin^2); loss + dL/d(J,l,m,S)",
+        "ms_per_step": ms_adj, "loss": float(loss.item()),
+        "fp64_ms_per_step_at_300_sources_extrapolated": per_upd_64 * c5.n_src * c5.n_vis,
+        "fp64_sources_timed": k_adj64, "speedup_mixed_vs_fp64": per_upd_64 / per_upd_mixed,
+    }
+    del v64
+    pa64.close()
+    pa.close()
+
+    # CPU oracle baseline on a bounded sample (rank 0, N = 1)
+    if rank == 0 and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        import oracle
+        oc, V = oracle_sample(n_chan=16, n_src=4)
+        val, dt = time_oracle(oc, V)
+        out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": (f"512 ant, 8 t, first {oc.n_chan} of 768 channels, {oc.n_src} "
+                                          f"sources, FP64 C oracle, {dt:.1f} s")}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

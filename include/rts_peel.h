@@ -1,0 +1,175 @@
+/* rts_peel.h - C ABI of the GB300 calibrate-and-peel library (librtspeel.so).
+ *
+ * The library implements the per-source loop of the Calibration-Measurement
+ * Loop (CML) of the MWA Real Time System (Edgar et al., arXiv:1003.5575,
+ * Section 3, the CML item of the stage list: the CML steps sequentially
+ * through a list of calibrator sources, reducing calibration to a set of
+ * linear equations per source whose unknowns include a 2x2 Jones matrix per
+ * tile in the direction of the calibrator).  For each source in list order it
+ * phase-rotates every 2x2 visibility to the source direction, averages over
+ * the cadence, solves per-antenna Jones matrices by alternating least squares
+ * and subtracts the predicted source from the residual.
+ *
+ * Conventions (the paper prints no formula for the loop; these are the
+ * standard measurement-equation readings the library follows):
+ *   V_ij(t,c)  = sum_k S_k J_i^k J_j^kH exp(-2 pi i phi_k(t,ij,c))
+ *   phi_k      = (u l_k + v m_k + w (n_k - 1)) nu_c / c_light  [turns],
+ *                n_k = sqrt(1 - l_k^2 - m_k^2), (u,v,w)_ij = uvw_i - uvw_j
+ *   baselines  i < j (no autocorrelations), index
+ *              bl(i,j) = i*n_ant - i*(i+1)/2 + (j - i - 1)
+ *   2x2 layout [XX, XY, YX, YY] row major, complex = interleaved (re, im)
+ *   cube       vis[n_time][n_bl][n_chan][4] complex
+ *              (complex64 in RTS_PREC_MIXED, complex128 in RTS_PREC_FP64)
+ *   Jones      jones[n_src][n_ant][4] complex, same precision as the cube
+ *   sources    host double [n_src][3] = (l, m, S in Jy), in peel order
+ *
+ * Ownership: the caller owns every pointer it passes; "d_" pointers are
+ * device memory, "h_" pointers host memory.  The handle owns the device
+ * workspace it allocates in rts_peel_init (the paper's advice in Section 5
+ * to pre-allocate all workspace at initialisation) and frees it in
+ * rts_peel_destroy.  Calls are asynchronous on `stream` (a cudaStream_t, NULL
+ * = legacy default stream) unless an h_status pointer is given, which makes
+ * the call wait for its stream.  A handle must not be used from two host
+ * threads at once.
+ *
+ * Errors: every int-returning call returns RTS_OK (0) or a negative code; the
+ * text of the last error is available from rts_peel_last_error.  Invalid
+ * arguments are rejected on the host before any device work.  No call aborts
+ * the process or traps on the device.
+ */
+#ifndef RTS_PEEL_H
+#define RTS_PEEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTS_OK               0
+#define RTS_NOT_CONVERGED    1   /* per-source status only */
+#define RTS_EINVAL         (-1)  /* bad argument */
+#define RTS_ENOMEM         (-2)  /* device allocation failed */
+#define RTS_ECUDA          (-3)  /* CUDA runtime error (launch, copy, device) */
+#define RTS_ENONFINITE     (-4)  /* NaN/Inf in averaged data or in a Jones solve */
+
+#define RTS_PREC_MIXED 0  /* complex64 cube; FP64 phase and normal-equation sums */
+#define RTS_PREC_FP64  1  /* complex128 cube; FP64 everywhere (plain comparator) */
+
+typedef struct rts_peel_t rts_peel_t;   /* opaque handle */
+
+typedef struct rts_peel_config {
+  int32_t n_ant;        /* tiles, 2 .. 8192 */
+  int32_t n_chan;       /* channels, 1 .. 65536 */
+  int32_t n_time;       /* time samples per cadence, 1 .. 1024 */
+  int32_t n_iter;       /* ALS sweeps per source, 1 .. 10000 (20 is the default reading) */
+  int32_t precision;    /* RTS_PREC_MIXED or RTS_PREC_FP64 */
+  int32_t max_sources;  /* largest n_src any call will pass, >= 1 */
+  const double* uvw;    /* host [n_time][n_ant][3] antenna (u, v, w) in metres; copied */
+  const double* freq_hz;/* host [n_chan] channel centres in Hz; must be uniformly spaced
+                           (nu_c = nu_0 + c dnu to 1e-9 relative); copied */
+} rts_peel_config;
+
+/* Validate `cfg`, allocate the device workspace on the current device, copy
+ * uvw and frequencies.  On success *out is a new handle.  Errors: RTS_EINVAL
+ * (cfg, sizes, non-uniform channels, non-finite uvw), RTS_ENOMEM, RTS_ECUDA;
+ * *out is then NULL and the message is available from rts_peel_last_error(NULL). */
+int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out);
+
+/* Replace the antenna uvw for the next cadence (host [n_time][n_ant][3] metres).
+ * Ordered on `stream` before later calls on that stream. */
+int rts_peel_set_uvw(rts_peel_t* h, const double* h_uvw, void* stream);
+
+/* One cadence of the calibrate-and-peel loop (Section 3, CML).
+ *   d_vis    [n_time][n_bl][n_chan][4] input visibilities (read only)
+ *   d_resid  same shape; receives the residual after all n_src sources are
+ *            subtracted.  d_resid == d_vis peels in place.  Other overlap is
+ *            undefined.
+ *   n_src    0 .. max_sources;  h_src  host [n_src][3] (l, m, S), peel order;
+ *            l^2 + m^2 < 1, S > 0 and finite.
+ *   d_jones  [n_src][n_ant][4] receives each source's solved Jones matrices.
+ *   h_status optional host [n_src]: 0 converged, 1 not converged (last relative
+ *            change of the ALS sweep > 1e-6), RTS_ENONFINITE.  When given,
+ *            the call waits for the stream and returns RTS_ENONFINITE if any
+ *            source hit a non-finite value.
+ * Each source: average in its direction (fused with the previous source's
+ * subtraction), n_iter Jacobi ALS sweeps from J = I with every second sweep
+ * averaged with the previous iterate, then subtraction. */
+int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
+                     const double* h_src, void* d_jones, int32_t* h_status, void* stream);
+
+/* rts_peel_cadence on host buffers: copies h_vis to the caller's device buffer
+ * d_work (cube-sized), peels it in place, copies the residual to h_resid and
+ * the Jones matrices to h_jones ([n_src][n_ant][4]), and waits for the stream.
+ * h_vis and h_resid may be the same buffer.  Page-locked host memory gives the
+ * fastest copies. */
+int rts_peel_cadence_host(rts_peel_t* h, const void* h_vis, void* h_resid, int32_t n_src,
+                          const double* h_src, void* h_jones, int32_t* h_status,
+                          void* d_work, void* stream);
+
+/* Model visibilities: d_vis = (accumulate ? d_vis : 0) +
+ * sum_k S_k J_i^k J_j^kH exp(-2 pi i phi_k) for the n_src sources in h_src with
+ * Jones d_jones [n_src][n_ant][4] (the predict step of the loop, for all sources). */
+int rts_peel_predict(rts_peel_t* h, void* d_vis, int32_t n_src, const double* h_src,
+                     const void* d_jones, int32_t accumulate, void* stream);
+
+/* The average step alone: d_avg[n_bl][4] = mean_{t,c} vis exp(+2 pi i phi(l, m)). */
+int rts_peel_rotate_average(rts_peel_t* h, const void* d_vis, double l, double m,
+                            void* d_avg, void* stream);
+
+/* The solve step alone: Jones d_jones[n_ant][4] for a source of flux S from its
+ * averaged visibilities d_avg[n_bl][4]; optional *h_status as in rts_peel_cadence. */
+int rts_peel_solve(rts_peel_t* h, const void* d_avg, double S, void* d_jones,
+                   int32_t* h_status, void* stream);
+
+/* Loss and gradient of the multi-source model (the adjoint of the predict step):
+ *   L = sum_{t,bl,c} || V - sum_k S_k J_i^k J_j^kH exp(-2 pi i phi_k) ||_F^2
+ *   d_vis   [n_time][n_bl][n_chan][4]; d_jones [n_src][n_ant][4];
+ *   d_src   DEVICE double [n_src][3] (l, m, S)
+ *   d_loss  device double[1] <- L
+ *   d_gJ    device [n_src][n_ant][4] complex (cube precision) <- dL/dRe J + i dL/dIm J,
+ *           or NULL
+ *   d_gsrc  device double [n_src][3] <- (dL/dl, dL/dm, dL/dS), or NULL
+ * Phasors are recomputed, never stored. */
+int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d_jones,
+                  const double* d_src, double* d_loss, void* d_gJ, double* d_gsrc,
+                  void* stream);
+
+/* Kernel timing and launch counts (the paper's Section 5 instruments every
+ * kernel for bandwidth and FLOP counts; this is the same tracing hook).
+ * Kernel classes, indices into the arrays below:                           */
+#define RTS_K_AVERAGE      0  /* rotate + average (first source of a cadence) */
+#define RTS_K_SUB_AVERAGE  1  /* subtract source k + average for source k+1 */
+#define RTS_K_SUBTRACT     2  /* subtract the last source */
+#define RTS_K_SOLVE        3  /* ALS sweeps + status of one source (timed as one group) */
+#define RTS_K_PREDICT      4  /* model prediction */
+#define RTS_K_GRAD         5  /* loss + adjoint sweep */
+#define RTS_K_GRAD_REDUCE  6  /* adjoint reductions (per antenna / source / loss) */
+#define RTS_K_CLASSES      8
+/* enable != 0: clear the counters and start bracketing every kernel (group)
+ * with CUDA events on its stream; enable == 0: stop recording.  Launch
+ * counts are always kept. */
+int rts_peel_timing(rts_peel_t* h, int32_t enable);
+/* Wait for the recorded events and return, per class, the summed device time
+ * in ms (ms[RTS_K_CLASSES]), the number of timed groups (groups[RTS_K_CLASSES])
+ * and the number of kernel launches since the last enable (launches[RTS_K_CLASSES]).
+ * Any pointer may be NULL. */
+int rts_peel_timing_read(rts_peel_t* h, double* ms, int64_t* groups, int64_t* launches);
+
+/* Page-locked host memory for the host-buffer calls (the paper, Section 4,
+ * moved its host allocator to pinned memory for faster DMA).  rts_host_alloc
+ * returns RTS_ENOMEM when the allocation fails; rts_host_free(NULL) is a no-op. */
+int rts_host_alloc(uint64_t bytes, void** out);
+int rts_host_free(void* p);
+
+/* Message of the last failed call on `h` (or of the last failed rts_peel_init
+ * when h is NULL).  The string stays valid until the next call on `h`. */
+const char* rts_peel_last_error(const rts_peel_t* h);
+
+/* Free the handle and its device workspace (NULL is accepted). */
+void rts_peel_destroy(rts_peel_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTS_PEEL_H */

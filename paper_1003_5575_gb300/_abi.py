@@ -1,0 +1,173 @@
+"""ctypes binding of librtspeel.so: the C ABI of include/rts_peel.h, same names,
+argument marshalling only.  Every step of the path runs in the library's CUDA
+kernels; there is no other implementation behind these functions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librtspeel.so")
+
+RTS_OK = 0
+RTS_NOT_CONVERGED = 1
+RTS_EINVAL = -1
+RTS_ENOMEM = -2
+RTS_ECUDA = -3
+RTS_ENONFINITE = -4
+RTS_PREC_MIXED = 0
+RTS_PREC_FP64 = 1
+
+RTS_K_AVERAGE, RTS_K_SUB_AVERAGE, RTS_K_SUBTRACT, RTS_K_SOLVE = 0, 1, 2, 3
+RTS_K_PREDICT, RTS_K_GRAD, RTS_K_GRAD_REDUCE, RTS_K_CLASSES = 4, 5, 6, 8
+KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "grad", "grad_reduce")
+
+EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_cadence_host",
+           "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad",
+           "rts_peel_timing", "rts_peel_timing_read", "rts_host_alloc", "rts_host_free",
+           "rts_peel_last_error", "rts_peel_destroy")
+
+
+class rts_peel_config(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int32), ("n_chan", ctypes.c_int32), ("n_time", ctypes.c_int32),
+                ("n_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_sources", ctypes.c_int32),
+                ("uvw", ctypes.POINTER(ctypes.c_double)),
+                ("freq_hz", ctypes.POINTER(ctypes.c_double))]
+
+
+class RtsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rts_peel error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_i32 = ctypes.c_int32
+
+
+def lib():
+    """Load librtspeel.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_1003_5575_gb300.build.build() (nvcc, sm_103a)")
+            L = ctypes.CDLL(LIB_PATH)
+            L.rts_peel_init.restype = ctypes.c_int
+            L.rts_peel_init.argtypes = [ctypes.POINTER(rts_peel_config), ctypes.POINTER(_vp)]
+            L.rts_peel_set_uvw.restype = ctypes.c_int
+            L.rts_peel_set_uvw.argtypes = [_vp, _dp, _vp]
+            L.rts_peel_cadence.restype = ctypes.c_int
+            L.rts_peel_cadence.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _ip, _vp]
+            L.rts_peel_cadence_host.restype = ctypes.c_int
+            L.rts_peel_cadence_host.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _ip, _vp, _vp]
+            L.rts_peel_predict.restype = ctypes.c_int
+            L.rts_peel_predict.argtypes = [_vp, _vp, _i32, _dp, _vp, _i32, _vp]
+            L.rts_peel_rotate_average.restype = ctypes.c_int
+            L.rts_peel_rotate_average.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]
+            L.rts_peel_solve.restype = ctypes.c_int
+            L.rts_peel_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp, _ip, _vp]
+            L.rts_peel_grad.restype = ctypes.c_int
+            L.rts_peel_grad.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.rts_peel_timing.restype = ctypes.c_int
+            L.rts_peel_timing.argtypes = [_vp, _i32]
+            L.rts_peel_timing_read.restype = ctypes.c_int
+            L.rts_peel_timing_read.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(ctypes.c_int64)]
+            L.rts_host_alloc.restype = ctypes.c_int
+            L.rts_host_alloc.argtypes = [ctypes.c_uint64, ctypes.POINTER(_vp)]
+            L.rts_host_free.restype = ctypes.c_int
+            L.rts_host_free.argtypes = [_vp]
+            L.rts_peel_last_error.restype = ctypes.c_char_p
+            L.rts_peel_last_error.argtypes = [_vp]
+            L.rts_peel_destroy.restype = None
+            L.rts_peel_destroy.argtypes = [_vp]
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, handle) -> int:
+    if rc < 0:
+        msg = lib().rts_peel_last_error(handle)
+        raise RtsError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def rts_peel_init(cfg: rts_peel_config):
+    h = _vp()
+    _check(lib().rts_peel_init(ctypes.byref(cfg), ctypes.byref(h)), None)
+    return h
+
+
+def rts_peel_set_uvw(h, uvw_ptr, stream):
+    return _check(lib().rts_peel_set_uvw(h, uvw_ptr, stream), h)
+
+
+def rts_peel_cadence(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, stream):
+    return _check(lib().rts_peel_cadence(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, stream), h)
+
+
+def rts_peel_cadence_host(h, h_vis, h_resid, n_src, h_src, h_jones, h_status, d_work, stream):
+    return _check(lib().rts_peel_cadence_host(h, h_vis, h_resid, n_src, h_src, h_jones, h_status,
+                                              d_work, stream), h)
+
+
+def rts_peel_predict(h, d_vis, n_src, h_src, d_jones, accumulate, stream):
+    return _check(lib().rts_peel_predict(h, d_vis, n_src, h_src, d_jones, accumulate, stream), h)
+
+
+def rts_peel_rotate_average(h, d_vis, l, m, d_avg, stream):
+    return _check(lib().rts_peel_rotate_average(h, d_vis, l, m, d_avg, stream), h)
+
+
+def rts_peel_solve(h, d_avg, S, d_jones, h_status, stream):
+    return _check(lib().rts_peel_solve(h, d_avg, S, d_jones, h_status, stream), h)
+
+
+def rts_peel_grad(h, d_vis, n_src, d_jones, d_src, d_loss, d_gJ, d_gsrc, stream):
+    return _check(lib().rts_peel_grad(h, d_vis, n_src, d_jones, d_src, d_loss, d_gJ, d_gsrc, stream), h)
+
+
+def rts_peel_timing(h, enable: int):
+    return _check(lib().rts_peel_timing(h, int(enable)), h)
+
+
+def rts_peel_timing_read(h):
+    """{class: (ms, groups, launches)} since the last rts_peel_timing(h, 1)."""
+    ms = (ctypes.c_double * RTS_K_CLASSES)()
+    gr = (ctypes.c_int64 * RTS_K_CLASSES)()
+    la = (ctypes.c_int64 * RTS_K_CLASSES)()
+    _check(lib().rts_peel_timing_read(h, ms, gr, la), h)
+    return {name: (ms[i], gr[i], la[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+
+def rts_host_alloc(nbytes: int) -> int:
+    p = _vp()
+    rc = lib().rts_host_alloc(int(nbytes), ctypes.byref(p))
+    if rc < 0:
+        raise RtsError(rc, rts_peel_last_error(None))
+    return p.value
+
+
+def rts_host_free(ptr: int) -> None:
+    rc = lib().rts_host_free(_vp(ptr))
+    if rc < 0:
+        raise RtsError(rc, "cudaFreeHost failed")
+
+
+def rts_peel_last_error(h) -> str:
+    m = lib().rts_peel_last_error(h)
+    return m.decode() if m else ""
+
+
+def rts_peel_destroy(h) -> None:
+    lib().rts_peel_destroy(h)

@@ -1,0 +1,418 @@
+// Adjoint of the multi-source predict step.
+//
+//   R = V - sum_k M_k exp(-2 pi i phi_k),  M_k = S_k J_i J_j^H,  L = sum ||R||_F^2
+//   G_k  = sum_{t,c} R exp(+2 pi i phi_k)
+//   H^l_k = sum_{t,c} R exp(+2 pi i phi_k) dphi_k/dl,  dphi/dl = (u - w l/n) nu_c / c
+//   (H^m_k likewise with v, m)
+//   dL/dJ_i += -2 S G J_j,  dL/dJ_j += -2 S G^H J_i    (dL/dRe + i dL/dIm)
+//   dL/dS   += -2 Re tr(G^H J_i J_j^H)
+//   dL/dl   += -4 pi Im tr(H^lH M),  dL/dm likewise.
+//
+// Kernel 1, one CTA per (baseline, chunk of sources): for each time and
+// channel tile it forms R for every channel of the tile in shared memory
+// (all K sources subtracted, phasors computed, never stored) and adds |R|^2 to
+// the loss; then threads = (source, channel group) accumulate
+// H0 = sum_c R e^{+i phi} and H1 = sum_c c R e^{+i phi}, from which
+// G += H0 and H^l += (u - w l/n)(nu_0/c H0 + dnu/c H1).  Per (source,
+// baseline) it stores G and the three scalar contributions (FP64).
+// Kernels 2-4 reduce those per antenna / per source / for the loss in a fixed
+// order, so the result is deterministic (no atomics).
+#pragma once
+#include <string>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace rts {
+
+constexpr int kGradThreads = 512;
+constexpr int kGradTile = 512;        // channels per shared-memory tile
+constexpr int kGradChunk = 512;       // sources per CTA in the backward phase
+
+struct __align__(16) DirQ { double x, y, z, w; };   // (l, m, n - 1, S) of one source
+
+struct GradWorkspace {
+  int cap_src = 0;
+  int64_t n_bl = 0;
+  double2* G = nullptr;     // [K][n_bl][4]
+  double* gsc = nullptr;    // [K][n_bl][3] (dl, dm, dS contributions)
+  double* loss_bl = nullptr;// [n_bl]
+  DirQ* dir = nullptr;   // [K] (l, m, nm1, S)
+};
+
+struct GradArgs {
+  const void* vis;
+  const void* jones;        // [K][n_ant][4] cube precision
+  const DirQ* dir;       // [K] (l, m, n-1, S)
+  const double* uvw;
+  const int2* bl_ant;
+  const double* freq_c;
+  double2* G;
+  double* gsc;
+  double* loss_bl;
+  int n_src, n_ant, n_chan, n_time;
+  int64_t n_bl;
+  double nu0_c, dnu_c;
+};
+
+__global__ void k_grad_dirs(const double* __restrict__ src, int n, DirQ* __restrict__ dir) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    double l = src[3 * k], m = src[3 * k + 1], S = src[3 * k + 2];
+    double r2 = l * l + m * m;
+    dir[k] = DirQ{l, m, -r2 / (1.0 + sqrt(1.0 - r2)), S};
+  }
+}
+
+template <typename T>
+__device__ inline typename cplx_of<T>::type load_j(const void* jones, size_t idx) {
+  using C = typename cplx_of<T>::type;
+  return static_cast<const C*>(jones)[idx];
+}
+
+// exp(+2 pi i phi) for channel c of source k at the current time
+template <bool MIXED>
+__device__ inline typename cplx_of<typename std::conditional<MIXED, float, double>::type>::type
+grad_phasor(unsigned long long A, unsigned long long B, double tau, const double* freq_c, int c) {
+  if constexpr (MIXED) {
+    return phasor_f(q64_to_turns(A + (unsigned long long)c * B));
+  } else {
+    return phasor_d(tau * freq_c[c]);
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kGradThreads) k_grad_sweep(GradArgs a) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  using C = typename cplx_of<T>::type;
+  extern __shared__ __align__(16) unsigned char g_smem[];
+  // layout (16-byte aligned pieces first):
+  //   R tile [kGradTile][4] C | M [K][4] C | part [threads][16] T | A, B [K] u64 | tau [K] double
+  C* sR = reinterpret_cast<C*>(g_smem);
+  C* sM = sR + kGradTile * 4;
+  T* sPart = reinterpret_cast<T*>(sM + (size_t)a.n_src * 4);
+  unsigned long long* sA = reinterpret_cast<unsigned long long*>(sPart + (size_t)kGradThreads * 16);
+  unsigned long long* sB = sA + a.n_src;
+  double* sTau = reinterpret_cast<double*>(sB + a.n_src);
+  __shared__ double s_uvw[3];
+  __shared__ double s_loss[kGradThreads / 32];
+
+  const int64_t bl = blockIdx.x;
+  const int2 ij = a.bl_ant[bl];
+  const int k0 = blockIdx.y * kGradChunk;
+  const int kc = max(1, min(kGradChunk, a.n_src - k0));   // sources of this CTA's backward phase
+  const int groups = max(1, kGradThreads / kc);
+  const int my_k = threadIdx.x % kc, my_g = threadIdx.x / kc;
+  const bool bw = my_g < groups && k0 + my_k < a.n_src;
+
+  // model matrices of all sources on this baseline
+  for (int k = threadIdx.x; k < a.n_src; k += blockDim.x) {
+    M22<double2> Ji, Jj;
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      C p = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.x) * 4 + e);
+      C q = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.y) * 4 + e);
+      Ji.e[e] = make_double2(p.x, p.y); Jj.e[e] = make_double2(q.x, q.y);
+    }
+    M22<double2> P = mmul_h(Ji, Jj);
+    const double S = a.dir[k].w;
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) sM[(size_t)k * 4 + e] = cmk<C>(S * P.e[e].x, S * P.e[e].y);
+  }
+  double G[8], Hl[8], Hm[8];
+  #pragma unroll
+  for (int e = 0; e < 8; ++e) { G[e] = 0.0; Hl[e] = 0.0; Hm[e] = 0.0; }
+  double loss = 0.0;
+  double lk_n = 0.0, mk_n = 0.0;
+  if (bw) {
+    const DirQ d = a.dir[k0 + my_k];
+    const double n = 1.0 + d.z;
+    lk_n = d.x / n; mk_n = d.y / n;
+  }
+
+  for (int t = 0; t < a.n_time; ++t) {
+    __syncthreads();                              // previous users of sA/sB/sTau/s_uvw done
+    for (int k = threadIdx.x; k < a.n_src; k += blockDim.x) {
+      SrcDir d; d.l = a.dir[k].x; d.m = a.dir[k].y; d.nm1 = a.dir[k].z; d.S = a.dir[k].w;
+      double tau = delay_m(a.uvw, a.n_ant, t, ij.x, ij.y, d);
+      sTau[k] = tau;
+      if (MIXED) { sA[k] = frac_q64(tau * a.nu0_c); sB[k] = frac_q64(tau * a.dnu_c); }
+    }
+    if (threadIdx.x < 3)
+      s_uvw[threadIdx.x] = a.uvw[((size_t)t * a.n_ant + ij.x) * 3 + threadIdx.x] -
+                           a.uvw[((size_t)t * a.n_ant + ij.y) * 3 + threadIdx.x];
+    for (int c0 = 0; c0 < a.n_chan; c0 += kGradTile) {
+      const int nc = min(kGradTile, a.n_chan - c0);
+      __syncthreads();                            // tables ready; previous tile consumed
+      // forward: R for each channel of the tile
+      for (int cl = threadIdx.x; cl < nc; cl += blockDim.x) {
+        const int c = c0 + cl;
+        const C* v = static_cast<const C*>(a.vis) + (((size_t)t * a.n_bl + bl) * a.n_chan + c) * 4;
+        C r[4];
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) r[e] = v[e];
+        for (int k = 0; k < a.n_src; ++k) {
+          C ph = grad_phasor<MIXED>(sA[k], sB[k], sTau[k], a.freq_c, c);
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) r[e] = csub(r[e], cmulc(sM[(size_t)k * 4 + e], ph));
+        }
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          sR[cl * 4 + e] = r[e];
+          loss += (double)r[e].x * r[e].x + (double)r[e].y * r[e].y;
+        }
+      }
+      __syncthreads();
+      // backward: partial H0, H1 over this thread's channel group
+      if (bw) {
+        const int k = k0 + my_k;
+        T h0[8], h1[8];
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) { h0[e] = T(0); h1[e] = T(0); }
+        for (int cl = my_g; cl < nc; cl += groups) {
+          const int c = c0 + cl;
+          C ph = grad_phasor<MIXED>(sA[k], sB[k], sTau[k], a.freq_c, c);
+          const T cw = (T)c;
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            C x = cmul(sR[cl * 4 + e], ph);
+            h0[2 * e] += x.x; h0[2 * e + 1] += x.y;
+            h1[2 * e] += cw * x.x; h1[2 * e + 1] += cw * x.y;
+          }
+        }
+        T* part = sPart + (size_t)threadIdx.x * 16;
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) { part[e] = h0[e]; part[8 + e] = h1[e]; }
+      }
+      __syncthreads();
+      if (bw && my_g == 0) {
+        double H0[8], H1[8];
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) { H0[e] = 0.0; H1[e] = 0.0; }
+        for (int g = 0; g < groups; ++g) {
+          const T* part = sPart + (size_t)(g * kc + my_k) * 16;
+          #pragma unroll
+          for (int e = 0; e < 8; ++e) { H0[e] += (double)part[e]; H1[e] += (double)part[8 + e]; }
+        }
+        const double wl = s_uvw[0] - s_uvw[2] * lk_n;
+        const double wm = s_uvw[1] - s_uvw[2] * mk_n;
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const double hn = a.nu0_c * H0[e] + a.dnu_c * H1[e];
+          G[e] += H0[e];
+          Hl[e] += wl * hn;
+          Hm[e] += wm * hn;
+        }
+      }
+    }
+  }
+  // loss of this baseline (chunk 0 only)
+  if (blockIdx.y == 0) {
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = loss;
+  }
+  __syncthreads();
+  if (blockIdx.y == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kGradThreads / 32; ++w) s += s_loss[w];
+    a.loss_bl[bl] = s;
+  }
+  if (bw && my_g == 0) {
+    const int k = k0 + my_k;
+    M22<double2> Ji, Jj, Gm, Hlm, Hmm;
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      C p = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.x) * 4 + e);
+      C q = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.y) * 4 + e);
+      Ji.e[e] = make_double2(p.x, p.y); Jj.e[e] = make_double2(q.x, q.y);
+      Gm.e[e] = make_double2(G[2 * e], G[2 * e + 1]);
+      Hlm.e[e] = make_double2(Hl[2 * e], Hl[2 * e + 1]);
+      Hmm.e[e] = make_double2(Hm[2 * e], Hm[2 * e + 1]);
+      a.G[((size_t)k * a.n_bl + bl) * 4 + e] = Gm.e[e];
+    }
+    const double S = a.dir[k].w;
+    M22<double2> P = mmul_h(Ji, Jj);                 // J_i J_j^H
+    // tr(X^H Y) = sum_e conj(X_e) Y_e
+    double2 tG = make_double2(0, 0), tl = make_double2(0, 0), tm = make_double2(0, 0);
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      tG = cadd(tG, cconjmul(Gm.e[e], P.e[e]));
+      tl = cadd(tl, cconjmul(Hlm.e[e], P.e[e]));
+      tm = cadd(tm, cconjmul(Hmm.e[e], P.e[e]));
+    }
+    const double four_pi = 12.566370614359172953850573533118;
+    double* o = a.gsc + ((size_t)k * a.n_bl + bl) * 3;
+    o[0] = -four_pi * S * tl.y;
+    o[1] = -four_pi * S * tm.y;
+    o[2] = -2.0 * tG.x;
+  }
+}
+
+// dL/dJ for antenna p of source k: -2 S [sum_{q>p} G(pq) J_q + sum_{q<p} G(qp)^H J_q]
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_grad_jones(const double2* __restrict__ G,
+                                                    const void* __restrict__ jones,
+                                                    const DirQ* __restrict__ dir,
+                                                    void* __restrict__ gJ, int n_ant, int64_t n_bl) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  using C = typename cplx_of<T>::type;
+  __shared__ double s_red[4 * 8];
+  const int p = blockIdx.x, k = blockIdx.y;
+  double acc[8];
+  #pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = 0.0;
+  const double2* Gk = G + (size_t)k * n_bl * 4;
+  for (int q = threadIdx.x; q < n_ant; q += 128) {
+    if (q == p) continue;
+    double2 g[4];
+    if (p < q) {
+      const double2* s = Gk + bl_index(n_ant, p, q) * 4;
+      g[0] = s[0]; g[1] = s[1]; g[2] = s[2]; g[3] = s[3];
+    } else {
+      const double2* s = Gk + bl_index(n_ant, q, p) * 4;
+      g[0] = cconj(s[0]); g[1] = cconj(s[2]); g[2] = cconj(s[1]); g[3] = cconj(s[3]);
+    }
+    double2 J[4];
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      C v = load_j<T>(jones, ((size_t)k * n_ant + q) * 4 + e);
+      J[e] = make_double2(v.x, v.y);
+    }
+    double2 r0 = cadd(cmul(g[0], J[0]), cmul(g[1], J[2]));
+    double2 r1 = cadd(cmul(g[0], J[1]), cmul(g[1], J[3]));
+    double2 r2 = cadd(cmul(g[2], J[0]), cmul(g[3], J[2]));
+    double2 r3 = cadd(cmul(g[2], J[1]), cmul(g[3], J[3]));
+    acc[0] += r0.x; acc[1] += r0.y; acc[2] += r1.x; acc[3] += r1.y;
+    acc[4] += r2.x; acc[5] += r2.y; acc[6] += r3.x; acc[7] += r3.y;
+  }
+  #pragma unroll
+  for (int e = 0; e < 8; ++e)
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+  if ((threadIdx.x & 31) == 0)
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) s_red[(threadIdx.x >> 5) * 8 + e] = acc[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double f = -2.0 * dir[k].w;
+    C* out = static_cast<C*>(gJ) + ((size_t)k * n_ant + p) * 4;
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      double re = 0.0, im = 0.0;
+      for (int w = 0; w < 4; ++w) { re += s_red[w * 8 + 2 * e]; im += s_red[w * 8 + 2 * e + 1]; }
+      out[e] = cmk<C>(f * re, f * im);
+    }
+  }
+}
+
+// per-source (dl, dm, dS) and the loss, summed over baselines in a fixed order
+__global__ void __launch_bounds__(256) k_grad_sum(const double* __restrict__ v, int64_t n, int stride,
+                                                  int width, double* __restrict__ out) {
+  __shared__ double s[256 * 3];
+  const double* base = v + (size_t)blockIdx.x * n * stride;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < n; i += 256)
+    for (int w = 0; w < width; ++w) acc[w] += base[i * stride + w];
+  for (int w = 0; w < width; ++w) s[w * 256 + threadIdx.x] = acc[w];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int w = 0; w < width; ++w) s[w * 256 + threadIdx.x] += s[w * 256 + threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int w = 0; w < width; ++w) out[(size_t)blockIdx.x * width + w] = s[w * 256];
+}
+
+inline void grad_free(GradWorkspace& w) {
+  if (w.G) cudaFree(w.G);
+  if (w.gsc) cudaFree(w.gsc);
+  if (w.loss_bl) cudaFree(w.loss_bl);
+  if (w.dir) cudaFree(w.dir);
+  w = GradWorkspace();
+}
+
+inline int grad_fail(std::string& err, cudaError_t e, const char* what) {
+  err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? -2 : -3;
+}
+
+// Allocates its workspace on first use (G and per-baseline terms for up to
+// max_src sources: (64 + 24) bytes per source and baseline) and keeps it.
+inline int grad_prepare(GradWorkspace& w, int n_src, const double* src, int64_t n_bl, int max_src,
+                        cudaStream_t s, std::string& err) {
+  cudaError_t e;
+  if (!w.loss_bl) {
+    w.cap_src = max_src; w.n_bl = n_bl;
+    if ((e = cudaMalloc(&w.G, (size_t)max_src * n_bl * 4 * sizeof(double2))) != cudaSuccess ||
+        (e = cudaMalloc(&w.gsc, (size_t)max_src * n_bl * 3 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&w.loss_bl, (size_t)n_bl * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&w.dir, (size_t)max_src * sizeof(DirQ))) != cudaSuccess) {
+      int rc = grad_fail(err, e, "cudaMalloc(gradient workspace)");
+      grad_free(w);
+      return rc;
+    }
+  }
+  if (n_src > 0) k_grad_dirs<<<(n_src + 127) / 128, 128, 0, s>>>(src, n_src, w.dir);
+  return 0;
+}
+
+inline size_t grad_smem_bytes(bool mixed, int n_src) {
+  const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
+  const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+  return (size_t)kGradTile * 4 * esz + (size_t)n_src * (2 * 8 + 8 + 4 * esz) +
+         (size_t)kGradThreads * 16 * tsz;
+}
+
+// the fused loss + adjoint sweep (one launch)
+inline int grad_sweep(GradWorkspace& w, bool mixed, const void* vis, int n_src, const void* jones,
+                      const double* uvw, const int2* bl_ant, const double* freq_c, int n_ant,
+                      int n_chan, int n_time, int64_t n_bl, double nu0_c, double dnu_c,
+                      cudaStream_t s, std::string& err) {
+  cudaError_t e;
+  GradArgs a;
+  a.vis = vis; a.jones = jones; a.dir = w.dir; a.uvw = uvw; a.bl_ant = bl_ant; a.freq_c = freq_c;
+  a.G = w.G; a.gsc = w.gsc; a.loss_bl = w.loss_bl;
+  a.n_src = n_src; a.n_ant = n_ant; a.n_chan = n_chan; a.n_time = n_time; a.n_bl = n_bl;
+  a.nu0_c = nu0_c; a.dnu_c = dnu_c;
+  const size_t smem = grad_smem_bytes(mixed, n_src);
+  const int chunks = n_src > 0 ? (n_src + kGradChunk - 1) / kGradChunk : 1;
+  if (smem > 227 * 1024) {
+    err = "too many sources for the gradient kernel's shared memory";
+    return -1;
+  }
+  const dim3 grid((unsigned)n_bl, (unsigned)chunks);
+  if (mixed) {
+    if ((e = cudaFuncSetAttribute(k_grad_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return grad_fail(err, e, "cudaFuncSetAttribute");
+    k_grad_sweep<true><<<grid, kGradThreads, smem, s>>>(a);
+  } else {
+    if ((e = cudaFuncSetAttribute(k_grad_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return grad_fail(err, e, "cudaFuncSetAttribute");
+    k_grad_sweep<false><<<grid, kGradThreads, smem, s>>>(a);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return grad_fail(err, e, "gradient sweep launch");
+  return 0;
+}
+
+// per-antenna dL/dJ, per-source (dl, dm, dS) and the loss; returns launches made
+inline int grad_reduce(GradWorkspace& w, bool mixed, int n_src, const void* jones, double* loss,
+                       void* gJ, double* gsrc, int n_ant, int64_t n_bl, cudaStream_t s,
+                       std::string& err, int* launches) {
+  cudaError_t e;
+  int n = 0;
+  if (n_src > 0 && gJ) {
+    const dim3 gj((unsigned)n_ant, (unsigned)n_src);
+    if (mixed) k_grad_jones<true><<<gj, 128, 0, s>>>(w.G, jones, w.dir, gJ, n_ant, n_bl);
+    else k_grad_jones<false><<<gj, 128, 0, s>>>(w.G, jones, w.dir, gJ, n_ant, n_bl);
+    ++n;
+  }
+  if (n_src > 0 && gsrc) { k_grad_sum<<<n_src, 256, 0, s>>>(w.gsc, n_bl, 3, 3, gsrc); ++n; }
+  k_grad_sum<<<1, 256, 0, s>>>(w.loss_bl, n_bl, 1, 1, loss);
+  ++n;
+  *launches = n;
+  if ((e = cudaGetLastError()) != cudaSuccess) return grad_fail(err, e, "gradient reduction launch");
+  return 0;
+}
+
+}  // namespace rts

@@ -1,0 +1,483 @@
+// librtspeel: C ABI of the GB300 calibrate-and-peel loop (see include/rts_peel.h).
+#include "rts_peel.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "als_kernels.cuh"
+#include "common.cuh"
+#include "grad_kernels.cuh"
+#include "stream_kernels.cuh"
+
+using namespace rts;
+
+struct rts_peel_t {
+  int n_ant = 0, n_chan = 0, n_time = 0, n_iter = 0, precision = 0, max_sources = 0;
+  int64_t n_bl = 0;
+  double nu0 = 0, dnu = 0;
+  int device = 0;
+  size_t elem = 8;                 // bytes per complex element of the cube
+  // device workspace, allocated once in rts_peel_init
+  double* d_uvw = nullptr;         // [n_time][n_ant][3]
+  int2* d_bl_ant = nullptr;        // [n_bl]
+  double* d_freq_c = nullptr;      // [n_chan] nu_c / c
+  void* d_avg = nullptr;           // [n_bl][4] cube precision
+  double2* d_J[2] = {nullptr, nullptr};
+  float2* d_Jf[2] = {nullptr, nullptr};
+  double* d_norms = nullptr;       // [n_ant][2]
+  int* d_flag = nullptr;           // [1]
+  int* d_status = nullptr;         // [max_sources]
+  double* d_rel = nullptr;         // [max_sources]
+  double* d_src = nullptr;         // [max_sources][3]
+  void* d_jones_stage = nullptr;   // [max_sources][n_ant][4] cube precision (host-buffer calls)
+  GradWorkspace grad;
+  // tracing: CUDA events around kernel groups, launch counters
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec { int cls; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  int64_t launches[RTS_K_CLASSES] = {};
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+int fail(rts_peel_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_init_err = msg;
+  return code;
+}
+
+int cuda_fail(rts_peel_t* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? RTS_ENOMEM : RTS_ECUDA, m);
+}
+
+#define RTS_CUDA(h, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+int check_launch(rts_peel_t* h, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, what);
+  return RTS_OK;
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+cudaEvent_t next_event(rts_peel_t* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// brackets one kernel (or group of kernels) of class `cls` on stream s
+struct Span {
+  rts_peel_t* h; int cls; cudaStream_t s; cudaEvent_t a = nullptr;
+  Span(rts_peel_t* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
+    if (h->timing && (a = next_event(h))) cudaEventRecord(a, s);
+  }
+  void end(int n_launch) {
+    h->launches[cls] += n_launch;
+    if (a) {
+      cudaEvent_t b = next_event(h);
+      if (b) { cudaEventRecord(b, s); h->recs.push_back({cls, a, b}); }
+      a = nullptr;
+    }
+  }
+};
+
+int validate_sources(rts_peel_t* h, int32_t n_src, const double* src) {
+  if (n_src < 0 || n_src > h->max_sources)
+    return fail(h, RTS_EINVAL, "n_src must be in [0, max_sources]");
+  if (n_src > 0 && !src) return fail(h, RTS_EINVAL, "source list is NULL");
+  for (int k = 0; k < n_src; ++k) {
+    const double l = src[3 * k], m = src[3 * k + 1], S = src[3 * k + 2];
+    if (!std::isfinite(l) || !std::isfinite(m) || !std::isfinite(S))
+      return fail(h, RTS_EINVAL, "source " + std::to_string(k) + " has a non-finite l, m or S");
+    if (!(l * l + m * m < 1.0))
+      return fail(h, RTS_EINVAL, "source " + std::to_string(k) + " is not above the horizon (l^2+m^2 >= 1)");
+    if (!(S > 0.0)) return fail(h, RTS_EINVAL, "source " + std::to_string(k) + " has flux S <= 0");
+  }
+  return RTS_OK;
+}
+
+StreamArgs stream_args(rts_peel_t* h, const void* src, void* dst, void* avg) {
+  StreamArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.src = src; a.dst = dst; a.uvw = h->d_uvw; a.bl_ant = h->d_bl_ant; a.freq_c = h->d_freq_c;
+  a.n_ant = h->n_ant; a.n_chan = h->n_chan; a.n_time = h->n_time; a.n_bl = h->n_bl;
+  a.nu0_c = h->nu0 / kCLight; a.dnu_c = h->dnu / kCLight;
+  a.avg = avg;
+  a.inv_n = 1.0 / ((double)h->n_time * h->n_chan);
+  return a;
+}
+
+// one streaming pass: sub (subtract source) and/or acc (average for source)
+int launch_stream(rts_peel_t* h, bool sub, bool acc, const StreamArgs& a, cudaStream_t s) {
+  const dim3 grid((unsigned)h->n_bl), block(kStreamThreads);
+  Span span(h, sub && acc ? RTS_K_SUB_AVERAGE : (sub ? RTS_K_SUBTRACT : RTS_K_AVERAGE), s);
+  if (h->precision == RTS_PREC_MIXED) {
+    const size_t smem = (size_t)h->n_time * 4 * sizeof(unsigned long long);
+    if (sub && acc) k_stream_mixed<true, true><<<grid, block, smem, s>>>(a);
+    else if (sub) k_stream_mixed<true, false><<<grid, block, smem, s>>>(a);
+    else k_stream_mixed<false, true><<<grid, block, smem, s>>>(a);
+  } else {
+    const size_t smem = (size_t)h->n_time * 2 * sizeof(double);
+    if (sub && acc) k_stream_fp64<true, true><<<grid, block, smem, s>>>(a);
+    else if (sub) k_stream_fp64<true, false><<<grid, block, smem, s>>>(a);
+    else k_stream_fp64<false, true><<<grid, block, smem, s>>>(a);
+  }
+  span.end(1);
+  return check_launch(h, "streaming kernel launch");
+}
+
+// n_iter ALS sweeps on avg; Jones to jones_out (cube precision) and the FP64
+// solution left in h->d_J[n_iter & 1]; status/rel to slot `slot`.
+int launch_als(rts_peel_t* h, const void* avg, double S, void* jones_out, int slot, cudaStream_t s) {
+  Span span(h, RTS_K_SOLVE, s);
+  for (int it = 1; it <= h->n_iter; ++it) {
+    AlsArgs a;
+    a.avg = avg;
+    a.J_old = h->d_J[(it - 1) & 1]; a.Jf_old = h->d_Jf[(it - 1) & 1];
+    a.J_new = h->d_J[it & 1]; a.Jf_new = h->d_Jf[it & 1];
+    a.norms = h->d_norms; a.flag = h->d_flag;
+    a.jones_out = it == h->n_iter ? jones_out : nullptr;
+    a.n_ant = h->n_ant; a.S = S; a.first = it == 1; a.average = (it % 2) == 0;
+    if (h->precision == RTS_PREC_MIXED) k_als_sweep<float><<<h->n_ant, kAlsThreads, 0, s>>>(a);
+    else k_als_sweep<double><<<h->n_ant, kAlsThreads, 0, s>>>(a);
+  }
+  k_als_finalize<<<1, 256, 0, s>>>(h->d_norms, h->n_ant, h->d_flag, h->d_status + slot, h->d_rel + slot);
+  span.end(h->n_iter + 1);
+  return check_launch(h, "ALS kernel launch");
+}
+
+const double2* als_solution(rts_peel_t* h) { return h->d_J[h->n_iter & 1]; }
+
+int read_status(rts_peel_t* h, int32_t n, int32_t* h_status, cudaStream_t s) {
+  RTS_CUDA(h, cudaMemcpyAsync(h_status, h->d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  RTS_CUDA(h, cudaStreamSynchronize(s));
+  for (int k = 0; k < n; ++k)
+    if (h_status[k] == RTS_ENONFINITE)
+      return fail(h, RTS_ENONFINITE, "non-finite value in the solve of source " + std::to_string(k));
+  return RTS_OK;
+}
+
+int peel_device(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
+                const double* h_src, void* d_jones, int32_t* h_status, cudaStream_t s) {
+  const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
+  if (n_src == 0) {
+    if (d_resid != d_vis) RTS_CUDA(h, cudaMemcpyAsync(d_resid, d_vis, cube, cudaMemcpyDeviceToDevice, s));
+    return RTS_OK;
+  }
+  const size_t jstride = (size_t)h->n_ant * 4 * h->elem;
+  StreamArgs a = stream_args(h, d_vis, d_resid, h->d_avg);
+  a.acc = make_dir(h_src[0], h_src[1], h_src[2]);
+  int rc = launch_stream(h, false, true, a, s);
+  if (rc) return rc;
+  for (int k = 0; k < n_src; ++k) {
+    rc = launch_als(h, h->d_avg, h_src[3 * k + 2], static_cast<char*>(d_jones) + k * jstride, k, s);
+    if (rc) return rc;
+    StreamArgs b = stream_args(h, k == 0 ? d_vis : d_resid, d_resid, h->d_avg);
+    b.sub = make_dir(h_src[3 * k], h_src[3 * k + 1], h_src[3 * k + 2]);
+    b.Jsub = als_solution(h);
+    const bool more = k + 1 < n_src;
+    if (more) b.acc = make_dir(h_src[3 * (k + 1)], h_src[3 * (k + 1) + 1], h_src[3 * (k + 1) + 2]);
+    rc = launch_stream(h, true, more, b, s);
+    if (rc) return rc;
+  }
+  if (h_status) return read_status(h, n_src, h_status, s);
+  return RTS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
+  g_init_err.clear();
+  if (!out) return fail(nullptr, RTS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, RTS_EINVAL, "cfg is NULL");
+  if (cfg->n_ant < 2 || cfg->n_ant > 8192) return fail(nullptr, RTS_EINVAL, "n_ant must be in [2, 8192]");
+  if (cfg->n_chan < 1 || cfg->n_chan > 65536) return fail(nullptr, RTS_EINVAL, "n_chan must be in [1, 65536]");
+  if (cfg->n_time < 1 || cfg->n_time > 1024) return fail(nullptr, RTS_EINVAL, "n_time must be in [1, 1024]");
+  if (cfg->n_iter < 1 || cfg->n_iter > 10000) return fail(nullptr, RTS_EINVAL, "n_iter must be in [1, 10000]");
+  if (cfg->precision != RTS_PREC_MIXED && cfg->precision != RTS_PREC_FP64)
+    return fail(nullptr, RTS_EINVAL, "precision must be RTS_PREC_MIXED or RTS_PREC_FP64");
+  if (cfg->max_sources < 1 || cfg->max_sources > (1 << 20))
+    return fail(nullptr, RTS_EINVAL, "max_sources must be in [1, 2^20]");
+  if (!cfg->uvw || !cfg->freq_hz) return fail(nullptr, RTS_EINVAL, "uvw and freq_hz are required");
+  const int64_t n_bl = (int64_t)cfg->n_ant * (cfg->n_ant - 1) / 2;
+  if ((double)cfg->n_time * cfg->n_chan * n_bl >= 4.0e12)
+    return fail(nullptr, RTS_EINVAL, "cube too large");
+  const size_t n_uvw = (size_t)cfg->n_time * cfg->n_ant * 3;
+  for (size_t i = 0; i < n_uvw; ++i)
+    if (!std::isfinite(cfg->uvw[i])) return fail(nullptr, RTS_EINVAL, "uvw has a non-finite value");
+  const double* f = cfg->freq_hz;
+  const double nu0 = f[0];
+  const double dnu = cfg->n_chan > 1 ? (f[cfg->n_chan - 1] - f[0]) / (cfg->n_chan - 1) : 0.0;
+  for (int c = 0; c < cfg->n_chan; ++c) {
+    if (!std::isfinite(f[c]) || !(f[c] > 0)) return fail(nullptr, RTS_EINVAL, "frequencies must be finite and > 0");
+    if (std::fabs(f[c] - (nu0 + c * dnu)) > 1e-9 * std::fabs(f[c]))
+      return fail(nullptr, RTS_EINVAL, "channels must be uniformly spaced (nu_c = nu_0 + c dnu)");
+  }
+
+  rts_peel_t* h = new rts_peel_t();
+  h->n_ant = cfg->n_ant; h->n_chan = cfg->n_chan; h->n_time = cfg->n_time;
+  h->n_iter = cfg->n_iter; h->precision = cfg->precision; h->max_sources = cfg->max_sources;
+  h->n_bl = n_bl; h->nu0 = nu0; h->dnu = dnu;
+  h->elem = cfg->precision == RTS_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+  auto bail = [&](cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    int code = e == cudaErrorMemoryAllocation ? RTS_ENOMEM : RTS_ECUDA;
+    rts_peel_destroy(h);
+    return fail(nullptr, code, m);
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+  std::vector<int2> map((size_t)n_bl);
+  {
+    int64_t b = 0;
+    for (int i = 0; i < h->n_ant; ++i)
+      for (int j = i + 1; j < h->n_ant; ++j) map[b++] = make_int2(i, j);
+  }
+  std::vector<double> fc(h->n_chan);
+  for (int c = 0; c < h->n_chan; ++c) fc[c] = f[c] / kCLight;
+  const size_t n_cplx_ant = (size_t)h->n_ant * 4;
+  struct { void** p; size_t bytes; } allocs[] = {
+      {(void**)&h->d_uvw, n_uvw * sizeof(double)},
+      {(void**)&h->d_bl_ant, (size_t)n_bl * sizeof(int2)},
+      {(void**)&h->d_freq_c, (size_t)h->n_chan * sizeof(double)},
+      {(void**)&h->d_avg, (size_t)n_bl * 4 * h->elem},
+      {(void**)&h->d_J[0], n_cplx_ant * sizeof(double2)},
+      {(void**)&h->d_J[1], n_cplx_ant * sizeof(double2)},
+      {(void**)&h->d_Jf[0], n_cplx_ant * sizeof(float2)},
+      {(void**)&h->d_Jf[1], n_cplx_ant * sizeof(float2)},
+      {(void**)&h->d_norms, (size_t)h->n_ant * 2 * sizeof(double)},
+      {(void**)&h->d_flag, sizeof(int)},
+      {(void**)&h->d_status, (size_t)h->max_sources * sizeof(int)},
+      {(void**)&h->d_rel, (size_t)h->max_sources * sizeof(double)},
+      {(void**)&h->d_src, (size_t)h->max_sources * 3 * sizeof(double)},
+      {(void**)&h->d_jones_stage, (size_t)h->max_sources * n_cplx_ant * h->elem},
+  };
+  for (auto& a : allocs)
+    if ((e = cudaMalloc(a.p, a.bytes)) != cudaSuccess) return bail(e, "cudaMalloc(workspace)");
+  if ((e = cudaMemcpy(h->d_uvw, cfg->uvw, n_uvw * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "copy uvw");
+  if ((e = cudaMemcpy(h->d_bl_ant, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "copy baseline map");
+  if ((e = cudaMemcpy(h->d_freq_c, fc.data(), fc.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "copy frequencies");
+  if ((e = cudaMemset(h->d_flag, 0, sizeof(int))) != cudaSuccess) return bail(e, "clear flag");
+  if ((e = cudaMemset(h->d_status, 0, (size_t)h->max_sources * sizeof(int))) != cudaSuccess)
+    return bail(e, "clear status");
+  *out = h;
+  return RTS_OK;
+}
+
+int rts_peel_set_uvw(rts_peel_t* h, const double* h_uvw, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!h_uvw) return fail(h, RTS_EINVAL, "uvw is NULL");
+  const size_t n = (size_t)h->n_time * h->n_ant * 3;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(h_uvw[i])) return fail(h, RTS_EINVAL, "uvw has a non-finite value");
+  RTS_CUDA(h, cudaMemcpyAsync(h->d_uvw, h_uvw, n * sizeof(double), cudaMemcpyHostToDevice, as_stream(stream)));
+  RTS_CUDA(h, cudaStreamSynchronize(as_stream(stream)));
+  return RTS_OK;
+}
+
+int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
+                     const double* h_src, void* d_jones, int32_t* h_status, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!d_vis || !d_resid) return fail(h, RTS_EINVAL, "d_vis and d_resid are required");
+  int rc = validate_sources(h, n_src, h_src);
+  if (rc) return rc;
+  if (n_src > 0 && !d_jones) return fail(h, RTS_EINVAL, "d_jones is NULL");
+  return peel_device(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, as_stream(stream));
+}
+
+int rts_peel_cadence_host(rts_peel_t* h, const void* h_vis, void* h_resid, int32_t n_src,
+                          const double* h_src, void* h_jones, int32_t* h_status,
+                          void* d_work, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!h_vis || !h_resid || !d_work) return fail(h, RTS_EINVAL, "h_vis, h_resid and d_work are required");
+  int rc = validate_sources(h, n_src, h_src);
+  if (rc) return rc;
+  if (n_src > 0 && !h_jones) return fail(h, RTS_EINVAL, "h_jones is NULL");
+  cudaStream_t s = as_stream(stream);
+  const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
+  RTS_CUDA(h, cudaMemcpyAsync(d_work, h_vis, cube, cudaMemcpyHostToDevice, s));
+  rc = peel_device(h, d_work, d_work, n_src, h_src, h->d_jones_stage, nullptr, s);
+  if (rc) return rc;
+  RTS_CUDA(h, cudaMemcpyAsync(h_resid, d_work, cube, cudaMemcpyDeviceToHost, s));
+  if (n_src > 0)
+    RTS_CUDA(h, cudaMemcpyAsync(h_jones, h->d_jones_stage, (size_t)n_src * h->n_ant * 4 * h->elem,
+                                cudaMemcpyDeviceToHost, s));
+  if (h_status && n_src > 0) return read_status(h, n_src, h_status, s);
+  RTS_CUDA(h, cudaStreamSynchronize(s));
+  return RTS_OK;
+}
+
+int rts_peel_predict(rts_peel_t* h, void* d_vis, int32_t n_src, const double* h_src,
+                     const void* d_jones, int32_t accumulate, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!d_vis) return fail(h, RTS_EINVAL, "d_vis is NULL");
+  int rc = validate_sources(h, n_src, h_src);
+  if (rc) return rc;
+  if (n_src > 0 && !d_jones) return fail(h, RTS_EINVAL, "d_jones is NULL");
+  cudaStream_t s = as_stream(stream);
+  const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
+  if (n_src == 0) {
+    if (!accumulate) RTS_CUDA(h, cudaMemsetAsync(d_vis, 0, cube, s));
+    return RTS_OK;
+  }
+  RTS_CUDA(h, cudaMemcpyAsync(h->d_src, h_src, sizeof(double) * 3 * n_src, cudaMemcpyHostToDevice, s));
+  const size_t per_src = (size_t)h->n_time * (h->precision == RTS_PREC_MIXED ? 16 : 8);
+  int chunk = (int)std::min<size_t>(kPredictChunk, std::max<size_t>(1, 40960 / per_src));
+  for (int k0 = 0; k0 < n_src; k0 += chunk) {
+    PredictArgs a;
+    a.vis = d_vis; a.uvw = h->d_uvw; a.bl_ant = h->d_bl_ant; a.freq_c = h->d_freq_c;
+    a.src = h->d_src + 3 * k0;
+    a.jones = static_cast<const char*>(d_jones) + (size_t)k0 * h->n_ant * 4 * h->elem;
+    a.n_src = std::min(chunk, n_src - k0);
+    a.n_ant = h->n_ant; a.n_chan = h->n_chan; a.n_time = h->n_time; a.n_bl = h->n_bl;
+    a.nu0_c = h->nu0 / kCLight; a.dnu_c = h->dnu / kCLight;
+    a.accumulate = (k0 > 0 || accumulate) ? 1 : 0;
+    const size_t smem = per_src * a.n_src;
+    Span span(h, RTS_K_PREDICT, s);
+    if (h->precision == RTS_PREC_MIXED) k_predict_mixed<<<(unsigned)h->n_bl, kStreamThreads, smem, s>>>(a);
+    else k_predict_fp64<<<(unsigned)h->n_bl, kStreamThreads, smem, s>>>(a);
+    span.end(1);
+    rc = check_launch(h, "predict kernel launch");
+    if (rc) return rc;
+  }
+  return RTS_OK;
+}
+
+int rts_peel_rotate_average(rts_peel_t* h, const void* d_vis, double l, double m, void* d_avg,
+                            void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!d_vis || !d_avg) return fail(h, RTS_EINVAL, "d_vis and d_avg are required");
+  if (!std::isfinite(l) || !std::isfinite(m) || !(l * l + m * m < 1.0))
+    return fail(h, RTS_EINVAL, "direction must be finite with l^2 + m^2 < 1");
+  StreamArgs a = stream_args(h, d_vis, nullptr, d_avg);
+  a.acc = make_dir(l, m, 1.0);
+  return launch_stream(h, false, true, a, as_stream(stream));
+}
+
+int rts_peel_solve(rts_peel_t* h, const void* d_avg, double S, void* d_jones, int32_t* h_status,
+                   void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!d_avg || !d_jones) return fail(h, RTS_EINVAL, "d_avg and d_jones are required");
+  if (!std::isfinite(S) || !(S > 0.0)) return fail(h, RTS_EINVAL, "S must be finite and > 0");
+  cudaStream_t s = as_stream(stream);
+  int rc = launch_als(h, d_avg, S, d_jones, 0, s);
+  if (rc) return rc;
+  if (h_status) return read_status(h, 1, h_status, s);
+  return RTS_OK;
+}
+
+int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d_jones,
+                  const double* d_src, double* d_loss, void* d_gJ, double* d_gsrc, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!d_vis || !d_loss) return fail(h, RTS_EINVAL, "d_vis and d_loss are required");
+  if (n_src < 0 || n_src > h->max_sources) return fail(h, RTS_EINVAL, "n_src must be in [0, max_sources]");
+  if (n_src > 0 && (!d_jones || !d_src)) return fail(h, RTS_EINVAL, "d_jones and d_src are required");
+  cudaStream_t s = as_stream(stream);
+  const bool mixed = h->precision == RTS_PREC_MIXED;
+  int rc = grad_prepare(h->grad, n_src, d_src, h->n_bl, h->max_sources, s, h->err);
+  if (rc) return rc;
+  {
+    Span span(h, RTS_K_GRAD, s);
+    rc = grad_sweep(h->grad, mixed, d_vis, n_src, d_jones, h->d_uvw, h->d_bl_ant, h->d_freq_c,
+                    h->n_ant, h->n_chan, h->n_time, h->n_bl, h->nu0 / kCLight, h->dnu / kCLight, s,
+                    h->err);
+    span.end(1);
+    if (rc) return rc;
+  }
+  Span span(h, RTS_K_GRAD_REDUCE, s);
+  int nl = 0;
+  rc = grad_reduce(h->grad, mixed, n_src, d_jones, d_loss, d_gJ, d_gsrc, h->n_ant, h->n_bl, s, h->err, &nl);
+  span.end(nl);
+  return rc;
+}
+
+int rts_peel_timing(rts_peel_t* h, int32_t enable) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (enable) {
+    h->recs.clear();
+    h->ev_used = 0;
+    for (auto& n : h->launches) n = 0;
+  }
+  h->timing = enable != 0;
+  return RTS_OK;
+}
+
+int rts_peel_timing_read(rts_peel_t* h, double* ms, int64_t* groups, int64_t* launches) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  double acc[RTS_K_CLASSES] = {};
+  int64_t cnt[RTS_K_CLASSES] = {};
+  for (const auto& r : h->recs) {
+    RTS_CUDA(h, cudaEventSynchronize(r.b));
+    float t = 0.f;
+    RTS_CUDA(h, cudaEventElapsedTime(&t, r.a, r.b));
+    acc[r.cls] += t;
+    cnt[r.cls] += 1;
+  }
+  for (int c = 0; c < RTS_K_CLASSES; ++c) {
+    if (ms) ms[c] = acc[c];
+    if (groups) groups[c] = cnt[c];
+    if (launches) launches[c] = h->launches[c];
+  }
+  return RTS_OK;
+}
+
+int rts_host_alloc(uint64_t bytes, void** out) {
+  if (!out) return RTS_EINVAL;
+  *out = nullptr;
+  cudaError_t e = cudaHostAlloc(out, (size_t)bytes, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("cudaHostAlloc: ") + cudaGetErrorString(e);
+    *out = nullptr;
+    return e == cudaErrorMemoryAllocation ? RTS_ENOMEM : RTS_ECUDA;
+  }
+  return RTS_OK;
+}
+
+int rts_host_free(void* p) {
+  if (!p) return RTS_OK;
+  return cudaFreeHost(p) == cudaSuccess ? RTS_OK : RTS_ECUDA;
+}
+
+const char* rts_peel_last_error(const rts_peel_t* h) {
+  return h ? h->err.c_str() : g_init_err.c_str();
+}
+
+void rts_peel_destroy(rts_peel_t* h) {
+  if (!h) return;
+  int prev = -1;
+  if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
+  void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
+                  h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  grad_free(h->grad);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+  delete h;
+}
+
+}  // extern "C"

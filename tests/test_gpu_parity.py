@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Inputs are the oracle's own simulation of seeded synthetic cadences (never the
+CUDA path's output).  Tolerances (written here, from the stated targets):
+  mixed path  residual |dR| <= 1e-5 x rms of the input cube's real components,
+              Jones ||dJ_k||_F / ||J_k||_F <= 1e-5 per source,
+              averages |dA| <= 1e-5 x rms, loss <= 1e-5 relative,
+              gradients <= 1e-4 relative (vs the oracle's analytic gradient);
+  FP64 path   1e-10 on all of these.
+Integer/index work (baseline order, status codes) is exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import Cadence, config
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"mixed": 1e-5, "fp64": 1e-10}
+CDT = {"mixed": (np.complex64, torch.complex64), "fp64": (np.complex128, torch.complex128)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_5575_gb300 import build
+    build.build()
+
+
+def rms_of(V):
+    return math.sqrt(float(np.mean(V.real.astype(np.float64) ** 2 + V.imag.astype(np.float64) ** 2) / 2))
+
+
+def to_dev(V, prec):
+    return torch.from_numpy(np.ascontiguousarray(V.astype(CDT[prec][0]))).cuda()
+
+
+def jones_rel(Jg, Jr):
+    return max(np.linalg.norm(Jg[k] - Jr[k]) / np.linalg.norm(Jr[k]) for k in range(len(Jr)))
+
+
+_cache = {}
+
+
+def oracle_case(cad, n_iter=20):
+    key = (cad, n_iter)
+    if key not in _cache:
+        V = oracle.simulate(cad)
+        if cad.precision == "mixed":
+            V = V.astype(np.complex64).astype(np.complex128)   # what the GPU sees
+        R, J, st = oracle.peel(cad.uvw(), cad.freqs(), V, cad.sources(), n_iter=n_iter)
+        _cache[key] = (V, R, J, st)
+    return _cache[key]
+
+
+def make_peeler(cad, prec, n_iter=20, max_sources=None):
+    from paper_1003_5575_gb300 import Peeler
+    return Peeler(cad.uvw(), cad.freqs(), n_iter=n_iter, precision=prec,
+                  max_sources=max_sources or max(cad.n_src, 1))
+
+
+# ---------------------------------------------------------------------------
+# full peel
+
+PEEL_CASES = [
+    ("cfg1-fp64", config(1), "fp64"),
+    ("cfg1-mixed", config(1, precision="mixed"), "mixed"),
+    ("cfg2-mixed", config(2), "mixed"),
+    ("ragged-mixed", Cadence(9, 37, 3, 4, seed=91), "mixed"),
+    ("ragged-fp64", Cadence(9, 37, 3, 4, precision="fp64", seed=91), "fp64"),
+    ("one-channel", Cadence(6, 1, 5, 2, seed=92), "mixed"),
+    ("one-time", Cadence(7, 300, 1, 2, seed=93), "mixed"),
+    ("two-antennas", Cadence(2, 64, 4, 1, seed=94), "mixed"),
+]
+
+
+@pytest.mark.parametrize("name,cad,prec", PEEL_CASES, ids=[c[0] for c in PEEL_CASES])
+def test_peel_matches_oracle(name, cad, prec):
+    V, R_ref, J_ref, st_ref = oracle_case(cad)
+    p = make_peeler(cad, prec)
+    vis = to_dev(V, prec)
+    resid, jones, st = p.cadence(vis, cad.sources())
+    torch.cuda.synchronize()
+    R = resid.cpu().numpy()
+    J = jones.cpu().numpy()
+    tol = TOL[prec]
+    err_r = np.abs(R - R_ref).max() / rms_of(V)
+    err_j = jones_rel(J, J_ref)
+    print(f"{name}: residual {err_r:.2e} x rms, Jones {err_j:.2e} relative")
+    assert err_r <= tol
+    assert err_j <= tol
+    assert set(st.tolist()) <= {0, 1}
+    # input untouched by the out-of-place call
+    np.testing.assert_array_equal(vis.cpu().numpy(), V.astype(CDT[prec][0]))
+    p.close()
+
+
+def test_in_place_equals_out_of_place_and_is_deterministic():
+    cad = config(2).with_(n_src=6)
+    V, _, _, _ = oracle_case(config(2))
+    p = make_peeler(cad, "mixed")
+    vis = to_dev(V, "mixed")
+    r1, j1, _ = p.cadence(vis, cad.sources())
+    r2, j2, _ = p.cadence(vis, cad.sources())
+    work = vis.clone()
+    r3, j3, _ = p.cadence(work, cad.sources(), resid=work)
+    torch.cuda.synchronize()
+    assert torch.equal(r1, r2) and torch.equal(j1, j2)
+    assert torch.equal(r1, r3) and torch.equal(j1, j3)
+    p.close()
+
+
+def test_zero_sources_copies_input():
+    cad = Cadence(5, 8, 2, 1, seed=5)
+    V = oracle.simulate(cad)
+    p = make_peeler(cad, "mixed")
+    vis = to_dev(V, "mixed")
+    resid, jones, st = p.cadence(vis, np.zeros((0, 3)))
+    torch.cuda.synchronize()
+    assert torch.equal(resid, vis) and jones.shape[0] == 0 and len(st) == 0
+    p.close()
+
+
+# ---------------------------------------------------------------------------
+# single steps
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_rotate_average_matches_oracle(prec):
+    cad = config(2).with_(precision=prec, n_src=8)
+    V = oracle.simulate(cad)
+    V = V.astype(CDT[prec][0]).astype(np.complex128)
+    p = make_peeler(cad, prec)
+    vis = to_dev(V, prec)
+    for (l, m, _) in cad.sources()[:3]:
+        ref = oracle.rotate_average(cad.uvw(), cad.freqs(), V, l, m)
+        got = p.rotate_average(vis, l, m).cpu().numpy()
+        assert np.abs(got - ref).max() <= TOL[prec] * rms_of(V)
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_solve_matches_oracle_on_oracle_average(prec):
+    cad = config(2).with_(precision=prec)
+    V = oracle.simulate(cad)
+    l, m, S = cad.sources()[0]
+    avg = oracle.rotate_average(cad.uvw(), cad.freqs(), V, l, m)
+    avg_in = avg.astype(CDT[prec][0]).astype(np.complex128)
+    J_ref, st_ref, rel = oracle.als(avg_in, S, cad.n_ant, n_iter=20)
+    p = make_peeler(cad, prec)
+    J, st = p.solve(torch.from_numpy(avg_in.astype(CDT[prec][0])).cuda(), S)
+    J = J.cpu().numpy()
+    assert np.linalg.norm(J - J_ref) / np.linalg.norm(J_ref) <= TOL[prec]
+    assert st in (0, 1)
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_predict_matches_oracle(prec):
+    cad = Cadence(11, 70, 3, 40, precision=prec, seed=55)
+    p = make_peeler(cad, prec)
+    J = torch.from_numpy(cad.jones().astype(CDT[prec][0])).cuda()
+    Jr = J.cpu().numpy().astype(np.complex128)
+    ref = oracle.predict(cad.uvw(), cad.freqs(), cad.sources(), Jr)
+    got = p.predict(cad.sources(), J).cpu().numpy()
+    assert np.abs(got - ref).max() <= TOL[prec] * rms_of(ref)
+    # accumulate = add to what is there
+    base = torch.ones(p.cube_shape, dtype=CDT[prec][1], device="cuda")
+    got2 = p.predict(cad.sources(), J, out=base, accumulate=True).cpu().numpy()
+    assert np.abs(got2 - (ref + 1.0)).max() <= TOL[prec] * rms_of(ref) + 1e-6
+    p.close()
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_loss_and_gradient_match_oracle(prec):
+    cad = Cadence(10, 90, 3, 5, precision=prec, pos_sigma_rad=2.909e-4, seed=66)
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0))
+    V = V.astype(CDT[prec][0]).astype(np.complex128)
+    src = cad.perturbed_sources()
+    J = cad.jones().astype(CDT[prec][0]).astype(np.complex128)
+    L_ref, gJ_ref, gl_ref, gm_ref, gS_ref = oracle.loss_grad(cad.uvw(), cad.freqs(), V, src, J)
+    p = make_peeler(cad, prec)
+    loss, gJ, gs = p.grad(to_dev(V, prec), torch.from_numpy(J.astype(CDT[prec][0])).cuda(),
+                          torch.from_numpy(src).cuda())
+    torch.cuda.synchronize()
+    gtol = 1e-4 if prec == "mixed" else 1e-9
+    assert abs(loss.item() - L_ref) <= TOL[prec] * L_ref
+    gJ = gJ.cpu().numpy()
+    assert np.abs(gJ - gJ_ref).max() <= gtol * np.abs(gJ_ref).max()
+    gs = gs.cpu().numpy()
+    for col, ref in ((0, gl_ref), (1, gm_ref), (2, gS_ref)):
+        assert np.abs(gs[:, col] - ref).max() <= gtol * np.abs(ref).max(), col
+    p.close()
+
+
+def test_gradient_matches_central_differences_of_gpu_loss():
+    """Central differences of the FP64 GPU loss against the mixed-path gradient."""
+    cad = Cadence(8, 64, 2, 4, precision="fp64", pos_sigma_rad=2.909e-4, seed=67)
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0))
+    src = cad.perturbed_sources()
+    J = cad.jones()
+    p64 = make_peeler(cad, "fp64")
+    pm = make_peeler(cad.with_(precision="mixed"), "mixed")
+    v64 = to_dev(V, "fp64")
+    _, gJ, gs = pm.grad(to_dev(V, "mixed"), torch.from_numpy(J.astype(np.complex64)).cuda(),
+                        torch.from_numpy(src).cuda())
+    gJ, gs = gJ.cpu().numpy(), gs.cpu().numpy()
+    J64 = torch.from_numpy(J.astype(np.complex64).astype(np.complex128)).cuda()
+
+    def L(Jt, s):
+        return p64.grad(v64, Jt, torch.from_numpy(s).cuda(), want_grad=False)[0].item()
+
+    rng = np.random.default_rng(8)
+    for _ in range(10):
+        k = int(rng.integers(cad.n_src))
+        kind = int(rng.integers(5))
+        if kind < 2:
+            a, e = int(rng.integers(cad.n_ant)), int(rng.integers(4))
+            h = 1e-6
+            d = torch.zeros_like(J64)
+            d[k, a, e] = h if kind == 0 else 1j * h
+            fd = (L(J64 + d, src) - L(J64 - d, src)) / (2 * h)
+            an = gJ[k, a, e].real if kind == 0 else gJ[k, a, e].imag
+            scale = np.abs(gJ).max()
+        else:
+            col = kind - 2
+            h = 1e-7 if col < 2 else 1e-6
+            s1, s2 = src.copy(), src.copy()
+            s1[k, col] += h
+            s2[k, col] -= h
+            fd = (L(J64, s1) - L(J64, s2)) / (2 * h)
+            an = gs[k, col]
+            scale = np.abs(gs[:, col]).max()
+        assert abs(an - fd) <= 1e-4 * max(abs(fd), 1e-2 * scale), (kind, an, fd)
+    p64.close()
+    pm.close()
+
+
+def test_peel_loss_autograd_function():
+    from paper_1003_5575_gb300 import PeelLoss
+    cad = Cadence(8, 32, 2, 3, pos_sigma_rad=2.909e-4, seed=68)
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0))
+    p = make_peeler(cad, "mixed")
+    vis = to_dev(V, "mixed")
+    J = torch.from_numpy(cad.jones().astype(np.complex64)).cuda().requires_grad_(True)
+    src = torch.from_numpy(cad.perturbed_sources()).cuda().requires_grad_(True)
+    loss = PeelLoss.apply(p, vis, J, src)
+    (3.0 * loss).backward()
+    _, gJ, gs = p.grad(vis, J.detach(), src.detach())
+    assert torch.allclose(J.grad, 3.0 * gJ) and torch.allclose(src.grad, 3.0 * gs)
+    p.close()
+
+
+# ---------------------------------------------------------------------------
+# errors (raised on the host or reported through status; nothing faults)
+
+
+def test_bad_sources_rejected():
+    from paper_1003_5575_gb300 import RtsError, RTS_EINVAL
+    cad = Cadence(5, 8, 2, 1, seed=5)
+    p = make_peeler(cad, "mixed", max_sources=2)
+    vis = to_dev(oracle.simulate(cad), "mixed")
+    for bad in ([[0.9, 0.9, 1.0]], [[0.1, 0.1, 0.0]], [[np.nan, 0.0, 1.0]], [[0.0, 0.0, 1.0]] * 3):
+        with pytest.raises(RtsError) as e:
+            p.cadence(vis, np.array(bad))
+        assert e.value.code == RTS_EINVAL
+    p.close()
+
+
+def test_nonfinite_input_reported():
+    from paper_1003_5575_gb300 import RtsError, RTS_ENONFINITE
+    cad = Cadence(6, 16, 2, 2, seed=6)
+    V = oracle.simulate(cad)
+    V[0, 3, 5, 0] = np.nan
+    p = make_peeler(cad, "mixed")
+    with pytest.raises(RtsError) as e:
+        p.cadence(to_dev(V, "mixed"), cad.sources())
+    assert e.value.code == RTS_ENONFINITE
+    p.close()
