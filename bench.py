@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sources", type=int, default=1000, help="sources peeled per cadence")
     ap.add_argument("--n-iter", type=int, default=20)
+    ap.add_argument("--channels", type=int, default=768,
+                    help="channels (768 = the workload; fewer only for small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / adjoint / CPU legs")
     args = ap.parse_args()
@@ -229,7 +231,7 @@ def main():
     from paper_1003_5575_gb300 import Peeler, _abi
     from synth import config
 
-    cad = config(3).with_(n_src=args.sources, seed=config(3).seed + 1000 * rank)
+    cad = config(3).with_(n_src=args.sources, n_chan=args.channels, seed=config(3).seed + 1000 * rank)
     src = cad.sources()
     K = cad.n_src
     log(f"[rank {rank}] building cadence: {cad.n_ant} ant, {cad.n_chan} ch, {cad.n_time} t, {K} sources")
