@@ -122,6 +122,29 @@ int rts_peel_rotate_average(rts_peel_t* h, const void* d_vis, double l, double m
 int rts_peel_solve(rts_peel_t* h, const void* d_avg, double S, void* d_jones,
                    int32_t* h_status, void* stream);
 
+/* The solve step without any allocation, for callers that cannot call
+ * cudaMalloc or create a handle: code that runs after a real-time pipeline has
+ * frozen its memory at start-up, code inside another framework whose device
+ * memory is owned by that framework's pool, or code in a stream-capture
+ * region, where allocation calls are not allowed.  The paper has no
+ * counterpart; this is an interface addition of this library.
+ *   d_avg    device [n_bl][4] averaged visibilities (complex64 for
+ *            RTS_PREC_MIXED, complex128 for RTS_PREC_FP64), as for rts_peel_solve
+ *   n_ant    2 .. RTS_NOALLOC_MAX_ANT; larger arrays are rejected with RTS_EINVAL
+ *   d_jones  device [n_ant][4] output, same precision as d_avg
+ *   h_status optional host int: as in rts_peel_solve (the call then waits)
+ * Scratch: one static device array of about 200 KB (sized for
+ * RTS_NOALLOC_MAX_ANT antennas) that every device loading the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * device address; make that first call before any stream capture begins.
+ * All calls share the array and it keeps the last call's contents, so calls
+ * that overlap on the GPU (different streams, or different host threads on
+ * one device) race with each other: serialise them.  Errors are reported by
+ * the return code and rts_peel_last_error(NULL). */
+#define RTS_NOALLOC_MAX_ANT 1024
+int rts_peel_solve_noalloc(const void* d_avg, int32_t n_ant, double S, int32_t n_iter,
+                           int32_t precision, void* d_jones, int32_t* h_status, void* stream);
+
 /* Loss and gradient of the multi-source model (the adjoint of the predict step):
  *   L = sum_{t,bl,c} || V - sum_k S_k J_i^k J_j^kH exp(-2 pi i phi_k) ||_F^2
  *   d_vis   [n_time][n_bl][n_chan][4]; d_jones [n_src][n_ant][4];

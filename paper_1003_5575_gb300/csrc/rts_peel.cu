@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -481,3 +482,84 @@ void rts_peel_destroy(rts_peel_t* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve.  Its scratch (Jones iterates, their FP32 copies, the
+// per-antenna norms and the status words) lives in one file-scope device
+// array, sized for RTS_NOALLOC_MAX_ANT antennas and held by every device that
+// loads this library until the process exits.  Host code cannot use the
+// array's name as a device address, so each device's address is looked up
+// once with cudaGetSymbolAddress (on the first call made on that device).
+
+namespace {
+
+struct NoallocScratch {
+  double2 J[2][RTS_NOALLOC_MAX_ANT * 4];
+  float2 Jf[2][RTS_NOALLOC_MAX_ANT * 4];
+  double norms[RTS_NOALLOC_MAX_ANT * 2];
+  double rel;
+  int flag;
+  int status;
+};
+
+__device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+NoallocScratch* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int rts_peel_solve_noalloc(const void* d_avg, int32_t n_ant, double S, int32_t n_iter,
+                                      int32_t precision, void* d_jones, int32_t* h_status,
+                                      void* stream) {
+  g_init_err.clear();
+  if (!d_avg || !d_jones) return fail(nullptr, RTS_EINVAL, "d_avg and d_jones are required");
+  if (n_ant < 2 || n_ant > RTS_NOALLOC_MAX_ANT)
+    return fail(nullptr, RTS_EINVAL, "rts_peel_solve_noalloc: n_ant must be in [2, " +
+                                         std::to_string(RTS_NOALLOC_MAX_ANT) + "] (static scratch limit)");
+  if (n_iter < 1 || n_iter > 10000) return fail(nullptr, RTS_EINVAL, "n_iter must be in [1, 10000]");
+  if (precision != RTS_PREC_MIXED && precision != RTS_PREC_FP64)
+    return fail(nullptr, RTS_EINVAL, "precision must be RTS_PREC_MIXED or RTS_PREC_FP64");
+  if (!std::isfinite(S) || !(S > 0.0)) return fail(nullptr, RTS_EINVAL, "S must be finite and > 0");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(nullptr, RTS_EINVAL, "device ordinal too large");
+  NoallocScratch* sc = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(scratch)");
+      g_noalloc_addr[dev] = static_cast<NoallocScratch*>(ptr);
+    }
+    sc = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = as_stream(stream);
+  // the flag must start at zero; the rest is written before it is read
+  e = cudaMemsetAsync(&sc->flag, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "clear scratch flag");
+  for (int it = 1; it <= n_iter; ++it) {
+    AlsArgs a;
+    a.avg = d_avg;
+    a.J_old = sc->J[(it - 1) & 1]; a.Jf_old = sc->Jf[(it - 1) & 1];
+    a.J_new = sc->J[it & 1]; a.Jf_new = sc->Jf[it & 1];
+    a.norms = sc->norms; a.flag = &sc->flag;
+    a.jones_out = it == n_iter ? d_jones : nullptr;
+    a.n_ant = n_ant; a.S = S; a.first = it == 1; a.average = (it % 2) == 0;
+    if (precision == RTS_PREC_MIXED) k_als_sweep<float><<<n_ant, kAlsThreads, 0, s>>>(a);
+    else k_als_sweep<double><<<n_ant, kAlsThreads, 0, s>>>(a);
+  }
+  k_als_finalize<<<1, 256, 0, s>>>(sc->norms, n_ant, &sc->flag, &sc->status, &sc->rel);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "ALS kernel launch (no-alloc)");
+  if (h_status) {
+    e = cudaMemcpyAsync(h_status, &sc->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "read status (no-alloc)");
+    if (*h_status == RTS_ENONFINITE) return fail(nullptr, RTS_ENONFINITE, "non-finite value in the solve");
+  }
+  return RTS_OK;
+}
