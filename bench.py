@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sources", type=int, default=1000, help="sources peeled per cadence")
     ap.add_argument("--n-iter", type=int, default=20)
+    ap.add_argument("--antennas", type=int, default=512,
+                    help="antennas (512 = the workload; fewer only for small profiling cases)")
     ap.add_argument("--channels", type=int, default=768,
                     help="channels (768 = the workload; fewer only for small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -231,7 +233,7 @@ def main():
     from paper_1003_5575_gb300 import Peeler, _abi
     from synth import config
 
-    cad = config(3).with_(n_src=args.sources, n_chan=args.channels, seed=config(3).seed + 1000 * rank)
+    cad = config(3).with_(n_src=args.sources, n_chan=args.channels, n_ant=args.antennas, seed=config(3).seed + 1000 * rank)
     src = cad.sources()
     K = cad.n_src
     log(f"[rank {rank}] building cadence: {cad.n_ant} ant, {cad.n_chan} ch, {cad.n_time} t, {K} sources")
@@ -318,6 +320,16 @@ def main():
             arr_o = np.ctypeslib.as_array((ctypes.c_float * (cad.n_vis * 8)).from_address(h_out))
             h_res = torch.from_numpy(arr_o).view(torch.complex64).view(p.cube_shape)
             p.cadence_host(h_vis, src, d_work=d_resid, h_resid=h_res)
+            # raw copy bandwidth of the same buffers (context for the e2e number)
+            e_a, e_b, e_c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e_a.record(stream)
+            d_resid.view(torch.float32).reshape(-1).copy_(torch.from_numpy(arr), non_blocking=True)
+            e_b.record(stream)
+            torch.from_numpy(arr_o).copy_(d_resid.view(torch.float32).reshape(-1), non_blocking=True)
+            e_c.record(stream)
+            torch.cuda.synchronize()
+            h2d_gbs = cube_bytes / (e_a.elapsed_time(e_b) / 1e3) / 1e9
+            d2h_gbs = cube_bytes / (e_b.elapsed_time(e_c) / 1e3) / 1e9
             n_e2e = max(1, min(args.steps, 2))
             barrier()
             t0 = time.perf_counter()
@@ -328,6 +340,7 @@ def main():
                            "h2d_bytes_per_step": cube_bytes + K * 24,
                            "d2h_bytes_per_step": cube_bytes + K * cad.n_ant * 32 + K * 4,
                            "ms_per_step": dt * 1e3, "steps": n_e2e,
+                           "h2d_GBps": h2d_gbs, "d2h_GBps": d2h_gbs,
                            "api": "rts_peel_cadence_host (pinned host buffers from rts_host_alloc)"}
         finally:
             _abi.rts_host_free(h_in)

@@ -7,16 +7,20 @@
 // V_qp = V_pq^H for q < p (one triangle is stored).  Jacobi sweep: every p
 // uses the previous iterate; every second sweep is averaged with it.
 //
-// One CTA per antenna; its threads split the q sum.  Mixed precision: the
-// products and each thread's partial sum (<= n_ant/128 terms) are FP32, the
-// sum across threads and the 2x2 solve are FP64.  The FP64 path does all of
-// it in FP64.
+// One CTA of kAlsThreads threads per antenna p; thread t takes q = t, t+128,
+// ... and issues all of its loads before any arithmetic.  Mixed precision: the
+// products and each thread's partial sum (<= ceil(n_ant/128) terms) are FP32;
+// the sum across threads is FP64 (a reduce-scatter butterfly inside each warp,
+// 16 FP64 adds per lane for the 12 sums, then the warps combined in shared
+// memory), and the 2x2 solve is FP64.  The FP64 path does all of it in FP64.
 #pragma once
 #include "common.cuh"
 
 namespace rts {
 
 constexpr int kAlsThreads = 128;
+constexpr int kAlsPerThread = 4;     // q terms whose loads are issued together
+inline unsigned als_grid(int n_ant) { return (unsigned)n_ant; }
 
 struct AlsArgs {
   const void* avg;          // [n_bl][4] complex, cube precision
@@ -44,11 +48,30 @@ __device__ inline void load_vpq(const C* __restrict__ avg, int n_ant, int p, int
   }
 }
 
+// Reduce 16 doubles over the 32 lanes of a warp.  Each level exchanges half of
+// the remaining values with the partner lane, so a lane does 8+4+2+1+1 adds;
+// afterwards lane L holds the warp total of value index L >> 1.
+__device__ inline double warp_reduce_scatter16(double (&v)[16], int lane) {
+  #pragma unroll
+  for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+    const bool upper = (lane & o) != 0;
+    #pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const double send = upper ? v[i] : v[i + n / 2];
+      const double keep = upper ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <typename T>   // T = float (mixed) or double (FP64)
 __global__ void __launch_bounds__(kAlsThreads) k_als_sweep(AlsArgs a) {
   using C = typename cplx_of<T>::type;
-  __shared__ double s_red[(kAlsThreads / 32) * 12];
+  __shared__ double s_red[kAlsThreads / 32][12];
+  __shared__ double s_tot[12];
   const int p = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // per-thread partials: A (4 complex) and Hermitian C (c00, c11, re c01, im c01)
   T A[8], Cm[4];
   #pragma unroll
@@ -56,105 +79,101 @@ __global__ void __launch_bounds__(kAlsThreads) k_als_sweep(AlsArgs a) {
   #pragma unroll
   for (int k = 0; k < 4; ++k) Cm[k] = T(0);
   const C* avg = static_cast<const C*>(a.avg);
-  for (int q = threadIdx.x; q < a.n_ant; q += kAlsThreads) {
-    if (q == p) continue;
-    C V[4];
-    load_vpq<C>(avg, a.n_ant, p, q, V);
-    C J[4];
-    if (a.first) {
-      J[0] = cmk<C>(1, 0); J[1] = cmk<C>(0, 0); J[2] = cmk<C>(0, 0); J[3] = cmk<C>(1, 0);
-    } else if (sizeof(T) == 4) {
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) { float2 f = a.Jf_old[(size_t)q * 4 + e]; J[e] = cmk<C>(f.x, f.y); }
-    } else {
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) { double2 d = a.J_old[(size_t)q * 4 + e]; J[e] = cmk<C>(d.x, d.y); }
+  for (int q0 = threadIdx.x; q0 < a.n_ant; q0 += kAlsThreads * kAlsPerThread) {
+    C V[kAlsPerThread][4], J[kAlsPerThread][4];
+    #pragma unroll
+    for (int u = 0; u < kAlsPerThread; ++u) {
+      const int q = q0 + u * kAlsThreads;
+      if (q < a.n_ant && q != p) {
+        load_vpq<C>(avg, a.n_ant, p, q, V[u]);
+        if (a.first) {
+          J[u][0] = cmk<C>(1, 0); J[u][1] = cmk<C>(0, 0); J[u][2] = cmk<C>(0, 0); J[u][3] = cmk<C>(1, 0);
+        } else if constexpr (sizeof(T) == 4) {
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) { float2 f = a.Jf_old[(size_t)q * 4 + e]; J[u][e] = cmk<C>(f.x, f.y); }
+        } else {
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) { double2 d = a.J_old[(size_t)q * 4 + e]; J[u][e] = cmk<C>(d.x, d.y); }
+        }
+      } else {
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) { V[u][e] = cmk<C>(0, 0); J[u][e] = cmk<C>(0, 0); }
+      }
     }
-    // A += V J
-    C a0 = cadd(cmul(V[0], J[0]), cmul(V[1], J[2]));
-    C a1 = cadd(cmul(V[0], J[1]), cmul(V[1], J[3]));
-    C a2 = cadd(cmul(V[2], J[0]), cmul(V[3], J[2]));
-    C a3 = cadd(cmul(V[2], J[1]), cmul(V[3], J[3]));
-    A[0] += a0.x; A[1] += a0.y; A[2] += a1.x; A[3] += a1.y;
-    A[4] += a2.x; A[5] += a2.y; A[6] += a3.x; A[7] += a3.y;
-    // C += J^H J  (c00 = |J00|^2 + |J10|^2, c11 = |J01|^2 + |J11|^2, c01 = conj(J00) J01 + conj(J10) J11)
-    Cm[0] += J[0].x * J[0].x + J[0].y * J[0].y + J[2].x * J[2].x + J[2].y * J[2].y;
-    Cm[1] += J[1].x * J[1].x + J[1].y * J[1].y + J[3].x * J[3].x + J[3].y * J[3].y;
-    C c01 = cadd(cconjmul(J[0], J[1]), cconjmul(J[2], J[3]));
-    Cm[2] += c01.x; Cm[3] += c01.y;
+    #pragma unroll
+    for (int u = 0; u < kAlsPerThread; ++u) {
+      const C* Vq = V[u];
+      const C* Jq = J[u];
+      // A += V J
+      C a0 = cadd(cmul(Vq[0], Jq[0]), cmul(Vq[1], Jq[2]));
+      C a1 = cadd(cmul(Vq[0], Jq[1]), cmul(Vq[1], Jq[3]));
+      C a2 = cadd(cmul(Vq[2], Jq[0]), cmul(Vq[3], Jq[2]));
+      C a3 = cadd(cmul(Vq[2], Jq[1]), cmul(Vq[3], Jq[3]));
+      A[0] += a0.x; A[1] += a0.y; A[2] += a1.x; A[3] += a1.y;
+      A[4] += a2.x; A[5] += a2.y; A[6] += a3.x; A[7] += a3.y;
+      // C += J^H J  (c00 = |J00|^2 + |J10|^2, c11 = |J01|^2 + |J11|^2, c01 = conj(J00) J01 + conj(J10) J11)
+      Cm[0] += Jq[0].x * Jq[0].x + Jq[0].y * Jq[0].y + Jq[2].x * Jq[2].x + Jq[2].y * Jq[2].y;
+      Cm[1] += Jq[1].x * Jq[1].x + Jq[1].y * Jq[1].y + Jq[3].x * Jq[3].x + Jq[3].y * Jq[3].y;
+      C c01 = cadd(cconjmul(Jq[0], Jq[1]), cconjmul(Jq[2], Jq[3]));
+      Cm[2] += c01.x; Cm[3] += c01.y;
+    }
   }
-  double v[12], tot[12];
+  double v[16];
   #pragma unroll
   for (int k = 0; k < 8; ++k) v[k] = (double)A[k];
   #pragma unroll
   for (int k = 0; k < 4; ++k) v[8 + k] = (double)Cm[k];
   #pragma unroll
-  for (int k = 0; k < 12; ++k)
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0)
-    #pragma unroll
-    for (int k = 0; k < 12; ++k) s_red[warp * 12 + k] = v[k];
+  for (int k = 12; k < 16; ++k) v[k] = 0.0;
+  const double wsum = warp_reduce_scatter16(v, lane);
+  if ((lane & 1) == 0 && (lane >> 1) < 12) s_red[warp][lane >> 1] = wsum;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    double s = 0.0;
-    for (int w = 0; w < kAlsThreads / 32; ++w) s += s_red[w * 12 + k];
-    tot[k] = s;
+  if (threadIdx.x < 12) {
+    double t = 0.0;
+    #pragma unroll
+    for (int w = 0; w < kAlsThreads / 32; ++w) t += s_red[w][threadIdx.x];
+    s_tot[threadIdx.x] = t;
   }
-  // solve J_p = A C^-1 / S in FP64, C = [c00 c01; conj(c01) c11]
-  const double2 A00 = make_double2(tot[0], tot[1]), A01 = make_double2(tot[2], tot[3]);
-  const double2 A10 = make_double2(tot[4], tot[5]), A11 = make_double2(tot[6], tot[7]);
-  const double c00 = tot[8], c11 = tot[9];
-  const double2 c01 = make_double2(tot[10], tot[11]);
+  __syncthreads();
+  // the 2x2 solve: lanes 0..3 of warp 0 each produce one entry J_new[e]
+  if (threadIdx.x >= 4) return;
+  const int e = threadIdx.x, r = e >> 1, c = e & 1;
+  // J_p = A C^-1 / S in FP64, C = [c00 c01; conj(c01) c11],
+  // C^-1 = [c11 -c01; -conj(c01) c00] / det
+  const double c00 = s_tot[8], c11 = s_tot[9];
+  const double2 c01 = make_double2(s_tot[10], s_tot[11]);
   const double det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);   // real, >= 0
   const double sc = 1.0 / (det * a.S);
-  // C^-1 = [c11 -c01; -conj(c01) c00] / det
-  const double2 i00 = make_double2(c11 * sc, 0.0), i11 = make_double2(c00 * sc, 0.0);
-  const double2 i01 = make_double2(-c01.x * sc, -c01.y * sc);
-  const double2 i10 = make_double2(-c01.x * sc, c01.y * sc);
-  double2 Jn[4];
-  Jn[0] = cadd(cmul(A00, i00), cmul(A01, i10));
-  Jn[1] = cadd(cmul(A00, i01), cmul(A01, i11));
-  Jn[2] = cadd(cmul(A10, i00), cmul(A11, i10));
-  Jn[3] = cadd(cmul(A10, i01), cmul(A11, i11));
-  double2 Jo[4];
-  if (a.first) {
-    Jo[0] = make_double2(1, 0); Jo[1] = make_double2(0, 0); Jo[2] = make_double2(0, 0); Jo[3] = make_double2(1, 0);
-  } else {
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) Jo[e] = a.J_old[(size_t)p * 4 + e];
-  }
-  if (a.average) {
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) Jn[e] = make_double2(0.5 * (Jn[e].x + Jo[e].x), 0.5 * (Jn[e].y + Jo[e].y));
-  }
-  double dn = 0.0, nn = 0.0;
-  bool finite = true;
+  // column c of C^-1: (i0c, i1c)
+  const double2 i0c = c == 0 ? make_double2(c11 * sc, 0.0) : make_double2(-c01.x * sc, -c01.y * sc);
+  const double2 i1c = c == 0 ? make_double2(-c01.x * sc, c01.y * sc) : make_double2(c00 * sc, 0.0);
+  // row r of A: (Ar0, Ar1)
+  const double2 Ar0 = make_double2(s_tot[4 * r], s_tot[4 * r + 1]);
+  const double2 Ar1 = make_double2(s_tot[4 * r + 2], s_tot[4 * r + 3]);
+  double2 Jn = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
+  const double2 Jo = a.first ? make_double2((e == 0 || e == 3) ? 1.0 : 0.0, 0.0)
+                             : a.J_old[(size_t)p * 4 + e];
+  if (a.average) Jn = make_double2(0.5 * (Jn.x + Jo.x), 0.5 * (Jn.y + Jo.y));
+  const double dx = Jn.x - Jo.x, dy = Jn.y - Jo.y;
+  double dn = dx * dx + dy * dy;
+  double nn = Jn.x * Jn.x + Jn.y * Jn.y;
+  int bad = !(isfinite(Jn.x) && isfinite(Jn.y));
   #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const double dx = Jn[e].x - Jo[e].x, dy = Jn[e].y - Jo[e].y;
-    dn += dx * dx + dy * dy;
-    nn += Jn[e].x * Jn[e].x + Jn[e].y * Jn[e].y;
-    finite = finite && isfinite(Jn[e].x) && isfinite(Jn[e].y);
-    a.J_new[(size_t)p * 4 + e] = Jn[e];
-    if (sizeof(T) == 4) a.Jf_new[(size_t)p * 4 + e] = make_float2((float)Jn[e].x, (float)Jn[e].y);
+  for (int o = 1; o <= 2; o <<= 1) {
+    dn += __shfl_xor_sync(0xfu, dn, o);
+    nn += __shfl_xor_sync(0xfu, nn, o);
+    bad |= __shfl_xor_sync(0xfu, bad, o);
   }
-  a.norms[2 * p] = dn;
-  a.norms[2 * p + 1] = nn;
-  if (!finite) *a.flag = 1;
+  a.J_new[(size_t)p * 4 + e] = Jn;
+  if constexpr (sizeof(T) == 4) a.Jf_new[(size_t)p * 4 + e] = make_float2((float)Jn.x, (float)Jn.y);
   if (a.jones_out) {
-    if (sizeof(T) == 4) {
-      float2* o = static_cast<float2*>(a.jones_out) + (size_t)p * 4;
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) o[e] = make_float2((float)Jn[e].x, (float)Jn[e].y);
-    } else {
-      double2* o = static_cast<double2*>(a.jones_out) + (size_t)p * 4;
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) o[e] = Jn[e];
-    }
+    if constexpr (sizeof(T) == 4) static_cast<float2*>(a.jones_out)[(size_t)p * 4 + e] = make_float2((float)Jn.x, (float)Jn.y);
+    else static_cast<double2*>(a.jones_out)[(size_t)p * 4 + e] = Jn;
+  }
+  if (e == 0) {
+    a.norms[2 * p] = dn;
+    a.norms[2 * p + 1] = nn;
+    if (bad) *a.flag = 1;
   }
 }
 

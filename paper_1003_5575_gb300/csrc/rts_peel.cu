@@ -13,6 +13,7 @@
 #include "als_kernels.cuh"
 #include "common.cuh"
 #include "grad_kernels.cuh"
+#include "predict_kernels.cuh"
 #include "stream_kernels.cuh"
 
 using namespace rts;
@@ -157,8 +158,8 @@ int launch_als(rts_peel_t* h, const void* avg, double S, void* jones_out, int sl
     a.norms = h->d_norms; a.flag = h->d_flag;
     a.jones_out = it == h->n_iter ? jones_out : nullptr;
     a.n_ant = h->n_ant; a.S = S; a.first = it == 1; a.average = (it % 2) == 0;
-    if (h->precision == RTS_PREC_MIXED) k_als_sweep<float><<<h->n_ant, kAlsThreads, 0, s>>>(a);
-    else k_als_sweep<double><<<h->n_ant, kAlsThreads, 0, s>>>(a);
+    if (h->precision == RTS_PREC_MIXED) k_als_sweep<float><<<als_grid(h->n_ant), kAlsThreads, 0, s>>>(a);
+    else k_als_sweep<double><<<als_grid(h->n_ant), kAlsThreads, 0, s>>>(a);
   }
   k_als_finalize<<<1, 256, 0, s>>>(h->d_norms, h->n_ant, h->d_flag, h->d_status + slot, h->d_rel + slot);
   span.end(h->n_iter + 1);
@@ -549,8 +550,8 @@ extern "C" int rts_peel_solve_noalloc(const void* d_avg, int32_t n_ant, double S
     a.norms = sc->norms; a.flag = &sc->flag;
     a.jones_out = it == n_iter ? d_jones : nullptr;
     a.n_ant = n_ant; a.S = S; a.first = it == 1; a.average = (it % 2) == 0;
-    if (precision == RTS_PREC_MIXED) k_als_sweep<float><<<n_ant, kAlsThreads, 0, s>>>(a);
-    else k_als_sweep<double><<<n_ant, kAlsThreads, 0, s>>>(a);
+    if (precision == RTS_PREC_MIXED) k_als_sweep<float><<<als_grid(n_ant), kAlsThreads, 0, s>>>(a);
+    else k_als_sweep<double><<<als_grid(n_ant), kAlsThreads, 0, s>>>(a);
   }
   k_als_finalize<<<1, 256, 0, s>>>(sc->norms, n_ant, &sc->flag, &sc->status, &sc->rel);
   e = cudaGetLastError();

@@ -2,7 +2,6 @@
 //   rotate + average      (the average step of one source)
 //   subtract + average    (subtract source k, average for source k+1, one pass)
 //   subtract              (last source)
-//   predict               (model visibilities of many sources)
 // One CTA per baseline: its N_t strips of N_c contiguous visibilities are read
 // with coalesced 16-byte loads (consecutive threads = consecutive channels) and
 // its average is reduced in the CTA (warp shuffles, FP64 across warps), so no
@@ -270,119 +269,6 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_fp64(StreamArgs a) {
       #pragma unroll
       for (int e = 0; e < 4; ++e) out[e] = make_double2(tot[2 * e] * a.inv_n, tot[2 * e + 1] * a.inv_n);
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// predict: vis (+)= sum over a chunk of sources of S_k J_i J_j^H exp(-2 pi i phi_k)
-
-constexpr int kPredictChunk = 32;
-
-struct PredictArgs {
-  void* vis;
-  const double* uvw;
-  const int2* bl_ant;
-  const double* freq_c;
-  const double* src;         // device [n_src][3] (l, m, S) of this chunk
-  const void* jones;         // device [n_src][n_ant][4] (cube precision) of this chunk
-  int n_src;                 // <= kPredictChunk
-  int n_ant, n_chan, n_time;
-  int64_t n_bl;
-  double nu0_c, dnu_c;
-  int accumulate;
-};
-
-__device__ inline SrcDir dev_dir(const double* s) {
-  SrcDir d; d.l = s[0]; d.m = s[1]; d.S = s[2];
-  double r2 = d.l * d.l + d.m * d.m;
-  d.nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
-  return d;
-}
-
-__global__ void __launch_bounds__(kStreamThreads) k_predict_mixed(PredictArgs a) {
-  extern __shared__ unsigned long long s_ab[];      // [n_time][n_src][2]
-  __shared__ float2 s_M[kPredictChunk][4];    // -S_k J_i J_j^H
-  const int64_t bl = blockIdx.x;
-  const int2 ij = a.bl_ant[bl];
-  for (int q = threadIdx.x; q < a.n_time * a.n_src; q += blockDim.x) {
-    const int t = q / a.n_src, k = q - t * a.n_src;
-    SrcDir d = dev_dir(a.src + 3 * k);
-    double tau = delay_m(a.uvw, a.n_ant, t, ij.x, ij.y, d);
-    s_ab[2 * q] = frac_q64(tau * a.nu0_c);
-    s_ab[2 * q + 1] = frac_q64(tau * a.dnu_c);
-  }
-  for (int k = threadIdx.x; k < a.n_src; k += blockDim.x) {
-    const float2* J = static_cast<const float2*>(a.jones) + (size_t)k * a.n_ant * 4;
-    M22<double2> Ji, Jj;
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      float2 p = J[(size_t)ij.x * 4 + e], q = J[(size_t)ij.y * 4 + e];
-      Ji.e[e] = make_double2(p.x, p.y); Jj.e[e] = make_double2(q.x, q.y);
-    }
-    M22<double2> P = mmul_h(Ji, Jj);
-    const double S = a.src[3 * k + 2];
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) s_M[k][e] = make_float2((float)(-S * P.e[e].x), (float)(-S * P.e[e].y));
-  }
-  __syncthreads();
-  float4* vis = static_cast<float4*>(a.vis);
-  const int n_s = a.n_time * a.n_chan;
-  TCWalk w;
-  w.init(threadIdx.x, a.n_chan);
-  for (int s = threadIdx.x; s < n_s; s += kStreamThreads, w.next()) {
-    const size_t idx = (((size_t)w.t * a.n_bl + bl) * a.n_chan + w.c) * 2;
-    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-    if (a.accumulate) { x0 = vis[idx]; x1 = vis[idx + 1]; }
-    for (int k = 0; k < a.n_src; ++k) {
-      const unsigned long long A = s_ab[2 * (w.t * a.n_src + k)];
-      const unsigned long long B = s_ab[2 * (w.t * a.n_src + k) + 1];
-      float2 ph = phasor_f(q64_to_turns(A + (unsigned long long)w.c * B));
-      // s_M holds -M, so "subtracting" it adds M exp(-2 pi i phi)
-      float2 nM[4] = {s_M[k][0], s_M[k][1], s_M[k][2], s_M[k][3]};
-      sub_model(x0, x1, nM, ph);
-    }
-    vis[idx] = x0;
-    vis[idx + 1] = x1;
-  }
-}
-
-__global__ void __launch_bounds__(kStreamThreads) k_predict_fp64(PredictArgs a) {
-  extern __shared__ double s_tau64[];               // [n_time][n_src]
-  __shared__ double2 s_M64[kPredictChunk][4];
-  const int64_t bl = blockIdx.x;
-  const int2 ij = a.bl_ant[bl];
-  for (int q = threadIdx.x; q < a.n_time * a.n_src; q += blockDim.x) {
-    const int t = q / a.n_src, k = q - t * a.n_src;
-    SrcDir d = dev_dir(a.src + 3 * k);
-    s_tau64[q] = delay_m(a.uvw, a.n_ant, t, ij.x, ij.y, d);
-  }
-  for (int k = threadIdx.x; k < a.n_src; k += blockDim.x) {
-    const double2* J = static_cast<const double2*>(a.jones) + (size_t)k * a.n_ant * 4;
-    M22<double2> Ji, Jj;
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) { Ji.e[e] = J[(size_t)ij.x * 4 + e]; Jj.e[e] = J[(size_t)ij.y * 4 + e]; }
-    M22<double2> P = mmul_h(Ji, Jj);
-    const double S = a.src[3 * k + 2];
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) s_M64[k][e] = make_double2(S * P.e[e].x, S * P.e[e].y);
-  }
-  __syncthreads();
-  double2* vis = static_cast<double2*>(a.vis);
-  const int n_s = a.n_time * a.n_chan;
-  TCWalk w;
-  w.init(threadIdx.x, a.n_chan);
-  for (int s = threadIdx.x; s < n_s; s += kStreamThreads, w.next()) {
-    const size_t idx = (((size_t)w.t * a.n_bl + bl) * a.n_chan + w.c) * 4;
-    double2 x[4];
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) x[e] = a.accumulate ? vis[idx + e] : make_double2(0.0, 0.0);
-    for (int k = 0; k < a.n_src; ++k) {
-      double2 ph = phasor_d(s_tau64[w.t * a.n_src + k] * a.freq_c[w.c]);
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) x[e] = cadd(x[e], cmulc(s_M64[k][e], ph));
-    }
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) vis[idx + e] = x[e];
   }
 }
 

@@ -1,0 +1,128 @@
+"""Full-size checks at the benchmark's shape (512 antennas, 768 channels, 8 times,
+1000 sources; the launch configuration bench.py times).
+
+The oracle cannot peel 1000 sources over 8e8 visibilities, so:
+  * outputs the oracle can compute one baseline at a time are compared with it
+    (model prediction, the first source's average), the oracle working on its
+    own 2-antenna sub-array simulation from the generator's parameters;
+  * the whole peel is checked through properties that hold at any size
+    (exact single-source recovery against the generator's truth; residual +
+    prediction of the solved sources = input; statuses valid).
+Tolerance: 1e-5 x rms of the input's real components, Jones 1e-5 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import config
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def full():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1003_5575_gb300 import Peeler, build
+    build.build()
+    cad = config(3)
+    p = Peeler(cad.uvw(), cad.freqs(), n_iter=20, precision="mixed", max_sources=cad.n_src)
+    J = cad.jones().astype(np.complex64)
+    vis = p.predict(cad.sources(), torch.from_numpy(J).cuda())
+    torch.cuda.synchronize()
+    yield cad, p, vis, J
+    del vis
+    p.close()
+    torch.cuda.empty_cache()
+
+
+def sub_array(cad, i, j):
+    """uvw of antennas (i, j) only: a 2-antenna array with the one baseline i-j."""
+    return cad.uvw()[:, [i, j], :]
+
+
+def rms_of(x):
+    x = x.view(torch.float32) if x.is_complex() else x
+    return math.sqrt(float(torch.mean(x.double() ** 2)))
+
+
+def sample_baselines(n_ant, n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        i, j = sorted(rng.choice(n_ant, 2, replace=False).tolist())
+        out.append((i, j))
+    return out
+
+
+def bl_index(n_ant, i, j):
+    return i * n_ant - i * (i + 1) // 2 + (j - i - 1)
+
+
+def test_fullsize_predict_matches_oracle_on_sampled_baselines(full):
+    cad, p, vis, J = full
+    rms = rms_of(vis)
+    for i, j in sample_baselines(cad.n_ant, 4, 1):
+        ref = oracle.predict(sub_array(cad, i, j), cad.freqs(), cad.sources(), J[:, [i, j], :])
+        got = vis[:, bl_index(cad.n_ant, i, j)].cpu().numpy()
+        assert np.abs(got - ref[:, 0]).max() <= TOL * rms, (i, j)
+
+
+def test_fullsize_first_average_matches_oracle_on_sampled_baselines(full):
+    cad, p, vis, J = full
+    rms = rms_of(vis)
+    l, m, _ = cad.sources()[0]
+    avg = p.rotate_average(vis, l, m).cpu().numpy()
+    for i, j in sample_baselines(cad.n_ant, 4, 2):
+        Vij = oracle.predict(sub_array(cad, i, j), cad.freqs(), cad.sources(), J[:, [i, j], :])
+        ref = oracle.rotate_average(sub_array(cad, i, j), cad.freqs(), Vij, l, m)
+        assert np.abs(avg[bl_index(cad.n_ant, i, j)] - ref[0]).max() <= TOL * rms, (i, j)
+
+
+def test_fullsize_single_source_recovered_exactly(full):
+    """One noise-free source at full size: the peel returns the true
+    gauge-invariant products J_i J_j^H and an empty residual."""
+    cad, p, _, J = full
+    src = cad.sources()[:1]
+    one = p.predict(src, torch.from_numpy(J[:1]).cuda())
+    resid, jones, st = p.cadence(one, src)
+    torch.cuda.synchronize()
+    assert rms_of(resid) <= TOL * rms_of(one)
+    Jg = jones[0].cpu().numpy().reshape(-1, 2, 2).astype(np.complex128)
+    Jt = J[0].reshape(-1, 2, 2).astype(np.complex128)
+    for i, j in sample_baselines(cad.n_ant, 64, 3):
+        got = Jg[i] @ Jg[j].conj().T
+        ref = Jt[i] @ Jt[j].conj().T
+        assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+    del one, resid
+
+
+def test_fullsize_peel_residual_plus_model_is_input(full):
+    """1000 sources: residual + prediction of the solved sources = input.
+
+    The residual is stored in FP32 after each of the 1000 sequential
+    subtractions, so its rounding error is a random walk of ~4000 steps of
+    half an ulp of |R|: the rms deviation must stay <= 1e-5 x rms (the stated
+    tolerance), and the extreme over 6.4e9 components <= 1e-4 x rms."""
+    cad, p, vis, J = full
+    resid, jones, st = p.cadence(vis, cad.sources())
+    assert set(np.unique(st).tolist()) <= {0, 1}
+    model = p.predict(cad.sources(), jones)
+    torch.cuda.synchronize()
+    rms = rms_of(vis)
+    sq, worst = 0.0, 0.0
+    for t in range(cad.n_time):
+        d = (resid[t] + model[t] - vis[t]).view(torch.float32)
+        sq += float(torch.sum(d.double() ** 2))
+        worst = max(worst, d.abs().max().item())
+    err_rms = math.sqrt(sq / (cad.n_vis * 8))
+    print(f"residual + model - input: rms {err_rms / rms:.2e} x rms, max {worst / rms:.2e} x rms")
+    assert err_rms <= TOL * rms
+    assert worst <= 10 * TOL * rms
+    assert rms_of(resid) < rms_of(vis)
+    del resid, model
