@@ -68,7 +68,14 @@ typedef struct rts_peel_config {
   const double* uvw;    /* host [n_time][n_ant][3] antenna (u, v, w) in metres; copied */
   const double* freq_hz;/* host [n_chan] channel centres in Hz; must be uniformly spaced
                            (nu_c = nu_0 + c dnu to 1e-9 relative); copied */
+  int32_t sources_per_pass; /* RTS_PREC_MIXED only: 1 = one streaming pass per source
+                           (subtract k fused with the average of k+1); 8, 16, 32 or 64 =
+                           one pass per block of that many sources, the averages inside a
+                           block corrected in closed form (same results); 0 = library
+                           default (RTS_BLOCK) */
 } rts_peel_config;
+
+#define RTS_BLOCK 64   /* default sources per streaming pass of the blocked peel */
 
 /* Validate `cfg`, allocate the device workspace on the current device, copy
  * uvw and frequencies.  On success *out is a new handle.  Errors: RTS_EINVAL
@@ -168,7 +175,9 @@ int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d
 #define RTS_K_PREDICT      4  /* model prediction */
 #define RTS_K_GRAD         5  /* loss + adjoint sweep */
 #define RTS_K_GRAD_REDUCE  6  /* adjoint reductions (per antenna / source / loss) */
-#define RTS_K_CLASSES      8
+#define RTS_K_BLOCK_PASS   7  /* blocked peel: subtract block b + average block b+1 */
+#define RTS_K_BLOCK_FIX    8  /* blocked peel: in-block closed-form corrections, model matrices */
+#define RTS_K_CLASSES     10
 /* enable != 0: clear the counters and start bracketing every kernel (group)
  * with CUDA events on its stream; enable == 0: stop recording.  Launch
  * counts are always kept. */

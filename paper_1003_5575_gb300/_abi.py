@@ -21,8 +21,11 @@ RTS_PREC_MIXED = 0
 RTS_PREC_FP64 = 1
 
 RTS_K_AVERAGE, RTS_K_SUB_AVERAGE, RTS_K_SUBTRACT, RTS_K_SOLVE = 0, 1, 2, 3
-RTS_K_PREDICT, RTS_K_GRAD, RTS_K_GRAD_REDUCE, RTS_K_CLASSES = 4, 5, 6, 8
-KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "grad", "grad_reduce")
+RTS_K_PREDICT, RTS_K_GRAD, RTS_K_GRAD_REDUCE, RTS_K_BLOCK_PASS, RTS_K_BLOCK_FIX = 4, 5, 6, 7, 8
+RTS_K_CLASSES = 10
+RTS_BLOCK = 64
+KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "grad", "grad_reduce",
+                  "block_pass", "block_fix")
 
 EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_cadence_host",
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad",
@@ -36,7 +39,8 @@ class rts_peel_config(ctypes.Structure):
                 ("n_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_sources", ctypes.c_int32),
                 ("uvw", ctypes.POINTER(ctypes.c_double)),
-                ("freq_hz", ctypes.POINTER(ctypes.c_double))]
+                ("freq_hz", ctypes.POINTER(ctypes.c_double)),
+                ("sources_per_pass", ctypes.c_int32)]
 
 
 class RtsError(RuntimeError):

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "als_kernels.cuh"
+#include "block_kernels.cuh"
 #include "common.cuh"
 #include "grad_kernels.cuh"
 #include "predict_kernels.cuh"
@@ -20,6 +21,7 @@ using namespace rts;
 
 struct rts_peel_t {
   int n_ant = 0, n_chan = 0, n_time = 0, n_iter = 0, precision = 0, max_sources = 0;
+  int per_pass = 1;                // sources per streaming pass (1 or RTS_BLOCK)
   int64_t n_bl = 0;
   double nu0 = 0, dnu = 0;
   int device = 0;
@@ -38,6 +40,11 @@ struct rts_peel_t {
   double* d_src = nullptr;         // [max_sources][3]
   void* d_jones_stage = nullptr;   // [max_sources][n_ant][4] cube precision (host-buffer calls)
   GradWorkspace grad;
+  // blocked peel workspace (allocated on the first blocked cadence)
+  PhaseAB* b_ph[2] = {nullptr, nullptr};  // [n_bl][n_time][BK] phases of a block
+  float2* b_avg = nullptr;         // [BK][n_bl][4] plain averages of a block
+  float2* b_model = nullptr;       // [BK][n_bl][4] model matrices of a block
+  float2* b_dir = nullptr;         // [n_bl][BK(BK-1)/2] in-block closed-form averages D_jk
   // tracing: CUDA events around kernel groups, launch counters
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -177,6 +184,135 @@ int read_status(rts_peel_t* h, int32_t n, int32_t* h_status, cudaStream_t s) {
   return RTS_OK;
 }
 
+size_t block_pass_smem(const rts_peel_t* h) {
+  return (size_t)h->n_chan * 2 * sizeof(float4) + (size_t)2 * h->n_time * h->per_pass * sizeof(PhaseAB);
+}
+
+template <int BK>
+int set_block_smem(rts_peel_t* h, int smem) {
+  RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass<BK, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass<BK, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass<BK, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return RTS_OK;
+}
+
+int ensure_block_workspace(rts_peel_t* h) {
+  if (h->b_avg) return RTS_OK;
+  const int BK = h->per_pass;
+  const size_t n_ph = (size_t)h->n_bl * h->n_time * BK;
+  struct { void** p; size_t bytes; } allocs[] = {
+      {(void**)&h->b_ph[0], n_ph * sizeof(PhaseAB)},
+      {(void**)&h->b_ph[1], n_ph * sizeof(PhaseAB)},
+      {(void**)&h->b_avg, (size_t)BK * h->n_bl * 4 * sizeof(float2)},
+      {(void**)&h->b_model, (size_t)BK * h->n_bl * 4 * sizeof(float2)},
+      {(void**)&h->b_dir, (size_t)h->n_bl * (BK * (BK - 1) / 2) * sizeof(float2)},
+  };
+  for (auto& a : allocs)
+    RTS_CUDA(h, cudaMalloc(a.p, a.bytes));
+  const int smem = (int)block_pass_smem(h);
+  switch (BK) {
+    case 8: return set_block_smem<8>(h, smem);
+    case 16: return set_block_smem<16>(h, smem);
+    case 32: return set_block_smem<32>(h, smem);
+    default: return set_block_smem<64>(h, smem);
+  }
+}
+
+template <int BK>
+void block_pass_t(bool sub, bool acc, const BlockPassArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  if (sub && acc) k_block_pass<BK, true, true><<<grid, kBlkThreads, smem, s>>>(a);
+  else if (sub) k_block_pass<BK, true, false><<<grid, kBlkThreads, smem, s>>>(a);
+  else k_block_pass<BK, false, true><<<grid, kBlkThreads, smem, s>>>(a);
+}
+
+int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a, cudaStream_t s) {
+  Span span(h, RTS_K_BLOCK_PASS, s);
+  const size_t smem = block_pass_smem(h);
+  const unsigned grid = (unsigned)h->n_bl;
+  switch (h->per_pass) {
+    case 8: block_pass_t<8>(sub, acc, a, grid, smem, s); break;
+    case 16: block_pass_t<16>(sub, acc, a, grid, smem, s); break;
+    case 32: block_pass_t<32>(sub, acc, a, grid, smem, s); break;
+    default: block_pass_t<64>(sub, acc, a, grid, smem, s); break;
+  }
+  span.end(1);
+  return check_launch(h, "block pass launch");
+}
+
+void launch_dirichlet(rts_peel_t* h, const PhaseAB* ph, int nblk, cudaStream_t s) {
+  const unsigned grid = (unsigned)h->n_bl;
+  switch (h->per_pass) {
+    case 8: k_block_dirichlet<8><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
+    case 16: k_block_dirichlet<16><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
+    case 32: k_block_dirichlet<32><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
+    default: k_block_dirichlet<64><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
+  }
+}
+
+// The blocked cadence: one HBM pass per block of BK sources (see block_kernels.cuh).
+int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
+                 const double* h_src, void* d_jones, int32_t* h_status, cudaStream_t s) {
+  int rc = ensure_block_workspace(h);
+  if (rc) return rc;
+  const int BK = h->per_pass, n_pairs = BK * (BK - 1) / 2;
+  RTS_CUDA(h, cudaMemcpyAsync(h->d_src, h_src, sizeof(double) * 3 * n_src, cudaMemcpyHostToDevice, s));
+  const size_t jstride = (size_t)h->n_ant * 4 * h->elem;
+  const unsigned bl_grid = (unsigned)((h->n_bl + 255) / 256);
+  const int nb = (n_src + BK - 1) / BK;
+  BlockPassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.uvw = h->d_uvw; a.bl_ant = h->d_bl_ant;
+  a.n_ant = h->n_ant; a.n_chan = h->n_chan; a.n_time = h->n_time; a.n_bl = h->n_bl;
+  a.nu0_c = h->nu0 / kCLight; a.dnu_c = h->dnu / kCLight;
+  a.inv_n = 1.0 / ((double)h->n_time * h->n_chan);
+  a.M_sub = h->b_model; a.avg = h->b_avg;
+  // first pass: plain averages of block 0 from the input
+  a.src = static_cast<const float4*>(d_vis);
+  a.n_acc = std::min(BK, (int)n_src); a.src_acc = h->d_src; a.ph_acc = h->b_ph[0];
+  rc = launch_block_pass(h, false, true, a, s);
+  if (rc) return rc;
+  for (int b = 0; b < nb; ++b) {
+    const int s0 = b * BK, nblk = std::min(BK, (int)n_src - s0);
+    {
+      Span span(h, RTS_K_BLOCK_FIX, s);
+      if (nblk > 1) launch_dirichlet(h, h->b_ph[b & 1], nblk, s);
+      span.end(nblk > 1 ? 1 : 0);
+    }
+    for (int q = 0; q < nblk; ++q) {
+      const int k = s0 + q;
+      {
+        Span span(h, RTS_K_BLOCK_FIX, s);
+        if (q > 0)
+          k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (k - 1) + 2], h->d_bl_ant, h->n_bl,
+                                                 h->b_model + (size_t)(q - 1) * h->n_bl * 4);
+        k_block_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, h->b_dir, n_pairs, h->n_bl,
+                                                static_cast<float2*>(h->d_avg));
+        span.end(q > 0 ? 2 : 1);
+      }
+      rc = launch_als(h, h->d_avg, h_src[3 * k + 2], static_cast<char*>(d_jones) + k * jstride, k, s);
+      if (rc) return rc;
+    }
+    {
+      Span span(h, RTS_K_BLOCK_FIX, s);
+      k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (s0 + nblk - 1) + 2], h->d_bl_ant,
+                                             h->n_bl, h->b_model + (size_t)(nblk - 1) * h->n_bl * 4);
+      span.end(1);
+    }
+    // subtract block b (input -> residual on the first block), average block b+1
+    const bool more = b + 1 < nb;
+    a.src = static_cast<const float4*>(b == 0 ? d_vis : d_resid);
+    a.dst = static_cast<float4*>(d_resid);
+    a.n_sub = nblk; a.ph_sub = h->b_ph[b & 1];
+    a.n_acc = more ? std::min(BK, (int)n_src - s0 - BK) : 0;
+    a.src_acc = h->d_src + 3 * (size_t)(s0 + BK);
+    a.ph_acc = h->b_ph[(b + 1) & 1];
+    rc = launch_block_pass(h, true, more, a, s);
+    if (rc) return rc;
+  }
+  if (h_status) return read_status(h, n_src, h_status, s);
+  return RTS_OK;
+}
+
 int peel_device(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
                 const double* h_src, void* d_jones, int32_t* h_status, cudaStream_t s) {
   const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
@@ -184,6 +320,7 @@ int peel_device(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
     if (d_resid != d_vis) RTS_CUDA(h, cudaMemcpyAsync(d_resid, d_vis, cube, cudaMemcpyDeviceToDevice, s));
     return RTS_OK;
   }
+  if (h->per_pass > 1) return peel_blocked(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, s);
   const size_t jstride = (size_t)h->n_ant * 4 * h->elem;
   StreamArgs a = stream_args(h, d_vis, d_resid, h->d_avg);
   a.acc = make_dir(h_src[0], h_src[1], h_src[2]);
@@ -237,7 +374,17 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
       return fail(nullptr, RTS_EINVAL, "channels must be uniformly spaced (nu_c = nu_0 + c dnu)");
   }
 
+  int per_pass = cfg->sources_per_pass;
+  if (per_pass == 0) per_pass = cfg->precision == RTS_PREC_MIXED ? RTS_BLOCK : 1;
+  if (per_pass != 1 && per_pass != 8 && per_pass != 16 && per_pass != 32 && per_pass != 64)
+    return fail(nullptr, RTS_EINVAL, "sources_per_pass must be 0, 1, 8, 16, 32 or 64");
+  if (per_pass > 1 && cfg->precision != RTS_PREC_MIXED)
+    return fail(nullptr, RTS_EINVAL, "the blocked peel (sources_per_pass = RTS_BLOCK) is RTS_PREC_MIXED only");
+  if (per_pass > 1 && (size_t)cfg->n_chan * 32 + (size_t)cfg->n_time * 32 * per_pass > 200 * 1024)
+    return fail(nullptr, RTS_EINVAL, "the blocked peel needs n_chan*32 + n_time*2048 <= 200 KB of shared memory");
+
   rts_peel_t* h = new rts_peel_t();
+  h->per_pass = per_pass;
   h->n_ant = cfg->n_ant; h->n_chan = cfg->n_chan; h->n_time = cfg->n_time;
   h->n_iter = cfg->n_iter; h->precision = cfg->precision; h->max_sources = cfg->max_sources;
   h->n_bl = n_bl; h->nu0 = nu0; h->dnu = dnu;
@@ -473,7 +620,8 @@ void rts_peel_destroy(rts_peel_t* h) {
   int prev = -1;
   if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
   void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
-                  h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage};
+                  h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage,
+                  h->b_ph[0], h->b_ph[1], h->b_avg, h->b_model, h->b_dir};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   grad_free(h->grad);

@@ -37,7 +37,7 @@ class Peeler:
     """One array configuration (antennas, channels, times) on the current CUDA device."""
 
     def __init__(self, uvw, freq_hz, n_iter: int = 20, precision: str = "mixed",
-                 max_sources: int = 1024):
+                 max_sources: int = 1024, sources_per_pass: int = 0):
         uvw = _host_f64(uvw)
         freq = _host_f64(freq_hz)
         if uvw.ndim != 3 or uvw.shape[2] != 3:
@@ -56,6 +56,8 @@ class Peeler:
         cfg.max_sources = self.max_sources
         cfg.uvw = uvw.ctypes.data_as(_dp)
         cfg.freq_hz = freq.ctypes.data_as(_dp)
+        cfg.sources_per_pass = int(sources_per_pass)
+        self.sources_per_pass = int(sources_per_pass)
         self._keep = (uvw, freq)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.h = _abi.rts_peel_init(cfg)
@@ -188,10 +190,12 @@ class PeelLoss(torch.autograd.Function):
         return None, None, g * gJ, g * gs
 
 
-def peel(vis: torch.Tensor, uvw, freq_hz, sources, n_iter: int = 20, precision: str = "mixed"):
+def peel(vis: torch.Tensor, uvw, freq_hz, sources, n_iter: int = 20, precision: str = "mixed",
+         sources_per_pass: int = 0):
     """One-shot peel of a cuda cube; returns (resid, jones, status)."""
     p = Peeler(uvw, freq_hz, n_iter=n_iter, precision=precision,
-               max_sources=max(1, len(_host_f64(sources).reshape(-1, 3))))
+               max_sources=max(1, len(_host_f64(sources).reshape(-1, 3))),
+               sources_per_pass=sources_per_pass)
     try:
         return p.cadence(vis, sources)
     finally:

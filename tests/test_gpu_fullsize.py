@@ -102,14 +102,18 @@ def test_fullsize_single_source_recovered_exactly(full):
     del one, resid
 
 
-def test_fullsize_peel_residual_plus_model_is_input(full):
+@pytest.mark.parametrize("per_pass", [1, 16, 64], ids=["one-source-per-pass", "blocks-of-16", "blocks-of-64"])
+def test_fullsize_peel_residual_plus_model_is_input(full, per_pass):
     """1000 sources: residual + prediction of the solved sources = input.
 
     The residual is stored in FP32 after each of the 1000 sequential
     subtractions, so its rounding error is a random walk of ~4000 steps of
     half an ulp of |R|: the rms deviation must stay <= 1e-5 x rms (the stated
     tolerance), and the extreme over 6.4e9 components <= 1e-4 x rms."""
-    cad, p, vis, J = full
+    from paper_1003_5575_gb300 import Peeler
+    cad, p0, vis, J = full
+    p = Peeler(cad.uvw(), cad.freqs(), n_iter=20, precision="mixed", max_sources=cad.n_src,
+               sources_per_pass=per_pass)
     resid, jones, st = p.cadence(vis, cad.sources())
     assert set(np.unique(st).tolist()) <= {0, 1}
     model = p.predict(cad.sources(), jones)
@@ -126,3 +130,4 @@ def test_fullsize_peel_residual_plus_model_is_input(full):
     assert worst <= 10 * TOL * rms
     assert rms_of(resid) < rms_of(vis)
     del resid, model
+    p.close()
