@@ -23,6 +23,12 @@ constexpr int kBlkPairsMax = kBlkMax * (kBlkMax - 1) / 2;
 
 struct __align__(16) PhaseAB { unsigned long long a, b; };   // Q0.64 A (channel 0) and B (step)
 
+// Per (baseline, time, source) trigonometry for the closed-form D_jk, with B
+// taken as its signed value (|B| < 1/2):
+//   u = exp(2 pi i P), P = A + (N-1) B / 2 (band-centre phase)
+//   (sn, cn) = (sin, cos)(pi N B)
+struct __align__(16) GeoTrig { float2 u; float sn, cn; };
+
 struct BlockPassArgs {
   const float4* src;        // cube read (input or residual)
   float4* dst;              // residual written (may equal src); unused when n_sub == 0
@@ -35,8 +41,7 @@ struct BlockPassArgs {
   const float2* M_sub;      // [BK][n_bl][4] their model matrices S J_i J_j^H
   const PhaseAB* ph_sub;    // [n_bl][n_time][BK] their phases (written by the previous pass)
   int n_acc;                // sources averaged in this pass (block b+1), 0..BK
-  const double* src_acc;    // device [n_acc][3] (l, m, S)
-  PhaseAB* ph_acc;          // [n_bl][n_time][BK] their phases (written here)
+  const PhaseAB* ph_acc;    // [n_bl][n_time][BK] their phases (precomputed)
   float2* avg;              // [BK][n_bl][4] plain averages of R_s in their directions
   double inv_n;
 };
@@ -44,11 +49,26 @@ struct BlockPassArgs {
 // exp(+2 pi i phi) from a Q0.64 phase, using its high word (truncation error
 // below 2^-32 turns)
 __device__ inline float2 phasor_hw(unsigned long long ph) {
-  return phasor_f((float)(int)(ph >> 32) * kTwoM32F);
+  constexpr float kRadPerUnit = kTwoM32F * kTwoPiF;      // 2 pi / 2^32
+  float s, c;
+  __sincosf((float)(int)(ph >> 32) * kRadPerUnit, &s, &c);
+  return make_float2(c, s);
+}
+
+// exp(2 pi i x) for a Q0.64 phase x: the top 24 bits through sincospif, the
+// remaining bits (|r| < 2^-25 turns) by the first-order rotation 1 + 2 pi i r
+__device__ inline float2 phasor_q64_fine(unsigned long long x) {
+  const long long sx = (long long)x;
+  const float hi = __ll2float_rn(sx) * 5.42101086242752217e-20f;          // 2^-64
+  const long long back = __float2ll_rn(hi * 1.8446744073709551616e19f);   // exact
+  const float lo = (float)(sx - back) * 5.42101086242752217e-20f;
+  float sn, cs;
+  sincospif(2.0f * hi, &sn, &cs);
+  const float w = 6.28318530717958647692f * lo;
+  return make_float2(cs - sn * w, sn + cs * w);
 }
 
 constexpr int kSubCh = 3;     // channels a thread keeps in registers while subtracting
-
 template <int BK, bool SUB, bool ACC>
 __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) {
   constexpr int kHalf = BK / 2;                   // averaging: two sources per thread
@@ -57,17 +77,18 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
   float4* sR = reinterpret_cast<float4*>(b_smem);                       // [n_chan][2]
   PhaseAB* sPs = reinterpret_cast<PhaseAB*>(sR + (size_t)a.n_chan * 2);  // [n_time][BK]
   PhaseAB* sPa = sPs + (size_t)a.n_time * BK;                            // [n_time][BK]
-  __shared__ float4 sM[BK][2];
+  __shared__ float2 sM[BK][4];       // model matrix entries (re, im)
+  __shared__ float2 sMs[BK][4];      // the same with re and im swapped
   __shared__ double sRed[kSplits][BK][8];
 
   const int64_t bl = blockIdx.x;
-  const int2 ij = a.bl_ant[bl];
   const int tid = threadIdx.x;
   if (SUB) {
-    const float4* Mg = reinterpret_cast<const float4*>(a.M_sub);
-    for (int q = tid; q < a.n_sub * 2; q += kBlkThreads) {
-      const int k = q >> 1, h = q & 1;
-      sM[k][h] = Mg[((size_t)k * a.n_bl + bl) * 2 + h];
+    for (int q = tid; q < a.n_sub * 4; q += kBlkThreads) {
+      const int k = q >> 2, e = q & 3;
+      const float2 m = a.M_sub[((size_t)k * a.n_bl + bl) * 4 + e];
+      sM[k][e] = m;
+      sMs[k][e] = make_float2(m.y, m.x);
     }
     for (int q = tid; q < a.n_time * a.n_sub; q += kBlkThreads) {
       const int t = q / a.n_sub, k = q - t * a.n_sub;
@@ -77,16 +98,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
   if (ACC) {
     for (int q = tid; q < a.n_time * a.n_acc; q += kBlkThreads) {
       const int t = q / a.n_acc, k = q - t * a.n_acc;
-      SrcDir d;
-      d.l = a.src_acc[3 * k]; d.m = a.src_acc[3 * k + 1]; d.S = a.src_acc[3 * k + 2];
-      const double r2 = d.l * d.l + d.m * d.m;
-      d.nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
-      const double tau = delay_m(a.uvw, a.n_ant, t, ij.x, ij.y, d);
-      PhaseAB p;
-      p.a = frac_q64(tau * a.nu0_c);
-      p.b = frac_q64(tau * a.dnu_c);
-      sPa[t * BK + k] = p;
-      a.ph_acc[((size_t)bl * a.n_time + t) * BK + k] = p;
+      sPa[t * BK + k] = a.ph_acc[((size_t)bl * a.n_time + t) * BK + k];
     }
   }
   // averaging role: sources k0 = tid % kHalf and k0 + kHalf over channels [c_beg, c_end)
@@ -104,32 +116,46 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
     for (int q = tid; q < a.n_chan * 2; q += kBlkThreads) sR[q] = __ldcs(a.src + base + q);
     __syncthreads();
     if (SUB) {
-      // channels c0, c0 + 256, c0 + 512 in registers; sources in the inner loop
+      // channels c0, c0 + 256, c0 + 512 in registers; sources in the inner loop.
+      // x_e -= M_e conj(ph) as two packed FMAs per entry:
+      //   x_e += M_e * (-pr, -pr);  x_e += swap(M_e) * (-pi, +pi)
       for (int c0 = tid; c0 < a.n_chan; c0 += kBlkThreads * kSubCh) {
-        float4 x0[kSubCh], x1[kSubCh];
+        float2 x[kSubCh][4];
         #pragma unroll
         for (int u = 0; u < kSubCh; ++u) {
           const int c = c0 + u * kBlkThreads;
-          if (c < a.n_chan) { x0[u] = sR[2 * c]; x1[u] = sR[2 * c + 1]; }
+          if (c < a.n_chan) {
+            const float4 v0 = sR[2 * c], v1 = sR[2 * c + 1];
+            x[u][0] = make_float2(v0.x, v0.y); x[u][1] = make_float2(v0.z, v0.w);
+            x[u][2] = make_float2(v1.x, v1.y); x[u][3] = make_float2(v1.z, v1.w);
+          }
         }
         for (int j = 0; j < a.n_sub; ++j) {
           const PhaseAB p = sPs[t * BK + j];
-          const float4 m01 = sM[j][0], m23 = sM[j][1];
-          const float2 M[4] = {make_float2(m01.x, m01.y), make_float2(m01.z, m01.w),
-                               make_float2(m23.x, m23.y), make_float2(m23.z, m23.w)};
+          float2 M[4], Ms[4];
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) { M[e] = sM[j][e]; Ms[e] = sMs[j][e]; }
           unsigned long long phase = p.a + (unsigned long long)c0 * p.b;
           const unsigned long long dstep = p.b * (unsigned long long)kBlkThreads;
           #pragma unroll
-          for (int u = 0; u < kSubCh; ++u, phase += dstep)
-            if (c0 + u * kBlkThreads < a.n_chan) sub_model(x0[u], x1[u], M, phasor_hw(phase));
+          for (int u = 0; u < kSubCh; ++u, phase += dstep) {
+            if (c0 + u * kBlkThreads < a.n_chan) {
+              const float2 ph = phasor_hw(phase);
+              const float2 nr = make_float2(-ph.x, -ph.x), si = make_float2(-ph.y, ph.y);
+              #pragma unroll
+              for (int e = 0; e < 4; ++e) x[u][e] = ffma2(Ms[e], si, ffma2(M[e], nr, x[u][e]));
+            }
+          }
         }
         #pragma unroll
         for (int u = 0; u < kSubCh; ++u) {
           const int c = c0 + u * kBlkThreads;
           if (c < a.n_chan) {
-            sR[2 * c] = x0[u]; sR[2 * c + 1] = x1[u];
-            __stcs(a.dst + base + 2 * c, x0[u]);
-            __stcs(a.dst + base + 2 * c + 1, x1[u]);
+            const float4 v0 = make_float4(x[u][0].x, x[u][0].y, x[u][1].x, x[u][1].y);
+            const float4 v1 = make_float4(x[u][2].x, x[u][2].y, x[u][3].x, x[u][3].y);
+            sR[2 * c] = v0; sR[2 * c + 1] = v1;
+            __stcs(a.dst + base + 2 * c, v0);
+            __stcs(a.dst + base + 2 * c + 1, v1);
           }
         }
       }
@@ -137,21 +163,37 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
     }
     if (ACC && has0 && c_beg < c_end) {
       // exact fixed-point phase per channel (a recurrence ph *= exp(2 pi i B) would
-      // carry the step's rounding coherently across channels)
+      // carry the step's rounding coherently across channels).  Packed sums
+      // P_e = sum x_e pr and Q_e = sum x_e pi give  acc_e = (P.x - Q.y, P.y + Q.x).
       const PhaseAB p0 = sPa[t * BK + k0];
       const PhaseAB p1 = has1 ? sPa[t * BK + k0 + kHalf] : p0;
-      float acc0[8], acc1[8];
+      float2 P0[4], Q0[4], P1[4], Q1[4];
       #pragma unroll
-      for (int e = 0; e < 8; ++e) { acc0[e] = 0.f; acc1[e] = 0.f; }
+      for (int e = 0; e < 4; ++e) {
+        P0[e] = make_float2(0.f, 0.f); Q0[e] = P0[e]; P1[e] = P0[e]; Q1[e] = P0[e];
+      }
       unsigned long long ph0 = p0.a + (unsigned long long)c_beg * p0.b;
       unsigned long long ph1 = p1.a + (unsigned long long)c_beg * p1.b;
       for (int c = c_beg; c < c_end; ++c, ph0 += p0.b, ph1 += p1.b) {
-        const float4 r0 = sR[2 * c], r1 = sR[2 * c + 1];
-        acc_rot(acc0, r0, r1, phasor_hw(ph0));
-        acc_rot(acc1, r0, r1, phasor_hw(ph1));
+        const float4 v0 = sR[2 * c], v1 = sR[2 * c + 1];
+        const float2 xs[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
+                              make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
+        const float2 e0 = phasor_hw(ph0), e1 = phasor_hw(ph1);
+        const float2 r0 = make_float2(e0.x, e0.x), i0 = make_float2(e0.y, e0.y);
+        const float2 r1 = make_float2(e1.x, e1.x), i1 = make_float2(e1.y, e1.y);
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          P0[e] = ffma2(xs[e], r0, P0[e]); Q0[e] = ffma2(xs[e], i0, Q0[e]);
+          P1[e] = ffma2(xs[e], r1, P1[e]); Q1[e] = ffma2(xs[e], i1, Q1[e]);
+        }
       }
       #pragma unroll
-      for (int e = 0; e < 8; ++e) { accd[e] += (double)acc0[e]; accd[8 + e] += (double)acc1[e]; }
+      for (int e = 0; e < 4; ++e) {
+        accd[2 * e] += (double)(P0[e].x - Q0[e].y);
+        accd[2 * e + 1] += (double)(P0[e].y + Q0[e].x);
+        accd[8 + 2 * e] += (double)(P1[e].x - Q1[e].y);
+        accd[8 + 2 * e + 1] += (double)(P1[e].y + Q1[e].x);
+      }
     }
   }
   if (ACC) {
@@ -186,46 +228,73 @@ __device__ inline unsigned long long pair_mid_phase(unsigned long long dA, long 
   return dA + ((hi << 63) | (lo >> 1));                                           // 128-bit value / 2
 }
 
-// sin(pi N x) / (N sin(pi x)) for x = dB (signed Q0.64 turns, |x| < 1/2); 1 at x = 0
-__device__ inline float dirichlet_ratio(long long x, int n_chan) {
-  if (x == 0) return 1.0f;
-  const float xf = (float)x * 5.42101086242752217e-20f;            // 2^-64
-  const float s1 = sinpif(xf);
-  // N x = hi * 2^64 + lo (two's complement).  With g = lo as a signed Q0.64
-  // value in [-1/2, 1/2): N x = (hi + [g < 0]) + g, so
-  // sin(pi N x) = (-1)^(hi + [g < 0]) sin(pi g), and g stays accurate in FP32.
-  const long long n = n_chan;
-  const unsigned long long lo = (unsigned long long)n * (unsigned long long)x;   // wraps mod 2^64
-  const long long hi = __mul64hi(n, x);
-  const long long g = (long long)lo;
-  const float gf = (float)g * 5.42101086242752217e-20f;
-  float s2 = sinpif(gf);
-  if ((hi + (g < 0 ? 1 : 0)) & 1) s2 = -s2;
-  return s2 / ((float)n_chan * s1);
-}
-
-// exp(2 pi i x) for a Q0.64 phase x: the top 24 bits through sincospif, the
-// remaining bits (|r| < 2^-25 turns) by the first-order rotation 1 + 2 pi i r
-__device__ inline float2 phasor_q64_fine(unsigned long long x) {
-  const long long sx = (long long)x;
-  const float hi = __ll2float_rn(sx) * 5.42101086242752217e-20f;          // 2^-64
-  const long long back = __float2ll_rn(hi * 1.8446744073709551616e19f);   // exact
-  const float lo = (float)(sx - back) * 5.42101086242752217e-20f;
-  float sn, cs;
-  sincospif(2.0f * hi, &sn, &cs);
-  const float w = 6.28318530717958647692f * lo;
-  return make_float2(cs - sn * w, sn + cs * w);
-}
+// ---------------------------------------------------------------------------
+// geometry of one block (no visibility data): Q0.64 phases of its sources,
+//   ph[bl][t][k] = (frac(tau nu_0 / c), frac(tau dnu / c))
 
 template <int BK>
-__global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restrict__ ph, int n_blk,
+__global__ void __launch_bounds__(256) k_block_phases(const double* __restrict__ src, int n_blk,
+                                                     const double* __restrict__ uvw,
+                                                     const int2* __restrict__ bl_ant, int n_ant,
+                                                     int n_time, int n_chan, int64_t n_bl, double nu0_c,
+                                                     double dnu_c, PhaseAB* __restrict__ ph,
+                                                     GeoTrig* __restrict__ trig) {
+  const int64_t n = n_bl * n_time * BK;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q % BK);
+    if (k >= n_blk) continue;
+    const int64_t r = q / BK;
+    const int t = (int)(r % n_time);
+    const int64_t bl = r / n_time;
+    const int2 ij = bl_ant[bl];
+    SrcDir d;
+    d.l = src[3 * k]; d.m = src[3 * k + 1]; d.S = src[3 * k + 2];
+    const double r2 = d.l * d.l + d.m * d.m;
+    d.nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
+    const double tau = delay_m(uvw, n_ant, t, ij.x, ij.y, d);
+    PhaseAB p;
+    p.a = frac_q64(tau * nu0_c);
+    p.b = frac_q64(tau * dnu_c);
+    ph[q] = p;
+    GeoTrig g;
+    const long long bs = (long long)p.b;                           // signed B
+    g.u = phasor_q64_fine(pair_mid_phase(p.a, bs, n_chan));
+    // pi N B: N B = hi + lo 2^-64 = (hi + [lo_s < 0]) + lo_s 2^-64 with lo_s in [-1/2, 1/2)
+    const long long nn = n_chan;
+    const unsigned long long lo = (unsigned long long)nn * (unsigned long long)bs;
+    const long long hi = __mul64hi(nn, bs);
+    const long long los = (long long)lo;
+    float sn, cn;
+    sincospif((float)los * 5.42101086242752217e-20f, &sn, &cn);
+    if ((hi + (los < 0 ? 1 : 0)) & 1) { sn = -sn; cn = -cn; }
+    g.sn = sn; g.cn = cn;
+    trig[q] = g;
+  }
+}
+
+// sin(z) / z by its Taylor series to z^12 (first omitted term z^14/15!, below
+// 5e-10 for |z| <= pi/2)
+__device__ inline float sinc_series(float z) {
+  const float z2 = z * z;
+  return 1.0f + z2 * (-1.0f / 6 + z2 * (1.0f / 120 + z2 * (-1.0f / 5040 + z2 * (1.0f / 362880
+         + z2 * (-1.0f / 39916800 + z2 * (1.0f / 6227020800.0f))))));
+}
+
+// sin(N th) / (N sin th) for |N th| <= pi/2
+__device__ inline float ratio_series(float z, float th) { return sinc_series(z) / sinc_series(th); }
+
+template <int BK>
+__global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restrict__ ph,
+                                                        const GeoTrig* __restrict__ trig, int n_blk,
                                                         float2* __restrict__ Dtab, int64_t n_bl,
                                                         int n_time, int n_chan) {
   constexpr int kPairs = BK * (BK - 1) / 2;
   constexpr int kU = (kPairs + 255) / 256;
-  __shared__ PhaseAB sP[16][BK];               // times handled in chunks of 16
+  __shared__ GeoTrig sG[16][BK];               // times handled in chunks of 16
+  __shared__ unsigned long long sB[16][BK];
   const int64_t bl = blockIdx.x;
   const int n_pairs = n_blk * (n_blk - 1) / 2;
+  const float fN = (float)n_chan;
   int pj[kU], pk[kU];
   float dre[kU], dim[kU];
   #pragma unroll
@@ -242,7 +311,9 @@ __global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restri
     __syncthreads();
     for (int q = threadIdx.x; q < nt * n_blk; q += blockDim.x) {
       const int t = q / n_blk, k = q - t * n_blk;
-      sP[t][k] = ph[((size_t)bl * n_time + t0 + t) * BK + k];
+      const size_t at = ((size_t)bl * n_time + t0 + t) * BK + k;
+      sG[t][k] = trig[at];
+      sB[t][k] = ph[at].b;
     }
     __syncthreads();
     #pragma unroll
@@ -250,12 +321,32 @@ __global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restri
       if (threadIdx.x + 256 * u < n_pairs) {
         const int j = pj[u], k = pk[u];
         for (int t = 0; t < nt; ++t) {
-          const long long dB = (long long)(sP[t][k].b - sP[t][j].b);
-          const unsigned long long mid = pair_mid_phase(sP[t][k].a - sP[t][j].a, dB, n_chan);
-          const float r = dirichlet_ratio(dB, n_chan);
-          const float2 e = phasor_q64_fine(mid);
-          dre[u] += r * e.x;
-          dim[u] += r * e.y;
+          const GeoTrig gk = sG[t][k], gj = sG[t][j];
+          // band-centre phase difference: u_k conj(u_j)
+          const float er = gk.u.x * gj.u.x + gk.u.y * gj.u.y;
+          const float ei = gk.u.y * gj.u.x - gk.u.x * gj.u.y;
+          // ratio sin(pi N x) / (N sin(pi x)) at x = B_k - B_j (signed values)
+          const long long dBw = (long long)(sB[t][k] - sB[t][j]);
+          const float xw = (float)dBw * 5.42101086242752217e-20f;
+          const float xs = (float)(long long)sB[t][k] * 5.42101086242752217e-20f -
+                           (float)(long long)sB[t][j] * 5.42101086242752217e-20f;
+          // near pairs (|N x| < 1/2): series in the exact x; others: the numerator
+          // by angle difference, the denominator N sin(pi x) from the exact x (an
+          // angle difference there would cancel).  When the signed difference
+          // wraps (|x| >= 1/2), sin(pi x) = -sin(pi x_wrapped).
+          const bool wrap = fabsf(xs) >= 0.5f;
+          const float th = 3.14159265358979f * xw;
+          float r;
+          if (!wrap && fabsf(fN * xw) < 0.5f) {
+            r = (dBw == 0) ? 1.0f : ratio_series(fN * th, th);
+          } else {
+            const float num = gk.sn * gj.cn - gk.cn * gj.sn;
+            float den = fN * th * sinc_series(th);
+            if (wrap) den = -den;
+            r = num / den;
+          }
+          dre[u] += r * er;
+          dim[u] += r * ei;
         }
       }
     }

@@ -40,11 +40,23 @@ struct rts_peel_t {
   double* d_src = nullptr;         // [max_sources][3]
   void* d_jones_stage = nullptr;   // [max_sources][n_ant][4] cube precision (host-buffer calls)
   GradWorkspace grad;
-  // blocked peel workspace (allocated on the first blocked cadence)
-  PhaseAB* b_ph[2] = {nullptr, nullptr};  // [n_bl][n_time][BK] phases of a block
+  // blocked peel workspace (allocated on the first blocked cadence).  The phase
+  // and D_jk tables depend on geometry only; a second stream fills a ring of
+  // kRing block slots ahead of the main stream (events order the reuse).
+  static constexpr int kRing = 4;
+  PhaseAB* b_ph[kRing] = {};       // [n_bl][n_time][BK] phases of a block
+  GeoTrig* b_trig[kRing] = {};     // [n_bl][n_time][BK] trigonometry for D_jk
+  float2* b_dir[kRing] = {};       // [n_bl][BK(BK-1)/2] in-block closed-form averages D_jk
   float2* b_avg = nullptr;         // [BK][n_bl][4] plain averages of a block
   float2* b_model = nullptr;       // [BK][n_bl][4] model matrices of a block
-  float2* b_dir = nullptr;         // [n_bl][BK(BK-1)/2] in-block closed-form averages D_jk
+  cudaStream_t b_main = nullptr;   // high-priority stream for passes, corrections and solves
+  cudaStream_t b_prep = nullptr;   // low-priority geometry stream
+  cudaEvent_t b_ev_in = nullptr;   // caller's stream -> main
+  cudaEvent_t b_ev_out = nullptr;  // main -> caller's stream
+  cudaEvent_t b_ev_src = nullptr;  // source list uploaded (main -> prep)
+  cudaEvent_t b_ev_ready[kRing] = {};   // slot filled (prep -> main)
+  cudaEvent_t b_ev_free[kRing] = {};    // slot consumed (main -> prep)
+  cudaEvent_t b_ev_done = nullptr; // prep finished (prep -> main)
   // tracing: CUDA events around kernel groups, launch counters
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -188,6 +200,32 @@ size_t block_pass_smem(const rts_peel_t* h) {
   return (size_t)h->n_chan * 2 * sizeof(float4) + (size_t)2 * h->n_time * h->per_pass * sizeof(PhaseAB);
 }
 
+// geometry of block b (phases, then D_jk) into ring slot b % kRing, on the prep stream
+void launch_block_geometry(rts_peel_t* h, int b, int n_src, cudaStream_t ps) {
+  const int BK = h->per_pass, s0 = b * BK, nblk = std::min(BK, n_src - s0);
+  const int r = b % rts_peel_t::kRing;
+  const double* src = h->d_src + 3 * (size_t)s0;
+  const unsigned g = 4 * 152;
+  const double nu0_c = h->nu0 / kCLight, dnu_c = h->dnu / kCLight;
+  const unsigned grid = (unsigned)h->n_bl;
+  PhaseAB* ph = h->b_ph[r];
+  GeoTrig* tg = h->b_trig[r];
+  float2* Dt = h->b_dir[r];
+#define RTS_GEOM(BKV)                                                                                   \
+  k_block_phases<BKV><<<g, 256, 0, ps>>>(src, nblk, h->d_uvw, h->d_bl_ant, h->n_ant, h->n_time,     \
+                                         h->n_chan, h->n_bl, nu0_c, dnu_c, ph, tg);                     \
+  if (nblk > 1)                                                                                          \
+    k_block_dirichlet<BKV><<<grid, 256, 0, ps>>>(ph, tg, nblk, Dt, h->n_bl, h->n_time, h->n_chan);
+  switch (BK) {
+    case 8: RTS_GEOM(8) break;
+    case 16: RTS_GEOM(16) break;
+    case 32: RTS_GEOM(32) break;
+    default: RTS_GEOM(64) break;
+  }
+#undef RTS_GEOM
+  h->launches[RTS_K_BLOCK_FIX] += nblk > 1 ? 2 : 1;
+}
+
 template <int BK>
 int set_block_smem(rts_peel_t* h, int smem) {
   RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass<BK, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -200,15 +238,23 @@ int ensure_block_workspace(rts_peel_t* h) {
   if (h->b_avg) return RTS_OK;
   const int BK = h->per_pass;
   const size_t n_ph = (size_t)h->n_bl * h->n_time * BK;
-  struct { void** p; size_t bytes; } allocs[] = {
-      {(void**)&h->b_ph[0], n_ph * sizeof(PhaseAB)},
-      {(void**)&h->b_ph[1], n_ph * sizeof(PhaseAB)},
-      {(void**)&h->b_avg, (size_t)BK * h->n_bl * 4 * sizeof(float2)},
-      {(void**)&h->b_model, (size_t)BK * h->n_bl * 4 * sizeof(float2)},
-      {(void**)&h->b_dir, (size_t)h->n_bl * (BK * (BK - 1) / 2) * sizeof(float2)},
-  };
-  for (auto& a : allocs)
-    RTS_CUDA(h, cudaMalloc(a.p, a.bytes));
+  for (int r = 0; r < rts_peel_t::kRing; ++r) {
+    RTS_CUDA(h, cudaMalloc((void**)&h->b_ph[r], n_ph * sizeof(PhaseAB)));
+    RTS_CUDA(h, cudaMalloc((void**)&h->b_trig[r], n_ph * sizeof(GeoTrig)));
+    RTS_CUDA(h, cudaMalloc((void**)&h->b_dir[r], (size_t)h->n_bl * (BK * (BK - 1) / 2) * sizeof(float2)));
+    RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_ready[r], cudaEventDisableTiming));
+    RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_free[r], cudaEventDisableTiming));
+  }
+  RTS_CUDA(h, cudaMalloc((void**)&h->b_avg, (size_t)BK * h->n_bl * 4 * sizeof(float2)));
+  RTS_CUDA(h, cudaMalloc((void**)&h->b_model, (size_t)BK * h->n_bl * 4 * sizeof(float2)));
+  int lo_prio = 0, hi_prio = 0;
+  RTS_CUDA(h, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+  RTS_CUDA(h, cudaStreamCreateWithPriority(&h->b_main, cudaStreamNonBlocking, hi_prio));
+  RTS_CUDA(h, cudaStreamCreateWithPriority(&h->b_prep, cudaStreamNonBlocking, lo_prio));
+  RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_in, cudaEventDisableTiming));
+  RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_out, cudaEventDisableTiming));
+  RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_src, cudaEventDisableTiming));
+  RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_done, cudaEventDisableTiming));
   const int smem = (int)block_pass_smem(h);
   switch (BK) {
     case 8: return set_block_smem<8>(h, smem);
@@ -239,45 +285,44 @@ int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a,
   return check_launch(h, "block pass launch");
 }
 
-void launch_dirichlet(rts_peel_t* h, const PhaseAB* ph, int nblk, cudaStream_t s) {
-  const unsigned grid = (unsigned)h->n_bl;
-  switch (h->per_pass) {
-    case 8: k_block_dirichlet<8><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
-    case 16: k_block_dirichlet<16><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
-    case 32: k_block_dirichlet<32><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
-    default: k_block_dirichlet<64><<<grid, 256, 0, s>>>(ph, nblk, h->b_dir, h->n_bl, h->n_time, h->n_chan); break;
-  }
-}
-
 // The blocked cadence: one HBM pass per block of BK sources (see block_kernels.cuh).
+// Main stream: passes, in-block corrections, solves.  Prep stream: the
+// geometry tables of the blocks, up to kRing blocks ahead.
 int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
                  const double* h_src, void* d_jones, int32_t* h_status, cudaStream_t s) {
   int rc = ensure_block_workspace(h);
   if (rc) return rc;
+  constexpr int R = rts_peel_t::kRing;
   const int BK = h->per_pass, n_pairs = BK * (BK - 1) / 2;
+  // work on the library's high-priority stream, ordered after the caller's stream
+  cudaStream_t user = s;
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_in, user));
+  s = h->b_main;
+  RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_in, 0));
   RTS_CUDA(h, cudaMemcpyAsync(h->d_src, h_src, sizeof(double) * 3 * n_src, cudaMemcpyHostToDevice, s));
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_src, s));
+  RTS_CUDA(h, cudaStreamWaitEvent(h->b_prep, h->b_ev_src, 0));
   const size_t jstride = (size_t)h->n_ant * 4 * h->elem;
   const unsigned bl_grid = (unsigned)((h->n_bl + 255) / 256);
   const int nb = (n_src + BK - 1) / BK;
+  for (int b = 0; b < std::min(nb, R); ++b) {
+    launch_block_geometry(h, b, n_src, h->b_prep);
+    RTS_CUDA(h, cudaEventRecord(h->b_ev_ready[b % R], h->b_prep));
+  }
   BlockPassArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.uvw = h->d_uvw; a.bl_ant = h->d_bl_ant;
   a.n_ant = h->n_ant; a.n_chan = h->n_chan; a.n_time = h->n_time; a.n_bl = h->n_bl;
-  a.nu0_c = h->nu0 / kCLight; a.dnu_c = h->dnu / kCLight;
   a.inv_n = 1.0 / ((double)h->n_time * h->n_chan);
   a.M_sub = h->b_model; a.avg = h->b_avg;
   // first pass: plain averages of block 0 from the input
+  RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_ready[0], 0));
   a.src = static_cast<const float4*>(d_vis);
-  a.n_acc = std::min(BK, (int)n_src); a.src_acc = h->d_src; a.ph_acc = h->b_ph[0];
+  a.n_acc = std::min(BK, (int)n_src); a.ph_acc = h->b_ph[0];
   rc = launch_block_pass(h, false, true, a, s);
   if (rc) return rc;
   for (int b = 0; b < nb; ++b) {
     const int s0 = b * BK, nblk = std::min(BK, (int)n_src - s0);
-    {
-      Span span(h, RTS_K_BLOCK_FIX, s);
-      if (nblk > 1) launch_dirichlet(h, h->b_ph[b & 1], nblk, s);
-      span.end(nblk > 1 ? 1 : 0);
-    }
+    const float2* Dt = h->b_dir[b % R];
     for (int q = 0; q < nblk; ++q) {
       const int k = s0 + q;
       {
@@ -285,7 +330,7 @@ int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
         if (q > 0)
           k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (k - 1) + 2], h->d_bl_ant, h->n_bl,
                                                  h->b_model + (size_t)(q - 1) * h->n_bl * 4);
-        k_block_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, h->b_dir, n_pairs, h->n_bl,
+        k_block_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, Dt, n_pairs, h->n_bl,
                                                 static_cast<float2*>(h->d_avg));
         span.end(q > 0 ? 2 : 1);
       }
@@ -300,16 +345,29 @@ int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
     }
     // subtract block b (input -> residual on the first block), average block b+1
     const bool more = b + 1 < nb;
+    if (more) RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_ready[(b + 1) % R], 0));
     a.src = static_cast<const float4*>(b == 0 ? d_vis : d_resid);
     a.dst = static_cast<float4*>(d_resid);
-    a.n_sub = nblk; a.ph_sub = h->b_ph[b & 1];
+    a.n_sub = nblk; a.ph_sub = h->b_ph[b % R];
     a.n_acc = more ? std::min(BK, (int)n_src - s0 - BK) : 0;
-    a.src_acc = h->d_src + 3 * (size_t)(s0 + BK);
-    a.ph_acc = h->b_ph[(b + 1) & 1];
+    a.ph_acc = h->b_ph[(b + 1) % R];
     rc = launch_block_pass(h, true, more, a, s);
     if (rc) return rc;
+    // slot b is free once that pass has run: the prep stream may fill it with block b + R
+    RTS_CUDA(h, cudaEventRecord(h->b_ev_free[b % R], s));
+    if (b + R < nb) {
+      RTS_CUDA(h, cudaStreamWaitEvent(h->b_prep, h->b_ev_free[b % R], 0));
+      launch_block_geometry(h, b + R, n_src, h->b_prep);
+      RTS_CUDA(h, cudaEventRecord(h->b_ev_ready[b % R], h->b_prep));
+    }
   }
-  if (h_status) return read_status(h, n_src, h_status, s);
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_done, h->b_prep));
+  RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_done, 0));
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_out, s));
+  RTS_CUDA(h, cudaStreamWaitEvent(user, h->b_ev_out, 0));
+  rc = check_launch(h, "block geometry launch");
+  if (rc) return rc;
+  if (h_status) return read_status(h, n_src, h_status, user);
   return RTS_OK;
 }
 
@@ -621,9 +679,22 @@ void rts_peel_destroy(rts_peel_t* h) {
   if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
   void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
                   h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage,
-                  h->b_ph[0], h->b_ph[1], h->b_avg, h->b_model, h->b_dir};
+                  h->b_avg, h->b_model};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int r = 0; r < rts_peel_t::kRing; ++r) {
+    if (h->b_ph[r]) cudaFree(h->b_ph[r]);
+    if (h->b_trig[r]) cudaFree(h->b_trig[r]);
+    if (h->b_dir[r]) cudaFree(h->b_dir[r]);
+    if (h->b_ev_ready[r]) cudaEventDestroy(h->b_ev_ready[r]);
+    if (h->b_ev_free[r]) cudaEventDestroy(h->b_ev_free[r]);
+  }
+  if (h->b_ev_src) cudaEventDestroy(h->b_ev_src);
+  if (h->b_ev_done) cudaEventDestroy(h->b_ev_done);
+  if (h->b_prep) cudaStreamDestroy(h->b_prep);
+  if (h->b_main) cudaStreamDestroy(h->b_main);
+  if (h->b_ev_in) cudaEventDestroy(h->b_ev_in);
+  if (h->b_ev_out) cudaEventDestroy(h->b_ev_out);
   grad_free(h->grad);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
