@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "source×visibility peel updates/s (512 ant, 768 ch); adjoint step ms vs FP64 path"
 UNIT = "updates/s"
 BYTES_PER_UPDATE = 64          # complex64 2x2 read + write per source x visibility
+FLOPS_PER_UPDATE = 32          # 2x2 complex times a complex phasor: 4 complex multiply-adds
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -111,9 +112,13 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {"k_stream_mixed<true,true>": ("common.cuh", "stream_kernels.cuh"),
+                  "k_block_pass<64,true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh")}
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("common.cuh", "stream_kernels.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_1003_5575_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -123,11 +128,16 @@ def ncu_traffic(kernel: str):
     try:
         t = json.load(open(TRAFFIC_FILE))
         e = t[kernel]
-        if e.get("source_hash") == kernel_source_hash():
+        if e.get("source_hash") == kernel_source_hash(kernel):
             return e["dram_bytes_per_launch"]
     except (OSError, KeyError, ValueError):
         pass
     return None
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -282,23 +292,40 @@ def main():
     _, _, st = p.cadence(d_vis, src, resid=d_resid, jones=d_jones, status=True)
     n_nonconv = int(np.sum(st == 1))
 
-    # roofline of the dominant kernel (subtract k + average k+1)
+    # roofline of the dominant kernel
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    ms_k3, n_k3, _ = ktimes["sub_average"]
-    per_launch_s = (ms_k3 / n_k3) / 1e3 if n_k3 else float("nan")
-    alg_bytes = cad.n_vis * BYTES_PER_UPDATE
-    achieved = alg_bytes / per_launch_s / 1e9
     shares = {k: round(v[0] / max(1e-9, sum(x[0] for x in ktimes.values())), 4) for k, v in ktimes.items()
               if v[2]}
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": ncu_traffic("k_stream_mixed<true,true>"),
-                "kernel": "k_stream_mixed<SUB,ACC> (subtract source k + rotate/average source k+1)",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": per_launch_s * 1e3,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
-                "device_time_share": shares}
-    log(f"[rank {rank}] {ms_step:.1f} ms/step, {value:.3e} updates/s, K3 {achieved:.0f} GB/s")
+    if ktimes["block_pass"][2]:
+        # blocked path: FP32-bound fused pass (subtract a block + average the next block)
+        ms_bp, n_bp, _ = ktimes["block_pass"]
+        flops = 2 * K * cad.n_vis * FLOPS_PER_UPDATE * args.steps        # every source subtracted and averaged once
+        achieved = flops / (ms_bp / 1e3) / 1e12
+        sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = fp32_peak_tflops(sm_mhz)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": ncu_traffic("k_block_pass<64,true,true>"),
+                    "kernel": "k_block_pass<64,SUB,ACC> (subtract 64 solved sources + average the next 64)",
+                    "algorithmic_flops_per_update": FLOPS_PER_UPDATE,
+                    "algorithmic_bytes_per_launch": cad.n_vis * BYTES_PER_UPDATE,
+                    "avg_launch_ms": ms_bp / n_bp,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock under load)",
+                    "device_time_share": shares}
+    else:
+        ms_k3, n_k3, _ = ktimes["sub_average"]
+        per_launch_s = (ms_k3 / n_k3) / 1e3 if n_k3 else float("nan")
+        alg_bytes = cad.n_vis * BYTES_PER_UPDATE
+        achieved = alg_bytes / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": ncu_traffic("k_stream_mixed<true,true>"),
+                    "kernel": "k_stream_mixed<SUB,ACC> (subtract source k + rotate/average source k+1)",
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "avg_launch_ms": per_launch_s * 1e3,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback",
+                    "device_time_share": shares}
+    log(f"[rank {rank}] {ms_step:.1f} ms/step, {value:.3e} updates/s, roofline {roofline['achieved']:.1f} "
+        f"{roofline['unit']} ({roofline['frac']:.2f} of {roofline['bound']} peak)")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -310,20 +337,17 @@ def main():
         "status": {"not_converged": n_nonconv, "sources": K},
     }
 
-    # ---- end to end through the host-buffer C-ABI call ---------------------
+    # ---- end to end through the pipelined host-buffer C-ABI calls -----------
     if not args.no_e2e:
+        import ctypes
         cube_bytes = cad.n_vis * 32
         h_in = _abi.rts_host_alloc(cube_bytes)
-        h_out = _abi.rts_host_alloc(cube_bytes)
+        h_out = [_abi.rts_host_alloc(cube_bytes), _abi.rts_host_alloc(cube_bytes)]
         try:
-            import ctypes
             arr = np.ctypeslib.as_array((ctypes.c_float * (cad.n_vis * 8)).from_address(h_in))
             torch.from_numpy(arr).copy_(d_vis.view(torch.float32).reshape(-1))
-            h_vis = torch.from_numpy(arr).view(torch.complex64).view(p.cube_shape)
-            arr_o = np.ctypeslib.as_array((ctypes.c_float * (cad.n_vis * 8)).from_address(h_out))
-            h_res = torch.from_numpy(arr_o).view(torch.complex64).view(p.cube_shape)
-            p.cadence_host(h_vis, src, d_work=d_resid, h_resid=h_res)
             # raw copy bandwidth of the same buffers (context for the e2e number)
+            arr_o = np.ctypeslib.as_array((ctypes.c_float * (cad.n_vis * 8)).from_address(h_out[0]))
             e_a, e_b, e_c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e_a.record(stream)
             d_resid.view(torch.float32).reshape(-1).copy_(torch.from_numpy(arr), non_blocking=True)
@@ -333,24 +357,41 @@ def main():
             torch.cuda.synchronize()
             h2d_gbs = cube_bytes / (e_a.elapsed_time(e_b) / 1e3) / 1e9
             d2h_gbs = cube_bytes / (e_b.elapsed_time(e_c) / 1e3) / 1e9
-            n_e2e = max(1, min(args.steps, 2))
+            src_c = np.ascontiguousarray(src, dtype=np.float64)
+            h_jones = [np.zeros((K, cad.n_ant, 4), np.complex64) for _ in range(2)]
+            h_st = [np.zeros(K, np.int32) for _ in range(2)]
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+
+            def submit(i):
+                _abi.rts_peel_pipeline_submit(p.h, ctypes.c_void_p(h_in), ctypes.c_void_p(h_out[i % 2]), K,
+                                              src_c.ctypes.data_as(dp),
+                                              ctypes.c_void_p(h_jones[i % 2].ctypes.data),
+                                              h_st[i % 2].ctypes.data_as(ip))
+            submit(0)
+            _abi.rts_peel_pipeline_wait(p.h)
+            n_e2e = max(2, args.steps)
             barrier()
             t0 = time.perf_counter()
-            for _ in range(n_e2e):
-                p.cadence_host(h_vis, src, d_work=d_resid, h_resid=h_res)
+            for i in range(n_e2e):
+                submit(i)
+            _abi.rts_peel_pipeline_wait(p.h)
             dt = max_over_ranks((time.perf_counter() - t0) / n_e2e)
             line["e2e"] = {"value": world * updates_per_step / dt, "unit": UNIT,
                            "h2d_bytes_per_step": cube_bytes + K * 24,
                            "d2h_bytes_per_step": cube_bytes + K * cad.n_ant * 32 + K * 4,
                            "ms_per_step": dt * 1e3, "steps": n_e2e,
                            "h2d_GBps": h2d_gbs, "d2h_GBps": d2h_gbs,
-                           "api": "rts_peel_cadence_host (pinned host buffers from rts_host_alloc)"}
+                           "api": ("rts_peel_pipeline_submit / rts_peel_pipeline_wait: each cadence copied in "
+                                   "from pinned host memory, peeled, copied out; copies of one cadence overlap "
+                                   "the peel of the other")}
         finally:
             _abi.rts_host_free(h_in)
-            _abi.rts_host_free(h_out)
+            for hb in h_out:
+                _abi.rts_host_free(hb)
 
     if not args.no_extra:
-        line.update(extra_legs(args, p, cad, d_vis, d_resid, src, rank))
+        line.update(extra_legs(args, p, cad, d_vis, d_resid, src, rank, value / world))
 
     p.close()
     if rank == 0:
@@ -360,8 +401,9 @@ def main():
     return 0
 
 
-def extra_legs(args, p, cad, d_vis, d_resid, src, rank):
-    """FP64-path comparison, adjoint step, CPU baseline (rank 0 at N=1 only)."""
+def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate):
+    """One-source-per-pass path, FP64-path comparison, adjoint step, CPU baseline
+    (rank 0 at N=1 only)."""
     import numpy as np
     import torch
     from paper_1003_5575_gb300 import Peeler
@@ -369,23 +411,46 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank):
     out = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    from paper_1003_5575_gb300 import _abi
+    # the one-source-per-pass path (HBM-bound fused subtract + average), 100 sources
+    k1 = 100
+    p1 = Peeler(cad.uvw(), cad.freqs(), n_iter=args.n_iter, precision="mixed", max_sources=k1,
+                sources_per_pass=1)
+    d_j1 = torch.empty((k1, cad.n_ant, 4), dtype=torch.complex64, device="cuda")
+    p1.cadence(d_vis, src[:k1], resid=d_resid, jones=d_j1, status=False)
+    _abi.rts_peel_timing(p1.h, 1)
+    a, b = ev(), ev()
+    a.record()
+    p1.cadence(d_vis, src[:k1], resid=d_resid, jones=d_j1, status=False)
+    b.record()
+    torch.cuda.synchronize()
+    kt1 = _abi.rts_peel_timing_read(p1.h)
+    ms_k3, n_k3, _ = kt1["sub_average"]
+    k3_gbs = cad.n_vis * BYTES_PER_UPDATE / (ms_k3 / n_k3 / 1e3) / 1e9
+    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    out["one_source_per_pass"] = {
+        "sources": k1, "ms": a.elapsed_time(b), "updates_per_s": k1 * cad.n_vis / (a.elapsed_time(b) / 1e3),
+        "roofline": {"bound": "hbm", "kernel": "k_stream_mixed<SUB,ACC>", "achieved": k3_gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": k3_gbs / hbm_peak,
+                     "traffic": ncu_traffic("k_stream_mixed<true,true>"),
+                     "algorithmic_bytes_per_launch": cad.n_vis * BYTES_PER_UPDATE}}
+    p1.close()
+    del d_j1
+
     # plain FP64 GPU path on the same input, first k64 sources, vs the mixed path on the same sources
     k64 = 4
     d_jm = torch.empty((k64, cad.n_ant, 4), dtype=torch.complex64, device="cuda")
-    a, b = ev(), ev()
     p.cadence(d_vis, src[:k64], resid=d_resid, jones=d_jm, status=False)
-    a.record()
-    p.cadence(d_vis, src[:k64], resid=d_resid, jones=d_jm, status=False)
-    b.record()
     torch.cuda.synchronize()
-    ms_mixed = a.elapsed_time(b)
     R_mixed_sample = d_resid[:, :64].cpu().numpy()
     J_mixed = d_jm.cpu().numpy()
     p64 = Peeler(cad.uvw(), cad.freqs(), n_iter=args.n_iter, precision="fp64", max_sources=k64)
-    v64 = d_vis.to(torch.complex128)
     d_j64 = torch.empty((k64, cad.n_ant, 4), dtype=torch.complex128, device="cuda")
-    r64 = torch.empty_like(v64)
-    p64.cadence(v64, src[:1], resid=r64, jones=d_j64[:1], status=False)     # warm
+    v64 = d_vis.to(torch.complex128)
+    p64.cadence(v64, src[:1], resid=v64, jones=d_j64[:1], status=False)     # warm (in place)
+    v64.copy_(d_vis)
+    r64 = v64
     a, b = ev(), ev()
     a.record()
     p64.cadence(v64, src[:k64], resid=r64, jones=d_j64, status=False)
@@ -395,9 +460,12 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank):
     R64 = r64[:, :64].cpu().numpy()
     J64 = d_j64.cpu().numpy()
     rms = float(torch.sqrt(torch.mean(d_vis.view(torch.float32).double() ** 2)).item())
+    rate64 = k64 * cad.n_vis / (ms_64 / 1e3)
     out["fp64_path"] = {
-        "sources": k64, "ms_mixed": ms_mixed, "ms_fp64": ms_64, "speedup_mixed_vs_fp64": ms_64 / ms_mixed,
-        "updates_per_s_fp64": k64 * cad.n_vis / (ms_64 / 1e3),
+        "sources": k64, "ms_fp64": ms_64, "updates_per_s_fp64": rate64,
+        "speedup_mixed_vs_fp64": mixed_rate / rate64,
+        "speedup_basis": "updates/s of the timed mixed cadence (1000 sources) over updates/s of the FP64 path "
+                         "(one pass per source, so its rate does not depend on the source count)",
         "mixed_vs_fp64_max_resid_err_x_rms": float(np.abs(R_mixed_sample - R64).max() / rms),
         "mixed_vs_fp64_jones_rel": float(max(np.linalg.norm(J_mixed[k] - J64[k]) / np.linalg.norm(J64[k])
                                              for k in range(k64))),
@@ -405,6 +473,8 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank):
     }
     del v64, r64
     p64.close()
+    p.close()                      # release the pipeline cubes before the adjoint leg
+    torch.cuda.empty_cache()
     torch.cuda.empty_cache()
 
     # adjoint step at the config-5 shape (300 sources, positions perturbed by 1 arcmin)

@@ -114,6 +114,25 @@ int rts_peel_cadence_host(rts_peel_t* h, const void* h_vis, void* h_resid, int32
                           const double* h_src, void* h_jones, int32_t* h_status,
                           void* d_work, void* stream);
 
+/* Pipelined cadences on host buffers (the paper's Section 5 proposes streaming
+ * the next data onto the GPU while the previous cadence is processed).
+ * rts_peel_pipeline_submit enqueues, and returns without waiting:
+ *   copy-in stream   h_vis -> one of two library-owned device cubes
+ *   compute stream   the peel of that cube in place (after its copy-in)
+ *   copy-out stream  residual -> h_resid, Jones -> h_jones [n_src][n_ant][4],
+ *                    statuses -> h_status [n_src] (after the peel)
+ * so the copies of one cadence overlap the peel of the other.  At most two
+ * cadences are in flight: a third submit first waits for the oldest one.  The
+ * host buffers of a cadence must stay valid and untouched until
+ * rts_peel_pipeline_wait returns (or until a later submit has waited for it);
+ * page-locked buffers (rts_host_alloc) are required for the copies to overlap.
+ * The two device cubes are allocated on the first submit and kept.
+ * rts_peel_pipeline_wait waits for every submitted cadence and returns
+ * RTS_ENONFINITE if any source of any of them had a non-finite solve. */
+int rts_peel_pipeline_submit(rts_peel_t* h, const void* h_vis, void* h_resid, int32_t n_src,
+                             const double* h_src, void* h_jones, int32_t* h_status);
+int rts_peel_pipeline_wait(rts_peel_t* h);
+
 /* Model visibilities: d_vis = (accumulate ? d_vis : 0) +
  * sum_k S_k J_i^k J_j^kH exp(-2 pi i phi_k) for the n_src sources in h_src with
  * Jones d_jones [n_src][n_ant][4] (the predict step of the loop, for all sources). */

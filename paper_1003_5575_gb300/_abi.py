@@ -29,7 +29,7 @@ KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "gra
 
 EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_cadence_host",
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad",
-           "rts_peel_solve_noalloc",
+           "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
            "rts_peel_timing", "rts_peel_timing_read", "rts_host_alloc", "rts_host_free",
            "rts_peel_last_error", "rts_peel_destroy")
 
@@ -83,6 +83,10 @@ def lib():
             L.rts_peel_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp, _ip, _vp]
             L.rts_peel_solve_noalloc.restype = ctypes.c_int
             L.rts_peel_solve_noalloc.argtypes = [_vp, _i32, ctypes.c_double, _i32, _i32, _vp, _ip, _vp]
+            L.rts_peel_pipeline_submit.restype = ctypes.c_int
+            L.rts_peel_pipeline_submit.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _ip]
+            L.rts_peel_pipeline_wait.restype = ctypes.c_int
+            L.rts_peel_pipeline_wait.argtypes = [_vp]
             L.rts_peel_grad.restype = ctypes.c_int
             L.rts_peel_grad.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]
             L.rts_peel_timing.restype = ctypes.c_int
@@ -143,6 +147,14 @@ def rts_peel_solve(h, d_avg, S, d_jones, h_status, stream):
 def rts_peel_solve_noalloc(d_avg, n_ant, S, n_iter, precision, d_jones, h_status, stream):
     return _check(lib().rts_peel_solve_noalloc(d_avg, n_ant, S, n_iter, precision, d_jones, h_status,
                                                stream), None)
+
+
+def rts_peel_pipeline_submit(h, h_vis, h_resid, n_src, h_src, h_jones, h_status):
+    return _check(lib().rts_peel_pipeline_submit(h, h_vis, h_resid, n_src, h_src, h_jones, h_status), h)
+
+
+def rts_peel_pipeline_wait(h):
+    return _check(lib().rts_peel_pipeline_wait(h), h)
 
 
 def rts_peel_grad(h, d_vis, n_src, d_jones, d_src, d_loss, d_gJ, d_gsrc, stream):

@@ -57,6 +57,16 @@ struct rts_peel_t {
   cudaEvent_t b_ev_ready[kRing] = {};   // slot filled (prep -> main)
   cudaEvent_t b_ev_free[kRing] = {};    // slot consumed (main -> prep)
   cudaEvent_t b_ev_done = nullptr; // prep finished (prep -> main)
+  // pipelined host-buffer cadences (two slots)
+  void* p_cube[2] = {nullptr, nullptr};     // device cubes
+  void* p_jones[2] = {nullptr, nullptr};    // device Jones staging [max_sources][n_ant][4]
+  int32_t* p_status[2] = {nullptr, nullptr};// device status copies [max_sources]
+  cudaStream_t p_in = nullptr, p_comp = nullptr, p_out = nullptr;
+  cudaEvent_t p_ev_in[2] = {}, p_ev_comp[2] = {}, p_ev_out[2] = {};
+  bool p_busy[2] = {false, false};
+  int32_t* p_hstatus[2] = {nullptr, nullptr};
+  int32_t p_nsrc[2] = {0, 0};
+  int p_next = 0;
   // tracing: CUDA events around kernel groups, launch counters
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -538,6 +548,91 @@ int rts_peel_cadence_host(rts_peel_t* h, const void* h_vis, void* h_resid, int32
   return RTS_OK;
 }
 
+namespace {
+
+int pipeline_setup(rts_peel_t* h) {
+  if (h->p_cube[0]) return RTS_OK;
+  const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
+  for (int k = 0; k < 2; ++k) {
+    RTS_CUDA(h, cudaMalloc(&h->p_cube[k], cube));
+    RTS_CUDA(h, cudaMalloc(&h->p_jones[k], (size_t)h->max_sources * h->n_ant * 4 * h->elem));
+    RTS_CUDA(h, cudaMalloc((void**)&h->p_status[k], (size_t)h->max_sources * sizeof(int32_t)));
+    RTS_CUDA(h, cudaEventCreateWithFlags(&h->p_ev_in[k], cudaEventDisableTiming));
+    RTS_CUDA(h, cudaEventCreateWithFlags(&h->p_ev_comp[k], cudaEventDisableTiming));
+    RTS_CUDA(h, cudaEventCreateWithFlags(&h->p_ev_out[k], cudaEventDisableTiming));
+  }
+  RTS_CUDA(h, cudaStreamCreateWithFlags(&h->p_in, cudaStreamNonBlocking));
+  RTS_CUDA(h, cudaStreamCreateWithFlags(&h->p_comp, cudaStreamNonBlocking));
+  RTS_CUDA(h, cudaStreamCreateWithFlags(&h->p_out, cudaStreamNonBlocking));
+  return RTS_OK;
+}
+
+// wait for slot k's cadence; RTS_ENONFINITE if one of its sources failed
+int pipeline_retire(rts_peel_t* h, int k) {
+  if (!h->p_busy[k]) return RTS_OK;
+  RTS_CUDA(h, cudaEventSynchronize(h->p_ev_out[k]));
+  h->p_busy[k] = false;
+  if (h->p_hstatus[k])
+    for (int i = 0; i < h->p_nsrc[k]; ++i)
+      if (h->p_hstatus[k][i] == RTS_ENONFINITE)
+        return fail(h, RTS_ENONFINITE, "non-finite value in the solve of source " + std::to_string(i));
+  return RTS_OK;
+}
+
+}  // namespace
+
+int rts_peel_pipeline_submit(rts_peel_t* h, const void* h_vis, void* h_resid, int32_t n_src,
+                             const double* h_src, void* h_jones, int32_t* h_status) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!h_vis || !h_resid) return fail(h, RTS_EINVAL, "h_vis and h_resid are required");
+  int rc = validate_sources(h, n_src, h_src);
+  if (rc) return rc;
+  if (n_src > 0 && !h_jones) return fail(h, RTS_EINVAL, "h_jones is NULL");
+  rc = pipeline_setup(h);
+  if (rc) return rc;
+  const int k = h->p_next;
+  rc = pipeline_retire(h, k);                       // the slot's previous cadence
+  if (rc) return rc;
+  const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
+  RTS_CUDA(h, cudaMemcpyAsync(h->p_cube[k], h_vis, cube, cudaMemcpyHostToDevice, h->p_in));
+  RTS_CUDA(h, cudaEventRecord(h->p_ev_in[k], h->p_in));
+  RTS_CUDA(h, cudaStreamWaitEvent(h->p_comp, h->p_ev_in[k], 0));
+  rc = peel_device(h, h->p_cube[k], h->p_cube[k], n_src, h_src, h->p_jones[k], nullptr, h->p_comp);
+  if (rc) return rc;
+  if (n_src > 0)
+    RTS_CUDA(h, cudaMemcpyAsync(h->p_status[k], h->d_status, sizeof(int32_t) * n_src,
+                                cudaMemcpyDeviceToDevice, h->p_comp));
+  RTS_CUDA(h, cudaEventRecord(h->p_ev_comp[k], h->p_comp));
+  RTS_CUDA(h, cudaStreamWaitEvent(h->p_out, h->p_ev_comp[k], 0));
+  RTS_CUDA(h, cudaMemcpyAsync(h_resid, h->p_cube[k], cube, cudaMemcpyDeviceToHost, h->p_out));
+  if (n_src > 0) {
+    RTS_CUDA(h, cudaMemcpyAsync(h_jones, h->p_jones[k], (size_t)n_src * h->n_ant * 4 * h->elem,
+                                cudaMemcpyDeviceToHost, h->p_out));
+    if (h_status)
+      RTS_CUDA(h, cudaMemcpyAsync(h_status, h->p_status[k], sizeof(int32_t) * n_src,
+                                  cudaMemcpyDeviceToHost, h->p_out));
+  }
+  RTS_CUDA(h, cudaEventRecord(h->p_ev_out[k], h->p_out));
+  // the next cadence's copy-in may not overwrite this slot until its copy-out is done;
+  // the next slot's copy-in only needs that slot's previous copy-out (checked at submit)
+  h->p_busy[k] = true;
+  h->p_hstatus[k] = h_status;
+  h->p_nsrc[k] = n_src;
+  h->p_next = 1 - k;
+  return RTS_OK;
+}
+
+int rts_peel_pipeline_wait(rts_peel_t* h) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  int worst = RTS_OK;
+  for (int i = 0; i < 2; ++i) {
+    const int k = (h->p_next + i) & 1;             // oldest first
+    int rc = pipeline_retire(h, k);
+    if (rc && !worst) worst = rc;
+  }
+  return worst;
+}
+
 int rts_peel_predict(rts_peel_t* h, void* d_vis, int32_t n_src, const double* h_src,
                      const void* d_jones, int32_t accumulate, void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
@@ -697,6 +792,17 @@ void rts_peel_destroy(rts_peel_t* h) {
   if (h->b_ev_out) cudaEventDestroy(h->b_ev_out);
   grad_free(h->grad);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k) {
+    if (h->p_cube[k]) cudaFree(h->p_cube[k]);
+    if (h->p_jones[k]) cudaFree(h->p_jones[k]);
+    if (h->p_status[k]) cudaFree(h->p_status[k]);
+    if (h->p_ev_in[k]) cudaEventDestroy(h->p_ev_in[k]);
+    if (h->p_ev_comp[k]) cudaEventDestroy(h->p_ev_comp[k]);
+    if (h->p_ev_out[k]) cudaEventDestroy(h->p_ev_out[k]);
+  }
+  if (h->p_in) cudaStreamDestroy(h->p_in);
+  if (h->p_comp) cudaStreamDestroy(h->p_comp);
+  if (h->p_out) cudaStreamDestroy(h->p_out);
   if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
   delete h;
 }

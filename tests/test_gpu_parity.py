@@ -327,3 +327,44 @@ def test_nonfinite_input_reported():
         p.cadence(to_dev(V, "mixed"), cad.sources())
     assert e.value.code == RTS_ENONFINITE
     p.close()
+
+
+def test_pipelined_host_cadences_equal_device_cadences():
+    """rts_peel_pipeline_submit/wait (copies of one cadence overlapping the peel
+    of the other) give the same bits as rts_peel_cadence on the device."""
+    import ctypes
+    from paper_1003_5575_gb300 import _abi
+    cad = Cadence(16, 64, 3, 20, seed=71)
+    V1 = oracle.simulate(cad).astype(np.complex64)
+    V2 = oracle.simulate(cad.with_(seed=72)).astype(np.complex64)
+    p = make_peeler(cad, "mixed")
+    refs = []
+    for V in (V1, V2, V1):
+        r, j, st = p.cadence(torch.from_numpy(V).cuda(), cad.sources())
+        refs.append((r.cpu().numpy(), j.cpu().numpy(), st.copy()))
+    nbytes = V1.nbytes
+    bufs = [_abi.rts_host_alloc(nbytes) for _ in range(5)]
+    try:
+        def view(ptr):
+            return np.ctypeslib.as_array((ctypes.c_float * (V1.size * 2)).from_address(ptr)).view(np.complex64).reshape(V1.shape)
+        ins = [view(bufs[0]), view(bufs[1])]
+        ins[0][...] = V1
+        ins[1][...] = V2
+        outs = [view(bufs[2]), view(bufs[3]), view(bufs[4])]
+        jones = [np.zeros((cad.n_src, cad.n_ant, 4), np.complex64) for _ in range(3)]
+        sts = [np.zeros(cad.n_src, np.int32) for _ in range(3)]
+        src = np.ascontiguousarray(cad.sources())
+        for i, vin in enumerate((ins[0], ins[1], ins[0])):
+            _abi.rts_peel_pipeline_submit(p.h, ctypes.c_void_p(vin.ctypes.data), ctypes.c_void_p(outs[i].ctypes.data),
+                                          cad.n_src, src.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          ctypes.c_void_p(jones[i].ctypes.data),
+                                          sts[i].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        _abi.rts_peel_pipeline_wait(p.h)
+        for i in range(3):
+            np.testing.assert_array_equal(outs[i], refs[i][0])
+            np.testing.assert_array_equal(jones[i], refs[i][1])
+            np.testing.assert_array_equal(sts[i], refs[i][2])
+    finally:
+        for b in bufs:
+            _abi.rts_host_free(b)
+        p.close()
