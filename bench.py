@@ -229,23 +229,19 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    from paper_1003_5575_gb300 import replicas
+    barrier = replicas.barrier
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, device="cuda")
 
     import __graft_entry__
     __graft_entry__.build()
     from paper_1003_5575_gb300 import Peeler, _abi
     from synth import config
 
-    cad = config(3).with_(n_src=args.sources, n_chan=args.channels, n_ant=args.antennas, seed=config(3).seed + 1000 * rank)
+    cad = config(3).with_(n_src=args.sources, n_chan=args.channels, n_ant=args.antennas,
+                          seed=replicas.rank_seed(config(3).seed, rank))
     src = cad.sources()
     K = cad.n_src
     log(f"[rank {rank}] building cadence: {cad.n_ant} ant, {cad.n_chan} ch, {cad.n_time} t, {K} sources")
@@ -285,7 +281,7 @@ def main():
     ktimes = _abi.rts_peel_timing_read(p.h)
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
-    value = world * updates_per_step * args.steps / (ms_total / 1e3)
+    value = replicas.job_rate(updates_per_step * args.steps, ms_total / 1e3, world)
     launches = sum(v[2] for v in ktimes.values())
 
     # results of the timed cadence: statuses (untimed re-run with status)

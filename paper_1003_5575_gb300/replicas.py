@@ -1,0 +1,57 @@
+"""Host-side logic of multi-GPU runs (one process per GPU, torch.distributed).
+
+The peel shards by cadence: each GPU owns its own channel group / cadence (the
+paper's per-GPU channel sets, weak scaling across GPUs) and needs no data-path
+collective.  What the ranks share is bookkeeping: a per-rank seed, a barrier
+around the timed region, the slowest rank's time and the job total.
+
+For a cadence split by channel across GPUs, the one exchange per source would
+be a sum of the per-rank partial averages (each rank's samples-weighted mean
+over its channels); `combine_partial_averages` is that reduction.
+"""
+from __future__ import annotations
+
+import torch
+import torch.distributed as dist
+
+
+def world() -> tuple[int, int]:
+    """(rank, world_size); (0, 1) outside torch.distributed."""
+    if dist.is_available() and dist.is_initialized():
+        return dist.get_rank(), dist.get_world_size()
+    return 0, 1
+
+
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Independent cadence per rank."""
+    return int(base_seed) + 1000 * int(rank)
+
+
+def barrier() -> None:
+    if world()[1] > 1:
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device: str | torch.device = "cpu") -> float:
+    """The slowest rank's value (the job's time)."""
+    if world()[1] == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds_max: float, world_size: int) -> float:
+    """Whole-job throughput of weakly scaled replicas: all ranks' units over the slowest time."""
+    return world_size * units_per_rank / seconds_max
+
+
+def combine_partial_averages(partial: torch.Tensor, n_local: int, n_total: int) -> torch.Tensor:
+    """Sum over ranks of n_local / n_total * partial (in place, returned).
+
+    `partial` is this rank's mean over its own samples; the result is the mean
+    over all samples of all ranks."""
+    partial.mul_(float(n_local) / float(n_total))
+    if world()[1] > 1:
+        dist.all_reduce(partial, op=dist.ReduceOp.SUM)
+    return partial
