@@ -70,16 +70,18 @@ __device__ inline float2 phasor_q64_fine(unsigned long long x) {
 
 constexpr int kSubCh = 3;     // channels a thread keeps in registers while subtracting
 template <int BK, bool SUB, bool ACC>
-__global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) {
+__global__ void __launch_bounds__(kBlkThreads, 3) k_block_pass(BlockPassArgs a) {
   constexpr int kHalf = BK / 2;                   // averaging: two sources per thread
   constexpr int kSplits = kBlkThreads / kHalf;    // channel ranges per source pair
   extern __shared__ __align__(16) unsigned char b_smem[];
   float4* sR = reinterpret_cast<float4*>(b_smem);                       // [n_chan][2]
-  PhaseAB* sPs = reinterpret_cast<PhaseAB*>(sR + (size_t)a.n_chan * 2);  // [n_time][BK]
-  PhaseAB* sPa = sPs + (size_t)a.n_time * BK;                            // [n_time][BK]
+  PhaseAB* sPs = reinterpret_cast<PhaseAB*>(sR + (size_t)a.n_chan * 2);  // [BK] at the current time
+  PhaseAB* sPa = sPs + BK;                                               // [BK] at the current time
   __shared__ float2 sM[BK][4];       // model matrix entries (re, im)
   __shared__ float2 sMs[BK][4];      // the same with re and im swapped
-  __shared__ double sRed[kSplits][BK][8];
+  // FP64 running sums of the averages, one slot per (channel range, source):
+  // [kSplits][BK][8] doubles (32 KB) after the strip and the phase tables
+  double (*sRed)[BK][8] = reinterpret_cast<double (*)[BK][8]>(sPa + BK);
 
   const int64_t bl = blockIdx.x;
   const int tid = threadIdx.x;
@@ -90,30 +92,23 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
       sM[k][e] = m;
       sMs[k][e] = make_float2(m.y, m.x);
     }
-    for (int q = tid; q < a.n_time * a.n_sub; q += kBlkThreads) {
-      const int t = q / a.n_sub, k = q - t * a.n_sub;
-      sPs[t * BK + k] = a.ph_sub[((size_t)bl * a.n_time + t) * BK + k];
-    }
-  }
-  if (ACC) {
-    for (int q = tid; q < a.n_time * a.n_acc; q += kBlkThreads) {
-      const int t = q / a.n_acc, k = q - t * a.n_acc;
-      sPa[t * BK + k] = a.ph_acc[((size_t)bl * a.n_time + t) * BK + k];
-    }
   }
   // averaging role: sources k0 = tid % kHalf and k0 + kHalf over channels [c_beg, c_end)
   const int k0 = tid % kHalf, split = tid / kHalf;
   const bool has0 = k0 < a.n_acc, has1 = k0 + kHalf < a.n_acc;
   const int chunk = (a.n_chan + kSplits - 1) / kSplits;
   const int c_beg = min(a.n_chan, split * chunk), c_end = min(a.n_chan, c_beg + chunk);
-  double accd[16];
-  #pragma unroll
-  for (int e = 0; e < 16; ++e) accd[e] = 0.0;
+  if (ACC) {
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) { sRed[split][k0][e] = 0.0; sRed[split][k0 + kHalf][e] = 0.0; }
+  }
 
   for (int t = 0; t < a.n_time; ++t) {
     __syncthreads();                                   // previous strip consumed; tables ready
     const size_t base = ((size_t)t * a.n_bl + bl) * a.n_chan * 2;
     for (int q = tid; q < a.n_chan * 2; q += kBlkThreads) sR[q] = __ldcs(a.src + base + q);
+    if (SUB && tid < a.n_sub) sPs[tid] = a.ph_sub[((size_t)bl * a.n_time + t) * BK + tid];
+    if (ACC && tid >= BK && tid - BK < a.n_acc) sPa[tid - BK] = a.ph_acc[((size_t)bl * a.n_time + t) * BK + tid - BK];
     __syncthreads();
     if (SUB) {
       // channels c0, c0 + 256, c0 + 512 in registers; sources in the inner loop.
@@ -131,7 +126,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
           }
         }
         for (int j = 0; j < a.n_sub; ++j) {
-          const PhaseAB p = sPs[t * BK + j];
+          const PhaseAB p = sPs[j];
           float2 M[4], Ms[4];
           #pragma unroll
           for (int e = 0; e < 4; ++e) { M[e] = sM[j][e]; Ms[e] = sMs[j][e]; }
@@ -165,8 +160,8 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
       // exact fixed-point phase per channel (a recurrence ph *= exp(2 pi i B) would
       // carry the step's rounding coherently across channels).  Packed sums
       // P_e = sum x_e pr and Q_e = sum x_e pi give  acc_e = (P.x - Q.y, P.y + Q.x).
-      const PhaseAB p0 = sPa[t * BK + k0];
-      const PhaseAB p1 = has1 ? sPa[t * BK + k0 + kHalf] : p0;
+      const PhaseAB p0 = sPa[k0];
+      const PhaseAB p1 = has1 ? sPa[k0 + kHalf] : p0;
       float2 P0[4], Q0[4], P1[4], Q1[4];
       #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -189,19 +184,16 @@ __global__ void __launch_bounds__(kBlkThreads, 2) k_block_pass(BlockPassArgs a) 
       }
       #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        accd[2 * e] += (double)(P0[e].x - Q0[e].y);
-        accd[2 * e + 1] += (double)(P0[e].y + Q0[e].x);
-        accd[8 + 2 * e] += (double)(P1[e].x - Q1[e].y);
-        accd[8 + 2 * e + 1] += (double)(P1[e].y + Q1[e].x);
+        sRed[split][k0][2 * e] += (double)(P0[e].x - Q0[e].y);
+        sRed[split][k0][2 * e + 1] += (double)(P0[e].y + Q0[e].x);
+        if (has1) {
+          sRed[split][k0 + kHalf][2 * e] += (double)(P1[e].x - Q1[e].y);
+          sRed[split][k0 + kHalf][2 * e + 1] += (double)(P1[e].y + Q1[e].x);
+        }
       }
     }
   }
   if (ACC) {
-    #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      if (has0) sRed[split][k0][e] = accd[e];
-      if (has1) sRed[split][k0 + kHalf][e] = accd[8 + e];
-    }
     __syncthreads();
     for (int q = tid; q < a.n_acc * 4; q += kBlkThreads) {
       const int k = q >> 2, e = q & 3;

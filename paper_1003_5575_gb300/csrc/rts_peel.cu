@@ -207,7 +207,9 @@ int read_status(rts_peel_t* h, int32_t n, int32_t* h_status, cudaStream_t s) {
 }
 
 size_t block_pass_smem(const rts_peel_t* h) {
-  return (size_t)h->n_chan * 2 * sizeof(float4) + (size_t)2 * h->n_time * h->per_pass * sizeof(PhaseAB);
+  // strip [n_chan][2] float4 | phases 2 x [BK] | FP64 sums [splits][BK][8] (splits*BK = 512)
+  return (size_t)h->n_chan * 2 * sizeof(float4) + (size_t)2 * h->per_pass * sizeof(PhaseAB) +
+         (size_t)2 * kBlkThreads * 8 * sizeof(double);
 }
 
 // geometry of block b (phases, then D_jk) into ring slot b % kRing, on the prep stream
@@ -448,8 +450,9 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
     return fail(nullptr, RTS_EINVAL, "sources_per_pass must be 0, 1, 8, 16, 32 or 64");
   if (per_pass > 1 && cfg->precision != RTS_PREC_MIXED)
     return fail(nullptr, RTS_EINVAL, "the blocked peel (sources_per_pass = RTS_BLOCK) is RTS_PREC_MIXED only");
-  if (per_pass > 1 && (size_t)cfg->n_chan * 32 + (size_t)cfg->n_time * 32 * per_pass > 200 * 1024)
-    return fail(nullptr, RTS_EINVAL, "the blocked peel needs n_chan*32 + n_time*2048 <= 200 KB of shared memory");
+  if (per_pass > 1 && (size_t)cfg->n_chan * 32 + 2048 + 32768 > 200 * 1024)
+    return fail(nullptr, RTS_EINVAL, "the blocked peel needs n_chan*32 + 34 KB <= 200 KB of shared memory "
+                                     "(n_chan <= 5300); use sources_per_pass = 1");
 
   rts_peel_t* h = new rts_peel_t();
   h->per_pass = per_pass;
