@@ -27,6 +27,15 @@
  *   loss    L = sum ||V - sum_k S_k J_i J_j^H exp(-2 pi i phi_k)||_F^2 and its
  *           gradient w.r.t. (J, l, m, S) in the PyTorch convention
  *           dL/dRe + i dL/dIm (hand-derived adjoint, checked by differences).
+ *   offsets Section 3 measures per calibrator a position offset (ionospheric
+ *           refraction) as well as the Jones matrices, from six numbers per
+ *           source of which the fit keeps two.  Reading: the Gauss-Newton
+ *           normal equations of L in (l_k, m_k) at the peel's solution:
+ *             H_pq = 2 sum_{t,bl,c} (2 pi)^2 w_p w_q tr(M_k^H M_k),
+ *             w_l = (u - w l/n) nu/c,  w_m = (v - w m/n) nu/c   [turns per unit]
+ *             g = (dL/dl_k, dL/dm_k),  offset = -H^-1 g,
+ *           reported as (H_ll, H_lm, H_mm, g_l, g_m, L); the step is (0, 0)
+ *           where det H <= 0 (no flux, zero gains, no baselines).
  *
  * Parallelism: baselines are independent in every streaming step; each
  * baseline's sums run serially in (t, c) order, and sums across baselines are
@@ -383,4 +392,50 @@ void orc_loss_grad(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* 
     if (g_S) g_S[k] = gS;
   }
   free(G); free(Hl); free(Hm); free(bl_loss); free(Mk);
+}
+
+/* ---- ionospheric position offsets (Gauss-Newton normal equations) ----------
+ * out[k][6] = (H_ll, H_lm, H_mm, dL/dl, dL/dm, L), offsets[k][2] = -H^-1 g.  */
+
+void orc_offsets(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                 const double* freq, const double* vis, int32_t n_src, const double* lmS,
+                 const double* jones, double* out, double* offsets) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  double loss = 0.0;
+  double* gJ = (double*)malloc(sizeof(double) * 8 * (size_t)(n_src > 0 ? n_src : 1) * n_ant);
+  double* gl = (double*)malloc(sizeof(double) * (n_src > 0 ? n_src : 1));
+  double* gm = (double*)malloc(sizeof(double) * (n_src > 0 ? n_src : 1));
+  double* gS = (double*)malloc(sizeof(double) * (n_src > 0 ? n_src : 1));
+  orc_loss_grad(n_ant, n_chan, n_time, uvw, freq, vis, n_src, lmS, jones, &loss, gJ, gl, gm, gS);
+  for (int32_t k = 0; k < n_src; ++k) {
+    double l = lmS[3 * k], m = lmS[3 * k + 1], S = lmS[3 * k + 2];
+    double n = sqrt(1.0 - l * l - m * m);
+    double hll = 0.0, hlm = 0.0, hmm = 0.0;
+    for (int64_t bl = 0; bl < n_bl; ++bl) {
+      int32_t i = ai[bl], j = aj[bl];
+      mat2 Ji = m_load(jones + ((int64_t)k * n_ant + i) * 8);
+      mat2 Jj = m_load(jones + ((int64_t)k * n_ant + j) * 8);
+      double mm = m_norm2(m_scale(m_mul(Ji, m_herm(Jj)), S));      /* tr(M^H M) */
+      for (int32_t t = 0; t < n_time; ++t) {
+        const double* a = uvw + ((int64_t)t * n_ant + i) * 3;
+        const double* b = uvw + ((int64_t)t * n_ant + j) * 3;
+        double u = a[0] - b[0], v = a[1] - b[1], w = a[2] - b[2];
+        for (int32_t c = 0; c < n_chan; ++c) {
+          double wl = (u - w * l / n) * freq[c] / C_LIGHT;
+          double wm = (v - w * m / n) * freq[c] / C_LIGHT;
+          hll += wl * wl * mm; hlm += wl * wm * mm; hmm += wm * wm * mm;
+        }
+      }
+    }
+    double f = 2.0 * TWO_PI * TWO_PI;
+    hll *= f; hlm *= f; hmm *= f;
+    double* o = out + 6 * (int64_t)k;
+    o[0] = hll; o[1] = hlm; o[2] = hmm; o[3] = gl[k]; o[4] = gm[k]; o[5] = loss;
+    double det = hll * hmm - hlm * hlm;       /* no step where H is singular */
+    offsets[2 * k] = det > 0.0 ? -(hmm * gl[k] - hlm * gm[k]) / det : 0.0;
+    offsets[2 * k + 1] = det > 0.0 ? -(-hlm * gl[k] + hll * gm[k]) / det : 0.0;
+  }
+  free(gJ); free(gl); free(gm); free(gS);
 }

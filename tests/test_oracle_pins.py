@@ -359,3 +359,50 @@ def test_loss_is_zero_at_truth_without_noise():
     L, gJ, gl, gm, gS = oracle.loss_grad(uvw, freq, V, src, J)
     assert L < 1e-20
     assert np.abs(gJ).max() < 1e-9 and np.abs(gl).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# ionospheric position offsets (Gauss-Newton normal equations in l, m)
+
+
+def test_offset_normal_matrix_equals_jacobian_products():
+    """H = 2 Re sum J_p^* J_q with J_p = d(model)/d(position) by Richardson-extrapolated
+    central differences of the oracle's prediction (no use of the closed-form weights)."""
+    cad = small(n_ant=6, n_chan=10, n_time=2, n_src=2)
+    uvw, freq, src, J = cad.uvw(), cad.freqs(), cad.sources(), cad.jones()
+    V = oracle.simulate(cad, noise=False)
+    out, _ = oracle.offsets(uvw, freq, V, src, J)
+    for k in range(cad.n_src):
+        def central(col, h):
+            s1, s2 = src.copy(), src.copy()
+            s1[k, col] += h
+            s2[k, col] -= h
+            return (oracle.predict(uvw, freq, s1[k:k + 1], J[k:k + 1]) -
+                    oracle.predict(uvw, freq, s2[k:k + 1], J[k:k + 1])).ravel() / (2 * h)
+        # Richardson: (4 D(h/2) - D(h)) / 3 cancels the h^2 term of the central difference
+        jac = [(4 * central(col, 5e-7) - central(col, 1e-6)) / 3 for col in (0, 1)]
+        H = np.array([[2 * np.real(np.vdot(a, b)) for b in jac] for a in jac])
+        np.testing.assert_allclose(out[k, [0, 1, 2]], [H[0, 0], H[0, 1], H[1, 1]], rtol=1e-6)
+
+
+def test_offset_is_zero_at_the_exact_model():
+    cad = small(n_ant=6, n_chan=10, n_time=2, n_src=2)
+    V = oracle.simulate(cad, noise=False)
+    out, off = oracle.offsets(cad.uvw(), cad.freqs(), V, cad.sources(), cad.jones())
+    assert np.abs(off).max() < 1e-12
+    assert out[0, 5] < 1e-20
+
+
+def test_offset_recovers_a_shifted_source_with_known_gains():
+    """A source observed 0.1 arcmin away from its catalogue position: one
+    Gauss-Newton step with the true gains returns the shift (first-order
+    accurate: relative error of the order of the shift's phase, here < 1 %)."""
+    cad = small(n_ant=16, n_chan=32, n_time=4, n_src=1, noise_sigma=0.0)
+    cat = np.array([[0.12, -0.07, 4.0]])
+    shift = np.array([2.0e-5, -3.0e-5])
+    true = cat.copy()
+    true[0, :2] += shift
+    J = cad.jones()
+    V = oracle.predict(cad.uvw(), cad.freqs(), true, J)
+    _, off = oracle.offsets(cad.uvw(), cad.freqs(), V, cat, J)
+    np.testing.assert_allclose(off[0], shift, rtol=1e-2)
