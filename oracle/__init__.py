@@ -63,7 +63,8 @@ def lib():
             L.orc_peel.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _ip, _dp]
             L.orc_loss_grad.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _dp,
                                         _dp, _dp, _dp, _dp, _dp]
-            L.orc_offsets.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _dp, _dp, _dp]
+            L.orc_offsets.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _dp, ctypes.c_double,
+                                      ctypes.c_double, _dp, _dp]
             L.orc_num_threads.restype = _i32
             _lib = L
     return _lib
@@ -179,17 +180,18 @@ def loss_grad(uvw, freq, vis, lmS, jones):
     return loss.value, gJ, gl[:n_src], gm[:n_src], gS[:n_src]
 
 
-def offsets(uvw, freq, vis, lmS, jones):
-    """Ionospheric position-offset normal equations per source.
+def offsets(uvw, freq, vis, lmS, jones, alpha=0.0, nu_ref=None):
+    """Position-offset normal equations per source, shift (nu_ref/nu)^alpha (dl, dm).
     Returns (out [n_src][6] = H_ll, H_lm, H_mm, dL/dl, dL/dm, L; offsets [n_src][2])."""
     uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
     vis = _f64(vis, np.complex128)
     jones = _f64(jones, np.complex128)
+    nu_ref = float(np.mean(freq)) if nu_ref is None else float(nu_ref)
     n_src = lmS.shape[0]
     out = np.zeros((max(n_src, 1), 6))
     off = np.zeros((max(n_src, 1), 2))
     lib().orc_offsets(uvw.shape[1], freq.shape[0], uvw.shape[0], _d(uvw), _d(freq), _d(vis), n_src,
-                      _d(lmS), _d(jones), _d(out), _d(off))
+                      _d(lmS), _d(jones), float(alpha), nu_ref, _d(out), _d(off))
     return out[:n_src], off[:n_src]
 
 

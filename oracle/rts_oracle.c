@@ -28,13 +28,16 @@
  *           gradient w.r.t. (J, l, m, S) in the PyTorch convention
  *           dL/dRe + i dL/dIm (hand-derived adjoint, checked by differences).
  *   offsets Section 3 measures per calibrator a position offset (ionospheric
- *           refraction) as well as the Jones matrices, from six numbers per
- *           source of which the fit keeps two.  Reading: the Gauss-Newton
- *           normal equations of L in (l_k, m_k) at the peel's solution:
- *             H_pq = 2 sum_{t,bl,c} (2 pi)^2 w_p w_q tr(M_k^H M_k),
- *             w_l = (u - w l/n) nu/c,  w_m = (v - w m/n) nu/c   [turns per unit]
- *             g = (dL/dl_k, dL/dm_k),  offset = -H^-1 g,
- *           reported as (H_ll, H_lm, H_mm, g_l, g_m, L); the step is (0, 0)
+ *           refraction) as well as the Jones matrices; Section 3.1 says the
+ *           fit needs six numbers per source and is described by two, that
+ *           the ionosphere's response is a known function of frequency, and
+ *           that workers send their numbers to a master that builds the
+ *           solution.  Reading: the six numbers are the Gauss-Newton
+ *           sufficient statistics of the two-parameter fit, additive over
+ *           channel groups: J^T J (3), J^T r (2) and r^T r (1), with the shift
+ *           at channel c equal to (nu_ref/nu_c)^alpha (dl, dm) (alpha = 2 for
+ *           refraction), reported as (H_ll, H_lm, H_mm, g_l, g_m, L) with
+ *           H = 2 J^T J, g = dL/d(dl, dm); the fit is -H^-1 g, or (0, 0)
  *           where det H <= 0 (no flux, zero gains, no baselines).
  *
  * Parallelism: baselines are independent in every streaming step; each
@@ -395,47 +398,78 @@ void orc_loss_grad(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* 
 }
 
 /* ---- ionospheric position offsets (Gauss-Newton normal equations) ----------
- * out[k][6] = (H_ll, H_lm, H_mm, dL/dl, dL/dm, L), offsets[k][2] = -H^-1 g.  */
+ * Offset model: at channel c source k sits at (l + s_c dl, m + s_c dm),
+ * s_c = (nu_ref/nu_c)^alpha (alpha = 2: refraction, which scales as lambda^2;
+ * alpha = 0: a frequency-independent shift).  At dl = dm = 0 the derivative of
+ * source k's model is  D_p = M_k e^{-2 pi i phi_k} (-2 pi i) s_c a_p nu_c/c,
+ * a_l = u - w l/n, a_m = v - w m/n, and with R the residual of all sources
+ *   H_pq = 2 Re sum tr(D_p^H D_q),  g_p = -2 Re sum tr(R^H D_p),  L = sum ||R||^2.
+ * out[k][6] = (H_ll, H_lm, H_mm, g_l, g_m, L), offsets[k][2] = -H^-1 g.      */
 
 void orc_offsets(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                  const double* freq, const double* vis, int32_t n_src, const double* lmS,
-                 const double* jones, double* out, double* offsets) {
+                 const double* jones, double alpha, double nu_ref, double* out,
+                 double* offsets) {
   int64_t n_bl = orc_n_baselines(n_ant);
   int32_t *ai, *aj;
   antenna_map(n_ant, &ai, &aj);
-  double loss = 0.0;
-  double* gJ = (double*)malloc(sizeof(double) * 8 * (size_t)(n_src > 0 ? n_src : 1) * n_ant);
-  double* gl = (double*)malloc(sizeof(double) * (n_src > 0 ? n_src : 1));
-  double* gm = (double*)malloc(sizeof(double) * (n_src > 0 ? n_src : 1));
-  double* gS = (double*)malloc(sizeof(double) * (n_src > 0 ? n_src : 1));
-  orc_loss_grad(n_ant, n_chan, n_time, uvw, freq, vis, n_src, lmS, jones, &loss, gJ, gl, gm, gS);
-  for (int32_t k = 0; k < n_src; ++k) {
-    double l = lmS[3 * k], m = lmS[3 * k + 1], S = lmS[3 * k + 2];
-    double n = sqrt(1.0 - l * l - m * m);
-    double hll = 0.0, hlm = 0.0, hmm = 0.0;
+  int64_t nkb = (int64_t)n_src * n_bl;
+  double* part = (double*)calloc((size_t)(nkb > 0 ? nkb : 1) * 5, sizeof(double));
+  double* bl_loss = (double*)calloc((size_t)(n_bl > 0 ? n_bl : 1), sizeof(double));
+  mat2* Mk = (mat2*)malloc(sizeof(mat2) * (nkb > 0 ? nkb : 1));
+  for (int32_t k = 0; k < n_src; ++k)
     for (int64_t bl = 0; bl < n_bl; ++bl) {
-      int32_t i = ai[bl], j = aj[bl];
-      mat2 Ji = m_load(jones + ((int64_t)k * n_ant + i) * 8);
-      mat2 Jj = m_load(jones + ((int64_t)k * n_ant + j) * 8);
-      double mm = m_norm2(m_scale(m_mul(Ji, m_herm(Jj)), S));      /* tr(M^H M) */
-      for (int32_t t = 0; t < n_time; ++t) {
-        const double* a = uvw + ((int64_t)t * n_ant + i) * 3;
-        const double* b = uvw + ((int64_t)t * n_ant + j) * 3;
-        double u = a[0] - b[0], v = a[1] - b[1], w = a[2] - b[2];
-        for (int32_t c = 0; c < n_chan; ++c) {
-          double wl = (u - w * l / n) * freq[c] / C_LIGHT;
-          double wm = (v - w * m / n) * freq[c] / C_LIGHT;
-          hll += wl * wl * mm; hlm += wl * wm * mm; hmm += wm * wm * mm;
+      mat2 Ji = m_load(jones + ((int64_t)k * n_ant + ai[bl]) * 8);
+      mat2 Jj = m_load(jones + ((int64_t)k * n_ant + aj[bl]) * 8);
+      Mk[k * n_bl + bl] = m_scale(m_mul(Ji, m_herm(Jj)), lmS[3 * k + 2]);
+    }
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    int32_t i = ai[bl], j = aj[bl];
+    mat2* Mph = (mat2*)malloc(sizeof(mat2) * (n_src > 0 ? n_src : 1));
+    for (int32_t t = 0; t < n_time; ++t) {
+      const double* a = uvw + ((int64_t)t * n_ant + i) * 3;
+      const double* b = uvw + ((int64_t)t * n_ant + j) * 3;
+      double u = a[0] - b[0], v = a[1] - b[1], w = a[2] - b[2];
+      for (int32_t c = 0; c < n_chan; ++c) {
+        mat2 R = m_load(vis_at((double*)vis, n_bl, n_chan, t, bl, c));
+        for (int32_t k = 0; k < n_src; ++k) {
+          double phi = orc_phase_turns(orc_delay_m(uvw, n_ant, t, i, j, lmS[3 * k], lmS[3 * k + 1]), freq[c]);
+          Mph[k] = m_scale(Mk[k * n_bl + bl], phasor(phi, -1.0));
+          R = m_sub(R, Mph[k]);
+        }
+        bl_loss[bl] += m_norm2(R);
+        double s_c = pow(nu_ref / freq[c], alpha);
+        for (int32_t k = 0; k < n_src; ++k) {
+          double l = lmS[3 * k], m = lmS[3 * k + 1];
+          double n = sqrt(1.0 - l * l - m * m);
+          cplx f = -2.0 * M_PI * I * s_c * freq[c] / C_LIGHT;
+          mat2 Dl = m_scale(Mph[k], f * (u - w * l / n));
+          mat2 Dm = m_scale(Mph[k], f * (v - w * m / n));
+          double* o = part + ((int64_t)k * n_bl + bl) * 5;
+          o[0] += 2.0 * creal(m_trace(m_mul(m_herm(Dl), Dl)));
+          o[1] += 2.0 * creal(m_trace(m_mul(m_herm(Dl), Dm)));
+          o[2] += 2.0 * creal(m_trace(m_mul(m_herm(Dm), Dm)));
+          o[3] += -2.0 * creal(m_trace(m_mul(m_herm(R), Dl)));
+          o[4] += -2.0 * creal(m_trace(m_mul(m_herm(R), Dm)));
         }
       }
     }
-    double f = 2.0 * TWO_PI * TWO_PI;
-    hll *= f; hlm *= f; hmm *= f;
-    double* o = out + 6 * (int64_t)k;
-    o[0] = hll; o[1] = hlm; o[2] = hmm; o[3] = gl[k]; o[4] = gm[k]; o[5] = loss;
-    double det = hll * hmm - hlm * hlm;       /* no step where H is singular */
-    offsets[2 * k] = det > 0.0 ? -(hmm * gl[k] - hlm * gm[k]) / det : 0.0;
-    offsets[2 * k + 1] = det > 0.0 ? -(-hlm * gl[k] + hll * gm[k]) / det : 0.0;
+    free(Mph);
   }
-  free(gJ); free(gl); free(gm); free(gS);
+  double L = 0.0;
+  for (int64_t bl = 0; bl < n_bl; ++bl) L += bl_loss[bl];
+  for (int32_t k = 0; k < n_src; ++k) {
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t bl = 0; bl < n_bl; ++bl)
+      for (int q = 0; q < 5; ++q) acc[q] += part[((int64_t)k * n_bl + bl) * 5 + q];
+    double* o = out + 6 * (int64_t)k;
+    for (int q = 0; q < 5; ++q) o[q] = acc[q];
+    o[5] = L;
+    double hll = acc[0], hlm = acc[1], hmm = acc[2], gl = acc[3], gm = acc[4];
+    double det = hll * hmm - hlm * hlm;       /* no step where H is singular */
+    offsets[2 * k] = det > 0.0 ? -(hmm * gl - hlm * gm) / det : 0.0;
+    offsets[2 * k + 1] = det > 0.0 ? -(hll * gm - hlm * gl) / det : 0.0;
+  }
+  free(part); free(bl_loss); free(Mk);
 }

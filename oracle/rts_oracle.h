@@ -50,7 +50,8 @@ void orc_loss_grad(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* 
                    double* g_m, double* g_S);
 void orc_offsets(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                  const double* freq, const double* vis, int32_t n_src, const double* lmS,
-                 const double* jones, double* out, double* offsets);
+                 const double* jones, double alpha, double nu_ref, double* out,
+                 double* offsets);
 int32_t orc_num_threads(void);
 
 #ifdef __cplusplus

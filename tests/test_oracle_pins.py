@@ -365,44 +365,104 @@ def test_loss_is_zero_at_truth_without_noise():
 # ionospheric position offsets (Gauss-Newton normal equations in l, m)
 
 
-def test_offset_normal_matrix_equals_jacobian_products():
-    """H = 2 Re sum J_p^* J_q with J_p = d(model)/d(position) by Richardson-extrapolated
-    central differences of the oracle's prediction (no use of the closed-form weights)."""
+def _predict_shifted(cad, src, J, k, dl, dm, alpha, nu_ref):
+    """Model with source k moved by (nu_ref/nu_c)^alpha (dl, dm) at each channel:
+    one single-channel prediction per channel (independent of the offset code)."""
+    freq = cad.freqs()
+    parts = []
+    for c in range(cad.n_chan):
+        s = src.copy()
+        sc = (nu_ref / freq[c]) ** alpha
+        s[k, 0] += sc * dl
+        s[k, 1] += sc * dm
+        parts.append(oracle.predict(cad.uvw(), freq[c:c + 1], s, J))
+    return np.concatenate(parts, axis=2)
+
+
+def _richardson(f, h):
+    """(4 D(h/2) - D(h)) / 3 with D the central difference: cancels the h^2 term."""
+    d = lambda hh: (f(hh) - f(-hh)) / (2 * hh)
+    return (4 * d(h / 2) - d(h)) / 3
+
+
+@pytest.mark.parametrize("alpha", [0.0, 2.0])
+def test_offset_normal_matrix_equals_jacobian_products(alpha):
+    """H = 2 Re J^H J with J = d(model)/d(dl, dm) by extrapolated central
+    differences of per-channel predictions (no use of the derivative formula)."""
     cad = small(n_ant=6, n_chan=10, n_time=2, n_src=2)
-    uvw, freq, src, J = cad.uvw(), cad.freqs(), cad.sources(), cad.jones()
+    src, J = cad.sources(), cad.jones()
+    nu_ref = 160e6
     V = oracle.simulate(cad, noise=False)
-    out, _ = oracle.offsets(uvw, freq, V, src, J)
+    out, _ = oracle.offsets(cad.uvw(), cad.freqs(), V, src, J, alpha=alpha, nu_ref=nu_ref)
     for k in range(cad.n_src):
-        def central(col, h):
-            s1, s2 = src.copy(), src.copy()
-            s1[k, col] += h
-            s2[k, col] -= h
-            return (oracle.predict(uvw, freq, s1[k:k + 1], J[k:k + 1]) -
-                    oracle.predict(uvw, freq, s2[k:k + 1], J[k:k + 1])).ravel() / (2 * h)
-        # Richardson: (4 D(h/2) - D(h)) / 3 cancels the h^2 term of the central difference
-        jac = [(4 * central(col, 5e-7) - central(col, 1e-6)) / 3 for col in (0, 1)]
+        jac = [_richardson(lambda h: _predict_shifted(cad, src[k:k + 1], J[k:k + 1], 0, h, 0.0, alpha,
+                                                      nu_ref).ravel(), 1e-6),
+               _richardson(lambda h: _predict_shifted(cad, src[k:k + 1], J[k:k + 1], 0, 0.0, h, alpha,
+                                                      nu_ref).ravel(), 1e-6)]
         H = np.array([[2 * np.real(np.vdot(a, b)) for b in jac] for a in jac])
         np.testing.assert_allclose(out[k, [0, 1, 2]], [H[0, 0], H[0, 1], H[1, 1]], rtol=1e-6)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 2.0])
+def test_offset_gradient_equals_loss_differences(alpha):
+    """g = dL/d(dl, dm) of L = sum |V - model|^2 (numpy), all sources in the model."""
+    cad = small(n_ant=6, n_chan=8, n_time=2, n_src=3, pos_sigma_rad=2e-4)
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0))
+    src, J = cad.perturbed_sources(), cad.jones()
+    nu_ref = 155e6
+    out, _ = oracle.offsets(cad.uvw(), cad.freqs(), V, src, J, alpha=alpha, nu_ref=nu_ref)
+    L0 = np.sum(np.abs(V - oracle.predict(cad.uvw(), cad.freqs(), src, J)) ** 2)
+    assert out[0, 5] == pytest.approx(L0, rel=1e-12)
+    for k in range(cad.n_src):
+        for col, (ul, um) in ((3, (1, 0)), (4, (0, 1))):
+            g = _richardson(lambda h: np.sum(np.abs(
+                V - _predict_shifted(cad, src, J, k, ul * h, um * h, alpha, nu_ref)) ** 2), 1e-6)
+            assert out[k, col] == pytest.approx(g, rel=1e-6, abs=1e-9 * abs(out[:, 3:5]).max())
+
+
+def test_offset_gradient_without_frequency_law_equals_adjoint_gradient():
+    """alpha = 0: the shift is a plain change of (l, m), so g is the adjoint's dL/dl, dL/dm."""
+    cad = small(n_ant=7, n_chan=9, n_time=2, n_src=3, pos_sigma_rad=2e-4)
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0))
+    src, J = cad.perturbed_sources(), cad.jones()
+    out, _ = oracle.offsets(cad.uvw(), cad.freqs(), V, src, J, alpha=0.0)
+    L, _, gl, gm, _ = oracle.loss_grad(cad.uvw(), cad.freqs(), V, src, J)
+    np.testing.assert_allclose(out[:, 3], gl, rtol=1e-10)
+    np.testing.assert_allclose(out[:, 4], gm, rtol=1e-10)
+    assert out[0, 5] == pytest.approx(L, rel=1e-12)
 
 
 def test_offset_is_zero_at_the_exact_model():
     cad = small(n_ant=6, n_chan=10, n_time=2, n_src=2)
     V = oracle.simulate(cad, noise=False)
-    out, off = oracle.offsets(cad.uvw(), cad.freqs(), V, cad.sources(), cad.jones())
+    out, off = oracle.offsets(cad.uvw(), cad.freqs(), V, cad.sources(), cad.jones(), alpha=2.0)
     assert np.abs(off).max() < 1e-12
     assert out[0, 5] < 1e-20
 
 
-def test_offset_recovers_a_shifted_source_with_known_gains():
-    """A source observed 0.1 arcmin away from its catalogue position: one
-    Gauss-Newton step with the true gains returns the shift (first-order
-    accurate: relative error of the order of the shift's phase, here < 1 %)."""
+@pytest.mark.parametrize("alpha", [0.0, 2.0])
+def test_offset_recovers_a_shifted_source_with_known_gains(alpha):
+    """A source observed 0.1 arcmin from its catalogue position (scaled by
+    (nu_ref/nu)^alpha per channel): one Gauss-Newton step with the true gains
+    returns the shift (first-order accurate: error of the order of the shift's
+    phase, here < 1 %)."""
     cad = small(n_ant=16, n_chan=32, n_time=4, n_src=1, noise_sigma=0.0)
     cat = np.array([[0.12, -0.07, 4.0]])
     shift = np.array([2.0e-5, -3.0e-5])
-    true = cat.copy()
-    true[0, :2] += shift
     J = cad.jones()
-    V = oracle.predict(cad.uvw(), cad.freqs(), true, J)
-    _, off = oracle.offsets(cad.uvw(), cad.freqs(), V, cat, J)
+    nu_ref = 150e6
+    V = _predict_shifted(cad, cat, J, 0, shift[0], shift[1], alpha, nu_ref)
+    _, off = oracle.offsets(cad.uvw(), cad.freqs(), V, cat, J, alpha=alpha, nu_ref=nu_ref)
     np.testing.assert_allclose(off[0], shift, rtol=1e-2)
+
+
+def test_offset_statistics_add_over_channel_groups():
+    """The six numbers are sums over channels: two halves of the band add up to
+    the full band (what lets channel groups on different GPUs be combined)."""
+    cad = small(n_ant=8, n_chan=12, n_time=2, n_src=3, pos_sigma_rad=2e-4)
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0))
+    src, J, f = cad.perturbed_sources(), cad.jones(), cad.freqs()
+    full, _ = oracle.offsets(cad.uvw(), f, V, src, J, alpha=2.0, nu_ref=150e6)
+    lo, _ = oracle.offsets(cad.uvw(), f[:5], V[:, :, :5], src, J, alpha=2.0, nu_ref=150e6)
+    hi, _ = oracle.offsets(cad.uvw(), f[5:], V[:, :, 5:], src, J, alpha=2.0, nu_ref=150e6)
+    np.testing.assert_allclose(lo + hi, full, rtol=1e-12, atol=1e-12 * np.abs(full).max())
