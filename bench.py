@@ -13,8 +13,8 @@ Metric: source x visibility peel updates per second = K N_bl N_chan N_t / time.
 Extra legs in the same run: end to end through rts_peel_cadence_host (pinned
 host buffers, copies timed), the plain FP64 GPU path on the same input for a
 bounded number of sources, the adjoint step (config with 300 sources,
-perturbed positions; mixed and FP64 paths), and the FP64 CPU oracle on a
-bounded sample (the CPU baseline).
+perturbed positions; mixed and FP64 paths), the ionospheric offset step at the
+same shape, and the FP64 CPU oracle on a bounded sample (the CPU baseline).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -398,8 +398,8 @@ def main():
 
 
 def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate):
-    """One-source-per-pass path, FP64-path comparison, adjoint step, CPU baseline
-    (rank 0 at N=1 only)."""
+    """One-source-per-pass path, FP64-path comparison, adjoint step, ionospheric
+    offsets, CPU baseline (rank 0 at N=1 only)."""
     import numpy as np
     import torch
     from paper_1003_5575_gb300 import Peeler
@@ -513,6 +513,26 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate):
     }
     del v64
     pa64.close()
+
+    # ionospheric position offsets at the same shape (Section 3, 3.1): refraction law
+    # alpha = 2, the adjoint sweep with frequency-law weights + FP64 normal equations + 2x2 solves
+    nu_ref = float(np.mean(c5.freqs()))
+    pa.offsets(d_resid, J_fit, s_fit, alpha=2.0, nu_ref_hz=nu_ref)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(steps):
+        six, off = pa.offsets(d_resid, J_fit, s_fit, alpha=2.0, nu_ref_hz=nu_ref)
+    b.record()
+    torch.cuda.synchronize()
+    ms_off = a.elapsed_time(b) / steps
+    off_arcsec = off.abs().max(dim=1).values.cpu().numpy() * 180 / math.pi * 3600
+    out["offsets"] = {
+        "workload": "512 ant x 768 ch x 8 t, 300 sources, positions perturbed N(0, 1 arcmin^2); six numbers "
+                    "per source + (dl, dm) under the refraction law (nu_ref/nu)^2",
+        "ms_per_step": ms_off, "updates_per_s": c5.n_src * c5.n_vis / (ms_off / 1e3),
+        "nu_ref_hz": nu_ref, "median_max_abs_offset_arcsec": float(np.median(off_arcsec)),
+    }
     pa.close()
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1)

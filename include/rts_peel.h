@@ -184,6 +184,43 @@ int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d
                   const double* d_src, double* d_loss, void* d_gJ, double* d_gsrc,
                   void* stream);
 
+/* Ionospheric position offsets of the peeled sources (Section 3: each
+ * calibrator's fit also returns a shift of its apparent position caused by
+ * ionospheric refraction; Section 3.1: that fit needs six numbers per source
+ * and is described by two, the ionosphere's response is a known function of
+ * frequency, and workers send their numbers to a master that builds the
+ * solution).  Reading: the shift of source k at channel c is
+ * s_c (dl, dm) with s_c = (nu_ref/nu_c)^alpha (alpha = 2: refraction scales as
+ * lambda^2; alpha = 0: a frequency-independent shift), and the six numbers are
+ * the Gauss-Newton statistics of the loss L of rts_peel_grad at dl = dm = 0:
+ *   H_pq = 2 (2 pi)^2 sum_{t,bl,c} a_p a_q w_c^2 ||S_k J_i J_j^H||_F^2,
+ *   a_l = u - w l/n, a_m = v - w m/n, w_c = s_c nu_c / c,
+ *   g = (dL/d dl, dL/d dm),  (dl, dm) = -H^-1 g, or (0, 0) where det H <= 0.
+ * All six are sums over channels: GPUs holding different channel groups add
+ * their d_out arrays (one all-reduce of 6 doubles per source, with a common
+ * nu_ref) and call rts_offsets_solve on the sum.  The Jones matrices should be
+ * ones calibrated without the shift (for instance from a previous cadence):
+ * free per-antenna gains absorb most of a shift as antenna phase gradients.
+ *   d_vis      [n_time][n_bl][n_chan][4] (cube precision); d_jones [n_src][n_ant][4]
+ *   d_src      DEVICE double [n_src][3] (l, m, S)
+ *   alpha      finite; nu_ref_hz > 0 (ignored when alpha == 0)
+ *   d_out      device double [n_src][6] <- (H_ll, H_lm, H_mm, g_l, g_m, L)
+ *   d_offsets  device double [n_src][2] <- (dl, dm) from this call's channels
+ * n_src = 0 is a no-op; n_src > max_sources, a non-finite alpha or a bad
+ * nu_ref_hz give RTS_EINVAL.  H and the solve are FP64; g and L come from the
+ * adjoint sweep in the handle's precision.  The gradient workspace of
+ * rts_peel_grad is reused (plus n_chan doubles on the first call with
+ * alpha != 0). */
+int rts_peel_offsets(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d_jones,
+                     const double* d_src, double alpha, double nu_ref_hz, double* d_out,
+                     double* d_offsets, void* stream);
+/* (dl, dm) = -H^-1 g for each source from six numbers per source laid out as
+ * rts_peel_offsets writes them (d_out [n_src][6], device), into d_offsets
+ * [n_src][2] (device); (0, 0) where det H <= 0.  Needs no handle; errors
+ * (RTS_EINVAL for n_src < 0 or NULL pointers, RTS_ECUDA for a failed launch)
+ * are reported by the return code and rts_peel_last_error(NULL). */
+int rts_offsets_solve(const double* d_out, int32_t n_src, double* d_offsets, void* stream);
+
 /* Kernel timing and launch counts (the paper's Section 5 instruments every
  * kernel for bandwidth and FLOP counts; this is the same tracing hook).
  * Kernel classes, indices into the arrays below:                           */
@@ -196,6 +233,7 @@ int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d
 #define RTS_K_GRAD_REDUCE  6  /* adjoint reductions (per antenna / source / loss) */
 #define RTS_K_BLOCK_PASS   7  /* blocked peel: subtract block b + average block b+1 */
 #define RTS_K_BLOCK_FIX    8  /* blocked peel: in-block closed-form corrections, model matrices */
+#define RTS_K_OFFSETS      9  /* position-offset normal equations and solve */
 #define RTS_K_CLASSES     10
 /* enable != 0: clear the counters and start bracketing every kernel (group)
  * with CUDA events on its stream; enable == 0: stop recording.  Launch

@@ -9,13 +9,14 @@ from ._abi import (  # noqa: F401
     RTS_PREC_MIXED, RTS_PREC_FP64, RtsError, rts_peel_config,
     rts_peel_init, rts_peel_set_uvw, rts_peel_cadence, rts_peel_cadence_host, rts_peel_predict,
     rts_peel_rotate_average, rts_peel_solve, rts_peel_solve_noalloc, rts_peel_grad,
+    rts_peel_offsets, rts_offsets_solve,
     rts_peel_pipeline_submit, rts_peel_pipeline_wait, rts_peel_last_error, rts_peel_destroy,
     rts_peel_timing, rts_peel_timing_read, rts_host_alloc, rts_host_free, KERNEL_CLASSES, RTS_BLOCK,
 )
 
 
 def __getattr__(name):
-    if name in ("Peeler", "PeelLoss", "peel"):
+    if name in ("Peeler", "PeelLoss", "peel", "offsets_solve"):
         from . import peeler
         return getattr(peeler, name)
     raise AttributeError(name)

@@ -22,13 +22,15 @@ RTS_PREC_FP64 = 1
 
 RTS_K_AVERAGE, RTS_K_SUB_AVERAGE, RTS_K_SUBTRACT, RTS_K_SOLVE = 0, 1, 2, 3
 RTS_K_PREDICT, RTS_K_GRAD, RTS_K_GRAD_REDUCE, RTS_K_BLOCK_PASS, RTS_K_BLOCK_FIX = 4, 5, 6, 7, 8
+RTS_K_OFFSETS = 9
 RTS_K_CLASSES = 10
 RTS_BLOCK = 64
 KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "grad", "grad_reduce",
-                  "block_pass", "block_fix")
+                  "block_pass", "block_fix", "offsets")
 
 EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_cadence_host",
-           "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad",
+           "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad", "rts_peel_offsets",
+           "rts_offsets_solve",
            "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
            "rts_peel_timing", "rts_peel_timing_read", "rts_host_alloc", "rts_host_free",
            "rts_peel_last_error", "rts_peel_destroy")
@@ -89,6 +91,11 @@ def lib():
             L.rts_peel_pipeline_wait.argtypes = [_vp]
             L.rts_peel_grad.restype = ctypes.c_int
             L.rts_peel_grad.argtypes = [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.rts_peel_offsets.restype = ctypes.c_int
+            L.rts_peel_offsets.argtypes = [_vp, _vp, _i32, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                           _vp, _vp, _vp]
+            L.rts_offsets_solve.restype = ctypes.c_int
+            L.rts_offsets_solve.argtypes = [_vp, _i32, _vp, _vp]
             L.rts_peel_timing.restype = ctypes.c_int
             L.rts_peel_timing.argtypes = [_vp, _i32]
             L.rts_peel_timing_read.restype = ctypes.c_int
@@ -159,6 +166,15 @@ def rts_peel_pipeline_wait(h):
 
 def rts_peel_grad(h, d_vis, n_src, d_jones, d_src, d_loss, d_gJ, d_gsrc, stream):
     return _check(lib().rts_peel_grad(h, d_vis, n_src, d_jones, d_src, d_loss, d_gJ, d_gsrc, stream), h)
+
+
+def rts_peel_offsets(h, d_vis, n_src, d_jones, d_src, alpha, nu_ref_hz, d_out, d_offsets, stream):
+    return _check(lib().rts_peel_offsets(h, d_vis, n_src, d_jones, d_src, float(alpha), float(nu_ref_hz),
+                                         d_out, d_offsets, stream), h)
+
+
+def rts_offsets_solve(d_out, n_src, d_offsets, stream):
+    return _check(lib().rts_offsets_solve(d_out, n_src, d_offsets, stream), None)
 
 
 def rts_peel_timing(h, enable: int):

@@ -15,6 +15,9 @@
 // H0 = sum_c R e^{+i phi} and H1 = sum_c c R e^{+i phi}, from which
 // G += H0 and H^l += (u - w l/n)(nu_0/c H0 + dnu/c H1).  Per (source,
 // baseline) it stores G and the three scalar contributions (FP64).
+// With WEIGHTED the channel weight of the position derivative is a table
+// (d phi/d shift = a_p wchan[c], used by the offset fit's frequency law) and
+// H^l = (u - w l/n) sum_c wchan[c] R e^{+i phi}.
 // Kernels 2-4 reduce those per antenna / per source / for the loss in a fixed
 // order, so the result is deterministic (no atomics).
 #pragma once
@@ -38,6 +41,7 @@ struct GradWorkspace {
   double* gsc = nullptr;    // [K][n_bl][3] (dl, dm, dS contributions)
   double* loss_bl = nullptr;// [n_bl]
   DirQ* dir = nullptr;   // [K] (l, m, nm1, S)
+  double* wchan = nullptr;  // [n_chan] per-channel weight of the position derivative (offsets)
 };
 
 struct GradArgs {
@@ -47,6 +51,7 @@ struct GradArgs {
   const double* uvw;
   const int2* bl_ant;
   const double* freq_c;
+  const double* wchan;      // WEIGHTED: d phi / d(shift) = a_p wchan[c]; else a_p nu_c / c
   double2* G;
   double* gsc;
   double* loss_bl;
@@ -81,7 +86,7 @@ grad_phasor(unsigned long long A, unsigned long long B, double tau, const double
   }
 }
 
-template <bool MIXED>
+template <bool MIXED, bool WEIGHTED>
 __global__ void __launch_bounds__(kGradThreads) k_grad_sweep(GradArgs a) {
   using T = typename std::conditional<MIXED, float, double>::type;
   using C = typename cplx_of<T>::type;
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_sweep(GradArgs a) {
         for (int cl = my_g; cl < nc; cl += groups) {
           const int c = c0 + cl;
           C ph = grad_phasor<MIXED>(sA[k], sB[k], sTau[k], a.freq_c, c);
-          const T cw = (T)c;
+          const T cw = WEIGHTED ? (T)a.wchan[c] : (T)c;
           #pragma unroll
           for (int e = 0; e < 4; ++e) {
             C x = cmul(sR[cl * 4 + e], ph);
@@ -198,7 +203,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_sweep(GradArgs a) {
         const double wm = s_uvw[1] - s_uvw[2] * mk_n;
         #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const double hn = a.nu0_c * H0[e] + a.dnu_c * H1[e];
+          const double hn = WEIGHTED ? H1[e] : a.nu0_c * H0[e] + a.dnu_c * H1[e];
           G[e] += H0[e];
           Hl[e] += wl * hn;
           Hm[e] += wm * hn;
@@ -329,6 +334,7 @@ inline void grad_free(GradWorkspace& w) {
   if (w.gsc) cudaFree(w.gsc);
   if (w.loss_bl) cudaFree(w.loss_bl);
   if (w.dir) cudaFree(w.dir);
+  if (w.wchan) cudaFree(w.wchan);
   w = GradWorkspace();
 }
 
@@ -368,10 +374,11 @@ inline size_t grad_smem_bytes(bool mixed, int n_src) {
 inline int grad_sweep(GradWorkspace& w, bool mixed, const void* vis, int n_src, const void* jones,
                       const double* uvw, const int2* bl_ant, const double* freq_c, int n_ant,
                       int n_chan, int n_time, int64_t n_bl, double nu0_c, double dnu_c,
-                      cudaStream_t s, std::string& err) {
+                      cudaStream_t s, std::string& err, const double* wchan = nullptr) {
   cudaError_t e;
   GradArgs a;
   a.vis = vis; a.jones = jones; a.dir = w.dir; a.uvw = uvw; a.bl_ant = bl_ant; a.freq_c = freq_c;
+  a.wchan = wchan;
   a.G = w.G; a.gsc = w.gsc; a.loss_bl = w.loss_bl;
   a.n_src = n_src; a.n_ant = n_ant; a.n_chan = n_chan; a.n_time = n_time; a.n_bl = n_bl;
   a.nu0_c = nu0_c; a.dnu_c = dnu_c;
@@ -382,15 +389,14 @@ inline int grad_sweep(GradWorkspace& w, bool mixed, const void* vis, int n_src, 
     return -1;
   }
   const dim3 grid((unsigned)n_bl, (unsigned)chunks);
-  if (mixed) {
-    if ((e = cudaFuncSetAttribute(k_grad_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return grad_fail(err, e, "cudaFuncSetAttribute");
-    k_grad_sweep<true><<<grid, kGradThreads, smem, s>>>(a);
-  } else {
-    if ((e = cudaFuncSetAttribute(k_grad_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return grad_fail(err, e, "cudaFuncSetAttribute");
-    k_grad_sweep<false><<<grid, kGradThreads, smem, s>>>(a);
-  }
+  auto launch = [&](auto kernel) -> cudaError_t {
+    cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r == cudaSuccess) kernel<<<grid, kGradThreads, smem, s>>>(a);
+    return r;
+  };
+  if (mixed) e = wchan ? launch(k_grad_sweep<true, true>) : launch(k_grad_sweep<true, false>);
+  else e = wchan ? launch(k_grad_sweep<false, true>) : launch(k_grad_sweep<false, false>);
+  if (e != cudaSuccess) return grad_fail(err, e, "cudaFuncSetAttribute");
   if ((e = cudaGetLastError()) != cudaSuccess) return grad_fail(err, e, "gradient sweep launch");
   return 0;
 }

@@ -14,6 +14,7 @@
 #include "block_kernels.cuh"
 #include "common.cuh"
 #include "grad_kernels.cuh"
+#include "offset_kernels.cuh"
 #include "predict_kernels.cuh"
 #include "stream_kernels.cuh"
 
@@ -718,6 +719,64 @@ int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d
   rc = grad_reduce(h->grad, mixed, n_src, d_jones, d_loss, d_gJ, d_gsrc, h->n_ant, h->n_bl, s, h->err, &nl);
   span.end(nl);
   return rc;
+}
+
+int rts_peel_offsets(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d_jones,
+                     const double* d_src, double alpha, double nu_ref_hz, double* d_out,
+                     double* d_offsets, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (n_src < 0 || n_src > h->max_sources) return fail(h, RTS_EINVAL, "n_src must be in [0, max_sources]");
+  if (!std::isfinite(alpha)) return fail(h, RTS_EINVAL, "alpha must be finite");
+  if (alpha != 0.0 && !(nu_ref_hz > 0.0 && std::isfinite(nu_ref_hz)))
+    return fail(h, RTS_EINVAL, "nu_ref_hz must be positive and finite when alpha != 0");
+  if (n_src == 0) return RTS_OK;
+  if (!d_vis || !d_jones || !d_src || !d_out || !d_offsets)
+    return fail(h, RTS_EINVAL, "d_vis, d_jones, d_src, d_out and d_offsets are required");
+  cudaStream_t s = as_stream(stream);
+  const bool mixed = h->precision == RTS_PREC_MIXED;
+  int rc = grad_prepare(h->grad, n_src, d_src, h->n_bl, h->max_sources, s, h->err);
+  if (rc) return rc;
+  const double* wtab = h->d_freq_c;              // alpha = 0: w_c = nu_c / c
+  if (alpha != 0.0) {
+    if (!h->grad.wchan) RTS_CUDA(h, cudaMalloc(&h->grad.wchan, (size_t)h->n_chan * sizeof(double)));
+    Span span(h, RTS_K_OFFSETS, s);
+    k_offset_weights<<<(h->n_chan + 255) / 256, 256, 0, s>>>(h->d_freq_c, h->n_chan, alpha,
+                                                             nu_ref_hz / kCLight, h->grad.wchan);
+    span.end(1);
+    wtab = h->grad.wchan;
+  }
+  {
+    Span span(h, RTS_K_GRAD, s);
+    rc = grad_sweep(h->grad, mixed, d_vis, n_src, d_jones, h->d_uvw, h->d_bl_ant, h->d_freq_c,
+                    h->n_ant, h->n_chan, h->n_time, h->n_bl, h->nu0 / kCLight, h->dnu / kCLight, s,
+                    h->err, alpha != 0.0 ? wtab : nullptr);
+    span.end(1);
+    if (rc) return rc;
+  }
+  Span span(h, RTS_K_OFFSETS, s);
+  if (mixed)
+    k_offset_normal<float><<<n_src, kOffThreads, 0, s>>>(d_jones, h->grad.dir, h->d_uvw, h->d_bl_ant,
+                                                         wtab, h->grad.gsc, h->grad.loss_bl,
+                                                         h->n_ant, h->n_chan, h->n_time, h->n_bl,
+                                                         d_out, d_offsets);
+  else
+    k_offset_normal<double><<<n_src, kOffThreads, 0, s>>>(d_jones, h->grad.dir, h->d_uvw, h->d_bl_ant,
+                                                          wtab, h->grad.gsc, h->grad.loss_bl,
+                                                          h->n_ant, h->n_chan, h->n_time, h->n_bl,
+                                                          d_out, d_offsets);
+  RTS_CUDA(h, cudaGetLastError());
+  span.end(1);
+  return RTS_OK;
+}
+
+int rts_offsets_solve(const double* d_out, int32_t n_src, double* d_offsets, void* stream) {
+  if (n_src < 0) return fail(nullptr, RTS_EINVAL, "n_src must be >= 0");
+  if (n_src == 0) return RTS_OK;
+  if (!d_out || !d_offsets) return fail(nullptr, RTS_EINVAL, "d_out and d_offsets are required");
+  k_offset_solve<<<(n_src + 127) / 128, 128, 0, as_stream(stream)>>>(d_out, n_src, d_offsets);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, RTS_ECUDA, std::string("offset solve launch: ") + cudaGetErrorString(e));
+  return RTS_OK;
 }
 
 int rts_peel_timing(rts_peel_t* h, int32_t enable) {

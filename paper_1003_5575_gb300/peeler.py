@@ -44,6 +44,7 @@ class Peeler:
             raise ValueError("uvw must be [n_time][n_ant][3]")
         self.n_time, self.n_ant = int(uvw.shape[0]), int(uvw.shape[1])
         self.n_chan = int(freq.shape[0])
+        self.freq_hz = freq
         self.n_bl = self.n_ant * (self.n_ant - 1) // 2
         self.n_iter = int(n_iter)
         self.precision = precision
@@ -168,6 +169,32 @@ class Peeler:
                            _stream(stream))
         return loss, gJ, gs
 
+    def offsets(self, vis: torch.Tensor, jones: torch.Tensor, src: torch.Tensor, alpha: float = 0.0,
+                nu_ref_hz: float | None = None, stream=None):
+        """Ionospheric position offsets with the shift law (nu_ref/nu)^alpha:
+        (six numbers [K][6] = H_ll, H_lm, H_mm, dL/d dl, dL/d dm, L;
+        offsets [K][2] = -H^-1 g), float64 cuda tensors.  nu_ref defaults to the
+        band centre; channel groups that are combined must share it."""
+        self._check_cube(vis)
+        k = int(src.shape[0])
+        jones = jones.detach().to(device=self.device, dtype=self.cdtype).contiguous()
+        src = src.detach().to(device=self.device, dtype=torch.float64).contiguous()
+        nu_ref = float(np.mean(self.freq_hz)) if nu_ref_hz is None else float(nu_ref_hz)
+        out = torch.empty((k, 6), dtype=torch.float64, device=self.device)
+        off = torch.empty((k, 2), dtype=torch.float64, device=self.device)
+        _abi.rts_peel_offsets(self.h, _ptr(vis), k, _ptr(jones), _ptr(src), float(alpha), nu_ref,
+                              _ptr(out), _ptr(off), _stream(stream))
+        return out, off
+
+
+def offsets_solve(six: torch.Tensor, stream=None) -> torch.Tensor:
+    """(dl, dm) = -H^-1 g per source from summed six numbers [K][6] (cuda float64)."""
+    six = six.to(dtype=torch.float64).contiguous()
+    if not six.is_cuda:
+        raise ValueError("offsets_solve needs a cuda tensor")
+    off = torch.empty((six.shape[0], 2), dtype=torch.float64, device=six.device)
+    _abi.rts_offsets_solve(_ptr(six), int(six.shape[0]), _ptr(off), _stream(stream))
+    return off
 
 class PeelLoss(torch.autograd.Function):
     """L(J, l, m, S) = sum ||V - sum_k S_k J_i J_j^H exp(-2 pi i phi_k)||^2.

@@ -7,7 +7,10 @@ around the timed region, the slowest rank's time and the job total.
 
 For a cadence split by channel across GPUs, the one exchange per source would
 be a sum of the per-rank partial averages (each rank's samples-weighted mean
-over its channels); `combine_partial_averages` is that reduction.
+over its channels); `combine_partial_averages` is that reduction.  The
+ionospheric offset fit is the exchange the paper itself plans (Section 3.1:
+six numbers per source from every worker, two-number solution built
+centrally): `combine_offset_statistics` sums the six numbers over ranks.
 """
 from __future__ import annotations
 
@@ -55,3 +58,15 @@ def combine_partial_averages(partial: torch.Tensor, n_local: int, n_total: int) 
     if world()[1] > 1:
         dist.all_reduce(partial, op=dist.ReduceOp.SUM)
     return partial
+
+
+def combine_offset_statistics(six: torch.Tensor) -> torch.Tensor:
+    """Sum over ranks of the six numbers per source [K][6] (in place, returned).
+
+    Each rank holds a group of channels and gets (H_ll, H_lm, H_mm, g_l, g_m, L)
+    from Peeler.offsets with a common nu_ref; all six are sums over channels,
+    so their sum over ranks is the whole band's, ready for offsets_solve
+    (Section 3.1: workers send six numbers per source, the master solves for two)."""
+    if world()[1] > 1:
+        dist.all_reduce(six, op=dist.ReduceOp.SUM)
+    return six

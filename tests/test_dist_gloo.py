@@ -3,7 +3,9 @@
 * replicas: per-rank seeds differ, the job time is the slowest rank's and the
   job rate counts every rank's units;
 * channel sharding: per-rank partial averages over disjoint channel ranges,
-  combined by an all-reduce, equal the full-band average (FP64 oracle).
+  combined by an all-reduce, equal the full-band average (FP64 oracle);
+* the ionospheric offset exchange: per-rank six numbers per source over
+  disjoint channel ranges, summed by an all-reduce, equal the full band's.
 """
 import os
 import socket
@@ -85,3 +87,23 @@ def test_channel_sharded_partial_averages_allreduce_to_full_average():
     out = _spawn(_sharded_average)
     for err, scale in out.values():
         assert err <= 1e-13 * scale
+
+
+def _sharded_offsets(rank, world):
+    import oracle
+    from paper_1003_5575_gb300 import replicas
+    from synth import Cadence
+    cad = Cadence(8, 20, 2, 3, pos_sigma_rad=2e-4, seed=322)
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0))
+    src, J, f = cad.perturbed_sources(), cad.jones(), cad.freqs()
+    full, off_full = oracle.offsets(cad.uvw(), f, V, src, J, alpha=2.0, nu_ref=150e6)
+    lo, hi = rank * cad.n_chan // world, (rank + 1) * cad.n_chan // world
+    part, _ = oracle.offsets(cad.uvw(), f[lo:hi], V[:, :, lo:hi], src, J, alpha=2.0, nu_ref=150e6)
+    comb = replicas.combine_offset_statistics(torch.from_numpy(part.copy())).numpy()
+    return np.abs(comb - full).max(), np.abs(full).max()
+
+
+def test_offset_statistics_allreduce_to_full_band():
+    out = _spawn(_sharded_offsets)
+    for err, scale in out.values():
+        assert err <= 1e-12 * scale
