@@ -38,6 +38,7 @@ METRIC = "source×visibility peel updates/s (512 ant, 768 ch); adjoint step ms v
 UNIT = "updates/s"
 BYTES_PER_UPDATE = 64          # complex64 2x2 read + write per source x visibility
 FLOPS_PER_UPDATE = 32          # 2x2 complex times a complex phasor: 4 complex multiply-adds
+ADJ_FLOPS_PER_UPDATE = 80      # adjoint: model MACs 32 + R e^{+i phi} 24 + plain and channel-weighted sums 24
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -387,7 +388,8 @@ def main():
                 _abi.rts_host_free(hb)
 
     if not args.no_extra:
-        line.update(extra_legs(args, p, cad, d_vis, d_resid, src, rank, value / world))
+        line.update(extra_legs(args, p, cad, d_vis, d_resid, src, rank, value / world,
+                               clk.get("sm_mhz") or 2070.0))
 
     p.close()
     if rank == 0:
@@ -397,7 +399,7 @@ def main():
     return 0
 
 
-def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate):
+def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
     """One-source-per-pass path, FP64-path comparison, adjoint step, ionospheric
     offsets, CPU baseline (rank 0 at N=1 only)."""
     import numpy as np
@@ -505,9 +507,14 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate):
     ms_adj64 = a.elapsed_time(b)
     per_upd_mixed = ms_adj / (c5.n_src * c5.n_vis)
     per_upd_64 = ms_adj64 / (k_adj64 * c5.n_vis)
+    adj_tflops = ADJ_FLOPS_PER_UPDATE * c5.n_src * c5.n_vis / (ms_adj / 1e3) / 1e12
+    adj_peak = fp32_peak_tflops(sm_mhz)
     out["adjoint"] = {
         "workload": "512 ant x 768 ch x 8 t, 300 sources, positions perturbed N(0, 1 arcmin^2); loss + dL/d(J,l,m,S)",
         "ms_per_step": ms_adj, "loss": float(loss.item()),
+        "roofline": {"bound": "alu", "kernel": "k_grad_sweep<true,false> (+ reductions, in the step time)",
+                     "achieved": adj_tflops, "peak": adj_peak, "unit": "TFLOP/s", "frac": adj_tflops / adj_peak,
+                     "algorithmic_flops_per_update": ADJ_FLOPS_PER_UPDATE, "traffic": None},
         "fp64_ms_per_step_at_300_sources_extrapolated": per_upd_64 * c5.n_src * c5.n_vis,
         "fp64_sources_timed": k_adj64, "speedup_mixed_vs_fp64": per_upd_64 / per_upd_mixed,
     }
@@ -538,7 +545,7 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate):
     # CPU oracle baseline on a bounded sample (rank 0, N = 1)
     if rank == 0 and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         import oracle
-        oc, V = oracle_sample(n_chan=16, n_src=4)
+        oc, V = oracle_sample(n_chan=64, n_src=10)          # about 10 s of 16-core work
         val, dt = time_oracle(oc, V)
         out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                                "sample": (f"512 ant, 8 t, first {oc.n_chan} of 768 channels, {oc.n_src} "

@@ -33,6 +33,8 @@ readings used where the paper is silent:
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, replace
 
 import numpy as np
@@ -46,6 +48,8 @@ MWA_LAT_DEG = -26.703               # site latitude; not printed in the paper
 
 # stream identifiers (fixed order: positions, antennas, sources, Jones, noise)
 S_ANT, S_SRC, S_JONES, S_NOISE, S_POS = 1, 2, 3, 4, 5
+
+_CHUNK = 1 << 20     # noise elements per work item
 
 
 def splitmix64(seed: int, stream: int, idx) -> np.ndarray:
@@ -186,10 +190,34 @@ class Cadence:
         indices into the [n_time][n_bl][n_chan][4] cube (all of it if None)."""
         if index is None:
             index = np.arange(self.n_vis * 4, dtype=np.int64)
-        index = np.asarray(index, dtype=np.int64)
-        g_re = normals(self.seed, S_NOISE, 2 * index)
-        g_im = normals(self.seed, S_NOISE, 2 * index + 1)
-        return self.noise_sigma * (g_re + 1j * g_im)
+        index = np.asarray(index, dtype=np.int64).ravel()
+        # element i takes normals 2i (Re) and 2i+1 (Im): the cosine and sine of
+        # one Box-Muller pair (pair index i), the same values as normals() gives
+        out = np.empty(index.shape, np.complex128)
+        sigma = self.noise_sigma
+
+        def fill(a):
+            pair = index[a:a + _CHUNK].astype(np.uint64)
+            z1 = splitmix64(self.seed, S_NOISE, pair * np.uint64(2))
+            z2 = splitmix64(self.seed, S_NOISE, pair * np.uint64(2) + np.uint64(1))
+            u1 = ((z1 >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+            u2 = (z2 >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+            r = np.sqrt(-2.0 * np.log(u1))
+            ang = 2.0 * math.pi * u2
+            o = out[a:a + _CHUNK]
+            o.real = r * np.cos(ang)
+            o.imag = r * np.sin(ang)
+            o.real *= sigma
+            o.imag *= sigma
+
+        starts = range(0, index.size, _CHUNK)
+        if index.size > _CHUNK:
+            with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+                list(ex.map(fill, starts))
+        else:
+            for a in starts:
+                fill(a)
+        return out
 
 
 def noise_cube(cad: Cadence) -> np.ndarray:
