@@ -213,6 +213,8 @@ def main():
                     help="channels (768 = the workload; fewer only for small profiling cases)")
     ap.add_argument("--per-pass", type=int, default=0,
                     help="sources per streaming pass: 1, 64 (blocked) or 0 (library default)")
+    ap.add_argument("--block-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="blocked pass: 0 library choice, 1 FP32 FMA pass, 2 tensor-core pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / adjoint / CPU legs")
     args = ap.parse_args()
@@ -247,7 +249,7 @@ def main():
     K = cad.n_src
     log(f"[rank {rank}] building cadence: {cad.n_ant} ant, {cad.n_chan} ch, {cad.n_time} t, {K} sources")
     p = Peeler(cad.uvw(), cad.freqs(), n_iter=args.n_iter, precision="mixed", max_sources=K,
-               sources_per_pass=args.per_pass)
+               sources_per_pass=args.per_pass, block_kernel=args.block_kernel)
     J_true = torch.from_numpy(cad.jones().astype(np.complex64)).cuda()
     stream = torch.cuda.current_stream()
     d_vis = p.predict(src, J_true)

@@ -73,7 +73,15 @@ typedef struct rts_peel_config {
                            one pass per block of that many sources, the averages inside a
                            block corrected in closed form (same results); 0 = library
                            default (RTS_BLOCK) */
+  int32_t block_kernel;  /* blocked peel only: RTS_BLOCK_AUTO (0: the tensor-core pass when
+                           n_chan <= 960, else the FP32 pass), RTS_BLOCK_FMA (the FP32
+                           FMA pass), RTS_BLOCK_TENSOR (TF32 MMAs with split operands,
+                           FP32-level accuracy; n_chan <= 960, else RTS_EINVAL) */
 } rts_peel_config;
+
+#define RTS_BLOCK_AUTO   0
+#define RTS_BLOCK_FMA    1
+#define RTS_BLOCK_TENSOR 2
 
 #define RTS_BLOCK 64   /* default sources per streaming pass of the blocked peel */
 

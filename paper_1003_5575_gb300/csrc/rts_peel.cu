@@ -12,6 +12,7 @@
 
 #include "als_kernels.cuh"
 #include "block_kernels.cuh"
+#include "block_tc_kernels.cuh"
 #include "common.cuh"
 #include "grad_kernels.cuh"
 #include "offset_kernels.cuh"
@@ -23,6 +24,7 @@ using namespace rts;
 struct rts_peel_t {
   int n_ant = 0, n_chan = 0, n_time = 0, n_iter = 0, precision = 0, max_sources = 0;
   int per_pass = 1;                // sources per streaming pass (1 or RTS_BLOCK)
+  bool block_tc = false;           // blocked passes on the tensor cores (k_block_pass_tc)
   int64_t n_bl = 0;
   double nu0 = 0, dnu = 0;
   int device = 0;
@@ -268,6 +270,13 @@ int ensure_block_workspace(rts_peel_t* h) {
   RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_out, cudaEventDisableTiming));
   RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_src, cudaEventDisableTiming));
   RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_done, cudaEventDisableTiming));
+  if (h->block_tc) {
+    const int tsm = (int)tc_pass_smem(h->n_chan);
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    return RTS_OK;
+  }
   const int smem = (int)block_pass_smem(h);
   switch (BK) {
     case 8: return set_block_smem<8>(h, smem);
@@ -286,8 +295,16 @@ void block_pass_t(bool sub, bool acc, const BlockPassArgs& a, unsigned grid, siz
 
 int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a, cudaStream_t s) {
   Span span(h, RTS_K_BLOCK_PASS, s);
-  const size_t smem = block_pass_smem(h);
   const unsigned grid = (unsigned)h->n_bl;
+  if (h->block_tc) {
+    const size_t tsm = tc_pass_smem(h->n_chan);
+    if (sub && acc) k_block_pass_tc<true, true><<<grid, kTcThreads, tsm, s>>>(a, h->per_pass);
+    else if (sub) k_block_pass_tc<true, false><<<grid, kTcThreads, tsm, s>>>(a, h->per_pass);
+    else k_block_pass_tc<false, true><<<grid, kTcThreads, tsm, s>>>(a, h->per_pass);
+    span.end(1);
+    return check_launch(h, "block pass launch");
+  }
+  const size_t smem = block_pass_smem(h);
   switch (h->per_pass) {
     case 8: block_pass_t<8>(sub, acc, a, grid, smem, s); break;
     case 16: block_pass_t<16>(sub, acc, a, grid, smem, s); break;
@@ -454,9 +471,14 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   if (per_pass > 1 && (size_t)cfg->n_chan * 32 + 2048 + 32768 > 200 * 1024)
     return fail(nullptr, RTS_EINVAL, "the blocked peel needs n_chan*32 + 34 KB <= 200 KB of shared memory "
                                      "(n_chan <= 5300); use sources_per_pass = 1");
+  if (cfg->block_kernel < RTS_BLOCK_AUTO || cfg->block_kernel > RTS_BLOCK_TENSOR)
+    return fail(nullptr, RTS_EINVAL, "block_kernel must be RTS_BLOCK_AUTO, RTS_BLOCK_FMA or RTS_BLOCK_TENSOR");
+  if (cfg->block_kernel == RTS_BLOCK_TENSOR && cfg->n_chan > kTcMaxChan)
+    return fail(nullptr, RTS_EINVAL, "the tensor-core blocked pass needs n_chan <= 960");
 
   rts_peel_t* h = new rts_peel_t();
   h->per_pass = per_pass;
+  h->block_tc = per_pass > 1 && cfg->block_kernel != RTS_BLOCK_FMA && cfg->n_chan <= kTcMaxChan;
   h->n_ant = cfg->n_ant; h->n_chan = cfg->n_chan; h->n_time = cfg->n_time;
   h->n_iter = cfg->n_iter; h->precision = cfg->precision; h->max_sources = cfg->max_sources;
   h->n_bl = n_bl; h->nu0 = nu0; h->dnu = dnu;

@@ -102,8 +102,9 @@ def test_fullsize_single_source_recovered_exactly(full):
     del one, resid
 
 
-@pytest.mark.parametrize("per_pass", [1, 16, 64], ids=["one-source-per-pass", "blocks-of-16", "blocks-of-64"])
-def test_fullsize_peel_residual_plus_model_is_input(full, per_pass):
+@pytest.mark.parametrize("per_pass,kernel", [(1, 0), (16, 1), (64, 1), (64, 2)],
+                         ids=["one-source-per-pass", "blocks-of-16-fma", "blocks-of-64-fma", "blocks-of-64-tensor"])
+def test_fullsize_peel_residual_plus_model_is_input(full, per_pass, kernel):
     """1000 sources: residual + prediction of the solved sources = input.
 
     The residual is stored in FP32 after each of the 1000 sequential
@@ -113,7 +114,7 @@ def test_fullsize_peel_residual_plus_model_is_input(full, per_pass):
     from paper_1003_5575_gb300 import Peeler
     cad, p0, vis, J = full
     p = Peeler(cad.uvw(), cad.freqs(), n_iter=20, precision="mixed", max_sources=cad.n_src,
-               sources_per_pass=per_pass)
+               sources_per_pass=per_pass, block_kernel=kernel)
     resid, jones, st = p.cadence(vis, cad.sources())
     assert set(np.unique(st).tolist()) <= {0, 1}
     model = p.predict(cad.sources(), jones)

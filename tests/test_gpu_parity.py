@@ -58,10 +58,11 @@ def oracle_case(cad, n_iter=20):
     return _cache[key]
 
 
-def make_peeler(cad, prec, n_iter=20, max_sources=None, per_pass=0):
+def make_peeler(cad, prec, n_iter=20, max_sources=None, per_pass=0, block_kernel=0):
     from paper_1003_5575_gb300 import Peeler
     return Peeler(cad.uvw(), cad.freqs(), n_iter=n_iter, precision=prec,
-                  max_sources=max_sources or max(cad.n_src, 1), sources_per_pass=per_pass)
+                  max_sources=max_sources or max(cad.n_src, 1), sources_per_pass=per_pass,
+                  block_kernel=block_kernel)
 
 
 # ---------------------------------------------------------------------------
@@ -114,15 +115,20 @@ BLOCK_CASES = [
     ("wide-block64", Cadence(64, 384, 4, 150, freq0_hz=167e6, seed=98), 64),   # 64, 64, 22
     ("cfg1-blocked", config(1, precision="mixed"), 16),             # 5 sources, 16 channels
     ("ragged-blocked", Cadence(9, 37, 3, 4, seed=91), 8),           # 37 channels, ragged tiles
+    ("max-channels", Cadence(8, 960, 2, 5, freq0_hz=167e6, seed=99), 64),    # largest tensor-core strip
+    ("odd-channels", Cadence(12, 203, 3, 9, seed=97), 64),          # ragged 16-channel row tiles
 ]
+KERNELS = [(1, "fma"), (2, "tensor")]
 
 
+@pytest.mark.parametrize("kernel", [k for k, _ in KERNELS], ids=[n for _, n in KERNELS])
 @pytest.mark.parametrize("name,cad,per_pass", BLOCK_CASES, ids=[c[0] for c in BLOCK_CASES])
-def test_blocked_peel_matches_sequential_oracle(name, cad, per_pass):
+def test_blocked_peel_matches_sequential_oracle(name, cad, per_pass, kernel):
     """One HBM pass per block of RTS_BLOCK sources with in-block closed-form
-    corrections: the same results as the oracle's one-source-at-a-time peel."""
+    corrections, with the FP32 FMA pass or the tensor-core pass: the same
+    results as the oracle's one-source-at-a-time peel."""
     V, R_ref, J_ref, st_ref = oracle_case(cad)
-    p = make_peeler(cad, "mixed", per_pass=per_pass)
+    p = make_peeler(cad, "mixed", per_pass=per_pass, block_kernel=kernel)
     vis = to_dev(V, "mixed")
     resid, jones, st = p.cadence(vis, cad.sources())
     torch.cuda.synchronize()
@@ -368,3 +374,20 @@ def test_pipelined_host_cadences_equal_device_cadences():
         for b in bufs:
             _abi.rts_host_free(b)
         p.close()
+
+
+def test_tensor_pass_channel_limit():
+    """The tensor-core pass holds a strip of up to 960 channels: above that the
+    automatic choice is the FP32 pass (same results), an explicit request fails."""
+    from paper_1003_5575_gb300 import RtsError, RTS_EINVAL
+    cad = Cadence(6, 976, 2, 3, freq0_hz=150e6, seed=96)
+    with pytest.raises(RtsError) as e:
+        make_peeler(cad, "mixed", per_pass=64, block_kernel=2)
+    assert e.value.code == RTS_EINVAL
+    V, R_ref, J_ref, _ = oracle_case(cad)
+    p = make_peeler(cad, "mixed", per_pass=64)
+    resid, jones, _ = p.cadence(to_dev(V, "mixed"), cad.sources())
+    torch.cuda.synchronize()
+    assert np.abs(resid.cpu().numpy() - R_ref).max() <= TOL["mixed"] * rms_of(V)
+    assert jones_rel(jones.cpu().numpy(), J_ref) <= TOL["mixed"]
+    p.close()
