@@ -77,7 +77,20 @@ typedef struct rts_peel_config {
                            n_chan <= 960, else the FP32 pass), RTS_BLOCK_FMA (the FP32
                            FMA pass), RTS_BLOCK_TENSOR (TF32 MMAs with split operands,
                            FP32-level accuracy; n_chan <= 960, else RTS_EINVAL) */
+  int32_t solve_kernel;  /* blocked peel only: RTS_SOLVE_AUTO (0: the corrected averages,
+                           ALS sweeps and model matrices of a whole block in one
+                           cooperative launch whose CTAs meet at grid-wide barriers, when
+                           the device supports cooperative launches and the rows of
+                           ceil(n_ant / n_SM) antennas fit in shared memory, about
+                           n_ant <= 900 on GB300; otherwise as RTS_SOLVE_LAUNCHES),
+                           RTS_SOLVE_LAUNCHES (1: one launch per ALS sweep, per
+                           correction and per model step).  Same arithmetic except
+                           the grouping of the FP32 partial sums of the normal
+                           equations (FP32-rounding-level differences). */
 } rts_peel_config;
+
+#define RTS_SOLVE_AUTO     0
+#define RTS_SOLVE_LAUNCHES 1
 
 #define RTS_BLOCK_AUTO   0
 #define RTS_BLOCK_FMA    1

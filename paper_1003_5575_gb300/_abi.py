@@ -26,6 +26,7 @@ RTS_K_OFFSETS = 9
 RTS_K_CLASSES = 10
 RTS_BLOCK = 64
 RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR = 0, 1, 2
+RTS_SOLVE_AUTO, RTS_SOLVE_LAUNCHES = 0, 1
 KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "grad", "grad_reduce",
                   "block_pass", "block_fix", "offsets")
 
@@ -43,7 +44,8 @@ class rts_peel_config(ctypes.Structure):
                 ("max_sources", ctypes.c_int32),
                 ("uvw", ctypes.POINTER(ctypes.c_double)),
                 ("freq_hz", ctypes.POINTER(ctypes.c_double)),
-                ("sources_per_pass", ctypes.c_int32), ("block_kernel", ctypes.c_int32)]
+                ("sources_per_pass", ctypes.c_int32), ("block_kernel", ctypes.c_int32),
+                ("solve_kernel", ctypes.c_int32)]
 
 
 class RtsError(RuntimeError):

@@ -17,6 +17,7 @@
 #include "grad_kernels.cuh"
 #include "offset_kernels.cuh"
 #include "predict_kernels.cuh"
+#include "solve_kernels.cuh"
 #include "stream_kernels.cuh"
 
 using namespace rts;
@@ -52,6 +53,13 @@ struct rts_peel_t {
   float2* b_dir[kRing] = {};       // [n_bl][BK(BK-1)/2] in-block closed-form averages D_jk
   float2* b_avg = nullptr;         // [BK][n_bl][4] plain averages of a block
   float2* b_model = nullptr;       // [BK][n_bl][4] model matrices of a block
+  // persistent block solve (k_block_solve, one cooperative launch per block)
+  int solve_kernel = RTS_SOLVE_AUTO;
+  bool bs_ok = false;              // set up and fits (shared memory, cooperative launch)
+  int bs_grid = 0, bs_apc = 0;
+  size_t bs_smem = 0;
+  unsigned* b_sync = nullptr;      // [2] barrier counter, abort flag
+  double* b_part = nullptr;        // [bs_grid][3] per-CTA convergence sums
   cudaStream_t b_main = nullptr;   // high-priority stream for passes, corrections and solves
   cudaStream_t b_prep = nullptr;   // low-priority geometry stream
   cudaEvent_t b_ev_in = nullptr;   // caller's stream -> main
@@ -204,6 +212,9 @@ int read_status(rts_peel_t* h, int32_t n, int32_t* h_status, cudaStream_t s) {
   RTS_CUDA(h, cudaMemcpyAsync(h_status, h->d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
   RTS_CUDA(h, cudaStreamSynchronize(s));
   for (int k = 0; k < n; ++k)
+    if (h_status[k] == kSolveStatusTimeout)
+      return fail(h, RTS_ECUDA, "a grid barrier of the block solve timed out at source " + std::to_string(k));
+  for (int k = 0; k < n; ++k)
     if (h_status[k] == RTS_ENONFINITE)
       return fail(h, RTS_ENONFINITE, "non-finite value in the solve of source " + std::to_string(k));
   return RTS_OK;
@@ -249,6 +260,8 @@ int set_block_smem(rts_peel_t* h, int smem) {
   return RTS_OK;
 }
 
+int setup_block_solve(rts_peel_t* h);
+
 int ensure_block_workspace(rts_peel_t* h) {
   if (h->b_avg) return RTS_OK;
   const int BK = h->per_pass;
@@ -270,6 +283,8 @@ int ensure_block_workspace(rts_peel_t* h) {
   RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_out, cudaEventDisableTiming));
   RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_src, cudaEventDisableTiming));
   RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_done, cudaEventDisableTiming));
+  int rc = setup_block_solve(h);
+  if (rc) return rc;
   if (h->block_tc) {
     const int tsm = (int)tc_pass_smem(h->n_chan);
     RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
@@ -284,6 +299,57 @@ int ensure_block_workspace(rts_peel_t* h) {
     case 32: return set_block_smem<32>(h, smem);
     default: return set_block_smem<64>(h, smem);
   }
+}
+
+// geometry of the persistent block solve: one CTA per SM at most (fewer for
+// small arrays), the rows of ceil(n_ant / G) antennas per CTA in shared memory.
+// Leaves bs_ok false (the per-sweep launches are used) when the device has no
+// cooperative launch or the rows do not fit.
+int setup_block_solve(rts_peel_t* h) {
+  if (h->solve_kernel != RTS_SOLVE_AUTO) return RTS_OK;
+  int coop = 0, n_sm = 0, smem_max = 0;
+  RTS_CUDA(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+  RTS_CUDA(h, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device));
+  RTS_CUDA(h, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  if (!coop || n_sm < 1) return RTS_OK;
+  const int64_t want = std::max<int64_t>(h->n_ant, (h->n_bl + kSolveThreads - 1) / kSolveThreads);
+  const int G = (int)std::min<int64_t>(n_sm, want);
+  const int apc = (h->n_ant + G - 1) / G;
+  const size_t smem = block_solve_smem(h->n_ant, apc);
+  if (smem + 1024 > (size_t)smem_max) return RTS_OK;
+  RTS_CUDA(h, cudaFuncSetAttribute(k_block_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  RTS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_block_solve, kSolveThreads, smem));
+  if (occ < 1) return RTS_OK;
+  RTS_CUDA(h, cudaMalloc((void**)&h->b_sync, 2 * sizeof(unsigned)));
+  RTS_CUDA(h, cudaMalloc((void**)&h->b_part, (size_t)G * 3 * sizeof(double)));
+  h->bs_grid = G;
+  h->bs_apc = apc;
+  h->bs_smem = smem;
+  h->bs_ok = true;
+  return RTS_OK;
+}
+
+// the solve chain of sources s0 .. s0 + nblk - 1 (corrected averages, ALS,
+// model matrices) as one cooperative launch
+int launch_block_solve(rts_peel_t* h, int s0, int nblk, const float2* Dt, void* d_jones, cudaStream_t s) {
+  Span span(h, RTS_K_SOLVE, s);
+  BlockSolveArgs a;
+  a.Ablk = h->b_avg; a.Dtab = Dt; a.n_pairs = h->per_pass * (h->per_pass - 1) / 2;
+  a.src = h->d_src; a.s0 = s0; a.n_blk = nblk;
+  a.bl_ant = h->d_bl_ant; a.n_ant = h->n_ant; a.n_bl = h->n_bl; a.n_iter = h->n_iter;
+  a.apc = h->bs_apc;
+  a.avg = static_cast<float2*>(h->d_avg); a.M = h->b_model; a.J64 = h->d_J[0];
+  a.Jf[0] = h->d_Jf[0]; a.Jf[1] = h->d_Jf[1];
+  a.part = h->b_part; a.status = h->d_status; a.rel = h->d_rel;
+  a.jones = static_cast<float2*>(d_jones);
+  a.sync = h->b_sync;
+  RTS_CUDA(h, cudaMemsetAsync(h->b_sync, 0, 2 * sizeof(unsigned), s));
+  void* args[] = {&a};
+  RTS_CUDA(h, cudaLaunchCooperativeKernel((const void*)k_block_solve, dim3(h->bs_grid), dim3(kSolveThreads), args,
+                                          h->bs_smem, s));
+  span.end(1);
+  return check_launch(h, "block solve launch");
 }
 
 template <int BK>
@@ -353,7 +419,11 @@ int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
   for (int b = 0; b < nb; ++b) {
     const int s0 = b * BK, nblk = std::min(BK, (int)n_src - s0);
     const float2* Dt = h->b_dir[b % R];
-    for (int q = 0; q < nblk; ++q) {
+    if (h->bs_ok) {
+      rc = launch_block_solve(h, s0, nblk, Dt, d_jones, s);
+      if (rc) return rc;
+    }
+    for (int q = 0; q < nblk && !h->bs_ok; ++q) {
       const int k = s0 + q;
       {
         Span span(h, RTS_K_BLOCK_FIX, s);
@@ -367,7 +437,7 @@ int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
       rc = launch_als(h, h->d_avg, h_src[3 * k + 2], static_cast<char*>(d_jones) + k * jstride, k, s);
       if (rc) return rc;
     }
-    {
+    if (!h->bs_ok) {
       Span span(h, RTS_K_BLOCK_FIX, s);
       k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (s0 + nblk - 1) + 2], h->d_bl_ant,
                                              h->n_bl, h->b_model + (size_t)(nblk - 1) * h->n_bl * 4);
@@ -476,8 +546,12 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   if (cfg->block_kernel == RTS_BLOCK_TENSOR && cfg->n_chan > kTcMaxChan)
     return fail(nullptr, RTS_EINVAL, "the tensor-core blocked pass needs n_chan <= 960");
 
+  if (cfg->solve_kernel != RTS_SOLVE_AUTO && cfg->solve_kernel != RTS_SOLVE_LAUNCHES)
+    return fail(nullptr, RTS_EINVAL, "solve_kernel must be RTS_SOLVE_AUTO or RTS_SOLVE_LAUNCHES");
+
   rts_peel_t* h = new rts_peel_t();
   h->per_pass = per_pass;
+  h->solve_kernel = cfg->solve_kernel;
   h->block_tc = per_pass > 1 && cfg->block_kernel != RTS_BLOCK_FMA && cfg->n_chan <= kTcMaxChan;
   h->n_ant = cfg->n_ant; h->n_chan = cfg->n_chan; h->n_time = cfg->n_time;
   h->n_iter = cfg->n_iter; h->precision = cfg->precision; h->max_sources = cfg->max_sources;
@@ -858,7 +932,7 @@ void rts_peel_destroy(rts_peel_t* h) {
   if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
   void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
                   h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage,
-                  h->b_avg, h->b_model};
+                  h->b_avg, h->b_model, h->b_sync, h->b_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int r = 0; r < rts_peel_t::kRing; ++r) {

@@ -44,7 +44,8 @@ def test_library_exports_every_declared_symbol(abi):
     assert set(abi.EXPORTS) == declared_symbols()
 
 
-def _cfg(abi, n_ant=8, n_chan=16, n_time=2, n_iter=20, precision=0, max_sources=4, freq=None, uvw=None):
+def _cfg(abi, n_ant=8, n_chan=16, n_time=2, n_iter=20, precision=0, max_sources=4, freq=None, uvw=None,
+         **fields):
     uvw = np.zeros((n_time, max(n_ant, 1), 3)) if uvw is None else uvw
     freq = 150e6 + 40e3 * np.arange(max(n_chan, 1)) if freq is None else freq
     cfg = abi.rts_peel_config()
@@ -53,6 +54,8 @@ def _cfg(abi, n_ant=8, n_chan=16, n_time=2, n_iter=20, precision=0, max_sources=
     dp = ctypes.POINTER(ctypes.c_double)
     cfg.uvw = uvw.ctypes.data_as(dp) if uvw is not False else None
     cfg.freq_hz = freq.ctypes.data_as(dp)
+    for k, v in fields.items():
+        setattr(cfg, k, v)
     return cfg, (uvw, freq)
 
 
@@ -66,6 +69,9 @@ def _cfg(abi, n_ant=8, n_chan=16, n_time=2, n_iter=20, precision=0, max_sources=
     (dict(freq=150e6 + 40e3 * np.arange(16) ** 1.01), "uniformly"),
     (dict(freq=np.full(16, -1.0)), "frequencies"),
     (dict(uvw=np.full((2, 8, 3), np.nan)), "non-finite"),
+    (dict(sources_per_pass=3), "sources_per_pass"),
+    (dict(sources_per_pass=64, block_kernel=5), "block_kernel"),
+    (dict(sources_per_pass=64, solve_kernel=7), "solve_kernel"),
 ])
 def test_init_rejects_bad_config_on_host(abi, kw, needle):
     cfg, keep = _cfg(abi, **kw)

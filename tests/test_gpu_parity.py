@@ -58,11 +58,11 @@ def oracle_case(cad, n_iter=20):
     return _cache[key]
 
 
-def make_peeler(cad, prec, n_iter=20, max_sources=None, per_pass=0, block_kernel=0):
+def make_peeler(cad, prec, n_iter=20, max_sources=None, per_pass=0, block_kernel=0, solve_kernel=0):
     from paper_1003_5575_gb300 import Peeler
     return Peeler(cad.uvw(), cad.freqs(), n_iter=n_iter, precision=prec,
                   max_sources=max_sources or max(cad.n_src, 1), sources_per_pass=per_pass,
-                  block_kernel=block_kernel)
+                  block_kernel=block_kernel, solve_kernel=solve_kernel)
 
 
 # ---------------------------------------------------------------------------
@@ -118,17 +118,20 @@ BLOCK_CASES = [
     ("max-channels", Cadence(8, 960, 2, 5, freq0_hz=167e6, seed=99), 64),    # largest tensor-core strip
     ("odd-channels", Cadence(12, 203, 3, 9, seed=97), 64),          # ragged 16-channel row tiles
 ]
-KERNELS = [(1, "fma"), (2, "tensor")]
+# (pass kernel, solve kernel): FP32 FMA or tensor-core pass; the block's solve
+# chain as one cooperative launch (0) or as one launch per step (1)
+KERNELS = [((1, 0), "fma"), ((2, 0), "tensor"), ((2, 1), "tensor-launches")]
 
 
 @pytest.mark.parametrize("kernel", [k for k, _ in KERNELS], ids=[n for _, n in KERNELS])
 @pytest.mark.parametrize("name,cad,per_pass", BLOCK_CASES, ids=[c[0] for c in BLOCK_CASES])
 def test_blocked_peel_matches_sequential_oracle(name, cad, per_pass, kernel):
     """One HBM pass per block of RTS_BLOCK sources with in-block closed-form
-    corrections, with the FP32 FMA pass or the tensor-core pass: the same
-    results as the oracle's one-source-at-a-time peel."""
+    corrections, with the FP32 FMA pass or the tensor-core pass, and the solve
+    chain of a block in one cooperative launch or in one launch per step: the
+    same results as the oracle's one-source-at-a-time peel."""
     V, R_ref, J_ref, st_ref = oracle_case(cad)
-    p = make_peeler(cad, "mixed", per_pass=per_pass, block_kernel=kernel)
+    p = make_peeler(cad, "mixed", per_pass=per_pass, block_kernel=kernel[0], solve_kernel=kernel[1])
     vis = to_dev(V, "mixed")
     resid, jones, st = p.cadence(vis, cad.sources())
     torch.cuda.synchronize()
@@ -391,3 +394,25 @@ def test_tensor_pass_channel_limit():
     assert np.abs(resid.cpu().numpy() - R_ref).max() <= TOL["mixed"] * rms_of(V)
     assert jones_rel(jones.cpu().numpy(), J_ref) <= TOL["mixed"]
     p.close()
+
+
+def test_persistent_solve_equals_per_step_launches():
+    """The cooperative block solve and the per-step launches compute the same
+    corrected averages, sweeps and model matrices; only the grouping of the FP32
+    partial sums of the normal equations differs, so Jones matrices and
+    residuals agree to FP32 rounding (far inside the oracle tolerance)."""
+    cad = Cadence(64, 384, 4, 150, freq0_hz=167e6, seed=98)
+    V = oracle.simulate(cad)
+    vis = to_dev(V, "mixed")
+    out = []
+    for solve in (0, 1):
+        p = make_peeler(cad, "mixed", per_pass=64, block_kernel=2, solve_kernel=solve)
+        r, j, st = p.cadence(vis, cad.sources())
+        torch.cuda.synchronize()
+        out.append((r.cpu().numpy(), j.cpu().numpy(), st))
+        p.close()
+    (r0, j0, s0), (r1, j1, s1) = out
+    assert jones_rel(j0, j1) <= 3e-6
+    assert np.abs(r0 - r1).max() <= 3e-6 * rms_of(V)
+    assert np.mean(s0 == s1) >= 0.95
+
