@@ -316,7 +316,9 @@ int setup_block_solve(rts_peel_t* h) {
   const int G = (int)std::min<int64_t>(n_sm, want);
   const int apc = (h->n_ant + G - 1) / G;
   const size_t smem = block_solve_smem(h->n_ant, apc);
-  if (smem + 1024 > (size_t)smem_max) return RTS_OK;
+  cudaFuncAttributes fa;
+  RTS_CUDA(h, cudaFuncGetAttributes(&fa, k_block_solve));
+  if (smem + fa.sharedSizeBytes + 1024 > (size_t)smem_max) return RTS_OK;
   RTS_CUDA(h, cudaFuncSetAttribute(k_block_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   RTS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_block_solve, kSolveThreads, smem));
@@ -339,7 +341,7 @@ int launch_block_solve(rts_peel_t* h, int s0, int nblk, const float2* Dt, void* 
   a.src = h->d_src; a.s0 = s0; a.n_blk = nblk;
   a.bl_ant = h->d_bl_ant; a.n_ant = h->n_ant; a.n_bl = h->n_bl; a.n_iter = h->n_iter;
   a.apc = h->bs_apc;
-  a.avg = static_cast<float2*>(h->d_avg); a.M = h->b_model; a.J64 = h->d_J[0];
+  a.avg = static_cast<float2*>(h->d_avg); a.M = h->b_model;
   a.Jf[0] = h->d_Jf[0]; a.Jf[1] = h->d_Jf[1];
   a.part = h->b_part; a.status = h->d_status; a.rel = h->d_rel;
   a.jones = static_cast<float2*>(d_jones);

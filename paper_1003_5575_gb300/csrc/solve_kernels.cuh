@@ -12,16 +12,23 @@
 //
 // Work split (G CTAs of kSolveThreads threads, G <= number of SMs):
 //   per baseline, grid-stride over all threads: the model matrix of source
-//     q-1 and the corrected average of source q, with the arithmetic of
-//     k_block_model and k_block_correct (same values);
-//   per antenna, one warp: antenna p belongs to CTA p % G (slot p / G).  Its
-//     row V_pq, q = 0..n_ant-1 (V_qp = V_pq^H applied while staging, V_pp = 0),
-//     is staged in shared memory once per source, and every sweep stages the
-//     FP32 iterate of all antennas.  Lane l takes q = l, l + 32, ...: the
-//     products and each lane's partial sums are FP32, the sum over the 32
-//     lanes is FP64 (one reduce-scatter per warp), and the 2x2 solve is FP64,
-//     as in k_als_sweep (which splits an antenna over 128 threads; one warp
-//     per antenna here quarters the FP64 additions, which are slow on GB300).
+//     q-1 (FP32, from the FP32 copy of its solution) and the corrected
+//     average of source q (the arithmetic of k_block_correct);
+//   per antenna: antenna p belongs to CTA p % G (slot p / G).  Its row V_pq,
+//     q = 0..n_ant-1 (V_qp = V_pq^H applied while staging, V_pp = 0), is staged
+//     in shared memory once per source, and every sweep stages the FP32
+//     iterate of all antennas.  Slots go in quads, a quad to four warps: lane
+//     l of warp w of the quad takes slot l >> 3 of the quad and q = (l & 7) +
+//     8 w + 32 u.  Products and per-lane partial sums are FP32 (at most
+//     ceil(n_ant / 32) terms each), the four warps' partials of a lane position
+//     are added in FP32, the sum over the 8 lane positions of an antenna is
+//     FP64, and the 2x2 solve is FP64.
+//
+// FP64 arithmetic runs at 1/64 of the FP32 rate on GB300 and a warp
+// instruction costs the same with 4 or 32 lanes active, so the FP64 part is
+// packed: one reduce-scatter over 8-lane groups and one solve for the four
+// antennas of a quad (16 lanes), 26 + ~40 FP64 warp instructions per quad and
+// sweep (k_als_sweep spends about 150 per antenna).
 //
 // Barriers spin on a global counter with a time limit: a CTA whose wait runs
 // out raises the abort flag, marks the current source's status
@@ -53,7 +60,6 @@ struct BlockSolveArgs {
   int apc;                 // antenna slots per CTA: ceil(n_ant / G)
   float2* avg;             // [n_bl][4] corrected average of the current source
   float2* M;               // [BK][n_bl][4] model matrices of the block (written)
-  double2* J64;            // [n_ant][4] FP64 solution of the current source
   float2* Jf[2];           // [n_ant][4] FP32 iterates (sweep it writes Jf[it & 1])
   double* part;            // [G][3] per-CTA sums of the last sweep: dn, nn, non-finite
   int* status;             // [n_src] per source: 0, 1 (not converged), -4, kSolveStatusTimeout
@@ -63,10 +69,26 @@ struct BlockSolveArgs {
 };
 
 // dynamic shared memory: rows [apc][n_ant][4] float2, iterate [n_ant][4] float2,
-// previous FP64 iterate of the CTA's antennas [apc][4] double2
+// previous FP64 iterate of the CTA's antennas [apc][4] double2, per-slot
+// convergence sums [apc][3] double, FP64 totals [apc][16] double
 inline size_t block_solve_smem(int n_ant, int apc) {
   return (size_t)apc * n_ant * 4 * sizeof(float2) + (size_t)n_ant * 4 * sizeof(float2) +
-         (size_t)apc * 4 * sizeof(double2);
+         (size_t)apc * 4 * sizeof(double2) + (size_t)apc * 3 * sizeof(double) + (size_t)apc * 16 * sizeof(double);
+}
+
+// Sum 16 doubles over the 8 lanes of a lane group (lanes 8i .. 8i+7): lane j of
+// the group ends with the group totals of values 2j and 2j + 1 in v[0], v[1].
+__device__ inline void group8_reduce_scatter16(double (&v)[16], int lane) {
+  #pragma unroll
+  for (int o = 4, n = 16; o >= 1; o >>= 1, n >>= 1) {
+    const bool upper = (lane & o) != 0;
+    #pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const double send = upper ? v[i] : v[i + n / 2];
+      const double keep = upper ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -86,8 +108,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ bool solve_barrier(unsigned* sync, unsigned n, int* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(sync, 1u);
+    // release: this CTA's writes (ordered before by the CTA barrier) are
+    // visible to every CTA whose acquire load sees the count
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(sync) : "memory");
     const unsigned target = n * gridDim.x;
     int ok = 1;
     const unsigned long long t0 = global_ns();
@@ -101,7 +124,6 @@ __device__ bool solve_barrier(unsigned* sync, unsigned n, int* s_flag) {
         }
       }
     }
-    __threadfence();
     *s_flag = ok;
   }
   __syncthreads();
@@ -115,34 +137,39 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
   float2* rows = reinterpret_cast<float2*>(solve_smem);                 // [apc][n_ant][4]
   float2* Js = rows + (size_t)a.apc * a.n_ant * 4;                       // [n_ant][4]
   double2* Jold = reinterpret_cast<double2*>(Js + (size_t)a.n_ant * 4);  // [apc][4]
-  __shared__ double s_wpart[kSolveWarps][3];
-  __shared__ double s_tot[kSolveWarps][12];
+  double* s_norm = reinterpret_cast<double*>(Jold + (size_t)a.apc * 4);  // [apc][3]
+  double* s_tot = s_norm + (size_t)a.apc * 3;                            // [apc][16]
+  __shared__ float s_p32[kSolveWarps][12][32];   // FP32 partials of every lane
   __shared__ int s_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
   const int64_t gstride = (int64_t)G * kSolveThreads;
+  const int nquad = (a.apc + 3) >> 2;
   unsigned nbar = 0;
 
   for (int q = 0; q <= a.n_blk; ++q) {
     const int k = a.s0 + q;
     // ---- per baseline: model matrix of source q-1, corrected average of source q
     const bool model = q > 0, corr = q < a.n_blk;
-    const double Sprev = model ? a.src[3 * (k - 1) + 2] : 0.0;
+    const float Sprev = model ? (float)a.src[3 * (k - 1) + 2] : 0.f;
+    const float4* Jlast = reinterpret_cast<const float4*>(a.Jf[a.n_iter & 1]);
     for (int64_t bl = blockIdx.x * (int64_t)kSolveThreads + tid; bl < a.n_bl; bl += gstride) {
       float2 Mp[4];
       if (model) {
+        // M = S J_i J_j^H, M[r][c] = S sum_k J_i[r][k] conj(J_j[c][k])
         const int2 ij = a.bl_ant[bl];
-        M22<double2> Ji, Jj;
+        const float4 i0 = __ldcg(Jlast + 2 * ij.x), i1 = __ldcg(Jlast + 2 * ij.x + 1);
+        const float4 j0 = __ldcg(Jlast + 2 * ij.y), j1 = __ldcg(Jlast + 2 * ij.y + 1);
+        const float2 I00 = make_float2(i0.x, i0.y), I01 = make_float2(i0.z, i0.w);
+        const float2 I10 = make_float2(i1.x, i1.y), I11 = make_float2(i1.z, i1.w);
+        const float2 J00 = make_float2(j0.x, j0.y), J01 = make_float2(j0.z, j0.w);
+        const float2 J10 = make_float2(j1.x, j1.y), J11 = make_float2(j1.z, j1.w);
+        const float2 P[4] = {cadd(cmulc(I00, J00), cmulc(I01, J01)), cadd(cmulc(I00, J10), cmulc(I01, J11)),
+                             cadd(cmulc(I10, J00), cmulc(I11, J01)), cadd(cmulc(I10, J10), cmulc(I11, J11))};
         #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          Ji.e[e] = __ldcg(a.J64 + (size_t)ij.x * 4 + e);
-          Jj.e[e] = __ldcg(a.J64 + (size_t)ij.y * 4 + e);
-        }
-        const M22<double2> P = mmul_h(Ji, Jj);
-        #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          Mp[e] = make_float2((float)(Sprev * P.e[e].x), (float)(Sprev * P.e[e].y));
+          Mp[e] = make_float2(Sprev * P[e].x, Sprev * P[e].y);
           a.M[((size_t)(q - 1) * a.n_bl + bl) * 4 + e] = Mp[e];
         }
       }
@@ -201,116 +228,131 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
         float4* dst4 = reinterpret_cast<float4*>(Js);
         for (int i = tid; i < a.n_ant * 2; i += kSolveThreads) dst4[i] = __ldcg(src4 + i);
       }
-      if (last && lane == 0) s_wpart[warp][0] = s_wpart[warp][1] = s_wpart[warp][2] = 0.0;
       __syncthreads();
       float2* Jf_new = a.Jf[it & 1];
-      for (int s = warp; s < a.apc; s += kSolveWarps) {
-        const int p = blockIdx.x + s * G;
-        if (p >= a.n_ant) break;             // warp-uniform; later slots are out of range too
-        const float4* row = reinterpret_cast<const float4*>(rows + (size_t)s * a.n_ant * 4);
-        const float4* Jq4 = reinterpret_cast<const float4*>(Js);
+      for (int g0 = 0; g0 < nquad; g0 += kSolveWarps / 4) {        // CTA-uniform trip count
+        const int g = g0 + (warp >> 2), w4 = warp & 3, sa = lane >> 3;
+        const int s = 4 * g + sa, p = blockIdx.x + s * G;
+        const bool live = g < nquad && s < a.apc && p < a.n_ant;
         float A[8], Cm[4];
         #pragma unroll
         for (int i = 0; i < 8; ++i) A[i] = 0.f;
         #pragma unroll
         for (int i = 0; i < 4; ++i) Cm[i] = 0.f;
-        for (int q0 = lane; q0 < a.n_ant; q0 += 32 * kSolveBatch) {
-          float2 V[kSolveBatch][4], J[kSolveBatch][4];
+        if (live) {
+          const float4* row = reinterpret_cast<const float4*>(rows + (size_t)s * a.n_ant * 4);
+          const float4* Jq4 = reinterpret_cast<const float4*>(Js);
+          for (int q0 = (lane & 7) + 8 * w4; q0 < a.n_ant; q0 += 32 * kSolveBatch) {
+            float2 V[kSolveBatch][4], J[kSolveBatch][4];
+            #pragma unroll
+            for (int u = 0; u < kSolveBatch; ++u) {
+              const int qq = q0 + 32 * u;
+              float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0, j0 = v0, j1 = v0;
+              if (qq < a.n_ant && qq != p) {   // V_pp = 0, and C excludes q = p
+                v0 = row[2 * qq];
+                v1 = row[2 * qq + 1];
+                if (first) {
+                  j0 = make_float4(1.f, 0.f, 0.f, 0.f);
+                  j1 = make_float4(0.f, 0.f, 1.f, 0.f);
+                } else {
+                  j0 = Jq4[2 * qq];
+                  j1 = Jq4[2 * qq + 1];
+                }
+              }
+              V[u][0] = make_float2(v0.x, v0.y); V[u][1] = make_float2(v0.z, v0.w);
+              V[u][2] = make_float2(v1.x, v1.y); V[u][3] = make_float2(v1.z, v1.w);
+              J[u][0] = make_float2(j0.x, j0.y); J[u][1] = make_float2(j0.z, j0.w);
+              J[u][2] = make_float2(j1.x, j1.y); J[u][3] = make_float2(j1.z, j1.w);
+            }
+            #pragma unroll
+            for (int u = 0; u < kSolveBatch; ++u) {
+              const float2* Vq = V[u];
+              const float2* Jq = J[u];
+              // A += V J
+              const float2 a0 = cadd(cmul(Vq[0], Jq[0]), cmul(Vq[1], Jq[2]));
+              const float2 a1 = cadd(cmul(Vq[0], Jq[1]), cmul(Vq[1], Jq[3]));
+              const float2 a2 = cadd(cmul(Vq[2], Jq[0]), cmul(Vq[3], Jq[2]));
+              const float2 a3 = cadd(cmul(Vq[2], Jq[1]), cmul(Vq[3], Jq[3]));
+              A[0] += a0.x; A[1] += a0.y; A[2] += a1.x; A[3] += a1.y;
+              A[4] += a2.x; A[5] += a2.y; A[6] += a3.x; A[7] += a3.y;
+              // C += J^H J
+              Cm[0] += Jq[0].x * Jq[0].x + Jq[0].y * Jq[0].y + Jq[2].x * Jq[2].x + Jq[2].y * Jq[2].y;
+              Cm[1] += Jq[1].x * Jq[1].x + Jq[1].y * Jq[1].y + Jq[3].x * Jq[3].x + Jq[3].y * Jq[3].y;
+              const float2 c01 = cadd(cconjmul(Jq[0], Jq[1]), cconjmul(Jq[2], Jq[3]));
+              Cm[2] += c01.x; Cm[3] += c01.y;
+            }
+          }
+        }
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) s_p32[warp][i][lane] = A[i];
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) s_p32[warp][8 + i][lane] = Cm[i];
+        __syncthreads();
+        if (w4 == 0 && g < nquad) {
+          // the quad's four warps' partials of this lane position (FP32, fixed
+          // order), then FP64 over the antenna's 8 lane positions
+          double v[16];
           #pragma unroll
-          for (int u = 0; u < kSolveBatch; ++u) {
-            const int qq = q0 + 32 * u;
-            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0, j0 = v0, j1 = v0;
-            if (qq < a.n_ant && qq != p) {     // V_pp = 0, and C excludes q = p
-              v0 = row[2 * qq];
-              v1 = row[2 * qq + 1];
-              if (first) {
-                j0 = make_float4(1.f, 0.f, 0.f, 0.f);
-                j1 = make_float4(0.f, 0.f, 1.f, 0.f);
-              } else {
-                j0 = Jq4[2 * qq];
-                j1 = Jq4[2 * qq + 1];
+          for (int i = 0; i < 12; ++i)
+            v[i] = (double)(((s_p32[warp][i][lane] + s_p32[warp + 1][i][lane]) + s_p32[warp + 2][i][lane]) +
+                            s_p32[warp + 3][i][lane]);
+          #pragma unroll
+          for (int i = 12; i < 16; ++i) v[i] = 0.0;
+          group8_reduce_scatter16(v, lane);
+          const int j = lane & 7;
+          if (live && j < 6) {
+            s_tot[s * 16 + 2 * j] = v[0];
+            s_tot[s * 16 + 2 * j + 1] = v[1];
+          }
+          const unsigned m4 = __ballot_sync(0xffffffffu, live && j < 4);   // solving lanes
+          __syncwarp();
+          if (live && j < 4) {
+            // J_p = A C^-1 / S in FP64, C = [c00 c01; conj(c01) c11]; lane j: entry e = j
+            const double* tot = s_tot + s * 16;
+            const int e = j, r = e >> 1, c = e & 1;
+            const double c00 = tot[8], c11 = tot[9];
+            const double2 c01 = make_double2(tot[10], tot[11]);
+            const double det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);
+            const double sc = 1.0 / (det * S);
+            const double2 i0c = c == 0 ? make_double2(c11 * sc, 0.0) : make_double2(-c01.x * sc, -c01.y * sc);
+            const double2 i1c = c == 0 ? make_double2(-c01.x * sc, c01.y * sc) : make_double2(c00 * sc, 0.0);
+            const double2 Ar0 = make_double2(tot[4 * r], tot[4 * r + 1]);
+            const double2 Ar1 = make_double2(tot[4 * r + 2], tot[4 * r + 3]);
+            double2 Jn = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
+            const double2 Jo = Jold[s * 4 + e];
+            if (average) Jn = make_double2(0.5 * (Jn.x + Jo.x), 0.5 * (Jn.y + Jo.y));
+            const double dx = Jn.x - Jo.x, dy = Jn.y - Jo.y;
+            double dn = dx * dx + dy * dy, nn = Jn.x * Jn.x + Jn.y * Jn.y;
+            int bad = !(isfinite(Jn.x) && isfinite(Jn.y));
+            #pragma unroll
+            for (int o = 1; o <= 2; o <<= 1) {
+              dn += __shfl_xor_sync(m4, dn, o);
+              nn += __shfl_xor_sync(m4, nn, o);
+              bad |= __shfl_xor_sync(m4, bad, o);
+            }
+            Jold[s * 4 + e] = Jn;
+            const float2 Jf = make_float2((float)Jn.x, (float)Jn.y);
+            Jf_new[(size_t)p * 4 + e] = Jf;
+            if (last) {
+              a.jones[((size_t)k * a.n_ant + p) * 4 + e] = Jf;
+              if (e == 0) {
+                s_norm[3 * s] = dn;
+                s_norm[3 * s + 1] = nn;
+                s_norm[3 * s + 2] = (double)bad;
               }
             }
-            V[u][0] = make_float2(v0.x, v0.y); V[u][1] = make_float2(v0.z, v0.w);
-            V[u][2] = make_float2(v1.x, v1.y); V[u][3] = make_float2(v1.z, v1.w);
-            J[u][0] = make_float2(j0.x, j0.y); J[u][1] = make_float2(j0.z, j0.w);
-            J[u][2] = make_float2(j1.x, j1.y); J[u][3] = make_float2(j1.z, j1.w);
-          }
-          #pragma unroll
-          for (int u = 0; u < kSolveBatch; ++u) {
-            const float2* Vq = V[u];
-            const float2* Jq = J[u];
-            // A += V J
-            const float2 a0 = cadd(cmul(Vq[0], Jq[0]), cmul(Vq[1], Jq[2]));
-            const float2 a1 = cadd(cmul(Vq[0], Jq[1]), cmul(Vq[1], Jq[3]));
-            const float2 a2 = cadd(cmul(Vq[2], Jq[0]), cmul(Vq[3], Jq[2]));
-            const float2 a3 = cadd(cmul(Vq[2], Jq[1]), cmul(Vq[3], Jq[3]));
-            A[0] += a0.x; A[1] += a0.y; A[2] += a1.x; A[3] += a1.y;
-            A[4] += a2.x; A[5] += a2.y; A[6] += a3.x; A[7] += a3.y;
-            // C += J^H J
-            Cm[0] += Jq[0].x * Jq[0].x + Jq[0].y * Jq[0].y + Jq[2].x * Jq[2].x + Jq[2].y * Jq[2].y;
-            Cm[1] += Jq[1].x * Jq[1].x + Jq[1].y * Jq[1].y + Jq[3].x * Jq[3].x + Jq[3].y * Jq[3].y;
-            const float2 c01 = cadd(cconjmul(Jq[0], Jq[1]), cconjmul(Jq[2], Jq[3]));
-            Cm[2] += c01.x; Cm[3] += c01.y;
           }
         }
-        double v[16];
-        #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = (double)A[i];
-        #pragma unroll
-        for (int i = 0; i < 4; ++i) v[8 + i] = (double)Cm[i];
-        #pragma unroll
-        for (int i = 12; i < 16; ++i) v[i] = 0.0;
-        const double wsum = warp_reduce_scatter16(v, lane);     // lane L: total L >> 1
-        double* tot = s_tot[warp];
-        if ((lane & 1) == 0 && lane < 24) tot[lane >> 1] = wsum;
-        __syncwarp();
-        if (lane < 4) {
-          // J_p = A C^-1 / S in FP64, C = [c00 c01; conj(c01) c11]
-          const int e = lane, r = e >> 1, c = e & 1;
-          const double c00 = tot[8], c11 = tot[9];
-          const double2 c01 = make_double2(tot[10], tot[11]);
-          const double det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);
-          const double sc = 1.0 / (det * S);
-          const double2 i0c = c == 0 ? make_double2(c11 * sc, 0.0) : make_double2(-c01.x * sc, -c01.y * sc);
-          const double2 i1c = c == 0 ? make_double2(-c01.x * sc, c01.y * sc) : make_double2(c00 * sc, 0.0);
-          const double2 Ar0 = make_double2(r ? tot[4] : tot[0], r ? tot[5] : tot[1]);
-          const double2 Ar1 = make_double2(r ? tot[6] : tot[2], r ? tot[7] : tot[3]);
-          double2 Jn = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
-          const double2 Jo = Jold[s * 4 + e];
-          if (average) Jn = make_double2(0.5 * (Jn.x + Jo.x), 0.5 * (Jn.y + Jo.y));
-          const double dx = Jn.x - Jo.x, dy = Jn.y - Jo.y;
-          double dn = dx * dx + dy * dy, nn = Jn.x * Jn.x + Jn.y * Jn.y;
-          int bad = !(isfinite(Jn.x) && isfinite(Jn.y));
-          #pragma unroll
-          for (int o = 1; o <= 2; o <<= 1) {
-            dn += __shfl_xor_sync(0xfu, dn, o);
-            nn += __shfl_xor_sync(0xfu, nn, o);
-            bad |= __shfl_xor_sync(0xfu, bad, o);
-          }
-          Jold[s * 4 + e] = Jn;
-          const float2 Jf = make_float2((float)Jn.x, (float)Jn.y);
-          Jf_new[(size_t)p * 4 + e] = Jf;
-          if (last) {
-            a.J64[(size_t)p * 4 + e] = Jn;
-            a.jones[((size_t)k * a.n_ant + p) * 4 + e] = Jf;
-            if (e == 0) {
-              s_wpart[warp][0] += dn;
-              s_wpart[warp][1] += nn;
-              s_wpart[warp][2] += (double)bad;
-            }
-          }
-        }
+        __syncthreads();                     // partials read before the next quad round
       }
-      if (last) {
-        __syncthreads();
-        if (tid == 0) {
-          double dn = 0.0, nn = 0.0, bad = 0.0;
-          for (int w = 0; w < kSolveWarps; ++w) { dn += s_wpart[w][0]; nn += s_wpart[w][1]; bad += s_wpart[w][2]; }
-          a.part[3 * blockIdx.x] = dn;
-          a.part[3 * blockIdx.x + 1] = nn;
-          a.part[3 * blockIdx.x + 2] = bad;
+      if (last && tid == 0) {
+        double dn = 0.0, nn = 0.0, bad = 0.0;
+        for (int s = 0; s < a.apc && blockIdx.x + s * G < a.n_ant; ++s) {
+          dn += s_norm[3 * s]; nn += s_norm[3 * s + 1]; bad += s_norm[3 * s + 2];
         }
+        a.part[3 * blockIdx.x] = dn;
+        a.part[3 * blockIdx.x + 1] = nn;
+        a.part[3 * blockIdx.x + 2] = bad;
       }
       if (!solve_barrier(a.sync, ++nbar, &s_flag)) {
         if (tid == 0) a.status[k] = kSolveStatusTimeout;
