@@ -213,8 +213,8 @@ def main():
                     help="channels (768 = the workload; fewer only for small profiling cases)")
     ap.add_argument("--per-pass", type=int, default=0,
                     help="sources per streaming pass: 1, 64 (blocked) or 0 (library default)")
-    ap.add_argument("--block-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="blocked pass: 0 library choice, 1 FP32 FMA pass, 2 tensor-core pass")
+    ap.add_argument("--block-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="blocked pass: 0 library choice, 1 FP32 FMA pass, 2 mma.sync pass, 3 tcgen05 pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / adjoint / CPU legs")
     args = ap.parse_args()
@@ -296,20 +296,40 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     shares = {k: round(v[0] / max(1e-9, sum(x[0] for x in ktimes.values())), 4) for k, v in ktimes.items()
               if v[2]}
+    block_kernel, solve_kernel = _abi.rts_peel_kernels(p.h)
     if ktimes["block_pass"][2]:
-        # blocked path: FP32-bound fused pass (subtract a block + average the next block)
+        # blocked path: the fused pass (subtract a block + average the next block)
         ms_bp, n_bp, _ = ktimes["block_pass"]
         flops = 2 * K * cad.n_vis * FLOPS_PER_UPDATE * args.steps        # every source subtracted and averaged once
         achieved = flops / (ms_bp / 1e3) / 1e12
         sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        peak = fp32_peak_tflops(sm_mhz)
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": ncu_traffic("k_block_pass<64,true,true>"),
-                    "kernel": "k_block_pass<64,SUB,ACC> (subtract 64 solved sources + average the next 64)",
+        name = {1: "k_block_pass<64,SUB,ACC> (FP32 FMA)", 2: "k_block_pass_tc<SUB,ACC> (TF32 mma.sync)",
+                3: "k_block_pass_t5<SUB,ACC> (tcgen05.mma kind::tf32, TMEM accumulators)"}[block_kernel]
+        if block_kernel == 1:
+            peak = fp32_peak_tflops(sm_mhz)
+            bound, peak_source = "alu", (f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                                         "(median SM clock under load)")
+        else:
+            # TF32 dense peak: measured bf16 (sustained: the pass runs inside a long step)
+            # x the nominal TF32/BF16 ratio 1.1/2.25
+            bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+            peak = bf16 * 1.1 / 2.25
+            bound = "tensor"
+            peak_source = (f"MEASURED_PEAKS.json bf16_tflops_sustained {bf16:.0f} x nominal TF32/BF16 ratio 1.1/2.25 "
+                           "(of measured)")
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "traffic": ncu_traffic("k_block_pass<64,true,true>") if block_kernel == 1 else None,
+                    "kernel": name + ": subtract 64 solved sources + average the next 64",
                     "algorithmic_flops_per_update": FLOPS_PER_UPDATE,
+                    "algorithmic_flops_note": ("32 FP32 flop per source x visibility for each of the subtraction and "
+                                               "the average (4 complex multiply-adds); the tensor-core passes execute "
+                                               "3 TF32 MMAs per product (split operands), so the tensor pipes do 3x "
+                                               "(subtraction 4x: its second 128-row tile is half padding)"),
                     "algorithmic_bytes_per_launch": cad.n_vis * BYTES_PER_UPDATE,
                     "avg_launch_ms": ms_bp / n_bp,
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock under load)",
+                    "hbm_GBps_of_the_pass": cad.n_vis * BYTES_PER_UPDATE / (ms_bp / n_bp / 1e3) / 1e9,
+                    "peak_source": peak_source,
                     "device_time_share": shares}
     else:
         ms_k3, n_k3, _ = ktimes["sub_average"]
@@ -332,6 +352,9 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MWA-shaped cadence, library-predicted sky + noise)",
         "config": dict(workload_config(cad, K, args.n_iter), parallelism=f"replicas{world}"),
         "clocks": clk, "gpu_launches": int(launches), "roofline": roofline,
+        "kernels": {"block_pass": {0: "one source per pass", 1: "fp32-fma", 2: "tf32-mma.sync",
+                                   3: "tcgen05-tf32"}[block_kernel],
+                    "block_solve": {0: "cooperative (one launch per block)", 1: "one launch per step"}[solve_kernel]},
         "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items() if v[2]},
         "status": {"not_converged": n_nonconv, "sources": K},
     }

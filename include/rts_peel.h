@@ -73,10 +73,13 @@ typedef struct rts_peel_config {
                            one pass per block of that many sources, the averages inside a
                            block corrected in closed form (same results); 0 = library
                            default (RTS_BLOCK) */
-  int32_t block_kernel;  /* blocked peel only: RTS_BLOCK_AUTO (0: the tensor-core pass when
-                           n_chan <= 960, else the FP32 pass), RTS_BLOCK_FMA (the FP32
-                           FMA pass), RTS_BLOCK_TENSOR (TF32 MMAs with split operands,
-                           FP32-level accuracy; n_chan <= 960, else RTS_EINVAL) */
+  int32_t block_kernel;  /* blocked peel only: RTS_BLOCK_AUTO (0: the tcgen05 pass when
+                           n_chan <= 768, else the mma.sync pass when n_chan <= 960, else
+                           the FP32 pass), RTS_BLOCK_FMA (the FP32 FMA pass),
+                           RTS_BLOCK_TENSOR (TF32 mma.sync with split operands;
+                           n_chan <= 960, else RTS_EINVAL), RTS_BLOCK_TCGEN05 (tcgen05.mma
+                           with TMEM accumulators, TF32 with split operands; n_chan <= 768,
+                           else RTS_EINVAL).  All give FP32-level accuracy. */
   int32_t solve_kernel;  /* blocked peel only: RTS_SOLVE_AUTO (0: the corrected averages,
                            ALS sweeps and model matrices of a whole block in one
                            cooperative launch whose CTAs meet at grid-wide barriers, when
@@ -95,6 +98,7 @@ typedef struct rts_peel_config {
 #define RTS_BLOCK_AUTO   0
 #define RTS_BLOCK_FMA    1
 #define RTS_BLOCK_TENSOR 2
+#define RTS_BLOCK_TCGEN05 3
 
 #define RTS_BLOCK 64   /* default sources per streaming pass of the blocked peel */
 
@@ -265,6 +269,16 @@ int rts_peel_timing(rts_peel_t* h, int32_t enable);
  * and the number of kernel launches since the last enable (launches[RTS_K_CLASSES]).
  * Any pointer may be NULL. */
 int rts_peel_timing_read(rts_peel_t* h, double* ms, int64_t* groups, int64_t* launches);
+
+/* The kernels the handle resolved at init (no paper counterpart: introspection
+ * for benchmarks and tests).  *block_kernel: 0 when the handle peels one source
+ * per pass, else RTS_BLOCK_FMA, RTS_BLOCK_TENSOR or RTS_BLOCK_TCGEN05 (the
+ * choice RTS_BLOCK_AUTO made).  *solve_kernel: RTS_SOLVE_AUTO when the blocked
+ * peel solves each block in one cooperative launch, else RTS_SOLVE_LAUNCHES
+ * (known once the first blocked cadence has set up its workspace; before
+ * that, the requested value).  Either pointer may be NULL.  RTS_EINVAL for a
+ * NULL handle. */
+int rts_peel_kernels(const rts_peel_t* h, int32_t* block_kernel, int32_t* solve_kernel);
 
 /* Page-locked host memory for the host-buffer calls (the paper, Section 4,
  * moved its host allocator to pinned memory for faster DMA).  rts_host_alloc

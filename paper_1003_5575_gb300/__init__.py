@@ -11,8 +11,8 @@ from ._abi import (  # noqa: F401
     rts_peel_rotate_average, rts_peel_solve, rts_peel_solve_noalloc, rts_peel_grad,
     rts_peel_offsets, rts_offsets_solve,
     rts_peel_pipeline_submit, rts_peel_pipeline_wait, rts_peel_last_error, rts_peel_destroy,
-    rts_peel_timing, rts_peel_timing_read, rts_host_alloc, rts_host_free, KERNEL_CLASSES, RTS_BLOCK,
-    RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR, RTS_SOLVE_AUTO, RTS_SOLVE_LAUNCHES,
+    rts_peel_timing, rts_peel_timing_read, rts_peel_kernels, rts_host_alloc, rts_host_free, KERNEL_CLASSES, RTS_BLOCK,
+    RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR, RTS_BLOCK_TCGEN05, RTS_SOLVE_AUTO, RTS_SOLVE_LAUNCHES,
 )
 
 

@@ -25,7 +25,7 @@ RTS_K_PREDICT, RTS_K_GRAD, RTS_K_GRAD_REDUCE, RTS_K_BLOCK_PASS, RTS_K_BLOCK_FIX 
 RTS_K_OFFSETS = 9
 RTS_K_CLASSES = 10
 RTS_BLOCK = 64
-RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR = 0, 1, 2
+RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR, RTS_BLOCK_TCGEN05 = 0, 1, 2, 3
 RTS_SOLVE_AUTO, RTS_SOLVE_LAUNCHES = 0, 1
 KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "grad", "grad_reduce",
                   "block_pass", "block_fix", "offsets")
@@ -34,7 +34,7 @@ EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_ca
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad", "rts_peel_offsets",
            "rts_offsets_solve",
            "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
-           "rts_peel_timing", "rts_peel_timing_read", "rts_host_alloc", "rts_host_free",
+           "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_host_alloc", "rts_host_free",
            "rts_peel_last_error", "rts_peel_destroy")
 
 
@@ -104,6 +104,8 @@ def lib():
             L.rts_peel_timing_read.restype = ctypes.c_int
             L.rts_peel_timing_read.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_int64),
                                                ctypes.POINTER(ctypes.c_int64)]
+            L.rts_peel_kernels.restype = ctypes.c_int
+            L.rts_peel_kernels.argtypes = [_vp, _ip, _ip]
             L.rts_host_alloc.restype = ctypes.c_int
             L.rts_host_alloc.argtypes = [ctypes.c_uint64, ctypes.POINTER(_vp)]
             L.rts_host_free.restype = ctypes.c_int
@@ -178,6 +180,13 @@ def rts_peel_offsets(h, d_vis, n_src, d_jones, d_src, alpha, nu_ref_hz, d_out, d
 
 def rts_offsets_solve(d_out, n_src, d_offsets, stream):
     return _check(lib().rts_offsets_solve(d_out, n_src, d_offsets, stream), None)
+
+
+def rts_peel_kernels(h):
+    """(block_kernel, solve_kernel) resolved by the handle."""
+    bk, sk = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().rts_peel_kernels(h, ctypes.byref(bk), ctypes.byref(sk)), h)
+    return bk.value, sk.value
 
 
 def rts_peel_timing(h, enable: int):

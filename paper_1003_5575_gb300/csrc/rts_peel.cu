@@ -12,6 +12,7 @@
 
 #include "als_kernels.cuh"
 #include "block_kernels.cuh"
+#include "block_t5_kernels.cuh"
 #include "block_tc_kernels.cuh"
 #include "common.cuh"
 #include "grad_kernels.cuh"
@@ -25,7 +26,9 @@ using namespace rts;
 struct rts_peel_t {
   int n_ant = 0, n_chan = 0, n_time = 0, n_iter = 0, precision = 0, max_sources = 0;
   int per_pass = 1;                // sources per streaming pass (1 or RTS_BLOCK)
-  bool block_tc = false;           // blocked passes on the tensor cores (k_block_pass_tc)
+  bool block_tc = false;           // blocked passes as TF32 mma.sync (k_block_pass_tc)
+  bool block_t5 = false;           // blocked passes as tcgen05 MMAs (k_block_pass_t5)
+  int* d_perr = nullptr;           // [1] set by a tcgen05 pass whose mbarrier wait ran out
   int64_t n_bl = 0;
   double nu0 = 0, dnu = 0;
   int device = 0;
@@ -210,7 +213,10 @@ const double2* als_solution(rts_peel_t* h) { return h->d_J[h->n_iter & 1]; }
 
 int read_status(rts_peel_t* h, int32_t n, int32_t* h_status, cudaStream_t s) {
   RTS_CUDA(h, cudaMemcpyAsync(h_status, h->d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  int perr = 0;
+  if (h->d_perr) RTS_CUDA(h, cudaMemcpyAsync(&perr, h->d_perr, sizeof(int), cudaMemcpyDeviceToHost, s));
   RTS_CUDA(h, cudaStreamSynchronize(s));
+  if (perr) return fail(h, RTS_ECUDA, "a tensor-core completion wait of the blocked pass timed out");
   for (int k = 0; k < n; ++k)
     if (h_status[k] == kSolveStatusTimeout)
       return fail(h, RTS_ECUDA, "a grid barrier of the block solve timed out at source " + std::to_string(k));
@@ -262,6 +268,10 @@ int set_block_smem(rts_peel_t* h, int smem) {
 
 int setup_block_solve(rts_peel_t* h);
 
+// the tcgen05 pass holds all 512 TMEM columns: at least 116 KB of shared memory
+// keeps it at one CTA per SM (a second CTA would wait in its TMEM allocation)
+size_t t5_launch_smem(const rts_peel_t* h) { return std::max<size_t>(t5_pass_smem(h->n_chan), 116 * 1024); }
+
 int ensure_block_workspace(rts_peel_t* h) {
   if (h->b_avg) return RTS_OK;
   const int BK = h->per_pass;
@@ -285,6 +295,15 @@ int ensure_block_workspace(rts_peel_t* h) {
   RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_done, cudaEventDisableTiming));
   int rc = setup_block_solve(h);
   if (rc) return rc;
+  RTS_CUDA(h, cudaMalloc((void**)&h->d_perr, sizeof(int)));
+  RTS_CUDA(h, cudaMemset(h->d_perr, 0, sizeof(int)));
+  if (h->block_t5) {
+    const int tsm = (int)t5_launch_smem(h);
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t5<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t5<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t5<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    return RTS_OK;
+  }
   if (h->block_tc) {
     const int tsm = (int)tc_pass_smem(h->n_chan);
     RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
@@ -364,6 +383,14 @@ void block_pass_t(bool sub, bool acc, const BlockPassArgs& a, unsigned grid, siz
 int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a, cudaStream_t s) {
   Span span(h, RTS_K_BLOCK_PASS, s);
   const unsigned grid = (unsigned)h->n_bl;
+  if (h->block_t5) {
+    const size_t tsm = t5_launch_smem(h);
+    if (sub && acc) k_block_pass_t5<true, true><<<grid, kT5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
+    else if (sub) k_block_pass_t5<true, false><<<grid, kT5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
+    else k_block_pass_t5<false, true><<<grid, kT5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
+    span.end(1);
+    return check_launch(h, "block pass launch");
+  }
   if (h->block_tc) {
     const size_t tsm = tc_pass_smem(h->n_chan);
     if (sub && acc) k_block_pass_tc<true, true><<<grid, kTcThreads, tsm, s>>>(a, h->per_pass);
@@ -543,10 +570,13 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   if (per_pass > 1 && (size_t)cfg->n_chan * 32 + 2048 + 32768 > 200 * 1024)
     return fail(nullptr, RTS_EINVAL, "the blocked peel needs n_chan*32 + 34 KB <= 200 KB of shared memory "
                                      "(n_chan <= 5300); use sources_per_pass = 1");
-  if (cfg->block_kernel < RTS_BLOCK_AUTO || cfg->block_kernel > RTS_BLOCK_TENSOR)
-    return fail(nullptr, RTS_EINVAL, "block_kernel must be RTS_BLOCK_AUTO, RTS_BLOCK_FMA or RTS_BLOCK_TENSOR");
+  if (cfg->block_kernel < RTS_BLOCK_AUTO || cfg->block_kernel > RTS_BLOCK_TCGEN05)
+    return fail(nullptr, RTS_EINVAL,
+                "block_kernel must be RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR or RTS_BLOCK_TCGEN05");
   if (cfg->block_kernel == RTS_BLOCK_TENSOR && cfg->n_chan > kTcMaxChan)
     return fail(nullptr, RTS_EINVAL, "the tensor-core blocked pass needs n_chan <= 960");
+  if (cfg->block_kernel == RTS_BLOCK_TCGEN05 && cfg->n_chan > kT5MaxChan)
+    return fail(nullptr, RTS_EINVAL, "the tcgen05 blocked pass needs n_chan <= 768");
 
   if (cfg->solve_kernel != RTS_SOLVE_AUTO && cfg->solve_kernel != RTS_SOLVE_LAUNCHES)
     return fail(nullptr, RTS_EINVAL, "solve_kernel must be RTS_SOLVE_AUTO or RTS_SOLVE_LAUNCHES");
@@ -554,7 +584,13 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   rts_peel_t* h = new rts_peel_t();
   h->per_pass = per_pass;
   h->solve_kernel = cfg->solve_kernel;
-  h->block_tc = per_pass > 1 && cfg->block_kernel != RTS_BLOCK_FMA && cfg->n_chan <= kTcMaxChan;
+  {
+    int bk = cfg->block_kernel;
+    if (bk == RTS_BLOCK_AUTO)
+      bk = cfg->n_chan <= kT5MaxChan ? RTS_BLOCK_TCGEN05 : (cfg->n_chan <= kTcMaxChan ? RTS_BLOCK_TENSOR : RTS_BLOCK_FMA);
+    h->block_t5 = per_pass > 1 && bk == RTS_BLOCK_TCGEN05;
+    h->block_tc = per_pass > 1 && bk == RTS_BLOCK_TENSOR;
+  }
   h->n_ant = cfg->n_ant; h->n_chan = cfg->n_chan; h->n_time = cfg->n_time;
   h->n_iter = cfg->n_iter; h->precision = cfg->precision; h->max_sources = cfg->max_sources;
   h->n_bl = n_bl; h->nu0 = nu0; h->dnu = dnu;
@@ -924,6 +960,15 @@ int rts_host_free(void* p) {
   return cudaFreeHost(p) == cudaSuccess ? RTS_OK : RTS_ECUDA;
 }
 
+int rts_peel_kernels(const rts_peel_t* h, int32_t* block_kernel, int32_t* solve_kernel) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (block_kernel)
+    *block_kernel = h->per_pass == 1 ? 0 : (h->block_t5 ? RTS_BLOCK_TCGEN05 : (h->block_tc ? RTS_BLOCK_TENSOR : RTS_BLOCK_FMA));
+  if (solve_kernel)
+    *solve_kernel = h->b_avg ? (h->bs_ok ? RTS_SOLVE_AUTO : RTS_SOLVE_LAUNCHES) : h->solve_kernel;
+  return RTS_OK;
+}
+
 const char* rts_peel_last_error(const rts_peel_t* h) {
   return h ? h->err.c_str() : g_init_err.c_str();
 }
@@ -934,7 +979,7 @@ void rts_peel_destroy(rts_peel_t* h) {
   if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
   void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
                   h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage,
-                  h->b_avg, h->b_model, h->b_sync, h->b_part};
+                  h->b_avg, h->b_model, h->b_sync, h->b_part, h->d_perr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int r = 0; r < rts_peel_t::kRing; ++r) {

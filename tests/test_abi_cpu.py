@@ -85,6 +85,7 @@ def test_init_rejects_bad_config_on_host(abi, kw, needle):
 def test_null_handle_is_rejected(abi):
     assert abi.lib().rts_peel_cadence(None, None, None, 0, None, None, None, None) == abi.RTS_EINVAL
     assert abi.lib().rts_peel_grad(None, None, 0, None, None, None, None, None, None) == abi.RTS_EINVAL
+    assert abi.lib().rts_peel_kernels(None, None, None) == abi.RTS_EINVAL
     abi.lib().rts_peel_destroy(None)
 
 

@@ -102,8 +102,9 @@ def test_fullsize_single_source_recovered_exactly(full):
     del one, resid
 
 
-@pytest.mark.parametrize("per_pass,kernel", [(1, 0), (16, 1), (64, 1), (64, 2)],
-                         ids=["one-source-per-pass", "blocks-of-16-fma", "blocks-of-64-fma", "blocks-of-64-tensor"])
+@pytest.mark.parametrize("per_pass,kernel", [(1, 0), (16, 1), (64, 1), (64, 2), (64, 3)],
+                         ids=["one-source-per-pass", "blocks-of-16-fma", "blocks-of-64-fma", "blocks-of-64-tensor",
+                              "blocks-of-64-tcgen05"])
 def test_fullsize_peel_residual_plus_model_is_input(full, per_pass, kernel):
     """1000 sources: residual + prediction of the solved sources = input.
 

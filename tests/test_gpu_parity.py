@@ -120,7 +120,7 @@ BLOCK_CASES = [
 ]
 # (pass kernel, solve kernel): FP32 FMA or tensor-core pass; the block's solve
 # chain as one cooperative launch (0) or as one launch per step (1)
-KERNELS = [((1, 0), "fma"), ((2, 0), "tensor"), ((2, 1), "tensor-launches")]
+KERNELS = [((1, 0), "fma"), ((2, 0), "tensor"), ((2, 1), "tensor-launches"), ((3, 0), "tcgen05")]
 
 
 @pytest.mark.parametrize("kernel", [k for k, _ in KERNELS], ids=[n for _, n in KERNELS])
@@ -130,6 +130,8 @@ def test_blocked_peel_matches_sequential_oracle(name, cad, per_pass, kernel):
     corrections, with the FP32 FMA pass or the tensor-core pass, and the solve
     chain of a block in one cooperative launch or in one launch per step: the
     same results as the oracle's one-source-at-a-time peel."""
+    if kernel[0] == 3 and cad.n_chan > 768:
+        pytest.skip("the tcgen05 pass holds at most 768 channels")
     V, R_ref, J_ref, st_ref = oracle_case(cad)
     p = make_peeler(cad, "mixed", per_pass=per_pass, block_kernel=kernel[0], solve_kernel=kernel[1])
     vis = to_dev(V, "mixed")
@@ -377,6 +379,23 @@ def test_pipelined_host_cadences_equal_device_cadences():
         for b in bufs:
             _abi.rts_host_free(b)
         p.close()
+
+
+def test_tcgen05_pass_channel_limit():
+    """The tcgen05 pass holds a strip of up to 768 channels: above that the
+    automatic choice is the mma.sync pass (same results), an explicit request fails."""
+    from paper_1003_5575_gb300 import RtsError, RTS_EINVAL
+    cad = Cadence(8, 800, 2, 5, freq0_hz=167e6, seed=95)
+    with pytest.raises(RtsError) as e:
+        make_peeler(cad, "mixed", per_pass=64, block_kernel=3)
+    assert e.value.code == RTS_EINVAL
+    V, R_ref, J_ref, _ = oracle_case(cad)
+    p = make_peeler(cad, "mixed", per_pass=64)
+    resid, jones, _ = p.cadence(to_dev(V, "mixed"), cad.sources())
+    torch.cuda.synchronize()
+    assert np.abs(resid.cpu().numpy() - R_ref).max() <= TOL["mixed"] * rms_of(V)
+    assert jones_rel(jones.cpu().numpy(), J_ref) <= TOL["mixed"]
+    p.close()
 
 
 def test_tensor_pass_channel_limit():
