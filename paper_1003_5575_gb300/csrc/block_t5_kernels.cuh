@@ -29,9 +29,10 @@
 // round-to-nearest.
 //
 // One CTA (16 warps, 1 per SM: ~217 KB of shared memory, all 512 TMEM columns)
-// per baseline, looping over time steps; thread 0 issues the MMAs and commits
-// them to an mbarrier that the consumers wait on (bounded polls: a wait that
-// runs out sets *err and the pass reports an error instead of hanging).
+// per baseline, looping over time steps; one lane in each of several warps
+// issues the MMAs of its accumulators and commits them to an mbarrier that
+// warp 0 waits on (bounded polls: a wait that runs out sets *err and the pass
+// reports an error instead of hanging).
 // Limits: at most 64 sources per role, n_chan <= kT5MaxChan.
 #pragma once
 #include "block_tc_kernels.cuh"
@@ -51,7 +52,7 @@ constexpr uint32_t kT5ColO = 256;
 constexpr uint32_t kT5ColDm = 0;
 constexpr uint32_t kT5ColDx = 256;
 constexpr uint32_t kT5Cols = 512;
-constexpr uint32_t kT5MaxPolls = 1u << 22;  // mbarrier polls before giving up
+constexpr uint32_t kT5MaxPolls = 1u << 17;  // mbarrier polls (each up to 20 us) before giving up
 
 // shared-memory layout (byte offsets) for nq4 = 16-channel tiles rounded up to 4
 struct T5Smem {
@@ -116,8 +117,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
 
   if (warp == 0) tmem_alloc(tslot, kT5Cols);
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    mbar_init(&mbar[0], 8);                   // the subtraction's 8 issuing warps commit to it
+    mbar_init(&mbar[1], 2);                   // the average's 2 issuing warps
   }
   // padding channels of both strips stay zero (the copies never write them)
   for (int i = tid; i < (n16 - a.n_chan) * 8; i += kT5Threads) {
@@ -191,52 +192,74 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
     }
   };
 
-  for (int t = 0; t < a.n_time; ++t) {
-    const int buf = t & 1;
-    if (tid < 2 * kT5Src) {
-      const bool sub = tid < kT5Src;
-      const int k = sub ? tid : tid - kT5Src;
+  // the subtraction's B operand, the real form of conj(T2): thread (r, j) makes
+  // T2 of sources 2j, 2j+1 at offset r and writes 16 bytes (K = 4j .. 4j+3) of
+  // rows 2r (T2r, T2i per source) and 2r+1 (-T2i, T2r).  Lanes: r & 3 = lane & 3,
+  // j & 7 = lane >> 2; the row written first alternates with j, so each store
+  // instruction covers 8 row residues x 4 core matrices (no extra conflicts).
+  auto bsub_fill = [&]() {
+    const int r = (tid & 3) + 4 * (tid >> 7), j = (tid >> 2) & 31;
+    const float2 z0 = phasor_hw((unsigned long long)r * ph[2 * j].b);
+    const float2 z1 = phasor_hw((unsigned long long)r * ph[2 * j + 1].b);
+    const float2 a0 = split_store(z0.x), a1 = split_store(z0.y), a2 = split_store(z1.x), a3 = split_store(z1.y);
+    const float2 n1 = split_store(-z0.y), n3 = split_store(-z1.y);
+    #pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int pout = u ^ (j & 1);
+      const int o = kmaj_byte(2 * r + pout, 4 * j, 128);
+      const float4 h = pout ? make_float4(n1.x, a0.x, n3.x, a2.x) : make_float4(a0.x, a1.x, a2.x, a3.x);
+      const float4 l = pout ? make_float4(n1.y, a0.y, n3.y, a2.y) : make_float4(a0.y, a1.y, a2.y, a3.y);
+      *reinterpret_cast<float4*>(bsub_hi + o) = h;
+      *reinterpret_cast<float4*>(bsub_lo + o) = l;
+    }
+  };
+  // one thread issues the MMAs; warp 0 (converged) waits for their commit
+  auto mma_wait = [&](uint64_t* bar, uint32_t parity) {
+    if (warp == 0) {
+      if (!mbar_wait(bar, parity, kT5MaxPolls) && lane == 0) s_bad = 1;
+      fence_before_sync();
+    }
+    __syncthreads();
+    fence_after_sync();
+  };
+  auto load_ph = [&](int t, bool sub) {     // 64 threads: the phases of one role at time t
+    const int base = sub ? 0 : kT5Src;
+    if (tid >= base && tid < base + kT5Src) {
+      const int k = tid - base;
       PhaseAB p;
       p.a = 0; p.b = 0;
       if (sub ? (SUB && k < a.n_sub) : (ACC && k < a.n_acc))
         p = (sub ? a.ph_sub : a.ph_acc)[((size_t)bl * a.n_time + t) * bk + k];
       ph[tid] = p;
     }
+  };
+  auto sub_tables = [&]() {                 // T1 of the subtracted sources and the subtraction's B operand
+    t1_fill(0);
+    bsub_fill();
+  };
+  const int ncg = (4 * nq4 + 47) / 48;      // column groups of the average with data
+
+  // tables of the first time step's subtraction
+  if (SUB) {
+    load_ph(0, true);
+    __syncthreads();
+    sub_tables();
+  }
+  for (int t = 0; t < a.n_time; ++t) {
+    const int buf = t & 1;
+    if (ACC) load_ph(t, false);
     if (t + 1 < a.n_time) prefetch(t + 1, buf ^ 1);
     cp_async_commit();
-    __syncthreads();                          // phases ready
-    // ---- tables of this time step: T1 of the subtracted sources and the
-    // subtraction's B operand now; T1 of the averaged sources and the average's
-    // A operand while the first subtraction tile runs on the tensor cores (or
-    // now, in the first pass)
-    if (SUB) t1_fill(0);
-    else t1_fill(kT5Src);
-    if (SUB) {
-      // real form of conj(T2) for the subtraction: thread (r, j) makes T2 of
-      // sources 2j, 2j+1 at offset r and writes 16 bytes (K = 4j .. 4j+3) of rows
-      // 2r (T2r, T2i per source) and 2r+1 (-T2i, T2r).  Lanes: r & 3 = lane & 3,
-      // j & 7 = lane >> 2; the row written first alternates with j, so each store
-      // instruction covers 8 row residues x 4 core matrices (no extra conflicts).
-      const int r = (tid & 3) + 4 * (tid >> 7), j = (tid >> 2) & 31;
-      const float2 z0 = phasor_hw((unsigned long long)r * ph[2 * j].b);
-      const float2 z1 = phasor_hw((unsigned long long)r * ph[2 * j + 1].b);
-      const float2 a0 = split_store(z0.x), a1 = split_store(z0.y), a2 = split_store(z1.x), a3 = split_store(z1.y);
-      const float2 n1 = split_store(-z0.y), n3 = split_store(-z1.y);
-      #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int pout = u ^ (j & 1);
-        const int o = kmaj_byte(2 * r + pout, 4 * j, 128);
-        const float4 h = pout ? make_float4(n1.x, a0.x, n3.x, a2.x) : make_float4(a0.x, a1.x, a2.x, a3.x);
-        const float4 l = pout ? make_float4(n1.y, a0.y, n3.y, a2.y) : make_float4(a0.y, a1.y, a2.y, a3.y);
-        *reinterpret_cast<float4*>(bsub_hi + o) = h;
-        *reinterpret_cast<float4*>(bsub_lo + o) = l;
-      }
-    }
-    if (!SUB) aavg_fill();
     cp_async_wait1();                         // this step's strip has landed
     fence_smem_async();
-    __syncthreads();                          // tables and strip ready
+    __syncthreads();                          // strip, phases and the subtraction's tables ready
     const float* strip = strip0 + (size_t)buf * n16 * 8;
+    if (!SUB) {                               // first pass: the average's tables now
+      t1_fill(kT5Src);
+      aavg_fill();
+      fence_smem_async();
+      __syncthreads();
+    }
 
     if (SUB) {
       float2* dst = reinterpret_cast<float2*>(a.dst + ((size_t)t * a.n_bl + bl) * a.n_chan * 2);
@@ -269,23 +292,22 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
         fence_before_sync();
         __syncthreads();
         fence_after_sync();
-        if (tid == 0) {
-          // accumulator g: sources 8g .. 8g+7 (k-steps 2g, 2g+1), lo(W) hi(B2),
-          // hi(W) lo(B2), then hi(W) hi(B2); k-step s adds 256 s bytes (16 s in the
-          // descriptor's address field)
+        if (warp < 8 && lane == 0) {
+          // warp g issues accumulator g: sources 8g .. 8g+7 (k-steps 2g, 2g+1),
+          // lo(W) hi(B2), hi(W) lo(B2), then hi(W) hi(B2); k-step s adds 256 s
+          // bytes (16 s in the descriptor's address field).  Eight issuers keep
+          // any one warp's delay short; each commits to the same mbarrier.
           const uint32_t id = idesc_tf32(128, 32);
-          #pragma unroll 1
-          for (int g = 0; g < 8; ++g) {
-            const uint32_t d = tmem + kT5ColO + 32 * g;
+          const int g = warp;
+          const uint32_t d = tmem + kT5ColO + 32 * g;
+          #pragma unroll
+          for (int pass = 0; pass < 3; ++pass) {
+            const uint32_t acol = tmem + kT5ColW + (pass == 0 ? 128 : 0);
+            const uint64_t bd = pass == 1 ? dsub_lo : dsub_hi;
             #pragma unroll
-            for (int pass = 0; pass < 3; ++pass) {
-              const uint32_t acol = tmem + kT5ColW + (pass == 0 ? 128 : 0);
-              const uint64_t bd = pass == 1 ? dsub_lo : dsub_hi;
-              #pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int s = 2 * g + u;
-                mma_ts(d, acol + 8 * s, bd + 16 * s, id, (pass | u) != 0);
-              }
+            for (int u = 0; u < 2; ++u) {
+              const int s = 2 * g + u;
+              mma_ts(d, acol + 8 * s, bd + 16 * s, id, (pass | u) != 0);
             }
           }
           commit(&mbar[0]);
@@ -295,13 +317,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
           aavg_fill();
           fence_smem_async();
         }
-        if (tid == 0) {
-          if (!mbar_wait(&mbar[0], par_sub, kT5MaxPolls)) s_bad = 1;
-          fence_before_sync();
-        }
+        mma_wait(&mbar[0], par_sub);          // subtraction MMAs of this tile complete
         par_sub ^= 1;
-        __syncthreads();                      // subtraction MMAs of this tile complete
-        fence_after_sync();
         // epilogue: residual = strip - O, to HBM, and split into the average's B
         // operand.  Warp (quarter, j) takes rows 32 quarter + lane of the tile and
         // channels 16 q + 4 j .. 16 q + 4 j + 3 (columns 8 j .. 8 j + 7 of each
@@ -366,26 +383,32 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
       fence_before_sync();
       __syncthreads();                        // residual split complete
       fence_after_sync();
-      if (tid == 0) {
-        // hi(A2) hi(R) into the main accumulator; lo(A2) hi(R) and hi(A2) lo(R)
-        // into the cross-term accumulator
+      if (warp >= 14 && lane == 0) {
+        // warp 14: hi(A2) hi(R) into the main accumulator; warp 15: lo(A2) hi(R)
+        // and hi(A2) lo(R) into the cross-term accumulator
         const uint32_t id = idesc_tf32(128, 4 * nq4);
-        #pragma unroll
-        for (int s = 0; s < 4; ++s) mma_ss(tmem + kT5ColDm, da_hi + 16 * s, db_hi + 16 * s, id, s != 0);
-        #pragma unroll
-        for (int s = 0; s < 4; ++s) mma_ss(tmem + kT5ColDx, da_lo + 16 * s, db_hi + 16 * s, id, s != 0);
-        #pragma unroll
-        for (int s = 0; s < 4; ++s) mma_ss(tmem + kT5ColDx, da_hi + 16 * s, db_lo + 16 * s, id, 1);
+        if (warp == 14) {
+          #pragma unroll
+          for (int s = 0; s < 4; ++s) mma_ss(tmem + kT5ColDm, da_hi + 16 * s, db_hi + 16 * s, id, s != 0);
+        } else {
+          #pragma unroll
+          for (int s = 0; s < 4; ++s) mma_ss(tmem + kT5ColDx, da_lo + 16 * s, db_hi + 16 * s, id, s != 0);
+          #pragma unroll
+          for (int s = 0; s < 4; ++s) mma_ss(tmem + kT5ColDx, da_hi + 16 * s, db_lo + 16 * s, id, 1);
+        }
         commit(&mbar[1]);
-        if (!mbar_wait(&mbar[1], par_avg, kT5MaxPolls)) s_bad = 1;
-        fence_before_sync();
       }
-      __syncthreads();                        // average MMAs complete
-      fence_after_sync();
+      if (SUB && t + 1 < a.n_time) {          // next step's subtraction tables, beside the average MMAs
+        load_ph(t + 1, true);
+        __syncthreads();
+        sub_tables();
+      }
+      mma_wait(&mbar[1], par_avg);            // average MMAs complete
+      par_avg ^= 1;
       // epilogue: warp (quarter, cg) takes rows m = 32 quarter + lane = (pout, k)
       // and tiles q = 12 cg .. 12 cg + 11; G = main + cross, then the T1-weighted
-      // sums, whose four column-group parts meet in shared memory (the
-      // subtraction's operand space, free now)
+      // sums, whose column-group parts meet in shared memory (in the average's
+      // B operand space, free once its MMAs are complete: ncg x 4 KB <= nq4 KB)
       {
         const int m = 32 * quarter + lane, pout = m >> 6, k = m & 63, cg = warp >> 2;
         const float2* t1k = t1 + (size_t)(kT5Src + k) * P;
@@ -408,32 +431,37 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
             }
           }
         }
-        float* part = reinterpret_cast<float*>(bsub_hi);      // [4 cg][128 m][8]
-        #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          part[(cg * 128 + m) * 8 + 2 * e] = sr[e];
-          part[(cg * 128 + m) * 8 + 2 * e + 1] = si[e];
-        }
+        float* part = reinterpret_cast<float*>(bavg_hi);     // [ncg][8][128 m]
+        if (cg < ncg)
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            part[(cg * 8 + 2 * e) * 128 + m] = sr[e];
+            part[(cg * 8 + 2 * e + 1) * 128 + m] = si[e];
+          }
       }
       __syncthreads();
       if (warp < 4) {
         const int m = 32 * quarter + lane;
-        const float* part = reinterpret_cast<const float*>(bsub_hi);
-        // compensated accumulation across time steps of the four parts (fixed order)
+        const float* part = reinterpret_cast<const float*>(bavg_hi);
+        // compensated accumulation across time steps of the parts (fixed order)
         #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const float x = ((part[m * 8 + i] + part[(128 + m) * 8 + i]) + part[(256 + m) * 8 + i]) +
-                          part[(384 + m) * 8 + i];
+          float x = part[i * 128 + m];
+          for (int c = 1; c < ncg; ++c) x += part[(c * 8 + i) * 128 + m];
           const float y = x - kc[i];
           const float tt = ks[i] + y;
           kc[i] = (tt - ks[i]) - y;
           ks[i] = tt;
         }
       }
-      par_avg ^= 1;
+    } else if (SUB && t + 1 < a.n_time) {    // last pass: next step's subtraction tables
+      load_ph(t + 1, true);
+      __syncthreads();
+      sub_tables();
     }
+    fence_smem_async();
     fence_before_sync();
-    __syncthreads();                          // tables, operands and accumulators free for the next step
+    __syncthreads();                          // tables, operands and accumulators ready for the next step
     fence_after_sync();
     if (s_bad) break;                         // a wait ran out: stop (reported through *err)
   }

@@ -67,16 +67,18 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// wait for completion of the mbarrier phase with the given parity; gives up
-// after max_polls polls and returns false
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t max_polls) {
+// wait for completion of the mbarrier phase with the given parity; each poll
+// may suspend the thread for up to suspend_ns (until the phase completes);
+// gives up after max_polls polls and returns false
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t max_polls,
+                                          uint32_t suspend_ns = 20000) {
   uint32_t done = 0;
   for (uint32_t it = 0; it < max_polls; ++it) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(parity)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(suspend_ns)
         : "memory");
     if (done) return true;
   }
