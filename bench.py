@@ -114,7 +114,9 @@ class Clocks:
 
 
 KERNEL_SOURCES = {"k_stream_mixed<true,true>": ("common.cuh", "stream_kernels.cuh"),
-                  "k_block_pass<64,true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh")}
+                  "k_block_pass<64,true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh"),
+                  "k_block_pass_t5<true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh",
+                                                 "block_tc_kernels.cuh", "tc05.cuh", "block_t5_kernels.cuh")}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -319,7 +321,8 @@ def main():
                            "(of measured)")
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": ncu_traffic("k_block_pass<64,true,true>") if block_kernel == 1 else None,
+                    "traffic": (ncu_traffic("k_block_pass<64,true,true>") if block_kernel == 1 else
+                                ncu_traffic("k_block_pass_t5<true,true>") if block_kernel == 3 else None),
                     "kernel": name + ": subtract 64 solved sources + average the next 64",
                     "algorithmic_flops_per_update": FLOPS_PER_UPDATE,
                     "algorithmic_flops_note": ("32 FP32 flop per source x visibility for each of the subtraction and "

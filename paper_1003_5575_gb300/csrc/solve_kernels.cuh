@@ -12,8 +12,10 @@
 //
 // Work split (G CTAs of kSolveThreads threads, G <= number of SMs):
 //   per baseline, grid-stride over all threads: the model matrix of source
-//     q-1 (FP32, from the FP32 copy of its solution) and the corrected
-//     average of source q (the arithmetic of k_block_correct);
+//     q-1 (FP32, from its solved FP32 Jones matrices) and the corrected average
+//     of source q (the sum of k_block_correct, with each M_j recomputed from the
+//     solved Jones matrices instead of read back: 8 bytes of HBM per (j, baseline)
+//     instead of 40);
 //   per antenna: antenna p belongs to CTA p % G (slot p / G).  Its row V_pq,
 //     q = 0..n_ant-1 (V_qp = V_pq^H applied while staging, V_pp = 0), is staged
 //     in shared memory once per source, and every sweep stages the FP32
@@ -68,7 +70,7 @@ struct BlockSolveArgs {
   unsigned* sync;          // [2] barrier counter, abort flag (zero at launch)
 };
 
-// dynamic shared memory: rows [apc][n_ant][4] float2, iterate [n_ant][4] float2,
+// dynamic shared memory: rows [apc][2][n_ant] float4, iterate [n_ant][4] float2,
 // previous FP64 iterate of the CTA's antennas [apc][4] double2, per-slot
 // convergence sums [apc][3] double, FP64 totals [apc][16] double
 inline size_t block_solve_smem(int n_ant, int apc) {
@@ -132,9 +134,26 @@ __device__ bool solve_barrier(unsigned* sync, unsigned n, int* s_flag) {
 
 // at most 64 registers a thread: half of an SM, so the geometry kernels of later
 // blocks (low-priority stream) keep running beside it
+// M = S J_i J_j^H in FP32 from a source's solved FP32 Jones matrices J [n_ant][4]
+// (M[r][c] = S sum_k J_i[r][k] conj(J_j[c][k])); written once per source during
+// the launch, so read through L1
+__device__ __forceinline__ void block_model_f(const float2* __restrict__ J, int2 ij, float S, float2 (&M)[4]) {
+  const float4* J4 = reinterpret_cast<const float4*>(J);
+  const float4 i0 = __ldg(J4 + 2 * ij.x), i1 = __ldg(J4 + 2 * ij.x + 1);
+  const float4 j0 = __ldg(J4 + 2 * ij.y), j1 = __ldg(J4 + 2 * ij.y + 1);
+  const float2 I00 = make_float2(i0.x, i0.y), I01 = make_float2(i0.z, i0.w);
+  const float2 I10 = make_float2(i1.x, i1.y), I11 = make_float2(i1.z, i1.w);
+  const float2 J00 = make_float2(j0.x, j0.y), J01 = make_float2(j0.z, j0.w);
+  const float2 J10 = make_float2(j1.x, j1.y), J11 = make_float2(j1.z, j1.w);
+  const float2 P[4] = {cadd(cmulc(I00, J00), cmulc(I01, J01)), cadd(cmulc(I00, J10), cmulc(I01, J11)),
+                       cadd(cmulc(I10, J00), cmulc(I11, J01)), cadd(cmulc(I10, J10), cmulc(I11, J11))};
+  #pragma unroll
+  for (int e = 0; e < 4; ++e) M[e] = make_float2(S * P[e].x, S * P[e].y);
+}
+
 __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs a) {
   extern __shared__ __align__(16) unsigned char solve_smem[];
-  float2* rows = reinterpret_cast<float2*>(solve_smem);                 // [apc][n_ant][4]
+  float2* rows = reinterpret_cast<float2*>(solve_smem);                 // [apc][2][n_ant] float4
   float2* Js = rows + (size_t)a.apc * a.n_ant * 4;                       // [n_ant][4]
   double2* Jold = reinterpret_cast<double2*>(Js + (size_t)a.n_ant * 4);  // [apc][4]
   double* s_norm = reinterpret_cast<double*>(Jold + (size_t)a.apc * 4);  // [apc][3]
@@ -153,39 +172,35 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
     // ---- per baseline: model matrix of source q-1, corrected average of source q
     const bool model = q > 0, corr = q < a.n_blk;
     const float Sprev = model ? (float)a.src[3 * (k - 1) + 2] : 0.f;
-    const float4* Jlast = reinterpret_cast<const float4*>(a.Jf[a.n_iter & 1]);
+    // a CTA's threads take consecutive baselines (mostly one first antenna), so
+    // the Jones rows they read come from L1
     for (int64_t bl = blockIdx.x * (int64_t)kSolveThreads + tid; bl < a.n_bl; bl += gstride) {
+      const int2 ij = a.bl_ant[bl];
       float2 Mp[4];
       if (model) {
-        // M = S J_i J_j^H, M[r][c] = S sum_k J_i[r][k] conj(J_j[c][k])
-        const int2 ij = a.bl_ant[bl];
-        const float4 i0 = __ldcg(Jlast + 2 * ij.x), i1 = __ldcg(Jlast + 2 * ij.x + 1);
-        const float4 j0 = __ldcg(Jlast + 2 * ij.y), j1 = __ldcg(Jlast + 2 * ij.y + 1);
-        const float2 I00 = make_float2(i0.x, i0.y), I01 = make_float2(i0.z, i0.w);
-        const float2 I10 = make_float2(i1.x, i1.y), I11 = make_float2(i1.z, i1.w);
-        const float2 J00 = make_float2(j0.x, j0.y), J01 = make_float2(j0.z, j0.w);
-        const float2 J10 = make_float2(j1.x, j1.y), J11 = make_float2(j1.z, j1.w);
-        const float2 P[4] = {cadd(cmulc(I00, J00), cmulc(I01, J01)), cadd(cmulc(I00, J10), cmulc(I01, J11)),
-                             cadd(cmulc(I10, J00), cmulc(I11, J01)), cadd(cmulc(I10, J10), cmulc(I11, J11))};
+        block_model_f(a.jones + (size_t)(k - 1) * a.n_ant * 4, ij, Sprev, Mp);
         #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          Mp[e] = make_float2(Sprev * P[e].x, Sprev * P[e].y);
-          a.M[((size_t)(q - 1) * a.n_bl + bl) * 4 + e] = Mp[e];
-        }
+        for (int e = 0; e < 4; ++e) a.M[((size_t)(q - 1) * a.n_bl + bl) * 4 + e] = Mp[e];
       }
       if (corr) {
         float2 v[4];
         #pragma unroll
         for (int e = 0; e < 4; ++e) v[e] = __ldg(a.Ablk + ((size_t)q * a.n_bl + bl) * 4 + e);
         const float2* D = a.Dtab + (size_t)bl * a.n_pairs + q * (q - 1) / 2;
+        // M_j recomputed from the solved Jones matrices (L1/L2) with the arithmetic
+        // that stored it, instead of read back from the [BK][n_bl][4] array in HBM
+        #pragma unroll 2
         for (int j = 0; j < q; ++j) {
           const float2 d = __ldg(D + j);
-          #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            // sources before q - 1 were modelled by this thread in earlier rounds
-            const float2 mj = j == q - 1 ? Mp[e] : a.M[((size_t)j * a.n_bl + bl) * 4 + e];
-            v[e] = csub(v[e], cmul(mj, d));
+          float2 mj[4];
+          if (j == q - 1) {
+            #pragma unroll
+            for (int e = 0; e < 4; ++e) mj[e] = Mp[e];
+          } else {
+            block_model_f(a.jones + (size_t)(a.s0 + j) * a.n_ant * 4, ij, (float)a.src[3 * (a.s0 + j) + 2], mj);
           }
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) v[e] = csub(v[e], cmul(mj[e], d));
         }
         #pragma unroll
         for (int e = 0; e < 4; ++e) a.avg[(size_t)bl * 4 + e] = v[e];
@@ -212,9 +227,11 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
         r0 = make_float4(w0.x, -w0.y, w1.x, -w1.y);
         r1 = make_float4(w0.z, -w0.w, w1.z, -w1.w);
       }
-      float4* d = reinterpret_cast<float4*>(rows + ((size_t)s * a.n_ant + qq) * 4);
-      d[0] = r0;
-      d[1] = r1;
+      // [slot][half][q] float4: entries (0, 1) and (2, 3) of V_pq in separate planes,
+      // so consecutive q are consecutive 16-byte words (conflict-free row reads)
+      float4* d = reinterpret_cast<float4*>(rows);
+      d[((size_t)s * 2) * a.n_ant + qq] = r0;
+      d[((size_t)s * 2 + 1) * a.n_ant + qq] = r1;
     }
     for (int i = tid; i < a.apc * 4; i += kSolveThreads)
       Jold[i] = make_double2((i & 3) == 0 || (i & 3) == 3 ? 1.0 : 0.0, 0.0);
@@ -240,7 +257,8 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
         #pragma unroll
         for (int i = 0; i < 4; ++i) Cm[i] = 0.f;
         if (live) {
-          const float4* row = reinterpret_cast<const float4*>(rows + (size_t)s * a.n_ant * 4);
+          const float4* row0 = reinterpret_cast<const float4*>(rows) + (size_t)s * 2 * a.n_ant;
+          const float4* row1 = row0 + a.n_ant;
           const float4* Jq4 = reinterpret_cast<const float4*>(Js);
           for (int q0 = (lane & 7) + 8 * w4; q0 < a.n_ant; q0 += 32 * kSolveBatch) {
             float2 V[kSolveBatch][4], J[kSolveBatch][4];
@@ -249,8 +267,8 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
               const int qq = q0 + 32 * u;
               float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0, j0 = v0, j1 = v0;
               if (qq < a.n_ant && qq != p) {   // V_pp = 0, and C excludes q = p
-                v0 = row[2 * qq];
-                v1 = row[2 * qq + 1];
+                v0 = row0[qq];
+                v1 = row1[qq];
                 if (first) {
                   j0 = make_float4(1.f, 0.f, 0.f, 0.f);
                   j1 = make_float4(0.f, 0.f, 1.f, 0.f);
