@@ -326,17 +326,16 @@ __global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restri
           // by angle difference, the denominator N sin(pi x) from the exact x (an
           // angle difference there would cancel).  When the signed difference
           // wraps (|x| >= 1/2), sin(pi x) = -sin(pi x_wrapped).
+          // branch-free (lanes of a warp mix near and far pairs): r = s(z) / sinc(th)
+          // with z = N th, s(z) = sin(z) / z from the series (near) or from the
+          // exact numerator (far, sign flipped when the difference wraps)
           const bool wrap = fabsf(xs) >= 0.5f;
-          const float th = 3.14159265358979f * xw;
-          float r;
-          if (!wrap && fabsf(fN * xw) < 0.5f) {
-            r = (dBw == 0) ? 1.0f : ratio_series(fN * th, th);
-          } else {
-            const float num = gk.sn * gj.cn - gk.cn * gj.sn;
-            float den = fN * th * sinc_series(th);
-            if (wrap) den = -den;
-            r = num / den;
-          }
+          const float th = 3.14159265358979f * xw, z = fN * th;
+          const bool near = !wrap && fabsf(fN * xw) < 0.5f;
+          const float num = gk.sn * gj.cn - gk.cn * gj.sn;
+          const float s_far = __fdividef(wrap ? -num : num, near ? 1.0f : z);
+          const float s_z = near ? sinc_series(z) : s_far;
+          const float r = __fdividef(s_z, sinc_series(th));
           dre[u] += r * er;
           dim[u] += r * ei;
         }

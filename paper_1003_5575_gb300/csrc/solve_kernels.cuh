@@ -19,18 +19,19 @@
 //   per antenna: antenna p belongs to CTA p % G (slot p / G).  Its row V_pq,
 //     q = 0..n_ant-1 (V_qp = V_pq^H applied while staging, V_pp = 0), is staged
 //     in shared memory once per source, and every sweep stages the FP32
-//     iterate of all antennas.  Slots go in quads, a quad to four warps: lane
-//     l of warp w of the quad takes slot l >> 3 of the quad and q = (l & 7) +
-//     8 w + 32 u.  Products and per-lane partial sums are FP32 (at most
-//     ceil(n_ant / 32) terms each), the four warps' partials of a lane position
-//     are added in FP32, the sum over the 8 lane positions of an antenna is
-//     FP64, and the 2x2 solve is FP64.
+//     iterate of all antennas.  Slots go in quads, a quad to W = 16, 8 or 4
+//     warps (16 when the CTA has one quad): lane l of warp w of the quad takes
+//     slot l >> 3 of the quad and q = (l & 7) + 8 w + 8 W u.  Products and
+//     per-lane partial sums are FP32, the W warps' partials of a lane position
+//     are added in FP32 in a fixed order, the sum over the 8 lane positions of
+//     an antenna is FP64 (the normal-equation accumulation), the 2x2 solve is
+//     FP32, and the iterate, its averaging and the convergence norms are FP64.
 //
-// FP64 arithmetic runs at 1/64 of the FP32 rate on GB300 and a warp
-// instruction costs the same with 4 or 32 lanes active, so the FP64 part is
-// packed: one reduce-scatter over 8-lane groups and one solve for the four
-// antennas of a quad (16 lanes), 26 + ~40 FP64 warp instructions per quad and
-// sweep (k_als_sweep spends about 150 per antenna).
+// FP64 arithmetic runs at 1/64 of the FP32 rate on GB300, a warp instruction
+// costs the same with 4 or 32 lanes active, and a dependent chain of FP64
+// operations is slow: the FP64 part is one reduce-scatter over 8-lane groups
+// for the four antennas of a quad (26 warp instructions) plus the short FP64
+// tail of the update (average, norms).
 //
 // Barriers spin on a global counter with a time limit: a CTA whose wait runs
 // out raises the abort flag, marks the current source's status
@@ -165,6 +166,8 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
   const int G = gridDim.x;
   const int64_t gstride = (int64_t)G * kSolveThreads;
   const int nquad = (a.apc + 3) >> 2;
+  // warps per quad: all 16 share the terms when the CTA has one quad (n_ant <= 4 G)
+  const int wpq = nquad <= 1 ? 16 : (nquad == 2 ? 8 : 4);
   unsigned nbar = 0;
 
   for (int q = 0; q <= a.n_blk; ++q) {
@@ -247,8 +250,8 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
       }
       __syncthreads();
       float2* Jf_new = a.Jf[it & 1];
-      for (int g0 = 0; g0 < nquad; g0 += kSolveWarps / 4) {        // CTA-uniform trip count
-        const int g = g0 + (warp >> 2), w4 = warp & 3, sa = lane >> 3;
+      for (int g0 = 0; g0 < nquad; g0 += kSolveWarps / wpq) {     // CTA-uniform trip count
+        const int g = g0 + warp / wpq, wq = warp % wpq, sa = lane >> 3;
         const int s = 4 * g + sa, p = blockIdx.x + s * G;
         const bool live = g < nquad && s < a.apc && p < a.n_ant;
         float A[8], Cm[4];
@@ -260,11 +263,12 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
           const float4* row0 = reinterpret_cast<const float4*>(rows) + (size_t)s * 2 * a.n_ant;
           const float4* row1 = row0 + a.n_ant;
           const float4* Jq4 = reinterpret_cast<const float4*>(Js);
-          for (int q0 = (lane & 7) + 8 * w4; q0 < a.n_ant; q0 += 32 * kSolveBatch) {
+          const int qstep = 8 * wpq;
+          for (int q0 = (lane & 7) + 8 * wq; q0 < a.n_ant; q0 += qstep * kSolveBatch) {
             float2 V[kSolveBatch][4], J[kSolveBatch][4];
             #pragma unroll
             for (int u = 0; u < kSolveBatch; ++u) {
-              const int qq = q0 + 32 * u;
+              const int qq = q0 + qstep * u;
               float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0, j0 = v0, j1 = v0;
               if (qq < a.n_ant && qq != p) {   // V_pp = 0, and C excludes q = p
                 v0 = row0[qq];
@@ -306,14 +310,16 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
         #pragma unroll
         for (int i = 0; i < 4; ++i) s_p32[warp][8 + i][lane] = Cm[i];
         __syncthreads();
-        if (w4 == 0 && g < nquad) {
-          // the quad's four warps' partials of this lane position (FP32, fixed
-          // order), then FP64 over the antenna's 8 lane positions
+        if (wq == 0 && g < nquad) {
+          // the quad's warps' partials of this lane position (FP32, fixed order),
+          // then FP64 over the antenna's 8 lane positions
           double v[16];
           #pragma unroll
-          for (int i = 0; i < 12; ++i)
-            v[i] = (double)(((s_p32[warp][i][lane] + s_p32[warp + 1][i][lane]) + s_p32[warp + 2][i][lane]) +
-                            s_p32[warp + 3][i][lane]);
+          for (int i = 0; i < 12; ++i) {
+            float x = s_p32[warp][i][lane];
+            for (int w = 1; w < wpq; ++w) x += s_p32[warp + w][i][lane];
+            v[i] = (double)x;
+          }
           #pragma unroll
           for (int i = 12; i < 16; ++i) v[i] = 0.0;
           group8_reduce_scatter16(v, lane);
@@ -325,18 +331,22 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
           const unsigned m4 = __ballot_sync(0xffffffffu, live && j < 4);   // solving lanes
           __syncwarp();
           if (live && j < 4) {
-            // J_p = A C^-1 / S in FP64, C = [c00 c01; conj(c01) c11]; lane j: entry e = j
+            // J_p = A C^-1 / S, C = [c00 c01; conj(c01) c11]; lane j: entry e = j.
+            // The 2x2 solve from the FP64 sums is FP32 (a dependent chain of ~25
+            // FP64 operations was half of a sweep on GB300); the iterate, its
+            // average with the previous one and the convergence norms are FP64.
             const double* tot = s_tot + s * 16;
             const int e = j, r = e >> 1, c = e & 1;
-            const double c00 = tot[8], c11 = tot[9];
-            const double2 c01 = make_double2(tot[10], tot[11]);
-            const double det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);
-            const double sc = 1.0 / (det * S);
-            const double2 i0c = c == 0 ? make_double2(c11 * sc, 0.0) : make_double2(-c01.x * sc, -c01.y * sc);
-            const double2 i1c = c == 0 ? make_double2(-c01.x * sc, c01.y * sc) : make_double2(c00 * sc, 0.0);
-            const double2 Ar0 = make_double2(tot[4 * r], tot[4 * r + 1]);
-            const double2 Ar1 = make_double2(tot[4 * r + 2], tot[4 * r + 3]);
-            double2 Jn = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
+            const float c00 = (float)tot[8], c11 = (float)tot[9];
+            const float2 c01 = make_float2((float)tot[10], (float)tot[11]);
+            const float det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);
+            const float sc = 1.0f / (det * (float)S);
+            const float2 i0c = c == 0 ? make_float2(c11 * sc, 0.f) : make_float2(-c01.x * sc, -c01.y * sc);
+            const float2 i1c = c == 0 ? make_float2(-c01.x * sc, c01.y * sc) : make_float2(c00 * sc, 0.f);
+            const float2 Ar0 = make_float2((float)tot[4 * r], (float)tot[4 * r + 1]);
+            const float2 Ar1 = make_float2((float)tot[4 * r + 2], (float)tot[4 * r + 3]);
+            const float2 Jn32 = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
+            double2 Jn = make_double2((double)Jn32.x, (double)Jn32.y);
             const double2 Jo = Jold[s * 4 + e];
             if (average) Jn = make_double2(0.5 * (Jn.x + Jo.x), 0.5 * (Jn.y + Jo.y));
             const double dx = Jn.x - Jo.x, dy = Jn.y - Jo.y;
