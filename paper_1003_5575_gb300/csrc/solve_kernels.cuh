@@ -24,14 +24,15 @@
 //     slot l >> 3 of the quad and q = (l & 7) + 8 w + 8 W u.  Products and
 //     per-lane partial sums are FP32, the W warps' partials of a lane position
 //     are added in FP32 in a fixed order, the sum over the 8 lane positions of
-//     an antenna is FP64 (the normal-equation accumulation), the 2x2 solve is
-//     FP32, and the iterate, its averaging and the convergence norms are FP64.
+//     an antenna is FP64 (the normal-equation accumulation, spread over four
+//     warps), and the 2x2 solve, the iterate, its averaging and the
+//     convergence norms are FP32 (per-source status sums FP64).
 //
 // FP64 arithmetic runs at 1/64 of the FP32 rate on GB300, a warp instruction
-// costs the same with 4 or 32 lanes active, and a dependent chain of FP64
-// operations is slow: the FP64 part is one reduce-scatter over 8-lane groups
-// for the four antennas of a quad (26 warp instructions) plus the short FP64
-// tail of the update (average, norms).
+// costs the same with 4 or 32 lanes active, and each dependent FP64 step
+// (conversions included) took ~100 cycles in a sweep: the FP64 part is the
+// accumulation only, 3 conversions + 4 additions + 1 conversion per warp in
+// four warps on the four sub-partitions.
 //
 // Barriers spin on a global counter with a time limit: a CTA whose wait runs
 // out raises the abort flag, marks the current source's status
@@ -45,7 +46,7 @@ namespace rts {
 
 constexpr int kSolveThreads = 512;
 constexpr int kSolveWarps = kSolveThreads / 32;
-constexpr int kSolveBatch = 2;             // q terms whose loads a lane issues together
+constexpr int kSolveBatch = 1;             // q terms per lane per loop iteration (2 spills registers)
 constexpr unsigned long long kSolveWaitNs = 2000000000ull;   // 2 s for one barrier wait
 constexpr unsigned kSolveMaxSpins = 1u << 24;                // and at most this many polls
 constexpr int kSolveStatusTimeout = -3;                      // status value (RTS_ECUDA)
@@ -72,11 +73,11 @@ struct BlockSolveArgs {
 };
 
 // dynamic shared memory: rows [apc][2][n_ant] float4, iterate [n_ant][4] float2,
-// previous FP64 iterate of the CTA's antennas [apc][4] double2, per-slot
-// convergence sums [apc][3] double, FP64 totals [apc][16] double
+// previous iterate of the CTA's antennas [apc][4] float2, per-slot convergence
+// sums [apc][3] double, normal-equation totals [apc][12] float
 inline size_t block_solve_smem(int n_ant, int apc) {
   return (size_t)apc * n_ant * 4 * sizeof(float2) + (size_t)n_ant * 4 * sizeof(float2) +
-         (size_t)apc * 4 * sizeof(double2) + (size_t)apc * 3 * sizeof(double) + (size_t)apc * 16 * sizeof(double);
+         (size_t)apc * 4 * sizeof(float2) + (size_t)apc * 3 * sizeof(double) + (size_t)apc * 12 * sizeof(float);
 }
 
 // Sum 16 doubles over the 8 lanes of a lane group (lanes 8i .. 8i+7): lane j of
@@ -156,9 +157,9 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
   extern __shared__ __align__(16) unsigned char solve_smem[];
   float2* rows = reinterpret_cast<float2*>(solve_smem);                 // [apc][2][n_ant] float4
   float2* Js = rows + (size_t)a.apc * a.n_ant * 4;                       // [n_ant][4]
-  double2* Jold = reinterpret_cast<double2*>(Js + (size_t)a.n_ant * 4);  // [apc][4]
+  float2* Jold = Js + (size_t)a.n_ant * 4;                               // [apc][4]
   double* s_norm = reinterpret_cast<double*>(Jold + (size_t)a.apc * 4);  // [apc][3]
-  double* s_tot = s_norm + (size_t)a.apc * 3;                            // [apc][16]
+  float* s_tot = reinterpret_cast<float*>(s_norm + (size_t)a.apc * 3);   // [apc][12]
   __shared__ float s_p32[kSolveWarps][12][32];   // FP32 partials of every lane
   __shared__ int s_flag;
 
@@ -237,8 +238,8 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
       d[((size_t)s * 2 + 1) * a.n_ant + qq] = r1;
     }
     for (int i = tid; i < a.apc * 4; i += kSolveThreads)
-      Jold[i] = make_double2((i & 3) == 0 || (i & 3) == 3 ? 1.0 : 0.0, 0.0);
-    const double S = a.src[3 * k + 2];
+      Jold[i] = make_float2((i & 3) == 0 || (i & 3) == 3 ? 1.f : 0.f, 0.f);
+    const float Sf = (float)a.src[3 * k + 2];
 
     // ---- n_iter Jacobi sweeps
     for (int it = 1; it <= a.n_iter; ++it) {
@@ -310,47 +311,58 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
         #pragma unroll
         for (int i = 0; i < 4; ++i) s_p32[warp][8 + i][lane] = Cm[i];
         __syncthreads();
-        if (wq == 0 && g < nquad) {
-          // the quad's warps' partials of this lane position (FP32, fixed order),
-          // then FP64 over the antenna's 8 lane positions
-          double v[16];
+        // FP64 sums: warp r (r = 0..3, one per SM sub-partition) of the quad takes
+        // values 3r .. 3r+2 of the 12 sums (A: 8 reals, C: 4) for the quad's four
+        // antennas: the W warps' FP32 partials of its lane position (fixed order),
+        // then FP64 over the antenna's 8 lane positions (a reduce-scatter of 4
+        // slots: 3 conversions, 4 additions); the totals go to shared memory as FP32
+        // for the solve
+        if (wq < 4 && g < nquad) {
+          double v[4];
           #pragma unroll
-          for (int i = 0; i < 12; ++i) {
-            float x = s_p32[warp][i][lane];
-            for (int w = 1; w < wpq; ++w) x += s_p32[warp + w][i][lane];
+          for (int i = 0; i < 3; ++i) {
+            float x = s_p32[warp - wq][3 * wq + i][lane];
+            for (int w = 1; w < wpq; ++w) x += s_p32[warp - wq + w][3 * wq + i][lane];
             v[i] = (double)x;
           }
+          v[3] = 0.0;
           #pragma unroll
-          for (int i = 12; i < 16; ++i) v[i] = 0.0;
-          group8_reduce_scatter16(v, lane);
-          const int j = lane & 7;
-          if (live && j < 6) {
-            s_tot[s * 16 + 2 * j] = v[0];
-            s_tot[s * 16 + 2 * j + 1] = v[1];
+          for (int o = 4, n = 4; o >= 2; o >>= 1, n >>= 1) {
+            const bool upper = (lane & o) != 0;
+            #pragma unroll
+            for (int i = 0; i < n / 2; ++i) {
+              const double send = upper ? v[i] : v[i + n / 2];
+              const double keep = upper ? v[i + n / 2] : v[i];
+              v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
           }
+          const float tot = (float)(v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1));   // lane j: slot j >> 1
+          const int j = lane & 7;
+          if (live && (j & 1) == 0 && j < 6) s_tot[s * 12 + 3 * wq + (j >> 1)] = tot;
+        }
+        __syncthreads();
+        if (wq == 0 && g < nquad) {
+          const int j = lane & 7;
           const unsigned m4 = __ballot_sync(0xffffffffu, live && j < 4);   // solving lanes
-          __syncwarp();
           if (live && j < 4) {
-            // J_p = A C^-1 / S, C = [c00 c01; conj(c01) c11]; lane j: entry e = j.
-            // The 2x2 solve from the FP64 sums is FP32 (a dependent chain of ~25
-            // FP64 operations was half of a sweep on GB300); the iterate, its
-            // average with the previous one and the convergence norms are FP64.
-            const double* tot = s_tot + s * 16;
+            // J_p = A C^-1 / S in FP32 from the FP64 sums, C = [c00 c01; conj(c01) c11];
+            // lane j: entry e = j.  Iterate, averaging and convergence norms FP32:
+            // on GB300 each dependent FP64 step of this tail cost ~100 cycles
+            const float* tot = s_tot + s * 12;
             const int e = j, r = e >> 1, c = e & 1;
-            const float c00 = (float)tot[8], c11 = (float)tot[9];
-            const float2 c01 = make_float2((float)tot[10], (float)tot[11]);
+            const float c00 = tot[8], c11 = tot[9];
+            const float2 c01 = make_float2(tot[10], tot[11]);
             const float det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);
-            const float sc = 1.0f / (det * (float)S);
+            const float sc = 1.0f / (det * Sf);
             const float2 i0c = c == 0 ? make_float2(c11 * sc, 0.f) : make_float2(-c01.x * sc, -c01.y * sc);
             const float2 i1c = c == 0 ? make_float2(-c01.x * sc, c01.y * sc) : make_float2(c00 * sc, 0.f);
-            const float2 Ar0 = make_float2((float)tot[4 * r], (float)tot[4 * r + 1]);
-            const float2 Ar1 = make_float2((float)tot[4 * r + 2], (float)tot[4 * r + 3]);
-            const float2 Jn32 = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
-            double2 Jn = make_double2((double)Jn32.x, (double)Jn32.y);
-            const double2 Jo = Jold[s * 4 + e];
-            if (average) Jn = make_double2(0.5 * (Jn.x + Jo.x), 0.5 * (Jn.y + Jo.y));
-            const double dx = Jn.x - Jo.x, dy = Jn.y - Jo.y;
-            double dn = dx * dx + dy * dy, nn = Jn.x * Jn.x + Jn.y * Jn.y;
+            const float2 Ar0 = make_float2(tot[4 * r], tot[4 * r + 1]);
+            const float2 Ar1 = make_float2(tot[4 * r + 2], tot[4 * r + 3]);
+            float2 Jn = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
+            const float2 Jo = Jold[s * 4 + e];
+            if (average) Jn = make_float2(0.5f * (Jn.x + Jo.x), 0.5f * (Jn.y + Jo.y));
+            const float dx = Jn.x - Jo.x, dy = Jn.y - Jo.y;
+            float dn = dx * dx + dy * dy, nn = Jn.x * Jn.x + Jn.y * Jn.y;
             int bad = !(isfinite(Jn.x) && isfinite(Jn.y));
             #pragma unroll
             for (int o = 1; o <= 2; o <<= 1) {
@@ -359,13 +371,12 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
               bad |= __shfl_xor_sync(m4, bad, o);
             }
             Jold[s * 4 + e] = Jn;
-            const float2 Jf = make_float2((float)Jn.x, (float)Jn.y);
-            Jf_new[(size_t)p * 4 + e] = Jf;
+            Jf_new[(size_t)p * 4 + e] = Jn;
             if (last) {
-              a.jones[((size_t)k * a.n_ant + p) * 4 + e] = Jf;
+              a.jones[((size_t)k * a.n_ant + p) * 4 + e] = Jn;
               if (e == 0) {
-                s_norm[3 * s] = dn;
-                s_norm[3 * s + 1] = nn;
+                s_norm[3 * s] = (double)dn;
+                s_norm[3 * s + 1] = (double)nn;
                 s_norm[3 * s + 2] = (double)bad;
               }
             }
