@@ -46,6 +46,14 @@ struct BlockPassArgs {
   double inv_n;
 };
 
+// a Q0.64 phase read as a signed fraction of a turn, x 2^-64, in FP32: the high
+// word exactly (scaled by 2^-32) plus the low word (scaled by 2^-64)
+__device__ __forceinline__ float q64_signed_to_float(unsigned long long x) {
+  const int hi = (int)(x >> 32);
+  const unsigned lo = (unsigned)x;
+  return fmaf((float)hi, 2.3283064365386963e-10f, (float)lo * 5.42101086242752217e-20f);
+}
+
 // exp(+2 pi i phi) from a Q0.64 phase, using its high word (truncation error
 // below 2^-32 turns)
 __device__ inline float2 phasor_hw(unsigned long long ph) {
@@ -56,12 +64,14 @@ __device__ inline float2 phasor_hw(unsigned long long ph) {
 }
 
 // exp(2 pi i x) for a Q0.64 phase x: the top 24 bits through sincospif, the
-// remaining bits (|r| < 2^-25 turns) by the first-order rotation 1 + 2 pi i r
+// remaining bits (0 <= r < 2^-24 turns) by the first-order rotation 1 + 2 pi i r
+// (second-order term below 1e-13).  32-bit integer conversions only (64-bit
+// integer-to-float conversions are slow on this GPU).
 __device__ inline float2 phasor_q64_fine(unsigned long long x) {
-  const long long sx = (long long)x;
-  const float hi = __ll2float_rn(sx) * 5.42101086242752217e-20f;          // 2^-64
-  const long long back = __float2ll_rn(hi * 1.8446744073709551616e19f);   // exact
-  const float lo = (float)(sx - back) * 5.42101086242752217e-20f;
+  const int xh = (int)(x >> 32);
+  const float hi = (float)(xh >> 8) * 5.9604644775390625e-08f;                           // 2^-24
+  const float lo = fmaf((float)(xh & 0xff), 2.3283064365386963e-10f,                     // 2^-32
+                        (float)(unsigned)x * 5.42101086242752217e-20f);                 // 2^-64
   float sn, cs;
   sincospif(2.0f * hi, &sn, &cs);
   const float w = 6.28318530717958647692f * lo;
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(256) k_block_phases(const double* __restrict__
     const long long hi = __mul64hi(nn, bs);
     const long long los = (long long)lo;
     float sn, cn;
-    sincospif((float)los * 5.42101086242752217e-20f, &sn, &cn);
+    sincospif(q64_signed_to_float((unsigned long long)los), &sn, &cn);
     if ((hi + (los < 0 ? 1 : 0)) & 1) { sn = -sn; cn = -cn; }
     g.sn = sn; g.cn = cn;
     trig[q] = g;
@@ -284,6 +294,7 @@ __global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restri
   constexpr int kU = (kPairs + 255) / 256;
   __shared__ GeoTrig sG[16][BK];               // times handled in chunks of 16
   __shared__ unsigned long long sB[16][BK];
+  __shared__ float sBf[16][BK];                // signed B in turns (FP32)
   const int64_t bl = blockIdx.x;
   const int n_pairs = n_blk * (n_blk - 1) / 2;
   const float fN = (float)n_chan;
@@ -305,7 +316,9 @@ __global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restri
       const int t = q / n_blk, k = q - t * n_blk;
       const size_t at = ((size_t)bl * n_time + t0 + t) * BK + k;
       sG[t][k] = trig[at];
-      sB[t][k] = ph[at].b;
+      const unsigned long long b = ph[at].b;
+      sB[t][k] = b;
+      sBf[t][k] = q64_signed_to_float(b);
     }
     __syncthreads();
     #pragma unroll
@@ -318,10 +331,10 @@ __global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restri
           const float er = gk.u.x * gj.u.x + gk.u.y * gj.u.y;
           const float ei = gk.u.y * gj.u.x - gk.u.x * gj.u.y;
           // ratio sin(pi N x) / (N sin(pi x)) at x = B_k - B_j (signed values)
-          const long long dBw = (long long)(sB[t][k] - sB[t][j]);
-          const float xw = (float)dBw * 5.42101086242752217e-20f;
-          const float xs = (float)(long long)sB[t][k] * 5.42101086242752217e-20f -
-                           (float)(long long)sB[t][j] * 5.42101086242752217e-20f;
+          // the exact 64-bit difference, converted through 32-bit halves (64-bit
+          // integer-to-float conversions are slow on this GPU)
+          const float xw = q64_signed_to_float(sB[t][k] - sB[t][j]);
+          const float xs = sBf[t][k] - sBf[t][j];
           // near pairs (|N x| < 1/2): series in the exact x; others: the numerator
           // by angle difference, the denominator N sin(pi x) from the exact x (an
           // angle difference there would cancel).  When the signed difference
