@@ -82,13 +82,23 @@ inline size_t t5_pass_smem(int n_chan) { return (size_t)T5Smem(t5_nq4(n_chan)).t
 // the subtraction epilogue (8 tiles x 4 pols per warp) reads conflict-free
 __device__ __forceinline__ int t5_swz(int c) { return c ^ ((c >> 4) & 3); }
 
-__device__ __forceinline__ uint32_t t5_tf32(float x) { return tf32_rna(x); }
+// TF32 rounding (to nearest, ties away from zero: the result of cvt.rna.tf32.f32
+// for finite x below the FP32 maximum) with two integer operations: add half of
+// the dropped 13-bit unit to the magnitude bits and clear them.  A conversion
+// instruction per value was a large share of this pass on GB300.
+__device__ __forceinline__ uint32_t t5_tf32(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 
 // x = hi + lo with hi the TF32 rounding of x and lo the exact remainder; the
 // MMA reads lo truncated to TF32 (error below 2^-21 |x|)
 __device__ __forceinline__ float2 t5_split(float x) {
-  const float hi = __uint_as_float(tf32_rna(x));
+  const float hi = __uint_as_float(t5_tf32(x));
   return make_float2(hi, x - hi);
+}
+
+// stored operand tables: hi and lo both rounded to TF32
+__device__ __forceinline__ float2 t5_split_store(float x) {
+  const float hi = __uint_as_float(t5_tf32(x));
+  return make_float2(hi, __uint_as_float(t5_tf32(x - hi)));
 }
 
 template <bool SUB, bool ACC>
@@ -177,7 +187,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
       #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float2 z = phasor_hw((unsigned long long)(4 * i + u) * ph[kT5Src + k].b);
-        zr[u] = split_store(z.x); zi[u] = split_store(z.y); zn[u] = split_store(-z.y);
+        zr[u] = t5_split_store(z.x); zi[u] = t5_split_store(z.y); zn[u] = t5_split_store(-z.y);
       }
       const int o0 = kmaj_byte(k, 4 * i, 32), o1 = kmaj_byte(k, 16 + 4 * i, 32);
       const int o2 = kmaj_byte(64 + k, 4 * i, 32), o3 = kmaj_byte(64 + k, 16 + 4 * i, 32);
@@ -201,8 +211,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_block_pass_t5(BlockPassArgs a
     const int r = (tid & 3) + 4 * (tid >> 7), j = (tid >> 2) & 31;
     const float2 z0 = phasor_hw((unsigned long long)r * ph[2 * j].b);
     const float2 z1 = phasor_hw((unsigned long long)r * ph[2 * j + 1].b);
-    const float2 a0 = split_store(z0.x), a1 = split_store(z0.y), a2 = split_store(z1.x), a3 = split_store(z1.y);
-    const float2 n1 = split_store(-z0.y), n3 = split_store(-z1.y);
+    const float2 a0 = t5_split_store(z0.x), a1 = t5_split_store(z0.y), a2 = t5_split_store(z1.x), a3 = t5_split_store(z1.y);
+    const float2 n1 = t5_split_store(-z0.y), n3 = t5_split_store(-z1.y);
     #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int pout = u ^ (j & 1);
