@@ -280,6 +280,18 @@ int rts_peel_timing_read(rts_peel_t* h, double* ms, int64_t* groups, int64_t* la
  * NULL handle. */
 int rts_peel_kernels(const rts_peel_t* h, int32_t* block_kernel, int32_t* solve_kernel);
 
+/* Failure-detection self-test of the grid barrier the cooperative block solve
+ * uses (no paper counterpart).  Launches n_cta CTAs (1 .. the device's
+ * co-resident limit, at most 1024) on the current device, cooperatively, that
+ * meet at `rounds` (1 .. 10000) barriers expecting n_cta + missing CTAs
+ * (missing 0 or 1).  With missing = 0 every wait completes and
+ * *h_completed = n_cta; with missing = 1 no wait can complete: each CTA's wait
+ * runs out its 2 s limit or sees another CTA's abort flag, and the kernel
+ * returns with *h_completed = 0 instead of hanging.  Synchronous; allocates
+ * and frees a few bytes of device memory.  RTS_EINVAL for bad arguments,
+ * RTS_ECUDA for a failed launch. */
+int rts_barrier_selftest(int32_t n_cta, int32_t missing, int32_t rounds, int32_t* h_completed);
+
 /* Page-locked host memory for the host-buffer calls (the paper, Section 4,
  * moved its host allocator to pinned memory for faster DMA).  rts_host_alloc
  * returns RTS_ENOMEM when the allocation fails; rts_host_free(NULL) is a no-op. */

@@ -34,7 +34,8 @@ EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_ca
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad", "rts_peel_offsets",
            "rts_offsets_solve",
            "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
-           "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_host_alloc", "rts_host_free",
+           "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_barrier_selftest",
+           "rts_host_alloc", "rts_host_free",
            "rts_peel_last_error", "rts_peel_destroy")
 
 
@@ -104,6 +105,8 @@ def lib():
             L.rts_peel_timing_read.restype = ctypes.c_int
             L.rts_peel_timing_read.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_int64),
                                                ctypes.POINTER(ctypes.c_int64)]
+            L.rts_barrier_selftest.restype = ctypes.c_int
+            L.rts_barrier_selftest.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _ip]
             L.rts_peel_kernels.restype = ctypes.c_int
             L.rts_peel_kernels.argtypes = [_vp, _ip, _ip]
             L.rts_host_alloc.restype = ctypes.c_int
@@ -187,6 +190,13 @@ def rts_peel_kernels(h):
     bk, sk = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().rts_peel_kernels(h, ctypes.byref(bk), ctypes.byref(sk)), h)
     return bk.value, sk.value
+
+
+def rts_barrier_selftest(n_cta: int, missing: int, rounds: int) -> int:
+    """CTAs whose waits all completed (see include/rts_peel.h)."""
+    out = ctypes.c_int32()
+    _check(lib().rts_barrier_selftest(int(n_cta), int(missing), int(rounds), ctypes.byref(out)), None)
+    return out.value
 
 
 def rts_peel_timing(h, enable: int):

@@ -1012,6 +1012,43 @@ void rts_peel_destroy(rts_peel_t* h) {
   delete h;
 }
 
+int rts_barrier_selftest(int32_t n_cta, int32_t missing, int32_t rounds, int32_t* h_completed) {
+  g_init_err.clear();
+  if (!h_completed) return fail(nullptr, RTS_EINVAL, "h_completed is NULL");
+  if (n_cta < 1 || n_cta > 1024 || missing < 0 || missing > 1 || rounds < 1 || rounds > 10000)
+    return fail(nullptr, RTS_EINVAL, "rts_barrier_selftest: n_cta in [1, 1024], missing in [0, 1], rounds in [1, 10000]");
+  int dev = 0, coop = 0, n_sm = 0, occ = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_barrier_selftest, 128, 0)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "device query");
+  if (!coop || n_cta > n_sm * occ) return fail(nullptr, RTS_EINVAL, "rts_barrier_selftest: n_cta above the co-resident limit");
+  unsigned* sync = nullptr;
+  int* ok = nullptr;
+  if ((e = cudaMalloc((void**)&sync, 2 * sizeof(unsigned))) != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc");
+  if ((e = cudaMalloc((void**)&ok, n_cta * sizeof(int))) != cudaSuccess) {
+    cudaFree(sync);
+    return cuda_fail(nullptr, e, "cudaMalloc");
+  }
+  std::vector<int> h_ok(n_cta, 0);
+  int r = missing;
+  void* args[] = {&sync, &rounds, &r, &ok};
+  if ((e = cudaMemset(sync, 0, 2 * sizeof(unsigned))) == cudaSuccess &&
+      (e = cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(n_cta), dim3(128), args, 0, 0)) ==
+          cudaSuccess &&
+      (e = cudaDeviceSynchronize()) == cudaSuccess)
+    e = cudaMemcpy(h_ok.data(), ok, n_cta * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(sync);
+  cudaFree(ok);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "barrier self-test");
+  int done = 0;
+  for (int v : h_ok) done += v != 0;
+  *h_completed = done;
+  return RTS_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

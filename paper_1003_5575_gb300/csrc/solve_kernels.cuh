@@ -107,15 +107,16 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Grid-wide barrier number n (1, 2, ...) of a cooperative launch.  Returns
-// false when the wait gave up (its own time limit, or another CTA's abort).
-__device__ bool solve_barrier(unsigned* sync, unsigned n, int* s_flag) {
+// Grid-wide barrier number n (1, 2, ...) of a cooperative launch in which
+// n_cta CTAs take part.  Returns false when the wait gave up (its own time
+// limit, or another CTA's abort).
+__device__ bool solve_barrier_n(unsigned* sync, unsigned n, unsigned n_cta, int* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
     // release: this CTA's writes (ordered before by the CTA barrier) are
     // visible to every CTA whose acquire load sees the count
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(sync) : "memory");
-    const unsigned target = n * gridDim.x;
+    const unsigned target = n * n_cta;
     int ok = 1;
     const unsigned long long t0 = global_ns();
     for (unsigned spin = 0; ld_acquire_u32(sync) < target; ++spin) {
@@ -132,6 +133,23 @@ __device__ bool solve_barrier(unsigned* sync, unsigned n, int* s_flag) {
   }
   __syncthreads();
   return *s_flag != 0;
+}
+
+__device__ __forceinline__ bool solve_barrier(unsigned* sync, unsigned n, int* s_flag) {
+  return solve_barrier_n(sync, n, gridDim.x, s_flag);
+}
+
+// Failure-detection self-test of the barrier: the CTAs of a cooperative launch
+// meet at `rounds` barriers that expect gridDim.x + missing CTAs.  With missing
+// = 0 every wait completes; with missing > 0 the first wait cannot complete, a
+// CTA's time limit runs out, it raises the abort flag and every CTA returns.
+// ok[c] = 1 when every wait of CTA c completed.
+__global__ void __launch_bounds__(128) k_barrier_selftest(unsigned* sync, int rounds, int missing, int* ok) {
+  __shared__ int s_flag;
+  int good = 1;
+  for (int r = 1; r <= rounds && good; ++r)
+    good = solve_barrier_n(sync, (unsigned)r, gridDim.x + (unsigned)missing, &s_flag);
+  if (threadIdx.x == 0) ok[blockIdx.x] = good;
 }
 
 // at most 64 registers a thread: half of an SM, so the geometry kernels of later
