@@ -540,7 +540,7 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
     out["adjoint"] = {
         "workload": "512 ant x 768 ch x 8 t, 300 sources, positions perturbed N(0, 1 arcmin^2); loss + dL/d(J,l,m,S)",
         "ms_per_step": ms_adj, "loss": float(loss.item()),
-        "roofline": {"bound": "alu", "kernel": "k_grad_sweep<true,false> (+ reductions, in the step time)",
+        "roofline": {"bound": "alu", "kernel": "k_grad_sweep_fac<false> (factorised phasor tables; + reductions, in the step time)",
                      "achieved": adj_tflops, "peak": adj_peak, "unit": "TFLOP/s", "frac": adj_tflops / adj_peak,
                      "algorithmic_flops_per_update": ADJ_FLOPS_PER_UPDATE, "traffic": None},
         "fp64_ms_per_step_at_300_sources_extrapolated": per_upd_64 * c5.n_src * c5.n_vis,

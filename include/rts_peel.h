@@ -20,6 +20,9 @@
  *   2x2 layout [XX, XY, YX, YY] row major, complex = interleaved (re, im)
  *   cube       vis[n_time][n_bl][n_chan][4] complex
  *              (complex64 in RTS_PREC_MIXED, complex128 in RTS_PREC_FP64)
+ *              device cubes and averages (d_vis, d_resid, d_avg) start on a
+ *              16-byte boundary (the kernels move a polarisation pair per
+ *              16-byte access; a misaligned pointer is RTS_EINVAL)
  *   Jones      jones[n_src][n_ant][4] complex, same precision as the cube
  *   sources    host double [n_src][3] = (l, m, S in Jy), in peel order
  *
@@ -90,7 +93,17 @@ typedef struct rts_peel_config {
                            correction and per model step).  Same arithmetic except
                            the grouping of the FP32 partial sums of the normal
                            equations (FP32-rounding-level differences). */
+  int32_t grad_kernel;   /* RTS_PREC_MIXED adjoint (rts_peel_grad, rts_peel_offsets):
+                           RTS_GRAD_AUTO (0: phasors factorised per 16-channel group into
+                           two shared-memory tables, T1[q] T2[r], when the tables of all
+                           n_src sources fit in shared memory, about n_src <= 580 on
+                           GB300; otherwise as RTS_GRAD_DIRECT), RTS_GRAD_DIRECT (1: one
+                           hardware sin/cos per source and sample).  FP32-level accuracy
+                           either way; RTS_PREC_FP64 always evaluates every phasor in FP64. */
 } rts_peel_config;
+
+#define RTS_GRAD_AUTO   0
+#define RTS_GRAD_DIRECT 1
 
 #define RTS_SOLVE_AUTO     0
 #define RTS_SOLVE_LAUNCHES 1

@@ -13,6 +13,7 @@ from ._abi import (  # noqa: F401
     rts_peel_pipeline_submit, rts_peel_pipeline_wait, rts_peel_last_error, rts_peel_destroy,
     rts_peel_timing, rts_peel_timing_read, rts_peel_kernels, rts_host_alloc, rts_host_free, KERNEL_CLASSES, RTS_BLOCK,
     RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR, RTS_BLOCK_TCGEN05, RTS_SOLVE_AUTO, RTS_SOLVE_LAUNCHES,
+    RTS_GRAD_AUTO, RTS_GRAD_DIRECT,
 )
 
 

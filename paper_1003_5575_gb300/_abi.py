@@ -27,6 +27,7 @@ RTS_K_CLASSES = 10
 RTS_BLOCK = 64
 RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR, RTS_BLOCK_TCGEN05 = 0, 1, 2, 3
 RTS_SOLVE_AUTO, RTS_SOLVE_LAUNCHES = 0, 1
+RTS_GRAD_AUTO, RTS_GRAD_DIRECT = 0, 1
 KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "grad", "grad_reduce",
                   "block_pass", "block_fix", "offsets")
 
@@ -46,7 +47,7 @@ class rts_peel_config(ctypes.Structure):
                 ("uvw", ctypes.POINTER(ctypes.c_double)),
                 ("freq_hz", ctypes.POINTER(ctypes.c_double)),
                 ("sources_per_pass", ctypes.c_int32), ("block_kernel", ctypes.c_int32),
-                ("solve_kernel", ctypes.c_int32)]
+                ("solve_kernel", ctypes.c_int32), ("grad_kernel", ctypes.c_int32)]
 
 
 class RtsError(RuntimeError):

@@ -31,6 +31,7 @@ namespace rts {
 constexpr int kGradThreads = 512;
 constexpr int kGradTile = 512;        // channels per shared-memory tile
 constexpr int kGradChunk = 512;       // sources per CTA in the backward phase
+constexpr size_t kGradMaxSmem = 227 * 1024;
 
 struct __align__(16) DirQ { double x, y, z, w; };   // (l, m, n - 1, S) of one source
 
@@ -84,6 +85,40 @@ grad_phasor(unsigned long long A, unsigned long long B, double tau, const double
   } else {
     return phasor_d(tau * freq_c[c]);
   }
+}
+
+// per (source k, baseline bl): G, and the (dl, dm, dS) contributions
+//   dL/dl = -4 pi S Im tr(H^lH J_i J_j^H), dL/dm likewise, dL/dS = -2 Re tr(G^H J_i J_j^H)
+template <typename T>
+__device__ inline void grad_store(const GradArgs& a, int k, int64_t bl, int2 ij, const double (&G)[8],
+                                  const double (&Hl)[8], const double (&Hm)[8]) {
+  using C = typename cplx_of<T>::type;
+  M22<double2> Ji, Jj, Gm, Hlm, Hmm;
+  #pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    C p = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.x) * 4 + e);
+    C q = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.y) * 4 + e);
+    Ji.e[e] = make_double2(p.x, p.y); Jj.e[e] = make_double2(q.x, q.y);
+    Gm.e[e] = make_double2(G[2 * e], G[2 * e + 1]);
+    Hlm.e[e] = make_double2(Hl[2 * e], Hl[2 * e + 1]);
+    Hmm.e[e] = make_double2(Hm[2 * e], Hm[2 * e + 1]);
+    a.G[((size_t)k * a.n_bl + bl) * 4 + e] = Gm.e[e];
+  }
+  const double S = a.dir[k].w;
+  M22<double2> P = mmul_h(Ji, Jj);                 // J_i J_j^H
+  // tr(X^H Y) = sum_e conj(X_e) Y_e
+  double2 tG = make_double2(0, 0), tl = make_double2(0, 0), tm = make_double2(0, 0);
+  #pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    tG = cadd(tG, cconjmul(Gm.e[e], P.e[e]));
+    tl = cadd(tl, cconjmul(Hlm.e[e], P.e[e]));
+    tm = cadd(tm, cconjmul(Hmm.e[e], P.e[e]));
+  }
+  const double four_pi = 12.566370614359172953850573533118;
+  double* o = a.gsc + ((size_t)k * a.n_bl + bl) * 3;
+  o[0] = -four_pi * S * tl.y;
+  o[1] = -four_pi * S * tm.y;
+  o[2] = -2.0 * tG.x;
 }
 
 template <bool MIXED, bool WEIGHTED>
@@ -222,34 +257,258 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_sweep(GradArgs a) {
     for (int w = 0; w < kGradThreads / 32; ++w) s += s_loss[w];
     a.loss_bl[bl] = s;
   }
-  if (bw && my_g == 0) {
-    const int k = k0 + my_k;
-    M22<double2> Ji, Jj, Gm, Hlm, Hmm;
+  if (bw && my_g == 0) grad_store<T>(a, k0 + my_k, bl, ij, G, Hl, Hm);
+}
+
+// exp(+2 pi i x) of a Q0.64 phase x rounded to Q0.32 (the hardware sin/cos,
+// as the per-sample sweep uses for every sample)
+__device__ inline float2 grad_phasor_tab(unsigned long long ph) { return phasor_f(q64_to_turns(ph)); }
+
+// The FP32 adjoint with factorised phasors.  Within a tile of kGfTile channels
+// starting at c0, channel c = c0 + 16 q + r has
+//   exp(+2 pi i phi_k(c)) = T1_k[q] T2_k[r],
+//   T1_k[q] = exp(2 pi i (A_k + (c0 + 16 q) B_k)),  T2_k[r] = exp(2 pi i r B_k)
+// (A_k, B_k the Q0.64 phase at channel 0 and its per-channel step), so both
+// halves of the sweep multiply table entries instead of evaluating sin/cos:
+//   forward   R(c) = V(c) - sum_k M_k conj(T1_k[q] T2_k[r])   (thread = channel)
+//   backward  sum_c R(c) P_k(c) = sum_q T1_k[q] s_q,  s_q = sum_r R(16q + r) T2_k[r]
+//             sum_c c R(c) P_k(c) = sum_q T1_k[q] [(c0 + 16q - 1) s_q + a_q]
+//             with a_q = sum_r (r + 1) x_r, x_r = R(16q + r) T2_k[r], built as
+//             the running sum of the suffix sums while r runs down from 15
+//             (thread = (source, group of q)).
+// Tables are [q or r][kp] with kp = 1 (mod 16): the forward's 16 distinct r of
+// a warp and the backward's consecutive sources fall on distinct banks.  The
+// per-(source, baseline) outputs are those of k_grad_sweep.
+constexpr int kGfThreads = 384;
+constexpr int kGfTile = 384;          // channels per tile: one per thread in the forward
+constexpr int kGfNq = kGfTile / 16;
+constexpr int kGfChunk = kGfThreads;  // sources per CTA in the backward
+
+__host__ __device__ inline int grad_fac_kp(int n_src) { return ((n_src + 15) / 16) * 16 + 1; }
+
+inline size_t grad_fac_smem_bytes(int n_src) {
+  const size_t kp = (size_t)grad_fac_kp(n_src);
+  return (size_t)kGfTile * 4 * sizeof(float2)           // R
+         + (size_t)n_src * 4 * sizeof(float2)            // M
+         + (size_t)kGfThreads * 16 * sizeof(float)        // backward partials
+         + (size_t)(kGfNq + 16) * kp * sizeof(float2)     // T1, T2
+         + (size_t)n_src * 2 * sizeof(unsigned long long) // A, B
+         + (size_t)kGfTile * sizeof(float);               // channel weights of the tile
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kGfThreads, 1) k_grad_sweep_fac(GradArgs a) {
+  extern __shared__ __align__(16) unsigned char g_smem[];
+  const int K = a.n_src;
+  const int kp = grad_fac_kp(K);
+  float2* sR = reinterpret_cast<float2*>(g_smem);                  // [kGfTile][4]
+  float2* sM = sR + kGfTile * 4;                                   // [K][4]
+  float* sPart = reinterpret_cast<float*>(sM + (size_t)K * 4);     // [16][threads]
+  float2* sT1 = reinterpret_cast<float2*>(sPart + (size_t)kGfThreads * 16);   // [kGfNq][kp]
+  float2* sT2 = sT1 + (size_t)kGfNq * kp;                          // [16][kp]
+  unsigned long long* sA = reinterpret_cast<unsigned long long*>(sT2 + (size_t)16 * kp);
+  unsigned long long* sB = sA + K;
+  float* sW = reinterpret_cast<float*>(sB + K);                    // [kGfTile]
+  __shared__ double s_uvw[3];
+  __shared__ double s_loss[kGfThreads / 32];
+
+  const int tid = threadIdx.x;
+  const int64_t bl = blockIdx.x;
+  const int2 ij = a.bl_ant[bl];
+  const int k0 = blockIdx.y * kGfChunk;
+  const int kc = max(1, min(kGfChunk, K - k0));            // sources of this CTA's backward phase
+  const int groups = max(1, min(kGfNq, kGfThreads / kc));
+  const int my_k = tid % kc, my_g = tid / kc;
+  const bool bw = my_g < groups && k0 + my_k < K;
+  const int kb = k0 + my_k;                                 // source of the backward item
+  const int qa = my_g * kGfNq / groups, qb = (my_g + 1) * kGfNq / groups;
+
+  for (int k = tid; k < K; k += kGfThreads) {
+    M22<double2> Ji, Jj;
     #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      C p = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.x) * 4 + e);
-      C q = load_j<T>(a.jones, ((size_t)k * a.n_ant + ij.y) * 4 + e);
+      float2 p = load_j<float>(a.jones, ((size_t)k * a.n_ant + ij.x) * 4 + e);
+      float2 q = load_j<float>(a.jones, ((size_t)k * a.n_ant + ij.y) * 4 + e);
       Ji.e[e] = make_double2(p.x, p.y); Jj.e[e] = make_double2(q.x, q.y);
-      Gm.e[e] = make_double2(G[2 * e], G[2 * e + 1]);
-      Hlm.e[e] = make_double2(Hl[2 * e], Hl[2 * e + 1]);
-      Hmm.e[e] = make_double2(Hm[2 * e], Hm[2 * e + 1]);
-      a.G[((size_t)k * a.n_bl + bl) * 4 + e] = Gm.e[e];
     }
+    M22<double2> P = mmul_h(Ji, Jj);
     const double S = a.dir[k].w;
-    M22<double2> P = mmul_h(Ji, Jj);                 // J_i J_j^H
-    // tr(X^H Y) = sum_e conj(X_e) Y_e
-    double2 tG = make_double2(0, 0), tl = make_double2(0, 0), tm = make_double2(0, 0);
     #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      tG = cadd(tG, cconjmul(Gm.e[e], P.e[e]));
-      tl = cadd(tl, cconjmul(Hlm.e[e], P.e[e]));
-      tm = cadd(tm, cconjmul(Hmm.e[e], P.e[e]));
+    for (int e = 0; e < 4; ++e) sM[(size_t)k * 4 + e] = make_float2((float)(S * P.e[e].x), (float)(S * P.e[e].y));
+  }
+  // per-(source, baseline) sums over tiles, compensated FP32 (the FP64 pipe
+  // is far slower than FP32 on this part; 2 x n_time terms per sum)
+  float G[8], Hl[8], Hm[8], Gc[8], Hlc[8], Hmc[8];
+  #pragma unroll
+  for (int e = 0; e < 8; ++e) { G[e] = Hl[e] = Hm[e] = Gc[e] = Hlc[e] = Hmc[e] = 0.f; }
+  double loss = 0.0;
+  double lk_n = 0.0, mk_n = 0.0;
+  if (bw) {
+    const DirQ d = a.dir[kb];
+    const double n = 1.0 + d.z;
+    lk_n = d.x / n; mk_n = d.y / n;
+  }
+
+  for (int t = 0; t < a.n_time; ++t) {
+    __syncthreads();                              // previous users of sA/sB/sT2/s_uvw done
+    for (int k = tid; k < K; k += kGfThreads) {
+      SrcDir d; d.l = a.dir[k].x; d.m = a.dir[k].y; d.nm1 = a.dir[k].z; d.S = a.dir[k].w;
+      const double tau = delay_m(a.uvw, a.n_ant, t, ij.x, ij.y, d);
+      sA[k] = frac_q64(tau * a.nu0_c); sB[k] = frac_q64(tau * a.dnu_c);
     }
-    const double four_pi = 12.566370614359172953850573533118;
-    double* o = a.gsc + ((size_t)k * a.n_bl + bl) * 3;
-    o[0] = -four_pi * S * tl.y;
-    o[1] = -four_pi * S * tm.y;
-    o[2] = -2.0 * tG.x;
+    if (tid < 3)
+      s_uvw[tid] = a.uvw[((size_t)t * a.n_ant + ij.x) * 3 + tid] - a.uvw[((size_t)t * a.n_ant + ij.y) * 3 + tid];
+    __syncthreads();
+    for (int k = tid; k < K; k += kGfThreads) {
+      const unsigned long long b = sB[k];
+      #pragma unroll 4
+      for (int r = 0; r < 16; ++r) sT2[(size_t)r * kp + k] = grad_phasor_tab((unsigned long long)r * b);
+    }
+    for (int c0 = 0; c0 < a.n_chan; c0 += kGfTile) {
+      const int nc = min(kGfTile, a.n_chan - c0);
+      const int nq = (nc + 15) / 16;
+      for (int k = tid; k < K; k += kGfThreads) {
+        const unsigned long long b = sB[k], a0 = sA[k] + (unsigned long long)c0 * b;
+        #pragma unroll 4
+        for (int q = 0; q < nq; ++q) sT1[(size_t)q * kp + k] = grad_phasor_tab(a0 + (unsigned long long)(16 * q) * b);
+      }
+      if (WEIGHTED)
+        for (int i = tid; i < nc; i += kGfThreads) sW[i] = (float)a.wchan[c0 + i];
+      __syncthreads();
+      // forward: R at channel c0 + tid, all sources subtracted
+      if (tid < nc) {
+        const int q = tid >> 4, r = tid & 15;
+        const float4* v = reinterpret_cast<const float4*>(
+            static_cast<const float2*>(a.vis) + (((size_t)t * a.n_bl + bl) * a.n_chan + c0 + tid) * 4);
+        const float4 v0 = v[0], v1 = v[1];
+        float ax[4] = {v0.x, v0.z, v1.x, v1.z}, ay[4] = {v0.y, v0.w, v1.y, v1.w};
+        const float2* t1p = sT1 + (size_t)q * kp;
+        const float2* t2p = sT2 + (size_t)r * kp;
+        #pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+          const float2 t1 = t1p[k], t2 = t2p[k];
+          const float px = fmaf(t1.x, t2.x, -t1.y * t2.y);
+          const float py = fmaf(t1.x, t2.y, t1.y * t2.x);
+          const float4 m01 = reinterpret_cast<const float4*>(sM)[2 * k];
+          const float4 m23 = reinterpret_cast<const float4*>(sM)[2 * k + 1];
+          const float mx[4] = {m01.x, m01.z, m23.x, m23.z}, my[4] = {m01.y, m01.w, m23.y, m23.w};
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) {          // R -= M conj(P)
+            ax[e] = fmaf(-mx[e], px, fmaf(-my[e], py, ax[e]));
+            ay[e] = fmaf(-my[e], px, fmaf(mx[e], py, ay[e]));
+          }
+        }
+        float4* o = reinterpret_cast<float4*>(sR + (size_t)tid * 4);
+        o[0] = make_float4(ax[0], ay[0], ax[1], ay[1]);
+        o[1] = make_float4(ax[2], ay[2], ax[3], ay[3]);
+        float l2 = 0.f;
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) l2 = fmaf(ax[e], ax[e], fmaf(ay[e], ay[e], l2));
+        loss += (double)l2;
+      }
+      __syncthreads();
+      // backward: this thread's source over its q groups
+      if (bw) {
+        float y0[8], y1[8];
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) { y0[e] = 0.f; y1[e] = 0.f; }
+        for (int q = qa; q < min(qb, nq); ++q) {
+          const int rv = min(16, nc - 16 * q);
+          float s0[8], s1[8];
+          #pragma unroll
+          for (int e = 0; e < 8; ++e) { s0[e] = 0.f; s1[e] = 0.f; }
+          auto step = [&](int r) {
+            const int cl = 16 * q + r;
+            const float4 ra = reinterpret_cast<const float4*>(sR)[2 * cl];
+            const float4 rb = reinterpret_cast<const float4*>(sR)[2 * cl + 1];
+            const float rx[4] = {ra.x, ra.z, rb.x, rb.z}, ry[4] = {ra.y, ra.w, rb.y, rb.w};
+            const float2 t2 = sT2[(size_t)r * kp + kb];
+            if (WEIGHTED) {
+              const float w = sW[cl];
+              #pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float xr = fmaf(rx[e], t2.x, -ry[e] * t2.y);
+                const float xi = fmaf(rx[e], t2.y, ry[e] * t2.x);
+                s0[2 * e] += xr; s0[2 * e + 1] += xi;
+                s1[2 * e] = fmaf(w, xr, s1[2 * e]); s1[2 * e + 1] = fmaf(w, xi, s1[2 * e + 1]);
+              }
+            } else {
+              #pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                s0[2 * e] = fmaf(rx[e], t2.x, fmaf(-ry[e], t2.y, s0[2 * e]));
+                s0[2 * e + 1] = fmaf(rx[e], t2.y, fmaf(ry[e], t2.x, s0[2 * e + 1]));
+              }
+              #pragma unroll
+              for (int e = 0; e < 8; ++e) s1[e] += s0[e];
+            }
+          };
+          if (rv == 16) {
+            #pragma unroll
+            for (int r = 15; r >= 0; --r) step(r);
+          } else {
+            for (int r = rv - 1; r >= 0; --r) step(r);
+          }
+          const float2 t1 = sT1[(size_t)q * kp + kb];
+          const float cw = (float)(c0 + 16 * q - 1);
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            y0[2 * e] = fmaf(t1.x, s0[2 * e], fmaf(-t1.y, s0[2 * e + 1], y0[2 * e]));
+            y0[2 * e + 1] = fmaf(t1.x, s0[2 * e + 1], fmaf(t1.y, s0[2 * e], y0[2 * e + 1]));
+            // unweighted: sum_r (c0 + 16q + r) x_r = (c0 + 16q - 1) s0 + sum_r (r + 1) x_r
+            const float zr = WEIGHTED ? s1[2 * e] : fmaf(cw, s0[2 * e], s1[2 * e]);
+            const float zi = WEIGHTED ? s1[2 * e + 1] : fmaf(cw, s0[2 * e + 1], s1[2 * e + 1]);
+            y1[2 * e] = fmaf(t1.x, zr, fmaf(-t1.y, zi, y1[2 * e]));
+            y1[2 * e + 1] = fmaf(t1.x, zi, fmaf(t1.y, zr, y1[2 * e + 1]));
+          }
+        }
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          sPart[e * kGfThreads + tid] = y0[e];
+          sPart[(8 + e) * kGfThreads + tid] = y1[e];
+        }
+      }
+      __syncthreads();
+      if (bw && my_g == 0) {
+        float H0[8], H1[8];
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) { H0[e] = 0.f; H1[e] = 0.f; }
+        for (int g = 0; g < groups; ++g) {
+          const float* part = sPart + g * kc + my_k;
+          #pragma unroll
+          for (int e = 0; e < 8; ++e) { H0[e] += part[e * kGfThreads]; H1[e] += part[(8 + e) * kGfThreads]; }
+        }
+        const float wl = (float)(s_uvw[0] - s_uvw[2] * lk_n);
+        const float wm = (float)(s_uvw[1] - s_uvw[2] * mk_n);
+        const float nu0 = (float)a.nu0_c, dnu = (float)a.dnu_c;
+        #pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float hn = WEIGHTED ? H1[e] : fmaf(nu0, H0[e], dnu * H1[e]);
+          kahan_add(G[e], Gc[e], H0[e]);
+          kahan_add(Hl[e], Hlc[e], wl * hn);
+          kahan_add(Hm[e], Hmc[e], wm * hn);
+        }
+      }
+    }
+  }
+  if (blockIdx.y == 0) {
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if ((tid & 31) == 0) s_loss[tid >> 5] = loss;
+  }
+  __syncthreads();
+  if (blockIdx.y == 0 && tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kGfThreads / 32; ++w) s += s_loss[w];
+    a.loss_bl[bl] = s;
+  }
+  if (bw && my_g == 0) {
+    double Gd[8], Hld[8], Hmd[8];
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      Gd[e] = (double)G[e] - (double)Gc[e];
+      Hld[e] = (double)Hl[e] - (double)Hlc[e];
+      Hmd[e] = (double)Hm[e] - (double)Hmc[e];
+    }
+    grad_store<float>(a, kb, bl, ij, Gd, Hld, Hmd);
   }
 }
 
@@ -374,7 +633,8 @@ inline size_t grad_smem_bytes(bool mixed, int n_src) {
 inline int grad_sweep(GradWorkspace& w, bool mixed, const void* vis, int n_src, const void* jones,
                       const double* uvw, const int2* bl_ant, const double* freq_c, int n_ant,
                       int n_chan, int n_time, int64_t n_bl, double nu0_c, double dnu_c,
-                      cudaStream_t s, std::string& err, const double* wchan = nullptr) {
+                      cudaStream_t s, std::string& err, const double* wchan = nullptr,
+                      bool direct = false) {
   cudaError_t e;
   GradArgs a;
   a.vis = vis; a.jones = jones; a.dir = w.dir; a.uvw = uvw; a.bl_ant = bl_ant; a.freq_c = freq_c;
@@ -382,19 +642,23 @@ inline int grad_sweep(GradWorkspace& w, bool mixed, const void* vis, int n_src, 
   a.G = w.G; a.gsc = w.gsc; a.loss_bl = w.loss_bl;
   a.n_src = n_src; a.n_ant = n_ant; a.n_chan = n_chan; a.n_time = n_time; a.n_bl = n_bl;
   a.nu0_c = nu0_c; a.dnu_c = dnu_c;
-  const size_t smem = grad_smem_bytes(mixed, n_src);
-  const int chunks = n_src > 0 ? (n_src + kGradChunk - 1) / kGradChunk : 1;
-  if (smem > 227 * 1024) {
+  const size_t smem_fac = grad_fac_smem_bytes(n_src);
+  const bool fac = mixed && smem_fac <= kGradMaxSmem && !direct;
+  const size_t smem = fac ? smem_fac : grad_smem_bytes(mixed, n_src);
+  const int chunk = fac ? kGfChunk : kGradChunk;
+  const int chunks = n_src > 0 ? (n_src + chunk - 1) / chunk : 1;
+  if (smem > kGradMaxSmem) {
     err = "too many sources for the gradient kernel's shared memory";
     return -1;
   }
   const dim3 grid((unsigned)n_bl, (unsigned)chunks);
   auto launch = [&](auto kernel) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (r == cudaSuccess) kernel<<<grid, kGradThreads, smem, s>>>(a);
+    if (r == cudaSuccess) kernel<<<grid, fac ? kGfThreads : kGradThreads, smem, s>>>(a);
     return r;
   };
-  if (mixed) e = wchan ? launch(k_grad_sweep<true, true>) : launch(k_grad_sweep<true, false>);
+  if (fac) e = wchan ? launch(k_grad_sweep_fac<true>) : launch(k_grad_sweep_fac<false>);
+  else if (mixed) e = wchan ? launch(k_grad_sweep<true, true>) : launch(k_grad_sweep<true, false>);
   else e = wchan ? launch(k_grad_sweep<false, true>) : launch(k_grad_sweep<false, false>);
   if (e != cudaSuccess) return grad_fail(err, e, "cudaFuncSetAttribute");
   if ((e = cudaGetLastError()) != cudaSuccess) return grad_fail(err, e, "gradient sweep launch");

@@ -7,14 +7,6 @@
 
 namespace rts {
 
-// compensated summation step (Kahan): sum + comp carries the running total
-__device__ inline void kahan_add(float& sum, float& comp, float x) {
-  const float y = x - comp;
-  const float t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
-}
-
 
 constexpr int kPredictChunk = 32;
 

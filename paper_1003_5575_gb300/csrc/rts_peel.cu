@@ -58,6 +58,7 @@ struct rts_peel_t {
   float2* b_model = nullptr;       // [BK][n_bl][4] model matrices of a block
   // persistent block solve (k_block_solve, one cooperative launch per block)
   int solve_kernel = RTS_SOLVE_AUTO;
+  bool grad_direct = false;        // adjoint with one sin/cos per sample (RTS_GRAD_DIRECT)
   bool bs_ok = false;              // set up and fits (shared memory, cooperative launch)
   int bs_grid = 0, bs_apc = 0;
   size_t bs_smem = 0;
@@ -99,6 +100,9 @@ int fail(rts_peel_t* h, int code, const std::string& msg) {
   if (h) h->err = msg; else g_init_err = msg;
   return code;
 }
+
+// device cubes are read and written 16 bytes at a time
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 
 int cuda_fail(rts_peel_t* h, cudaError_t e, const char* what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
@@ -580,10 +584,13 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
 
   if (cfg->solve_kernel != RTS_SOLVE_AUTO && cfg->solve_kernel != RTS_SOLVE_LAUNCHES)
     return fail(nullptr, RTS_EINVAL, "solve_kernel must be RTS_SOLVE_AUTO or RTS_SOLVE_LAUNCHES");
+  if (cfg->grad_kernel != RTS_GRAD_AUTO && cfg->grad_kernel != RTS_GRAD_DIRECT)
+    return fail(nullptr, RTS_EINVAL, "grad_kernel must be RTS_GRAD_AUTO or RTS_GRAD_DIRECT");
 
   rts_peel_t* h = new rts_peel_t();
   h->per_pass = per_pass;
   h->solve_kernel = cfg->solve_kernel;
+  h->grad_direct = cfg->grad_kernel == RTS_GRAD_DIRECT;
   {
     int bk = cfg->block_kernel;
     if (bk == RTS_BLOCK_AUTO)
@@ -658,6 +665,8 @@ int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_
                      const double* h_src, void* d_jones, int32_t* h_status, void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (!d_vis || !d_resid) return fail(h, RTS_EINVAL, "d_vis and d_resid are required");
+  if (misaligned(d_vis) || misaligned(d_resid))
+    return fail(h, RTS_EINVAL, "d_vis and d_resid must start on a 16-byte boundary");
   int rc = validate_sources(h, n_src, h_src);
   if (rc) return rc;
   if (n_src > 0 && !d_jones) return fail(h, RTS_EINVAL, "d_jones is NULL");
@@ -775,6 +784,7 @@ int rts_peel_predict(rts_peel_t* h, void* d_vis, int32_t n_src, const double* h_
                      const void* d_jones, int32_t accumulate, void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (!d_vis) return fail(h, RTS_EINVAL, "d_vis is NULL");
+  if (misaligned(d_vis)) return fail(h, RTS_EINVAL, "d_vis must start on a 16-byte boundary");
   int rc = validate_sources(h, n_src, h_src);
   if (rc) return rc;
   if (n_src > 0 && !d_jones) return fail(h, RTS_EINVAL, "d_jones is NULL");
@@ -811,6 +821,8 @@ int rts_peel_rotate_average(rts_peel_t* h, const void* d_vis, double l, double m
                             void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (!d_vis || !d_avg) return fail(h, RTS_EINVAL, "d_vis and d_avg are required");
+  if (misaligned(d_vis) || misaligned(d_avg))
+    return fail(h, RTS_EINVAL, "d_vis and d_avg must start on a 16-byte boundary");
   if (!std::isfinite(l) || !std::isfinite(m) || !(l * l + m * m < 1.0))
     return fail(h, RTS_EINVAL, "direction must be finite with l^2 + m^2 < 1");
   StreamArgs a = stream_args(h, d_vis, nullptr, d_avg);
@@ -834,6 +846,7 @@ int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d
                   const double* d_src, double* d_loss, void* d_gJ, double* d_gsrc, void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (!d_vis || !d_loss) return fail(h, RTS_EINVAL, "d_vis and d_loss are required");
+  if (misaligned(d_vis)) return fail(h, RTS_EINVAL, "d_vis must start on a 16-byte boundary");
   if (n_src < 0 || n_src > h->max_sources) return fail(h, RTS_EINVAL, "n_src must be in [0, max_sources]");
   if (n_src > 0 && (!d_jones || !d_src)) return fail(h, RTS_EINVAL, "d_jones and d_src are required");
   cudaStream_t s = as_stream(stream);
@@ -844,7 +857,7 @@ int rts_peel_grad(rts_peel_t* h, const void* d_vis, int32_t n_src, const void* d
     Span span(h, RTS_K_GRAD, s);
     rc = grad_sweep(h->grad, mixed, d_vis, n_src, d_jones, h->d_uvw, h->d_bl_ant, h->d_freq_c,
                     h->n_ant, h->n_chan, h->n_time, h->n_bl, h->nu0 / kCLight, h->dnu / kCLight, s,
-                    h->err);
+                    h->err, nullptr, h->grad_direct);
     span.end(1);
     if (rc) return rc;
   }
@@ -866,6 +879,7 @@ int rts_peel_offsets(rts_peel_t* h, const void* d_vis, int32_t n_src, const void
   if (n_src == 0) return RTS_OK;
   if (!d_vis || !d_jones || !d_src || !d_out || !d_offsets)
     return fail(h, RTS_EINVAL, "d_vis, d_jones, d_src, d_out and d_offsets are required");
+  if (misaligned(d_vis)) return fail(h, RTS_EINVAL, "d_vis must start on a 16-byte boundary");
   cudaStream_t s = as_stream(stream);
   const bool mixed = h->precision == RTS_PREC_MIXED;
   int rc = grad_prepare(h->grad, n_src, d_src, h->n_bl, h->max_sources, s, h->err);
@@ -883,7 +897,7 @@ int rts_peel_offsets(rts_peel_t* h, const void* d_vis, int32_t n_src, const void
     Span span(h, RTS_K_GRAD, s);
     rc = grad_sweep(h->grad, mixed, d_vis, n_src, d_jones, h->d_uvw, h->d_bl_ant, h->d_freq_c,
                     h->n_ant, h->n_chan, h->n_time, h->n_bl, h->nu0 / kCLight, h->dnu / kCLight, s,
-                    h->err, alpha != 0.0 ? wtab : nullptr);
+                    h->err, alpha != 0.0 ? wtab : nullptr, h->grad_direct);
     span.end(1);
     if (rc) return rc;
   }

@@ -38,7 +38,7 @@ class Peeler:
 
     def __init__(self, uvw, freq_hz, n_iter: int = 20, precision: str = "mixed",
                  max_sources: int = 1024, sources_per_pass: int = 0, block_kernel: int = 0,
-                 solve_kernel: int = 0):
+                 solve_kernel: int = 0, grad_kernel: int = 0):
         uvw = _host_f64(uvw)
         freq = _host_f64(freq_hz)
         if uvw.ndim != 3 or uvw.shape[2] != 3:
@@ -61,6 +61,7 @@ class Peeler:
         cfg.sources_per_pass = int(sources_per_pass)
         cfg.block_kernel = int(block_kernel)
         cfg.solve_kernel = int(solve_kernel)
+        cfg.grad_kernel = int(grad_kernel)
         self.sources_per_pass = int(sources_per_pass)
         self._keep = (uvw, freq)
         self.device = torch.device("cuda", torch.cuda.current_device())

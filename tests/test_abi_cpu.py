@@ -72,6 +72,7 @@ def _cfg(abi, n_ant=8, n_chan=16, n_time=2, n_iter=20, precision=0, max_sources=
     (dict(sources_per_pass=3), "sources_per_pass"),
     (dict(sources_per_pass=64, block_kernel=5), "block_kernel"),
     (dict(sources_per_pass=64, solve_kernel=7), "solve_kernel"),
+    (dict(grad_kernel=2), "grad_kernel"),
 ])
 def test_init_rejects_bad_config_on_host(abi, kw, needle):
     cfg, keep = _cfg(abi, **kw)

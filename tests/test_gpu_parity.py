@@ -58,11 +58,12 @@ def oracle_case(cad, n_iter=20):
     return _cache[key]
 
 
-def make_peeler(cad, prec, n_iter=20, max_sources=None, per_pass=0, block_kernel=0, solve_kernel=0):
+def make_peeler(cad, prec, n_iter=20, max_sources=None, per_pass=0, block_kernel=0, solve_kernel=0,
+                grad_kernel=0):
     from paper_1003_5575_gb300 import Peeler
     return Peeler(cad.uvw(), cad.freqs(), n_iter=n_iter, precision=prec,
                   max_sources=max_sources or max(cad.n_src, 1), sources_per_pass=per_pass,
-                  block_kernel=block_kernel, solve_kernel=solve_kernel)
+                  block_kernel=block_kernel, solve_kernel=solve_kernel, grad_kernel=grad_kernel)
 
 
 # ---------------------------------------------------------------------------
@@ -251,6 +252,53 @@ def test_loss_and_gradient_match_oracle(prec):
     gs = gs.cpu().numpy()
     for col, ref in ((0, gl_ref), (1, gm_ref), (2, gS_ref)):
         assert np.abs(gs[:, col] - ref).max() <= gtol * np.abs(ref).max(), col
+    p.close()
+
+
+# the mixed adjoint's two sweeps: factorised phasor tables (default) and one
+# sin/cos per sample; shapes with several channel tiles of the factorised sweep
+# (384 channels), ragged 16-channel groups, a source count whose tables do not
+# fit in shared memory (the default then takes the per-sample sweep), and one source
+ADJ_CASES = [
+    ("two-tiles-ragged", Cadence(6, 410, 2, 7, pos_sigma_rad=2.909e-4, seed=68)),
+    ("one-channel", Cadence(5, 1, 3, 4, pos_sigma_rad=2.909e-4, seed=69)),
+    ("one-source", Cadence(7, 100, 2, 1, pos_sigma_rad=2.909e-4, seed=70)),
+    ("600-sources", Cadence(3, 24, 1, 600, pos_sigma_rad=2.909e-4, seed=71)),
+]
+
+
+@pytest.mark.parametrize("grad_kernel", [0, 1], ids=["auto", "direct"])
+@pytest.mark.parametrize("name,cad", ADJ_CASES, ids=[c[0] for c in ADJ_CASES])
+def test_mixed_adjoint_sweeps_match_oracle(name, cad, grad_kernel):
+    V = oracle.simulate(cad.with_(pos_sigma_rad=0.0)).astype(np.complex64).astype(np.complex128)
+    src = cad.perturbed_sources()
+    J = cad.jones().astype(np.complex64).astype(np.complex128)
+    L_ref, gJ_ref, gl_ref, gm_ref, gS_ref = oracle.loss_grad(cad.uvw(), cad.freqs(), V, src, J)
+    p = make_peeler(cad, "mixed", grad_kernel=grad_kernel)
+    loss, gJ, gs = p.grad(to_dev(V, "mixed"), torch.from_numpy(J.astype(np.complex64)).cuda(),
+                          torch.from_numpy(src).cuda())
+    torch.cuda.synchronize()
+    p.close()
+    assert abs(loss.item() - L_ref) <= 1e-5 * L_ref
+    gJ = gJ.cpu().numpy()
+    assert np.abs(gJ - gJ_ref).max() <= 1e-4 * np.abs(gJ_ref).max()
+    gs = gs.cpu().numpy()
+    for col, ref in ((0, gl_ref), (1, gm_ref), (2, gS_ref)):
+        assert np.abs(gs[:, col] - ref).max() <= 1e-4 * np.abs(ref).max(), col
+
+
+def test_misaligned_cube_rejected():
+    """A cube that does not start on a 16-byte boundary is refused on the host."""
+    cad = Cadence(4, 16, 2, 2, seed=72)
+    p = make_peeler(cad, "mixed")
+    buf = torch.zeros(cad.n_vis * 4 + 1, dtype=torch.complex64, device="cuda")
+    v = buf[1:].view(p.cube_shape)
+    J = torch.from_numpy(cad.jones().astype(np.complex64)).cuda()
+    src = torch.from_numpy(cad.sources()).cuda()
+    with pytest.raises(RuntimeError, match="16-byte"):
+        p.grad(v, J, src)
+    with pytest.raises(RuntimeError, match="16-byte"):
+        p.cadence(v, cad.sources())
     p.close()
 
 
