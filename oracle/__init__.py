@@ -65,6 +65,12 @@ def lib():
                                         _dp, _dp, _dp, _dp, _dp]
             L.orc_offsets.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _dp, ctypes.c_double,
                                       ctypes.c_double, _dp, _dp]
+            L.orc_predict_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _i32, _dp, _dp, _dp, _dp, _i32]
+            L.orc_als_taylor.restype = _i32
+            L.orc_als_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, _i32, _dp, _dp, _dp]
+            L.orc_peel_taylor.restype = _i32
+            L.orc_peel_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _dp, _ip]
             L.orc_num_threads.restype = _i32
             _lib = L
     return _lib
@@ -193,6 +199,48 @@ def offsets(uvw, freq, vis, lmS, jones, alpha=0.0, nu_ref=None):
     lib().orc_offsets(uvw.shape[1], freq.shape[0], uvw.shape[0], _d(uvw), _d(freq), _d(vis), n_src,
                       _d(lmS), _d(jones), float(alpha), nu_ref, _d(out), _d(off))
     return out[:n_src], off[:n_src]
+
+
+def predict_taylor(uvw, freq, lmS, gain, slope, vis=None):
+    """Model with gains linear in frequency, J_p(c) = G_p + x_c H_p,
+    x_c = (nu_c - nu_mid) / (n_chan dnu): [n_time][n_bl][n_chan][4] complex128."""
+    uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
+    gain, slope = _f64(gain, np.complex128), _f64(slope, np.complex128)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    n_chan, n_src = freq.shape[0], lmS.shape[0]
+    nb = n_ant * (n_ant - 1) // 2
+    acc = vis is not None
+    out = _f64(vis, np.complex128).copy() if acc else np.zeros((n_time, nb, n_chan, 4), np.complex128)
+    lib().orc_predict_taylor(n_ant, n_chan, n_time, _d(uvw), _d(freq), n_src, _d(lmS),
+                             _d(gain), _d(slope), _d(out), int(acc))
+    return out
+
+
+def als_taylor(uvw, freq, vis, l, m, S, n_iter=20):
+    """Frequency-linear gains of one source from the residual cube: (G, H, status, rel)."""
+    uvw, freq = _f64(uvw), _f64(freq)
+    vis = _f64(vis, np.complex128)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    G = np.zeros((n_ant, 4), np.complex128)
+    H = np.zeros((n_ant, 4), np.complex128)
+    rel = ctypes.c_double(0.0)
+    st = lib().orc_als_taylor(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(vis), float(l),
+                              float(m), float(S), n_iter, _d(G), _d(H), ctypes.byref(rel))
+    return G, H, int(st), rel.value
+
+
+def peel_taylor(uvw, freq, vis, lmS, n_iter=20):
+    """Sequential peel with gains linear in frequency: (residual, G, H, status)."""
+    uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
+    R = _f64(vis, np.complex128).copy()
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    n_src = lmS.shape[0]
+    G = np.zeros((n_src, n_ant, 4), np.complex128)
+    H = np.zeros((n_src, n_ant, 4), np.complex128)
+    st = np.zeros(max(n_src, 1), np.int32)
+    lib().orc_peel_taylor(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(R), n_src, _d(lmS),
+                          n_iter, _d(G), _d(H), st.ctypes.data_as(_ip))
+    return R, G, H, st[:n_src]
 
 
 def simulate(cad, noise=True, sources=None, jones=None):

@@ -473,3 +473,181 @@ void orc_offsets(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uv
   }
   free(part); free(bl_loss); free(Mk);
 }
+
+/* ---- gains Taylor-expanded in frequency ------------------------------------
+ * Section 3.1: combining consecutive channels helps the calibration because the
+ * unknown tile gain can then be Taylor-expanded in frequency.  Reading (R16):
+ * first order about the band centre,
+ *   J_p(c) = G_p + x_c H_p,   x_c = (nu_c - nu_mid) / (n_chan dnu),
+ *   nu_mid = (nu_0 + nu_last) / 2, dnu the channel spacing,
+ * so the model of source k on baseline (i, j) at channel c is
+ *   S_k (G_i + x_c H_i)(G_j + x_c H_j)^H exp(-2 pi i phi_k).
+ * The solve is the same Jacobi alternating least squares with the 2 x 4
+ * unknown X_p = [G_p H_p]: with the rotated residual R~ = R exp(+2 pi i phi_k)
+ * and Z_pq(c) = S [W_q(c); x_c W_q(c)] (4 x 2), W_q(c) = (G_q + x_c H_q)^H,
+ *   X_p <- [sum_q sum_{t,c} R~_pq Z_pq^H] [sum_q sum_{t,c} Z_pq Z_pq^H]^-1
+ * (R~_qp = R~_pq^H), from G = I, H = 0, every second sweep averaged with the
+ * previous iterate, fixed n_iter; status from ||X_new - X_old|| / ||X_new||.
+ * Sums run over every sample (t, c), as the least-squares problem states.   */
+
+static double taylor_x(const double* freq, int32_t n_chan, int32_t c) {
+  if (n_chan < 2) return 0.0;
+  double dnu = (freq[n_chan - 1] - freq[0]) / (n_chan - 1);
+  double mid = 0.5 * (freq[0] + freq[n_chan - 1]);
+  return (freq[c] - mid) / (n_chan * dnu);
+}
+
+/* Gauss-Jordan inverse of an n x n complex matrix (partial pivoting); 0 if singular */
+static int c_inverse(int n, const cplx* a, cplx* inv) {
+  cplx m[4][8];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c) m[r][c] = c < n ? a[r * n + c] : (c - n == r ? 1.0 : 0.0);
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (cabs(m[r][col]) > cabs(m[piv][col])) piv = r;
+    if (cabs(m[piv][col]) == 0.0) return 0;
+    if (piv != col)
+      for (int c = 0; c < 2 * n; ++c) { cplx tmp = m[col][c]; m[col][c] = m[piv][c]; m[piv][c] = tmp; }
+    cplx d = m[col][col];
+    for (int c = 0; c < 2 * n; ++c) m[col][c] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      cplx f = m[r][col];
+      for (int c = 0; c < 2 * n; ++c) m[r][c] -= f * m[col][c];
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) inv[r * n + c] = m[r][n + c];
+  return 1;
+}
+
+void orc_predict_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                        const double* freq, int32_t n_src, const double* lmS, const double* gain,
+                        const double* slope, double* vis, int32_t accumulate) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    int32_t i = ai[bl], j = aj[bl];
+    for (int32_t t = 0; t < n_time; ++t)
+      for (int32_t c = 0; c < n_chan; ++c) {
+        double x = taylor_x(freq, n_chan, c);
+        double* out = vis_at(vis, n_bl, n_chan, t, bl, c);
+        mat2 v = accumulate ? m_load(out) : m_zero();
+        for (int32_t k = 0; k < n_src; ++k) {
+          double l = lmS[3 * k], m = lmS[3 * k + 1], S = lmS[3 * k + 2];
+          int64_t oi = ((int64_t)k * n_ant + i) * 8, oj = ((int64_t)k * n_ant + j) * 8;
+          mat2 Ji = m_add(m_load(gain + oi), m_scale(m_load(slope + oi), x));
+          mat2 Jj = m_add(m_load(gain + oj), m_scale(m_load(slope + oj), x));
+          mat2 M = m_scale(m_mul(Ji, m_herm(Jj)), S);
+          double phi = orc_phase_turns(orc_delay_m(uvw, n_ant, t, i, j, l, m), freq[c]);
+          v = m_add(v, m_scale(M, phasor(phi, -1.0)));
+        }
+        m_store(out, v);
+      }
+  }
+}
+
+int32_t orc_als_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                       const double* freq, const double* vis, double l, double m, double S,
+                       int32_t n_iter, double* gain, double* slope, double* rel_change) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int64_t n_s = (int64_t)n_time * n_chan;
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  /* the residual rotated to the source, per baseline and sample */
+  mat2* Rr = (mat2*)malloc(sizeof(mat2) * (size_t)(n_bl * n_s > 0 ? n_bl * n_s : 1));
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl)
+    for (int32_t t = 0; t < n_time; ++t) {
+      double tau = orc_delay_m(uvw, n_ant, t, ai[bl], aj[bl], l, m);
+      for (int32_t c = 0; c < n_chan; ++c)
+        Rr[bl * n_s + (int64_t)t * n_chan + c] =
+            m_scale(m_load(vis_at((double*)vis, n_bl, n_chan, t, bl, c)), phasor(orc_phase_turns(tau, freq[c]), +1.0));
+    }
+  mat2* G = (mat2*)malloc(sizeof(mat2) * n_ant);
+  mat2* H = (mat2*)malloc(sizeof(mat2) * n_ant);
+  mat2* Gn = (mat2*)malloc(sizeof(mat2) * n_ant);
+  mat2* Hn = (mat2*)malloc(sizeof(mat2) * n_ant);
+  for (int32_t p = 0; p < n_ant; ++p) { G[p] = m_eye(); H[p] = m_zero(); }
+  double rel = 0.0;
+  int finite = 1;
+  for (int32_t it = 1; it <= n_iter; ++it) {
+#pragma omp parallel for schedule(static)
+    for (int32_t p = 0; p < n_ant; ++p) {
+      cplx A[2][4] = {{0}}, C[16] = {0}, Ci[16];
+      for (int32_t q = 0; q < n_ant; ++q) {
+        if (q == p) continue;
+        int64_t bl = p < q ? orc_baseline_index(n_ant, p, q) : orc_baseline_index(n_ant, q, p);
+        for (int32_t t = 0; t < n_time; ++t)
+          for (int32_t c = 0; c < n_chan; ++c) {
+            double x = taylor_x(freq, n_chan, c);
+            mat2 R = Rr[bl * n_s + (int64_t)t * n_chan + c];
+            if (p > q) R = m_herm(R);
+            mat2 W = m_herm(m_add(G[q], m_scale(H[q], x)));     /* W_q(c) */
+            cplx Z[4][2];                                        /* S [W; x W] */
+            for (int r = 0; r < 2; ++r)
+              for (int s = 0; s < 2; ++s) { Z[r][s] = S * W.e[2 * r + s]; Z[2 + r][s] = S * x * W.e[2 * r + s]; }
+            for (int r = 0; r < 2; ++r)                          /* A += R Z^H */
+              for (int s = 0; s < 4; ++s)
+                for (int u = 0; u < 2; ++u) A[r][s] += R.e[2 * r + u] * conj(Z[s][u]);
+            for (int r = 0; r < 4; ++r)                          /* C += Z Z^H */
+              for (int s = 0; s < 4; ++s)
+                for (int u = 0; u < 2; ++u) C[4 * r + s] += Z[r][u] * conj(Z[s][u]);
+          }
+      }
+      if (!c_inverse(4, C, Ci))
+        for (int k = 0; k < 16; ++k) Ci[k] = NAN;
+      cplx X[2][4];
+      for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 4; ++s) {
+          X[r][s] = 0.0;
+          for (int u = 0; u < 4; ++u) X[r][s] += A[r][u] * Ci[4 * u + s];
+        }
+      for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s) { Gn[p].e[2 * r + s] = X[r][s]; Hn[p].e[2 * r + s] = X[r][2 + s]; }
+    }
+    if (it % 2 == 0)
+      for (int32_t p = 0; p < n_ant; ++p) {
+        Gn[p] = m_scale(m_add(Gn[p], G[p]), 0.5);
+        Hn[p] = m_scale(m_add(Hn[p], H[p]), 0.5);
+      }
+    double dn = 0.0, nn = 0.0;
+    for (int32_t p = 0; p < n_ant; ++p) {
+      dn += m_norm2(m_sub(Gn[p], G[p])) + m_norm2(m_sub(Hn[p], H[p]));
+      nn += m_norm2(Gn[p]) + m_norm2(Hn[p]);
+      if (!m_finite(Gn[p]) || !m_finite(Hn[p])) finite = 0;
+    }
+    rel = sqrt(dn / nn);
+    mat2* tmp = G; G = Gn; Gn = tmp;
+    tmp = H; H = Hn; Hn = tmp;
+  }
+  for (int32_t p = 0; p < n_ant; ++p) {
+    m_store(gain + (int64_t)p * 8, G[p]);
+    m_store(slope + (int64_t)p * 8, H[p]);
+  }
+  free(Rr); free(G); free(H); free(Gn); free(Hn);
+  if (rel_change) *rel_change = rel;
+  if (!finite || !isfinite(rel)) return -4;
+  return rel > 1e-6 ? 1 : 0;
+}
+
+int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                        const double* freq, double* vis, int32_t n_src, const double* lmS,
+                        int32_t n_iter, double* gain, double* slope, int32_t* status) {
+  int32_t worst = 0;
+  for (int32_t k = 0; k < n_src; ++k) {
+    double l = lmS[3 * k], m = lmS[3 * k + 1], S = lmS[3 * k + 2];
+    double* Gk = gain + (int64_t)k * n_ant * 8;
+    double* Hk = slope + (int64_t)k * n_ant * 8;
+    int32_t st = orc_als_taylor(n_ant, n_chan, n_time, uvw, freq, vis, l, m, S, n_iter, Gk, Hk, NULL);
+    if (status) status[k] = st;
+    if (st < 0) worst = st;
+    /* subtract S (G_i + x H_i)(G_j + x H_j)^H exp(-2 pi i phi) */
+    double one[3] = {l, m, -S};
+    orc_predict_taylor(n_ant, n_chan, n_time, uvw, freq, 1, one, Gk, Hk, vis, 1);
+  }
+  return worst;
+}

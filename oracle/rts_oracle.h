@@ -52,6 +52,16 @@ void orc_offsets(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uv
                  const double* freq, const double* vis, int32_t n_src, const double* lmS,
                  const double* jones, double alpha, double nu_ref, double* out,
                  double* offsets);
+/* gains Taylor-expanded in frequency, J_p(c) = G_p + x_c H_p (reading R16) */
+void orc_predict_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                        const double* freq, int32_t n_src, const double* lmS, const double* gain,
+                        const double* slope, double* vis, int32_t accumulate);
+int32_t orc_als_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                       const double* freq, const double* vis, double l, double m, double S,
+                       int32_t n_iter, double* gain, double* slope, double* rel_change);
+int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                        const double* freq, double* vis, int32_t n_src, const double* lmS,
+                        int32_t n_iter, double* gain, double* slope, int32_t* status);
 int32_t orc_num_threads(void);
 
 #ifdef __cplusplus

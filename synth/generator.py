@@ -46,8 +46,9 @@ _M2 = np.uint64(0x94D049BB133111EB)
 OMEGA_EARTH = 7.2921159e-5          # rad / s (sidereal)
 MWA_LAT_DEG = -26.703               # site latitude; not printed in the paper
 
-# stream identifiers (fixed order: positions, antennas, sources, Jones, noise)
-S_ANT, S_SRC, S_JONES, S_NOISE, S_POS = 1, 2, 3, 4, 5
+# stream identifiers (fixed order: positions, antennas, sources, Jones, noise;
+# then the Jones slopes over the band, drawn only by jones_slope())
+S_ANT, S_SRC, S_JONES, S_NOISE, S_POS, S_SLOPE = 1, 2, 3, 4, 5, 6
 
 _CHUNK = 1 << 20     # noise elements per work item
 
@@ -184,6 +185,15 @@ class Cadence:
         j[..., 0] += 1.0
         j[..., 3] += 1.0
         return j
+
+    def jones_slope(self, sigma: float = 0.2) -> np.ndarray:
+        """[n_src][n_ant][4] complex128 Jones slopes H for gains linear in frequency,
+        J(c) = jones() + x_c H with x_c the channel's offset from the band centre in
+        band widths (|x_c| <= 1/2): CN(0, sigma^2) per entry."""
+        k = self.n_src * self.n_ant * 4
+        g = normals(self.seed, S_SLOPE, np.arange(2 * k)).reshape(self.n_src, self.n_ant, 4, 2)
+        sd = sigma / math.sqrt(2.0)
+        return sd * (g[..., 0] + 1j * g[..., 1])
 
     def noise(self, index=None) -> np.ndarray:
         """Complex noise, sigma on Re and Im.  ``index`` are flat complex-element

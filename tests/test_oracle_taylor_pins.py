@@ -1,0 +1,164 @@
+"""Pins of the oracle's gains Taylor-expanded in frequency (Section 3.1: the
+gain of a tile may be Taylor-expanded in frequency when consecutive channels
+are combined; reading R16: J_p(c) = G_p + x_c H_p, x_c the channel's offset
+from the band centre in band widths).
+
+Each test ties the oracle's Taylor functions to something outside their code:
+the already-pinned constant-gain oracle applied channel by channel, exact
+recovery of noise-free frequency-linear gains, the closed form of the first
+Jacobi sweep from G = I, H = 0, and the global least-squares minimum found by
+Levenberg-Marquardt from many starts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import Cadence, baseline_pairs
+
+
+def mats(J):
+    return np.asarray(J).reshape(*np.shape(J)[:-1], 2, 2)
+
+
+def herm(a):
+    return np.conj(np.swapaxes(a, -1, -2))
+
+
+def xc(freq):
+    """Offset of each channel from the band centre in band widths (numpy, from the definition)."""
+    f = np.asarray(freq, np.float64)
+    dnu = (f[-1] - f[0]) / (len(f) - 1)
+    return (f - 0.5 * (f[0] + f[-1])) / (len(f) * dnu)
+
+
+def channel_products(G, H, x, n_ant):
+    """(G_i + x H_i)(G_j + x H_j)^H per baseline at offset x."""
+    pairs = baseline_pairs(n_ant)
+    J = mats(G) + x * mats(H)
+    return J[pairs[:, 0]] @ herm(J[pairs[:, 1]])
+
+
+def small(n_ant=6, n_chan=9, n_time=2, n_src=1, seed=5151):
+    return Cadence(n_ant, n_chan, n_time, n_src, freq0_hz=150e6, seed=seed)
+
+
+def test_taylor_prediction_is_the_constant_gain_prediction_channel_by_channel():
+    cad = small(n_src=3)
+    G, H = cad.jones(), cad.jones_slope()
+    src, freq = cad.sources(), cad.freqs()
+    V = oracle.predict_taylor(cad.uvw(), freq, src, G, H)
+    x = xc(freq)
+    assert abs(x[len(x) // 2]) < 1e-15 and np.isclose(x[-1] - x[0], (len(x) - 1) / len(x))
+    for c in range(cad.n_chan):
+        Vc = oracle.predict(cad.uvw(), freq[c:c + 1], src, G + x[c] * H)
+        np.testing.assert_allclose(V[:, :, c:c + 1], Vc, rtol=0, atol=1e-13)
+
+
+def test_taylor_peel_recovers_frequency_linear_gains():
+    """Noise-free single source with gains linear in frequency: the fitted model
+    (G_i + x H_i)(G_j + x H_j)^H equals the truth at every channel and the
+    residual vanishes.  The Taylor solve converges slowly (a common
+    frequency-linear rotation of all slopes, H_p -> H_p + i G_p K, changes the
+    model only at second order in x), so the pin runs 8000 sweeps."""
+    cad = small(n_ant=7, n_chan=11, n_time=3)
+    Gt, Ht = cad.jones(), cad.jones_slope()
+    src = np.array([[0.12, -0.05, 4.0]])
+    V = oracle.predict_taylor(cad.uvw(), cad.freqs(), src, Gt, Ht)
+    R, G, H, st = oracle.peel_taylor(cad.uvw(), cad.freqs(), V, src, n_iter=8000)
+    for x in xc(cad.freqs()):
+        np.testing.assert_allclose(channel_products(G[0], H[0], x, cad.n_ant),
+                                   channel_products(Gt[0], Ht[0], x, cad.n_ant), rtol=0, atol=1e-9)
+    assert st[0] == 0
+    assert np.abs(R).max() < 1e-9 * np.abs(V).max()
+
+
+def test_taylor_peel_of_constant_gains_has_no_slope():
+    """Gains constant over the band: the Taylor fit reproduces the constant-gain
+    products and its slope terms vanish."""
+    cad = small(n_ant=7, n_chan=8, n_time=2)
+    Jt = cad.jones()
+    src = np.array([[-0.2, 0.1, 2.5]])
+    V = oracle.predict(cad.uvw(), cad.freqs(), src, Jt)
+    R, G, H, st = oracle.peel_taylor(cad.uvw(), cad.freqs(), V, src, n_iter=400)
+    pairs = baseline_pairs(cad.n_ant)
+    Gm, Hm, Jm = mats(G[0]), mats(H[0]), mats(Jt[0])
+    np.testing.assert_allclose(Gm[pairs[:, 0]] @ herm(Gm[pairs[:, 1]]),
+                               Jm[pairs[:, 0]] @ herm(Jm[pairs[:, 1]]), rtol=0, atol=1e-9)
+    slope = Gm[pairs[:, 0]] @ herm(Hm[pairs[:, 1]]) + Hm[pairs[:, 0]] @ herm(Gm[pairs[:, 1]])
+    assert np.abs(slope).max() < 1e-9
+    assert np.abs(R).max() < 1e-9 * np.abs(V).max()
+
+
+def test_taylor_first_sweep_closed_form():
+    """From G = I, H = 0 (and channels symmetric about the centre, so sum_c x_c = 0)
+    the normal matrix is block diagonal and one sweep gives
+      G_p = sum_q mean_{t,c} R~_pq / ((N-1) S),
+      H_p = sum_q mean_{t,c} x_c R~_pq / ((N-1) S mean_c x_c^2),
+    R~ the residual rotated to the source; the means come from the pinned
+    constant-gain rotate + average applied to R and to x_c R."""
+    cad = small(n_ant=5, n_chan=10, n_time=2, n_src=2)
+    V = oracle.simulate(cad)
+    l, m, S = 0.07, -0.11, 3.3
+    x = xc(cad.freqs())
+    A0 = oracle.rotate_average(cad.uvw(), cad.freqs(), V, l, m)
+    A1 = oracle.rotate_average(cad.uvw(), cad.freqs(), V * x[None, None, :, None], l, m)
+    n = cad.n_ant
+    pairs = baseline_pairs(n)
+    full0 = np.zeros((n, n, 2, 2), np.complex128)
+    full1 = np.zeros((n, n, 2, 2), np.complex128)
+    for b, (i, j) in enumerate(pairs):
+        full0[i, j], full0[j, i] = A0[b].reshape(2, 2), herm(A0[b].reshape(2, 2))
+        full1[i, j], full1[j, i] = A1[b].reshape(2, 2), herm(A1[b].reshape(2, 2))
+    G1 = np.stack([sum(full0[p, q] for q in range(n) if q != p) for p in range(n)]) / ((n - 1) * S)
+    H1 = np.stack([sum(full1[p, q] for q in range(n) if q != p) for p in range(n)]) / (
+        (n - 1) * S * np.mean(x ** 2))
+    G, H, _, _ = oracle.als_taylor(cad.uvw(), cad.freqs(), V, l, m, S, n_iter=1)
+    np.testing.assert_allclose(mats(G), G1, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(mats(H), H1, rtol=1e-12, atol=1e-12)
+
+
+def test_taylor_als_matches_brute_force_least_squares():
+    """Four antennas, a source at the phase centre (no rotation), noisy data: the
+    Taylor ALS fixed point reaches the least-squares minimum over all (G, H)
+    found by Levenberg-Marquardt from 30 starts."""
+    opt = pytest.importorskip("scipy.optimize")
+    cad = Cadence(4, 6, 1, 1, freq0_hz=150e6, noise_sigma=0.05, seed=7373)
+    S = 3.0
+    src = np.array([[0.0, 0.0, S]])
+    V = oracle.predict_taylor(cad.uvw(), cad.freqs(), src, cad.jones(), cad.jones_slope(0.4))
+    V = V + cad.noise().reshape(V.shape)
+    x = xc(cad.freqs())
+    n = cad.n_ant
+    pairs = baseline_pairs(n)
+    data = V[0]                                         # [bl][c][4], no rotation at l = m = 0
+
+    def unpack(p):                                      # 8 n complex = 16 n reals
+        z = p[:8 * n] + 1j * p[8 * n:]
+        return z[:4 * n].reshape(n, 2, 2), z[4 * n:].reshape(n, 2, 2)
+
+    def resid(p):
+        G, H = unpack(p)
+        out = []
+        for c in range(cad.n_chan):
+            J = G + x[c] * H
+            M = S * (J[pairs[:, 0]] @ herm(J[pairs[:, 1]])).reshape(-1, 4)
+            out.append((data[:, c] - M).ravel())
+        r = np.concatenate(out)
+        return np.concatenate([r.real, r.imag])
+
+    eye = np.concatenate([np.tile(np.eye(2).ravel(), n), np.zeros(4 * n)])
+    best = None
+    for s in range(30):
+        p0 = np.concatenate([eye, np.zeros(8 * n)]) + 0.3 * np.random.default_rng(900 + s).normal(size=16 * n)
+        r = opt.least_squares(resid, p0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=40000)
+        if best is None or r.cost < best.cost:
+            best = r
+    G, H, st, _ = oracle.als_taylor(cad.uvw(), cad.freqs(), V, 0.0, 0.0, S, n_iter=20000)
+    p_als = np.concatenate([np.concatenate([G.ravel(), H.ravel()]).real,
+                            np.concatenate([G.ravel(), H.ravel()]).imag])
+    cost_als = 0.5 * np.sum(resid(p_als) ** 2)
+    assert cost_als <= best.cost * (1 + 1e-9) + 1e-14
+    Gl, Hl = unpack(best.x)
+    for xx in x:
+        np.testing.assert_allclose(channel_products(G, H, xx, n),
+                                   channel_products(Gl.reshape(n, 4), Hl.reshape(n, 4), xx, n), atol=1e-6)
