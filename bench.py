@@ -428,8 +428,8 @@ def main():
 
 
 def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
-    """One-source-per-pass path, FP64-path comparison, adjoint step, ionospheric
-    offsets, CPU baseline (rank 0 at N=1 only)."""
+    """One-source-per-pass path, gains Taylor-expanded in frequency, FP64-path
+    comparison, adjoint step, ionospheric offsets, CPU baseline (rank 0 at N=1 only)."""
     import numpy as np
     import torch
     from paper_1003_5575_gb300 import Peeler
@@ -460,6 +460,29 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
         "roofline": {"bound": "hbm", "kernel": "k_stream_mixed<SUB,ACC>", "achieved": k3_gbs, "peak": hbm_peak,
                      "unit": "GB/s", "frac": k3_gbs / hbm_peak,
                      "traffic": ncu_traffic("k_stream_mixed<true,true>"),
+                     "algorithmic_bytes_per_launch": cad.n_vis * BYTES_PER_UPDATE}}
+    # gains Taylor-expanded in frequency (Section 3.1), one pass per source, same cube
+    _abi.rts_peel_timing(p1.h, 0)
+    _abi.rts_peel_timing(p1.h, 1)
+    p1.cadence_taylor(d_vis, src[:k1], resid=d_resid, status=False)
+    _abi.rts_peel_timing(p1.h, 0)
+    _abi.rts_peel_timing(p1.h, 1)
+    a, b = ev(), ev()
+    a.record()
+    _, _, _, st_t = p1.cadence_taylor(d_vis, src[:k1], resid=d_resid, status=True)
+    b.record()
+    torch.cuda.synchronize()
+    ktt = _abi.rts_peel_timing_read(p1.h)
+    ms_tp, n_tp, _ = ktt["sub_average"]
+    ms_ts, n_ts, _ = ktt["solve"]
+    tp_gbs = cad.n_vis * BYTES_PER_UPDATE / (ms_tp / n_tp / 1e3) / 1e9
+    out["taylor_gains"] = {
+        "workload": "512 ant x 768 ch x 8 t, 100 sources, one pass per source; gains G + x_c H",
+        "sources": k1, "ms": a.elapsed_time(b), "updates_per_s": k1 * cad.n_vis / (a.elapsed_time(b) / 1e3),
+        "ms_per_pass": ms_tp / n_tp, "ms_per_solve": ms_ts / n_ts,
+        "not_converged": int(np.sum(st_t == 1)),
+        "roofline": {"bound": "hbm", "kernel": "k_stream_taylor<SUB,ACC>", "achieved": tp_gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": tp_gbs / hbm_peak, "traffic": None,
                      "algorithmic_bytes_per_launch": cad.n_vis * BYTES_PER_UPDATE}}
     p1.close()
     del d_j1

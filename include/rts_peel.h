@@ -143,6 +143,29 @@ int rts_peel_set_uvw(rts_peel_t* h, const double* h_uvw, void* stream);
 int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
                      const double* h_src, void* d_jones, int32_t* h_status, void* stream);
 
+/* One cadence with the gains Taylor-expanded in frequency (Section 3.1: when
+ * consecutive channels are combined, the unknown tile gain may be
+ * Taylor-expanded in frequency).  First order about the band centre:
+ *   J_p^k(c) = G_p^k + x_c H_p^k,  x_c = (c - (n_chan - 1)/2) / n_chan,
+ * so each source's model is S (G_i + x_c H_i)(G_j + x_c H_j)^H e^{-2 pi i phi}.
+ * Each source in list order: one streaming pass subtracts the previous
+ * source's model and takes three channel moments mean_{t,c} x_c^n R e^{+2 pi i phi}
+ * (n = 0, 1, 2) of the residual in its direction; n_iter Jacobi ALS sweeps on
+ * X_p = [G_p H_p] (2x4) from G = I, H = 0, every second averaged with the
+ * previous iterate, each solving the 4x4 normal equations (FP64 sums and
+ * Cholesky solve); then its model is subtracted.  One pass per source
+ * whatever sources_per_pass says.
+ *   d_vis, d_resid, n_src, h_src, h_status, stream: as rts_peel_cadence
+ *            (status from the relative change of X in the last sweep).
+ *   d_gain   [n_src][n_ant][4] complex64 receives G (the gain at the band centre).
+ *   d_slope  [n_src][n_ant][4] complex64 receives H (the change of the gain
+ *            across one band width).
+ * RTS_PREC_MIXED handles only, n_chan >= 2 (else RTS_EINVAL).  The first call
+ * allocates the moments and iterates (3 n_bl x 32 B + 192 B per antenna). */
+int rts_peel_cadence_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
+                            const double* h_src, void* d_gain, void* d_slope, int32_t* h_status,
+                            void* stream);
+
 /* rts_peel_cadence on host buffers: copies h_vis to the caller's device buffer
  * d_work (cube-sized), peels it in place, copies the residual to h_resid and
  * the Jones matrices to h_jones ([n_src][n_ant][4]), and waits for the stream.

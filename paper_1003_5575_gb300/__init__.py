@@ -7,7 +7,7 @@ the library; the first call does, and raises if the library was not built.
 from ._abi import (  # noqa: F401
     RTS_OK, RTS_NOT_CONVERGED, RTS_EINVAL, RTS_ENOMEM, RTS_ECUDA, RTS_ENONFINITE,
     RTS_PREC_MIXED, RTS_PREC_FP64, RtsError, rts_peel_config,
-    rts_peel_init, rts_peel_set_uvw, rts_peel_cadence, rts_peel_cadence_host, rts_peel_predict,
+    rts_peel_init, rts_peel_set_uvw, rts_peel_cadence, rts_peel_cadence_host, rts_peel_cadence_taylor, rts_peel_predict,
     rts_peel_rotate_average, rts_peel_solve, rts_peel_solve_noalloc, rts_peel_grad,
     rts_peel_offsets, rts_offsets_solve,
     rts_peel_pipeline_submit, rts_peel_pipeline_wait, rts_peel_last_error, rts_peel_destroy,

@@ -32,6 +32,7 @@ KERNEL_CLASSES = ("average", "sub_average", "subtract", "solve", "predict", "gra
                   "block_pass", "block_fix", "offsets")
 
 EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_cadence_host",
+           "rts_peel_cadence_taylor",
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad", "rts_peel_offsets",
            "rts_offsets_solve",
            "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
@@ -80,6 +81,8 @@ def lib():
             L.rts_peel_set_uvw.argtypes = [_vp, _dp, _vp]
             L.rts_peel_cadence.restype = ctypes.c_int
             L.rts_peel_cadence.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _ip, _vp]
+            L.rts_peel_cadence_taylor.restype = ctypes.c_int
+            L.rts_peel_cadence_taylor.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _vp, _ip, _vp]
             L.rts_peel_cadence_host.restype = ctypes.c_int
             L.rts_peel_cadence_host.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _ip, _vp, _vp]
             L.rts_peel_predict.restype = ctypes.c_int
@@ -141,6 +144,11 @@ def rts_peel_set_uvw(h, uvw_ptr, stream):
 
 def rts_peel_cadence(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, stream):
     return _check(lib().rts_peel_cadence(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, stream), h)
+
+
+def rts_peel_cadence_taylor(h, d_vis, d_resid, n_src, h_src, d_gain, d_slope, h_status, stream):
+    return _check(lib().rts_peel_cadence_taylor(h, d_vis, d_resid, n_src, h_src, d_gain, d_slope,
+                                                h_status, stream), h)
 
 
 def rts_peel_cadence_host(h, h_vis, h_resid, n_src, h_src, h_jones, h_status, d_work, stream):

@@ -20,6 +20,7 @@
 #include "predict_kernels.cuh"
 #include "solve_kernels.cuh"
 #include "stream_kernels.cuh"
+#include "taylor_kernels.cuh"
 
 using namespace rts;
 
@@ -47,6 +48,10 @@ struct rts_peel_t {
   double* d_src = nullptr;         // [max_sources][3]
   void* d_jones_stage = nullptr;   // [max_sources][n_ant][4] cube precision (host-buffer calls)
   GradWorkspace grad;
+  // gains Taylor-expanded in frequency (allocated on the first Taylor cadence)
+  float2* t_mom = nullptr;         // [3][n_bl][4] channel moments of the averaged source
+  double2* t_X[2] = {nullptr, nullptr};   // [n_ant][8] FP64 iterates (G then H)
+  float2* t_Xf[2] = {nullptr, nullptr};   // FP32 copies
   // blocked peel workspace (allocated on the first blocked cadence).  The phase
   // and D_jk tables depend on geometry only; a second stream fills a ring of
   // kRing block slots ahead of the main stream (events order the reuse).
@@ -532,9 +537,124 @@ int peel_device(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
   return RTS_OK;
 }
 
+// ---- gains Taylor-expanded in frequency (taylor_kernels.cuh) -------------------
+
+// allocates whatever is still missing (a failed call leaves the rest for the next)
+int taylor_setup(rts_peel_t* h) {
+  if (!h->t_mom) RTS_CUDA(h, cudaMalloc(&h->t_mom, (size_t)3 * h->n_bl * 4 * sizeof(float2)));
+  for (int k = 0; k < 2; ++k) {
+    if (!h->t_X[k]) RTS_CUDA(h, cudaMalloc(&h->t_X[k], (size_t)h->n_ant * 8 * sizeof(double2)));
+    if (!h->t_Xf[k]) RTS_CUDA(h, cudaMalloc(&h->t_Xf[k], (size_t)h->n_ant * 8 * sizeof(float2)));
+  }
+  return RTS_OK;
+}
+
+// x_c = x0 + c dx, the channel's offset from the band centre in band widths
+void taylor_axis(const rts_peel_t* h, float* x0, float* dx, double (&mu)[5]) {
+  const int n = h->n_chan;
+  for (int k = 0; k < 5; ++k) mu[k] = 0.0;
+  for (int c = 0; c < n; ++c) {
+    const double x = (c - 0.5 * (n - 1)) / n;
+    double xp = 1.0;
+    for (int k = 0; k < 5; ++k) { mu[k] += xp; xp *= x; }
+  }
+  for (int k = 0; k < 5; ++k) mu[k] /= n;
+  *x0 = (float)(-0.5 * (n - 1) / n);
+  *dx = (float)(1.0 / n);
+}
+
+int launch_stream_taylor(rts_peel_t* h, bool sub, bool acc, const TaylorStreamArgs& a, cudaStream_t s) {
+  const dim3 grid((unsigned)h->n_bl), block(kStreamThreads);
+  const size_t smem = (size_t)h->n_time * 4 * sizeof(unsigned long long);
+  Span span(h, sub && acc ? RTS_K_SUB_AVERAGE : (sub ? RTS_K_SUBTRACT : RTS_K_AVERAGE), s);
+  if (sub && acc) k_stream_taylor<true, true><<<grid, block, smem, s>>>(a);
+  else if (sub) k_stream_taylor<true, false><<<grid, block, smem, s>>>(a);
+  else k_stream_taylor<false, true><<<grid, block, smem, s>>>(a);
+  span.end(1);
+  return check_launch(h, "Taylor streaming kernel launch");
+}
+
+// n_iter Taylor sweeps on h->t_mom; G, H of the last sweep to gain_out / slope_out,
+// the FP64 solution left in h->t_X[n_iter & 1]; status/rel to slot `slot`
+int launch_als_taylor(rts_peel_t* h, double S, float2* gain_out, float2* slope_out, int slot,
+                      cudaStream_t s) {
+  float x0, dx;
+  double mu[5];
+  taylor_axis(h, &x0, &dx, mu);
+  Span span(h, RTS_K_SOLVE, s);
+  for (int it = 1; it <= h->n_iter; ++it) {
+    TaylorAlsArgs a;
+    a.mom = h->t_mom;
+    a.X_old = h->t_X[(it - 1) & 1]; a.Xf_old = h->t_Xf[(it - 1) & 1];
+    a.X_new = h->t_X[it & 1]; a.Xf_new = h->t_Xf[it & 1];
+    a.norms = h->d_norms; a.flag = h->d_flag;
+    a.gain_out = it == h->n_iter ? gain_out : nullptr;
+    a.slope_out = it == h->n_iter ? slope_out : nullptr;
+    a.n_ant = h->n_ant; a.n_bl = h->n_bl; a.S = S;
+    for (int k = 0; k < 5; ++k) a.mu[k] = mu[k];
+    a.first = it == 1; a.average = (it % 2) == 0;
+    k_als_taylor_sweep<<<(unsigned)h->n_ant, kAlsThreads, 0, s>>>(a);
+  }
+  k_als_finalize<<<1, 256, 0, s>>>(h->d_norms, h->n_ant, h->d_flag, h->d_status + slot, h->d_rel + slot);
+  span.end(h->n_iter + 1);
+  return check_launch(h, "Taylor ALS kernel launch");
+}
+
+int peel_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src, const double* h_src,
+                void* d_gain, void* d_slope, int32_t* h_status, cudaStream_t s) {
+  const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
+  if (n_src == 0) {
+    if (d_resid != d_vis) RTS_CUDA(h, cudaMemcpyAsync(d_resid, d_vis, cube, cudaMemcpyDeviceToDevice, s));
+    return RTS_OK;
+  }
+  int rc = taylor_setup(h);
+  if (rc) return rc;
+  float x0, dx;
+  double mu[5];
+  taylor_axis(h, &x0, &dx, mu);
+  const size_t jstride = (size_t)h->n_ant * 4;
+  TaylorStreamArgs a;
+  a.s = stream_args(h, d_vis, d_resid, nullptr);
+  a.s.acc = make_dir(h_src[0], h_src[1], h_src[2]);
+  a.Xsub = nullptr; a.mom = h->t_mom; a.x0 = x0; a.dx = dx;
+  rc = launch_stream_taylor(h, false, true, a, s);
+  if (rc) return rc;
+  for (int k = 0; k < n_src; ++k) {
+    rc = launch_als_taylor(h, h_src[3 * k + 2], static_cast<float2*>(d_gain) + k * jstride,
+                           static_cast<float2*>(d_slope) + k * jstride, k, s);
+    if (rc) return rc;
+    TaylorStreamArgs b;
+    b.s = stream_args(h, k == 0 ? d_vis : d_resid, d_resid, nullptr);
+    b.s.sub = make_dir(h_src[3 * k], h_src[3 * k + 1], h_src[3 * k + 2]);
+    b.Xsub = h->t_X[h->n_iter & 1];
+    b.mom = h->t_mom; b.x0 = x0; b.dx = dx;
+    const bool more = k + 1 < n_src;
+    if (more) b.s.acc = make_dir(h_src[3 * (k + 1)], h_src[3 * (k + 1) + 1], h_src[3 * (k + 1) + 2]);
+    rc = launch_stream_taylor(h, true, more, b, s);
+    if (rc) return rc;
+  }
+  if (h_status) return read_status(h, n_src, h_status, s);
+  return RTS_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int rts_peel_cadence_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
+                            const double* h_src, void* d_gain, void* d_slope, int32_t* h_status,
+                            void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (h->precision != RTS_PREC_MIXED) return fail(h, RTS_EINVAL, "Taylor gains need an RTS_PREC_MIXED handle");
+  if (h->n_chan < 2) return fail(h, RTS_EINVAL, "Taylor gains need n_chan >= 2");
+  if (!d_vis || !d_resid) return fail(h, RTS_EINVAL, "d_vis and d_resid are required");
+  if (misaligned(d_vis) || misaligned(d_resid))
+    return fail(h, RTS_EINVAL, "d_vis and d_resid must start on a 16-byte boundary");
+  int rc = validate_sources(h, n_src, h_src);
+  if (rc) return rc;
+  if (n_src > 0 && (!d_gain || !d_slope)) return fail(h, RTS_EINVAL, "d_gain and d_slope are required");
+  return peel_taylor(h, d_vis, d_resid, n_src, h_src, d_gain, d_slope, h_status, as_stream(stream));
+}
 
 int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   g_init_err.clear();
@@ -993,7 +1113,8 @@ void rts_peel_destroy(rts_peel_t* h) {
   if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
   void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
                   h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage,
-                  h->b_avg, h->b_model, h->b_sync, h->b_part, h->d_perr};
+                  h->b_avg, h->b_model, h->b_sync, h->b_part, h->d_perr, h->t_mom, h->t_X[0],
+                  h->t_X[1], h->t_Xf[0], h->t_Xf[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int r = 0; r < rts_peel_t::kRing; ++r) {

@@ -1,0 +1,386 @@
+// Gains Taylor-expanded in frequency (Section 3.1: when consecutive channels
+// are combined, the unknown tile gain may be Taylor-expanded in frequency).
+// First order about the band centre (uniform channels):
+//   J_p(c) = G_p + x_c H_p,   x_c = (c - (N_c - 1)/2) / N_c,
+// so source k's model on baseline (i, j) at channel c is
+//   S (G_i + x_c H_i)(G_j + x_c H_j)^H exp(-2 pi i phi) = (P0 + x_c P1 + x_c^2 P2) exp(-2 pi i phi),
+//   P0 = S G_i G_j^H,  P1 = S (G_i H_j^H + H_i G_j^H),  P2 = S H_i H_j^H.
+// The least-squares solve over every sample uses the unknown X_p = [G_p H_p]
+// (2 x 4) and Z_pq(c) = S [W_q(c); x_c W_q(c)], W_q(c) = (G_q + x_c H_q)^H.
+// Because the model depends on c only through x_c, its normal equations
+// reduce exactly to three channel moments of the rotated residual per baseline,
+//   M_n(bl) = mean_{t,c} x_c^n R exp(+2 pi i phi),  n = 0, 1, 2,
+// and five scalar channel moments mu_n = mean_c x_c^n:
+//   A_p = S sum_q [M0 G_q + M1 H_q,  M1 G_q + M2 H_q]          (M_n,qp = M_n,pq^H)
+//   C_p = S^2 [mu0 K0 + mu1 K1 + mu2 K2,  mu1 K0 + mu2 K1 + mu3 K2;
+//              mu1 K0 + mu2 K1 + mu3 K2,  mu2 K0 + mu3 K1 + mu4 K2]
+//   K0 = sum_q G_q^H G_q,  K1 = sum_q (G_q^H H_q + H_q^H G_q),  K2 = sum_q H_q^H H_q
+//   X_p <- A_p C_p^-1   (Jacobi sweeps from G = I, H = 0, every second averaged).
+// One streaming pass per source subtracts source k's model and accumulates the
+// moments for source k+1 (as the constant-gain pass does with one average).
+#pragma once
+#include "als_kernels.cuh"
+#include "stream_kernels.cuh"
+
+namespace rts {
+
+struct TaylorStreamArgs {
+  StreamArgs s;             // cube, geometry, sources; s.avg unused
+  const double2* Xsub;      // [n_ant][8] FP64 G (4) then H (4) of the subtracted source
+  float2* mom;              // [3][n_bl][4] moments M0, M1, M2 of the averaged source
+  float x0, dx;             // x_c = x0 + c dx
+};
+
+// model matrices P0, P1, P2 of one baseline from the FP64 Taylor Jones
+__device__ inline void taylor_model(const double2* __restrict__ X, int i, int j, double S,
+                                    float2 (&P)[3][4]) {
+  M22<double2> Gi, Hi, Gj, Hj;
+  #pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    Gi.e[e] = X[(size_t)i * 8 + e]; Hi.e[e] = X[(size_t)i * 8 + 4 + e];
+    Gj.e[e] = X[(size_t)j * 8 + e]; Hj.e[e] = X[(size_t)j * 8 + 4 + e];
+  }
+  const M22<double2> a = mmul_h(Gi, Gj), b = mmul_h(Gi, Hj), c = mmul_h(Hi, Gj), d = mmul_h(Hi, Hj);
+  #pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    P[0][e] = make_float2((float)(S * a.e[e].x), (float)(S * a.e[e].y));
+    P[1][e] = make_float2((float)(S * (b.e[e].x + c.e[e].x)), (float)(S * (b.e[e].y + c.e[e].y)));
+    P[2][e] = make_float2((float)(S * d.e[e].x), (float)(S * d.e[e].y));
+  }
+}
+
+template <bool SUB, bool ACC>
+__global__ void __launch_bounds__(kStreamThreads, 2) k_stream_taylor(TaylorStreamArgs ta) {
+  const StreamArgs& a = ta.s;
+  extern __shared__ unsigned long long s_ph[];   // [n_time][4]: A_sub B_sub A_acc B_acc
+  __shared__ float2 s_P[3][4];
+  __shared__ double s_red[(kStreamThreads / 32) * 24];
+  const int64_t bl = blockIdx.x;
+  const int2 ij = a.bl_ant[bl];
+  for (int t = threadIdx.x; t < a.n_time; t += blockDim.x) {
+    if (SUB) {
+      const double tau = delay_m(a.uvw, a.n_ant, t, ij.x, ij.y, a.sub);
+      s_ph[4 * t + 0] = frac_q64(tau * a.nu0_c);
+      s_ph[4 * t + 1] = frac_q64(tau * a.dnu_c);
+    }
+    if (ACC) {
+      const double tau = delay_m(a.uvw, a.n_ant, t, ij.x, ij.y, a.acc);
+      s_ph[4 * t + 2] = frac_q64(tau * a.nu0_c);
+      s_ph[4 * t + 3] = frac_q64(tau * a.dnu_c);
+    }
+  }
+  if (SUB && threadIdx.x == 0) {
+    float2 P[3][4];
+    taylor_model(ta.Xsub, ij.x, ij.y, a.sub.S, P);
+    #pragma unroll
+    for (int n = 0; n < 3; ++n)
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) s_P[n][e] = P[n][e];
+  }
+  __syncthreads();
+  float2 P[3][4];
+  if (SUB) {
+    #pragma unroll
+    for (int n = 0; n < 3; ++n)
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) P[n][e] = s_P[n][e];
+  }
+  float acc[24];
+  #pragma unroll
+  for (int k = 0; k < 24; ++k) acc[k] = 0.f;
+
+  const float4* src = static_cast<const float4*>(a.src);   // may alias dst (in place)
+  float4* dst = static_cast<float4*>(a.dst);
+  const int n_s = a.n_time * a.n_chan;
+  TCWalk w;
+  w.init(threadIdx.x, a.n_chan);
+  for (int s0 = threadIdx.x; s0 < n_s; s0 += kStreamBatch * kStreamThreads) {
+    float4 x0[kStreamBatch], x1[kStreamBatch];
+    int tt[kStreamBatch], cc[kStreamBatch];
+    size_t idx[kStreamBatch];
+    #pragma unroll
+    for (int u = 0; u < kStreamBatch; ++u) {
+      tt[u] = w.t; cc[u] = w.c;
+      idx[u] = (((size_t)w.t * a.n_bl + bl) * a.n_chan + w.c) * 2;
+      if (s0 + u * kStreamThreads < n_s) {
+        x0[u] = __ldcs(src + idx[u]);
+        x1[u] = __ldcs(src + idx[u] + 1);
+      }
+      w.next();
+    }
+    #pragma unroll
+    for (int u = 0; u < kStreamBatch; ++u) {
+      if (s0 + u * kStreamThreads < n_s) {
+        const float x = fmaf((float)cc[u], ta.dx, ta.x0);
+        if (SUB) {
+          const unsigned long long A = s_ph[4 * tt[u]], B = s_ph[4 * tt[u] + 1];
+          const float2 ph = phasor_f(q64_to_turns(A + (unsigned long long)cc[u] * B));
+          float2 M[4];
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) {               // P0 + x (P1 + x P2)
+            M[e].x = fmaf(x, fmaf(x, P[2][e].x, P[1][e].x), P[0][e].x);
+            M[e].y = fmaf(x, fmaf(x, P[2][e].y, P[1][e].y), P[0][e].y);
+          }
+          sub_model(x0[u], x1[u], M, ph);
+          __stcs(dst + idx[u], x0[u]);
+          __stcs(dst + idx[u] + 1, x1[u]);
+        }
+        if (ACC) {
+          const unsigned long long A = s_ph[4 * tt[u] + 2], B = s_ph[4 * tt[u] + 3];
+          const float2 ph = phasor_f(q64_to_turns(A + (unsigned long long)cc[u] * B));
+          float y[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          acc_rot(y, x0[u], x1[u], ph);
+          const float x2 = x * x;
+          #pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            acc[k] += y[k];
+            acc[8 + k] = fmaf(x, y[k], acc[8 + k]);
+            acc[16 + k] = fmaf(x2, y[k], acc[16 + k]);
+          }
+        }
+      }
+    }
+  }
+  if (ACC) {
+    double tot[24];
+    block_sum_f32_to_f64<24>(acc, s_red, tot);
+    if (threadIdx.x == 0) {
+      #pragma unroll
+      for (int n = 0; n < 3; ++n) {
+        float4* out = reinterpret_cast<float4*>(ta.mom + ((size_t)n * a.n_bl + bl) * 4);
+        const double* v = tot + 8 * n;
+        out[0] = make_float4((float)(v[0] * a.inv_n), (float)(v[1] * a.inv_n), (float)(v[2] * a.inv_n),
+                             (float)(v[3] * a.inv_n));
+        out[1] = make_float4((float)(v[4] * a.inv_n), (float)(v[5] * a.inv_n), (float)(v[6] * a.inv_n),
+                             (float)(v[7] * a.inv_n));
+      }
+    }
+  }
+}
+
+struct TaylorAlsArgs {
+  const float2* mom;        // [3][n_bl][4]
+  const double2* X_old;     // [n_ant][8] FP64 iterate (ignored on the first sweep)
+  const float2* Xf_old;     // FP32 copy of X_old
+  double2* X_new;
+  float2* Xf_new;
+  double* norms;            // [n_ant][2]
+  int* flag;
+  float2* gain_out;         // [n_ant][4] G, last sweep only (else NULL)
+  float2* slope_out;        // [n_ant][4] H, last sweep only
+  int n_ant;
+  int64_t n_bl;
+  double S;
+  double mu[5];             // mean_c x_c^n
+  int first, average;
+};
+
+// M_n,pq of one baseline pair (conjugate transpose when q < p)
+__device__ inline void load_mom(const float2* __restrict__ mom, int64_t n_bl, int n_ant, int p, int q,
+                                int n, float2 (&v)[4]) {
+  const float2* base = mom + (size_t)n * n_bl * 4;
+  load_vpq<float2>(base, n_ant, p, q, v);
+}
+
+// 2x2 complex FP32 helpers on [0 1; 2 3]
+__device__ inline void mm_acc(const float2 (&a)[4], const float2 (&b)[4], float (&o)[8]) {   // o += a b
+  #pragma unroll
+  for (int r = 0; r < 2; ++r)
+    #pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float2 x = cadd(cmul(a[2 * r], b[c]), cmul(a[2 * r + 1], b[2 + c]));
+      o[2 * (2 * r + c)] += x.x; o[2 * (2 * r + c) + 1] += x.y;
+    }
+}
+__device__ inline void mhm_acc(const float2 (&a)[4], const float2 (&b)[4], float (&o)[8]) {  // o += a^H b
+  #pragma unroll
+  for (int r = 0; r < 2; ++r)
+    #pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float2 x = cadd(cconjmul(a[r], b[c]), cconjmul(a[2 + r], b[2 + c]));
+      o[2 * (2 * r + c)] += x.x; o[2 * (2 * r + c) + 1] += x.y;
+    }
+}
+
+// In-place Cholesky of a 4x4 Hermitian positive-definite matrix (lower
+// triangle used); solves C y^H = b^H for the two rows b of B (y B-shaped):
+// X = B C^-1.  Returns false when C is not positive definite.
+__device__ inline bool chol_solve4(double2 (&C)[4][4], double2 (&B)[2][4]) {
+  double2 L[4][4];
+  #pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    double d = C[j][j].x;
+    #pragma unroll
+    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
+    if (!(d > 0.0)) return false;
+    const double ljj = sqrt(d), inv = 1.0 / ljj;
+    L[j][j] = make_double2(ljj, 0.0);
+    #pragma unroll
+    for (int i = j + 1; i < 4; ++i) {
+      double2 s = C[i][j];
+      #pragma unroll
+      for (int k = 0; k < j; ++k) s = csub(s, cmul(L[i][k], cconj(L[j][k])));
+      L[i][j] = make_double2(s.x * inv, s.y * inv);
+    }
+  }
+  #pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    double2 y[4];
+    #pragma unroll
+    for (int i = 0; i < 4; ++i) {            // L y = b^H
+      double2 s = cconj(B[r][i]);
+      #pragma unroll
+      for (int k = 0; k < i; ++k) s = csub(s, cmul(L[i][k], y[k]));
+      y[i] = make_double2(s.x / L[i][i].x, s.y / L[i][i].x);
+    }
+    double2 z[4];
+    #pragma unroll
+    for (int i = 3; i >= 0; --i) {           // L^H z = y
+      double2 s = y[i];
+      #pragma unroll
+      for (int k = i + 1; k < 4; ++k) s = csub(s, cmul(cconj(L[k][i]), z[k]));
+      z[i] = make_double2(s.x / L[i][i].x, s.y / L[i][i].x);
+    }
+    #pragma unroll
+    for (int i = 0; i < 4; ++i) B[r][i] = cconj(z[i]);   // x = z^H
+  }
+  return true;
+}
+
+// One Jacobi sweep for antenna p = blockIdx.x (kAlsThreads threads).
+__global__ void __launch_bounds__(kAlsThreads) k_als_taylor_sweep(TaylorAlsArgs a) {
+  __shared__ double s_red[kAlsThreads / 32][32];
+  __shared__ double s_tot[32];
+  __shared__ double2 s_X[8];
+  const int p = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per-thread partials: A (2x4 complex: left M0 G + M1 H, right M1 G + M2 H),
+  // K0 = G^H G, K1 = G^H H + H^H G, K2 = H^H H (full 2x2 complex each)
+  float Al[8], Ar[8], K0[8], K1[8], K2[8];
+  #pragma unroll
+  for (int k = 0; k < 8; ++k) { Al[k] = 0.f; Ar[k] = 0.f; K0[k] = 0.f; K1[k] = 0.f; K2[k] = 0.f; }
+  for (int q = threadIdx.x; q < a.n_ant; q += kAlsThreads) {
+    if (q == p) continue;
+    float2 M0[4], M1[4], M2[4], G[4], H[4];
+    load_mom(a.mom, a.n_bl, a.n_ant, p, q, 0, M0);
+    load_mom(a.mom, a.n_bl, a.n_ant, p, q, 1, M1);
+    load_mom(a.mom, a.n_bl, a.n_ant, p, q, 2, M2);
+    if (a.first) {
+      G[0] = make_float2(1.f, 0.f); G[1] = make_float2(0.f, 0.f); G[2] = make_float2(0.f, 0.f);
+      G[3] = make_float2(1.f, 0.f);
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) H[e] = make_float2(0.f, 0.f);
+    } else {
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) { G[e] = a.Xf_old[(size_t)q * 8 + e]; H[e] = a.Xf_old[(size_t)q * 8 + 4 + e]; }
+    }
+    mm_acc(M0, G, Al); mm_acc(M1, H, Al);
+    mm_acc(M1, G, Ar); mm_acc(M2, H, Ar);
+    mhm_acc(G, G, K0);
+    mhm_acc(G, H, K1); mhm_acc(H, G, K1);
+    mhm_acc(H, H, K2);
+  }
+  // FP64 sums across the CTA: 40 values in two reduce-scatter rounds of 16 + 24
+  double v[16];
+  #pragma unroll
+  for (int k = 0; k < 8; ++k) { v[k] = (double)Al[k]; v[8 + k] = (double)Ar[k]; }
+  double w0 = warp_reduce_scatter16(v, lane);
+  #pragma unroll
+  for (int k = 0; k < 8; ++k) { v[k] = (double)K0[k]; v[8 + k] = (double)K1[k]; }
+  double w1 = warp_reduce_scatter16(v, lane);
+  #pragma unroll
+  for (int k = 0; k < 8; ++k) { v[k] = (double)K2[k]; v[8 + k] = 0.0; }
+  double w2 = warp_reduce_scatter16(v, lane);
+  __shared__ double s_red2[kAlsThreads / 32][8];
+  if ((lane & 1) == 0) {
+    s_red[warp][lane >> 1] = w0;            // 0..15: A left, A right
+    s_red[warp][16 + (lane >> 1)] = w1;     // 16..31: K0, K1
+    if ((lane >> 1) < 8) s_red2[warp][lane >> 1] = w2;   // K2
+  }
+  __syncthreads();
+  __shared__ double s_k2[8];
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    #pragma unroll
+    for (int w = 0; w < kAlsThreads / 32; ++w) t += s_red[w][threadIdx.x];
+    s_tot[threadIdx.x] = t;
+  } else if (threadIdx.x < 40) {
+    double t = 0.0;
+    #pragma unroll
+    for (int w = 0; w < kAlsThreads / 32; ++w) t += s_red2[w][threadIdx.x - 32];
+    s_k2[threadIdx.x - 32] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    auto cm = [&](const double* b, int e) { return make_double2(b[2 * e], b[2 * e + 1]); };
+    const double* k0 = s_tot + 16;
+    const double* k1 = s_tot + 24;
+    const double* k2 = s_k2;
+    const double S = a.S, S2 = S * S;
+    double2 C[4][4];
+    // block (bi, bj) = S^2 (mu[bi+bj] K0 + mu[bi+bj+1] K1 + mu[bi+bj+2] K2)
+    #pragma unroll
+    for (int bi = 0; bi < 2; ++bi)
+      #pragma unroll
+      for (int bj = 0; bj < 2; ++bj) {
+        const double c0 = S2 * a.mu[bi + bj], c1 = S2 * a.mu[bi + bj + 1], c2 = S2 * a.mu[bi + bj + 2];
+        #pragma unroll
+        for (int r = 0; r < 2; ++r)
+          #pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int e = 2 * r + c;
+            const double2 x0 = cm(k0, e), x1 = cm(k1, e), x2 = cm(k2, e);
+            C[2 * bi + r][2 * bj + c] = make_double2(c0 * x0.x + c1 * x1.x + c2 * x2.x,
+                                                     c0 * x0.y + c1 * x1.y + c2 * x2.y);
+          }
+      }
+    double2 B[2][4];
+    #pragma unroll
+    for (int r = 0; r < 2; ++r)
+      #pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const double2 l = cm(s_tot, 2 * r + c), rr = cm(s_tot + 8, 2 * r + c);
+        B[r][c] = make_double2(S * l.x, S * l.y);
+        B[r][2 + c] = make_double2(S * rr.x, S * rr.y);
+      }
+    const bool ok = chol_solve4(C, B);
+    #pragma unroll
+    for (int r = 0; r < 2; ++r)
+      #pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        s_X[2 * r + c] = ok ? B[r][c] : make_double2(NAN, NAN);          // G
+        s_X[4 + 2 * r + c] = ok ? B[r][2 + c] : make_double2(NAN, NAN);  // H
+      }
+  }
+  __syncthreads();
+  if (threadIdx.x >= 8) return;
+  const int e = threadIdx.x;
+  double2 Xn = s_X[e];
+  double2 Xo;
+  if (a.first) Xo = make_double2((e == 0 || e == 3) ? 1.0 : 0.0, 0.0);
+  else Xo = a.X_old[(size_t)p * 8 + e];
+  if (a.average) Xn = make_double2(0.5 * (Xn.x + Xo.x), 0.5 * (Xn.y + Xo.y));
+  const double dx = Xn.x - Xo.x, dy = Xn.y - Xo.y;
+  double dn = dx * dx + dy * dy;
+  double nn = Xn.x * Xn.x + Xn.y * Xn.y;
+  int bad = !(isfinite(Xn.x) && isfinite(Xn.y));
+  #pragma unroll
+  for (int o = 1; o <= 4; o <<= 1) {
+    dn += __shfl_xor_sync(0xffu, dn, o);
+    nn += __shfl_xor_sync(0xffu, nn, o);
+    bad |= __shfl_xor_sync(0xffu, bad, o);
+  }
+  a.X_new[(size_t)p * 8 + e] = Xn;
+  a.Xf_new[(size_t)p * 8 + e] = make_float2((float)Xn.x, (float)Xn.y);
+  if (a.gain_out) {
+    float2* o = e < 4 ? a.gain_out + (size_t)p * 4 + e : a.slope_out + (size_t)p * 4 + (e - 4);
+    *o = make_float2((float)Xn.x, (float)Xn.y);
+  }
+  if (e == 0) {
+    a.norms[2 * p] = dn;
+    a.norms[2 * p + 1] = nn;
+    if (bad) *a.flag = 1;
+  }
+}
+
+}  // namespace rts

@@ -116,6 +116,25 @@ class Peeler:
                               _ptr(jones), st.ctypes.data_as(_ip) if status else None, _stream(stream))
         return resid, jones, (st[:k] if status else None)
 
+    def cadence_taylor(self, vis: torch.Tensor, sources, resid: torch.Tensor | None = None,
+                       status: bool = True, stream=None):
+        """Peel with gains linear in frequency, J(c) = G + x_c H (x_c the channel's
+        offset from the band centre in band widths).  Returns (resid, G, H
+        [K][n_ant][4], status int32[K] or None)."""
+        self._check_cube(vis)
+        src = _host_f64(sources).reshape(-1, 3)
+        k = src.shape[0]
+        if resid is None:
+            resid = self.empty_cube()
+        self._check_cube(resid, "resid")
+        gain = torch.empty((k, self.n_ant, 4), dtype=self.cdtype, device=self.device)
+        slope = torch.empty_like(gain)
+        st = np.zeros(max(k, 1), np.int32) if status else None
+        _abi.rts_peel_cadence_taylor(self.h, _ptr(vis), _ptr(resid), k, src.ctypes.data_as(_dp),
+                                     _ptr(gain), _ptr(slope), st.ctypes.data_as(_ip) if status else None,
+                                     _stream(stream))
+        return resid, gain, slope, (st[:k] if status else None)
+
     def cadence_host(self, h_vis: torch.Tensor, sources, d_work: torch.Tensor,
                      h_resid: torch.Tensor | None = None, stream=None):
         """The same peel on host (ideally pinned) tensors, copies included."""
