@@ -31,22 +31,38 @@ struct TaylorStreamArgs {
   float x0, dx;             // x_c = x0 + c dx
 };
 
-// model matrices P0, P1, P2 of one baseline from the FP64 Taylor Jones
-__device__ inline void taylor_model(const double2* __restrict__ X, int i, int j, double S,
-                                    float2 (&P)[3][4]) {
-  M22<double2> Gi, Hi, Gj, Hj;
+// Entry e = 2r + c of model matrix n (P0, P1 or P2) of baseline (i, j) from
+// the FP64 Taylor Jones X [n_ant][8] (G then H), one entry per calling thread:
+// (A B^H)[r][c] = sum_k A[r][k] conj(B[c][k]).
+__device__ inline float2 taylor_model_entry(const double2* __restrict__ X, int i, int j, double S, int n,
+                                            int e) {
+  const int r = e >> 1, c = e & 1;
+  auto ent = [&](const double2* A, const double2* B) {
+    return cadd(cmul(A[2 * r], cconj(B[2 * c])), cmul(A[2 * r + 1], cconj(B[2 * c + 1])));
+  };
+  const double2 *Gi = X + (size_t)i * 8, *Hi = Gi + 4, *Gj = X + (size_t)j * 8, *Hj = Gj + 4;
+  double2 v;
+  if (n == 0) v = ent(Gi, Gj);
+  else if (n == 1) v = cadd(ent(Gi, Hj), ent(Hi, Gj));
+  else v = ent(Hi, Hj);
+  return make_float2((float)(S * v.x), (float)(S * v.y));
+}
+
+// Reduce 16 floats over the 32 lanes of a warp (each level exchanges half of the
+// remaining values with the partner lane); afterwards lane L holds the warp
+// total of value index L >> 1.
+__device__ inline float warp_reduce_scatter16f(float (&v)[16], int lane) {
   #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    Gi.e[e] = X[(size_t)i * 8 + e]; Hi.e[e] = X[(size_t)i * 8 + 4 + e];
-    Gj.e[e] = X[(size_t)j * 8 + e]; Hj.e[e] = X[(size_t)j * 8 + 4 + e];
+  for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+    const bool upper = (lane & o) != 0;
+    #pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = upper ? v[i] : v[i + n / 2];
+      const float keep = upper ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
   }
-  const M22<double2> a = mmul_h(Gi, Gj), b = mmul_h(Gi, Hj), c = mmul_h(Hi, Gj), d = mmul_h(Hi, Hj);
-  #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    P[0][e] = make_float2((float)(S * a.e[e].x), (float)(S * a.e[e].y));
-    P[1][e] = make_float2((float)(S * (b.e[e].x + c.e[e].x)), (float)(S * (b.e[e].y + c.e[e].y)));
-    P[2][e] = make_float2((float)(S * d.e[e].x), (float)(S * d.e[e].y));
-  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 template <bool SUB, bool ACC>
@@ -54,7 +70,8 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_taylor(TaylorStrea
   const StreamArgs& a = ta.s;
   extern __shared__ unsigned long long s_ph[];   // [n_time][4]: A_sub B_sub A_acc B_acc
   __shared__ float2 s_P[3][4];
-  __shared__ double s_red[(kStreamThreads / 32) * 24];
+  __shared__ double s_red[kStreamThreads / 32][32];
+  __shared__ double s_tot[24];
   const int64_t bl = blockIdx.x;
   const int2 ij = a.bl_ant[bl];
   for (int t = threadIdx.x; t < a.n_time; t += blockDim.x) {
@@ -69,14 +86,9 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_taylor(TaylorStrea
       s_ph[4 * t + 3] = frac_q64(tau * a.dnu_c);
     }
   }
-  if (SUB && threadIdx.x == 0) {
-    float2 P[3][4];
-    taylor_model(ta.Xsub, ij.x, ij.y, a.sub.S, P);
-    #pragma unroll
-    for (int n = 0; n < 3; ++n)
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) s_P[n][e] = P[n][e];
-  }
+  if (SUB && threadIdx.x < 12)
+    s_P[threadIdx.x >> 2][threadIdx.x & 3] =
+        taylor_model_entry(ta.Xsub, ij.x, ij.y, a.sub.S, threadIdx.x >> 2, threadIdx.x & 3);
   __syncthreads();
   float2 P[3][4];
   if (SUB) {
@@ -142,18 +154,33 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_taylor(TaylorStrea
     }
   }
   if (ACC) {
-    double tot[24];
-    block_sum_f32_to_f64<24>(acc, s_red, tot);
-    if (threadIdx.x == 0) {
+    // warp totals of the 24 sums (two reduce-scatter rounds), then one thread per
+    // sum adds the warps' totals in FP64 in warp order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float v[16];
+    #pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = acc[k];
+    const float w0 = warp_reduce_scatter16f(v, lane);
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) { v[k] = acc[16 + k]; v[8 + k] = 0.f; }
+    const float w1 = warp_reduce_scatter16f(v, lane);
+    if ((lane & 1) == 0) {
+      s_red[warp][lane >> 1] = (double)w0;
+      s_red[warp][16 + (lane >> 1)] = (double)w1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 24) {
+      double t = 0.0;
       #pragma unroll
-      for (int n = 0; n < 3; ++n) {
-        float4* out = reinterpret_cast<float4*>(ta.mom + ((size_t)n * a.n_bl + bl) * 4);
-        const double* v = tot + 8 * n;
-        out[0] = make_float4((float)(v[0] * a.inv_n), (float)(v[1] * a.inv_n), (float)(v[2] * a.inv_n),
-                             (float)(v[3] * a.inv_n));
-        out[1] = make_float4((float)(v[4] * a.inv_n), (float)(v[5] * a.inv_n), (float)(v[6] * a.inv_n),
-                             (float)(v[7] * a.inv_n));
-      }
+      for (int w2 = 0; w2 < kStreamThreads / 32; ++w2) t += s_red[w2][threadIdx.x];
+      s_tot[threadIdx.x] = t * a.inv_n;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {           // moment n, half h (two polarisations)
+      const int n = threadIdx.x >> 1, hh = threadIdx.x & 1;
+      const double* t = s_tot + 8 * n + 4 * hh;
+      reinterpret_cast<float4*>(ta.mom + ((size_t)n * a.n_bl + bl) * 4)[hh] =
+          make_float4((float)t[0], (float)t[1], (float)t[2], (float)t[3]);
     }
   }
 }
