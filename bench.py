@@ -116,7 +116,10 @@ class Clocks:
 KERNEL_SOURCES = {"k_stream_mixed<true,true>": ("common.cuh", "stream_kernels.cuh"),
                   "k_block_pass<64,true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh"),
                   "k_block_pass_t5<true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh",
-                                                 "block_tc_kernels.cuh", "tc05.cuh", "block_t5_kernels.cuh")}
+                                                 "block_tc_kernels.cuh", "tc05.cuh", "block_t5_kernels.cuh"),
+                  "k_grad_sweep_fac<false>": ("common.cuh", "kahan.cuh", "grad_kernels.cuh"),
+                  "k_stream_taylor<true,true>": ("common.cuh", "stream_kernels.cuh", "als_kernels.cuh",
+                                                 "taylor_kernels.cuh")}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -219,9 +222,15 @@ def main():
                     help="blocked pass: 0 library choice, 1 FP32 FMA pass, 2 mma.sync pass, 3 tcgen05 pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / adjoint / CPU legs")
+    ap.add_argument("--profile-case", choices=["adjoint", "taylor"], default=None,
+                    help="only this workload, twice, at --antennas antennas (small ncu captures; "
+                         "adjoint: 300 sources of the config-5 cadence, taylor: --sources sources); "
+                         "prints its own one-line summary, not the benchmark line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
 
     import numpy as np
     import torch
@@ -427,6 +436,39 @@ def main():
     return 0
 
 
+def run_profile_case(args):
+    """A small case of one extra-leg workload for profiling captures."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1003_5575_gb300 import Peeler
+    from synth import config
+    if args.profile_case == "adjoint":
+        c = config(5).with_(n_ant=args.antennas)
+        p = Peeler(c.uvw(), c.freqs(), n_iter=args.n_iter, precision="mixed", max_sources=c.n_src)
+        J = torch.from_numpy(c.jones().astype(np.complex64)).cuda()
+        d = p.predict(c.sources(), J)
+        s_fit = torch.from_numpy(c.perturbed_sources()).cuda()
+        for _ in range(2):
+            loss = p.grad(d, J, s_fit)[0]
+        summary = {"loss": float(loss.item())}
+    else:
+        c = config(3).with_(n_ant=args.antennas, n_src=args.sources)
+        p = Peeler(c.uvw(), c.freqs(), n_iter=args.n_iter, precision="mixed", max_sources=c.n_src,
+                   sources_per_pass=1)
+        J = torch.from_numpy(c.jones().astype(np.complex64)).cuda()
+        d = p.predict(c.sources(), J)
+        for _ in range(2):
+            _, _, _, st = p.cadence_taylor(d, c.sources())
+        summary = {"status": [int(x) for x in st]}
+    torch.cuda.synchronize()
+    p.close()
+    print(json.dumps({"profile_case": args.profile_case, "antennas": c.n_ant, "channels": c.n_chan,
+                      "times": c.n_time, "sources": c.n_src, **summary}), flush=True)
+    return 0
+
+
 def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
     """One-source-per-pass path, gains Taylor-expanded in frequency, FP64-path
     comparison, adjoint step, ionospheric offsets, CPU baseline (rank 0 at N=1 only)."""
@@ -482,7 +524,7 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
         "ms_per_pass": ms_tp / n_tp, "ms_per_solve": ms_ts / n_ts,
         "not_converged": int(np.sum(st_t == 1)),
         "roofline": {"bound": "hbm", "kernel": "k_stream_taylor<SUB,ACC>", "achieved": tp_gbs, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": tp_gbs / hbm_peak, "traffic": None,
+                     "unit": "GB/s", "frac": tp_gbs / hbm_peak, "traffic": ncu_traffic("k_stream_taylor<true,true>"),
                      "algorithmic_bytes_per_launch": cad.n_vis * BYTES_PER_UPDATE}}
     p1.close()
     del d_j1
@@ -565,7 +607,9 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
         "ms_per_step": ms_adj, "loss": float(loss.item()),
         "roofline": {"bound": "alu", "kernel": "k_grad_sweep_fac<false> (factorised phasor tables; + reductions, in the step time)",
                      "achieved": adj_tflops, "peak": adj_peak, "unit": "TFLOP/s", "frac": adj_tflops / adj_peak,
-                     "algorithmic_flops_per_update": ADJ_FLOPS_PER_UPDATE, "traffic": None},
+                     "algorithmic_flops_per_update": ADJ_FLOPS_PER_UPDATE,
+                     "traffic": ncu_traffic("k_grad_sweep_fac<false>"),
+                     "algorithmic_bytes_per_launch": c5.n_vis * 32 + c5.n_src * c5.n_bl * (64 + 24)},
         "fp64_ms_per_step_at_300_sources_extrapolated": per_upd_64 * c5.n_src * c5.n_vis,
         "fp64_sources_timed": k_adj64, "speedup_mixed_vs_fp64": per_upd_64 / per_upd_mixed,
     }

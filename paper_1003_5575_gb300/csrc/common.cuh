@@ -38,14 +38,6 @@ template <typename C> __device__ inline C cconjmul(C a, C b) {
   C r; r.x = a.x * b.x + a.y * b.y; r.y = a.x * b.y - a.y * b.x; return r;
 }
 
-// compensated summation step (Kahan): the running total is sum - comp
-__device__ inline void kahan_add(float& sum, float& comp, float x) {
-  const float y = x - comp;
-  const float t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
-}
-
 // packed FP32x2 fused multiply-add (one instruction for two lanes): a * b + c
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   unsigned long long ra, rb, rc, rd;

@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "kahan.cuh"
 
 namespace rts {
 

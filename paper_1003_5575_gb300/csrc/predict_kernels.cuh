@@ -4,6 +4,7 @@
 // few ulp of the exact sum.
 #pragma once
 #include "stream_kernels.cuh"
+#include "kahan.cuh"
 
 namespace rts {
 
