@@ -71,6 +71,7 @@ def lib():
                                          ctypes.c_double, ctypes.c_double, _i32, _dp, _dp, _dp]
             L.orc_peel_taylor.restype = _i32
             L.orc_peel_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _dp, _ip]
+            L.orc_grid.argtypes = [_i32, ctypes.c_double, _dp, _i32, _i32, _i32, _dp, _dp, _dp]
             L.orc_num_threads.restype = _i32
             _lib = L
     return _lib
@@ -241,6 +242,20 @@ def peel_taylor(uvw, freq, vis, lmS, n_iter=20):
     lib().orc_peel_taylor(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(R), n_src, _d(lmS),
                           n_iter, _d(G), _d(H), st.ctypes.data_as(_ip))
     return R, G, H, st[:n_src]
+
+
+def grid(n_pix, r_max, gcf, xy, vis):
+    """Gridded visibilities [n_pol][n_pix][n_pix] complex128: each visibility i at
+    pixel coordinates xy[i] adds f(r) vis[i] to every pixel centre within r < r_max,
+    f the linear interpolation of the radial table gcf on [0, r_max]."""
+    gcf = _f64(gcf)
+    xy = _f64(xy).reshape(-1, 2)
+    vis = _f64(vis, np.complex128)
+    vis = vis.reshape(vis.shape[0], -1)
+    n_vis, n_pol = vis.shape
+    out = np.zeros((n_pol, n_pix, n_pix), np.complex128)
+    lib().orc_grid(int(n_pix), float(r_max), _d(gcf), gcf.shape[0], n_vis, n_pol, _d(xy), _d(vis), _d(out))
+    return out
 
 
 def simulate(cad, noise=True, sources=None, jones=None):

@@ -651,3 +651,48 @@ int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const dou
   }
   return worst;
 }
+
+/* ---- gridder (Section 6, the gridding equation) ---------------------------
+ * V_grid(x, y) = sum_i f(r_i) V_i over visibilities with r_i < r_max, where
+ * r_i = |(x, y) - (x_i, y_i)| is the distance from the pixel centre (integer
+ * coordinates) to the visibility, in pixels, and the gridding convolution
+ * function f is radial (reading R18): the linear interpolation of the table
+ * gcf[0 .. n_tab-1] sampled at r_k = k r_max / (n_tab - 1).  Visibilities
+ * outside [0, n_pix) in either coordinate are not gridded.  Each of n_pol
+ * complex values per visibility goes to its own plane.  Plain scatter in
+ * input order, FP64.                                                        */
+
+static double gcf_at(const double* gcf, int32_t n_tab, double r_max, double r) {
+  double s = r / r_max * (n_tab - 1);
+  int32_t k = (int32_t)floor(s);
+  if (k >= n_tab - 1) return gcf[n_tab - 1];
+  double w = s - k;
+  return gcf[k] + w * (gcf[k + 1] - gcf[k]);
+}
+
+void orc_grid(int32_t n_pix, double r_max, const double* gcf, int32_t n_tab, int32_t n_vis,
+              int32_t n_pol, const double* xy, const double* vis, double* grid) {
+  int64_t plane = (int64_t)n_pix * n_pix;
+  memset(grid, 0, sizeof(double) * 2 * plane * n_pol);
+  for (int32_t i = 0; i < n_vis; ++i) {
+    double x = xy[2 * i], y = xy[2 * i + 1];
+    if (!(x >= 0.0 && x < n_pix && y >= 0.0 && y < n_pix)) continue;
+    int32_t x0 = (int32_t)ceil(x - r_max), x1 = (int32_t)floor(x + r_max);
+    int32_t y0 = (int32_t)ceil(y - r_max), y1 = (int32_t)floor(y + r_max);
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > n_pix - 1) x1 = n_pix - 1;
+    if (y1 > n_pix - 1) y1 = n_pix - 1;
+    for (int32_t py = y0; py <= y1; ++py)
+      for (int32_t px = x0; px <= x1; ++px) {
+        double r = sqrt((px - x) * (px - x) + (py - y) * (py - y));
+        if (!(r < r_max)) continue;
+        double f = gcf_at(gcf, n_tab, r_max, r);
+        for (int32_t p = 0; p < n_pol; ++p) {
+          double* g = grid + 2 * ((int64_t)p * plane + (int64_t)py * n_pix + px);
+          g[0] += f * vis[2 * ((int64_t)i * n_pol + p)];
+          g[1] += f * vis[2 * ((int64_t)i * n_pol + p) + 1];
+        }
+      }
+  }
+}

@@ -62,6 +62,9 @@ int32_t orc_als_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const doub
 int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                         const double* freq, double* vis, int32_t n_src, const double* lmS,
                         int32_t n_iter, double* gain, double* slope, int32_t* status);
+/* gridder: radial gridding convolution function from a table (reading R18) */
+void orc_grid(int32_t n_pix, double r_max, const double* gcf, int32_t n_tab, int32_t n_vis,
+              int32_t n_pol, const double* xy, const double* vis, double* grid);
 int32_t orc_num_threads(void);
 
 #ifdef __cplusplus
