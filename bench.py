@@ -469,6 +469,62 @@ def run_profile_case(args):
     return 0
 
 
+def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_deg=21.4, reps=3):
+    """Time the gridder over n_grid_chan channels of the residual cube."""
+    import numpy as np
+    import torch
+    from paper_1003_5575_gb300 import Gridder
+    from synth import baseline_pairs
+    r = np.linspace(0.0, 1.0, 1025)
+    kb = np.i0(8.0 * np.sqrt(np.clip(1.0 - r * r, 0.0, None)))
+    gcf = (kb - kb[-1]) / (kb[0] - kb[-1])                  # Kaiser-Bessel, vanishing at r_max
+    pairs = baseline_pairs(cad.n_ant)
+    t_mid = cad.n_time // 2
+    uvw = cad.uvw()[t_mid]
+    duv = uvw[pairs[:, 0]] - uvw[pairs[:, 1]]               # metres
+    cell = math.radians(fov_deg)                            # pixels per wavelength
+    freqs = cad.freqs()[:n_grid_chan]
+    xy, vis, n_in = [], [], 0
+    for c, f in enumerate(freqs):
+        pix = duv[:, :2] * (f / 299792458.0) * cell + n_pix / 2.0
+        n_in += int(np.sum(np.all((pix >= 0) & (pix < n_pix), axis=1)))
+        xy.append(torch.from_numpy(pix.astype(np.float32)).cuda())
+        vis.append(d_resid[t_mid, :, c, :].contiguous())
+    g = Gridder(n_pix, r_max, gcf, bin=24, n_pol=4, max_vis=cad.n_bl)
+    grids = torch.empty((n_grid_chan, 4, n_pix, n_pix), dtype=torch.complex64, device="cuda")
+    for c in range(n_grid_chan):
+        g.run(xy[c], vis[c], out=grids[c])
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    ms_sort = ms_gather = 0.0
+    a.record()
+    for _ in range(reps):
+        for c in range(n_grid_chan):
+            g.run(xy[c], vis[c], out=grids[c])
+    b.record()
+    torch.cuda.synchronize()
+    for c in range(n_grid_chan):                            # sort / gather split of one pass
+        g.run(xy[c], vis[c], out=grids[c])
+        s_ms, g_ms = g.last_ms()
+        ms_sort += s_ms
+        ms_gather += g_ms
+    ms = a.elapsed_time(b) / reps
+    g.close()
+    flops = n_in * math.pi * r_max * r_max * 16              # 4 complex values x real weight per pair
+    peak = fp32_peak_tflops(2070.0)
+    return {"workload": f"{n_pix} x {n_pix} pixels, r_max {r_max:g} (24 x 24 convolution function), 24 x 24 bins, "
+                        f"{n_grid_chan} channels x {cad.n_bl} visibilities (one per baseline, middle time), 4 pol, "
+                        f"{fov_deg} deg field",
+            "ms_per_12_channels": ms, "ms_sort": ms_sort, "ms_gather": ms_gather,
+            "visibilities_per_s": n_grid_chan * cad.n_bl / (ms / 1e3), "visibilities_in_grid": n_in,
+            "roofline": {"bound": "alu", "kernel": "k_grid_gather<4>", "achieved": flops / (ms_gather / 1e3) / 1e12,
+                         "peak": peak, "unit": "TFLOP/s", "frac": flops / (ms_gather / 1e3) / 1e12 / peak,
+                         "algorithmic_flops": flops, "traffic": None,
+                         "note": "algorithmic = visibilities in the grid x pi r_max^2 pixels x 16 flop"},
+            "paper_tesla_c1060_ms": 590, "paper_note": "the paper's CUDA gridding work time for 12 channels "
+                                                      "(Table of work times; another machine: context only)"}
+
+
 def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
     """One-source-per-pass path, gains Taylor-expanded in frequency, FP64-path
     comparison, adjoint step, ionospheric offsets, CPU baseline (rank 0 at N=1 only)."""
@@ -615,6 +671,11 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
     }
     del v64
     pa64.close()
+
+    # gridder (Section 6) at the paper's benchmark shape: 1125 x 1125 pixels, a 24 x 24 pixel
+    # convolution function (r_max = 12) in 24 x 24 bins, 12 channels of one visibility per
+    # baseline (130 816) at the cadence's middle time, 4 polarisations, 21.4 deg field of view
+    out["gridder"] = gridder_leg(cad, d_resid, ev)
 
     # ionospheric position offsets at the same shape (Section 3, 3.1): refraction law
     # alpha = 2, the adjoint sweep with frequency-law weights + FP64 normal equations + 2x2 solves

@@ -21,4 +21,7 @@ def __getattr__(name):
     if name in ("Peeler", "PeelLoss", "peel", "offsets_solve"):
         from . import peeler
         return getattr(peeler, name)
+    if name == "Gridder":
+        from . import gridder
+        return gridder.Gridder
     raise AttributeError(name)

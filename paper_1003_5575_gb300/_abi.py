@@ -38,7 +38,8 @@ EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_ca
            "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
            "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_barrier_selftest",
            "rts_host_alloc", "rts_host_free",
-           "rts_peel_last_error", "rts_peel_destroy")
+           "rts_peel_last_error", "rts_peel_destroy",
+           "rts_grid_init", "rts_grid_run", "rts_grid_last_ms", "rts_grid_last_error", "rts_grid_destroy")
 
 
 class rts_peel_config(ctypes.Structure):
@@ -49,6 +50,12 @@ class rts_peel_config(ctypes.Structure):
                 ("freq_hz", ctypes.POINTER(ctypes.c_double)),
                 ("sources_per_pass", ctypes.c_int32), ("block_kernel", ctypes.c_int32),
                 ("solve_kernel", ctypes.c_int32), ("grad_kernel", ctypes.c_int32)]
+
+
+class rts_grid_config(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int32), ("bin", ctypes.c_int32), ("r_max", ctypes.c_double),
+                ("gcf", ctypes.POINTER(ctypes.c_double)), ("n_tab", ctypes.c_int32),
+                ("n_pol", ctypes.c_int32), ("max_vis", ctypes.c_int32)]
 
 
 class RtsError(RuntimeError):
@@ -121,6 +128,16 @@ def lib():
             L.rts_peel_last_error.argtypes = [_vp]
             L.rts_peel_destroy.restype = None
             L.rts_peel_destroy.argtypes = [_vp]
+            L.rts_grid_init.restype = ctypes.c_int
+            L.rts_grid_init.argtypes = [ctypes.POINTER(rts_grid_config), ctypes.POINTER(_vp)]
+            L.rts_grid_run.restype = ctypes.c_int
+            L.rts_grid_run.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp]
+            L.rts_grid_last_ms.restype = ctypes.c_int
+            L.rts_grid_last_ms.argtypes = [_vp, _dp, _dp]
+            L.rts_grid_last_error.restype = ctypes.c_char_p
+            L.rts_grid_last_error.argtypes = [_vp]
+            L.rts_grid_destroy.restype = None
+            L.rts_grid_destroy.argtypes = [_vp]
             _lib = L
     return _lib
 
@@ -242,3 +259,37 @@ def rts_peel_last_error(h) -> str:
 
 def rts_peel_destroy(h) -> None:
     lib().rts_peel_destroy(h)
+
+
+# ---- gridder (include/rts_grid.h) ---------------------------------------------
+
+def _gcheck(rc: int, handle) -> int:
+    if rc < 0:
+        msg = lib().rts_grid_last_error(handle)
+        raise RtsError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def rts_grid_init(cfg: rts_grid_config):
+    h = _vp()
+    _gcheck(lib().rts_grid_init(ctypes.byref(cfg), ctypes.byref(h)), None)
+    return h
+
+
+def rts_grid_run(h, d_xy, d_vis, n_vis, d_grid, stream):
+    return _gcheck(lib().rts_grid_run(h, d_xy, d_vis, n_vis, d_grid, stream), h)
+
+
+def rts_grid_last_ms(h):
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _gcheck(lib().rts_grid_last_ms(h, ctypes.byref(a), ctypes.byref(b)), h)
+    return a.value, b.value
+
+
+def rts_grid_last_error(h):
+    m = lib().rts_grid_last_error(h)
+    return m.decode() if m else ""
+
+
+def rts_grid_destroy(h):
+    lib().rts_grid_destroy(h)
