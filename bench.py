@@ -222,10 +222,11 @@ def main():
                     help="blocked pass: 0 library choice, 1 FP32 FMA pass, 2 mma.sync pass, 3 tcgen05 pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / adjoint / CPU legs")
-    ap.add_argument("--profile-case", choices=["adjoint", "taylor"], default=None,
+    ap.add_argument("--profile-case", choices=["adjoint", "taylor", "grid"], default=None,
                     help="only this workload, twice, at --antennas antennas (small ncu captures; "
-                         "adjoint: 300 sources of the config-5 cadence, taylor: --sources sources); "
-                         "prints its own one-line summary, not the benchmark line")
+                         "adjoint: 300 sources of the config-5 cadence, taylor: --sources sources, "
+                         "grid: the gridder leg on random values); prints its own one-line summary, "
+                         "not the benchmark line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -444,6 +445,13 @@ def run_profile_case(args):
     __graft_entry__.build()
     from paper_1003_5575_gb300 import Peeler
     from synth import config
+    if args.profile_case == "grid":
+        c = config(3).with_(n_ant=args.antennas)
+        vals = torch.randn((c.n_time, c.n_bl, 12, 4), dtype=torch.complex64, device="cuda")
+        res = gridder_leg(c, vals, lambda: torch.cuda.Event(enable_timing=True), reps=1)
+        print(json.dumps({"profile_case": "grid", "antennas": c.n_ant, "ms_per_12_channels": res["ms_per_12_channels"]}),
+              flush=True)
+        return 0
     if args.profile_case == "adjoint":
         c = config(5).with_(n_ant=args.antennas)
         p = Peeler(c.uvw(), c.freqs(), n_iter=args.n_iter, precision="mixed", max_sources=c.n_src)

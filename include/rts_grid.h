@@ -43,7 +43,7 @@ typedef struct rts_grid_t rts_grid_t;
 
 typedef struct rts_grid_config {
   int32_t n_pix;        /* grid side in pixels (square grid), 1 .. 16384 */
-  int32_t bin;          /* bin side in pixels, r_max <= bin <= 45, and
+  int32_t bin;          /* bin side in pixels, r_max <= bin <= 40, and
                            ceil(n_pix / bin)^2 <= 8192 bins */
   double r_max;         /* support radius of the GCF in pixels, > 0 */
   const double* gcf;    /* host [n_tab] radial GCF samples at r_k = k r_max/(n_tab - 1); copied */

@@ -46,7 +46,10 @@ int gcuda(rts_grid_t* g, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return gcuda((g), e_, #call);     \
   } while (0)
 
-int gather_threads(int bin) { return ((bin * bin + kGridPix - 1) / kGridPix + 31) / 32 * 32; }
+int gather_threads(int bin) {
+  const int tpb = (bin + kGridTile - 1) / kGridTile;
+  return 32 * tpb * tpb;
+}
 
 }  // namespace
 
@@ -59,8 +62,8 @@ int rts_grid_init(const rts_grid_config* cfg, rts_grid_t** out) {
   if (!cfg) return gfail(nullptr, RTS_EINVAL, "cfg is NULL");
   if (cfg->n_pix < 1 || cfg->n_pix > 16384) return gfail(nullptr, RTS_EINVAL, "n_pix must be in [1, 16384]");
   if (!(cfg->r_max > 0.0) || !std::isfinite(cfg->r_max)) return gfail(nullptr, RTS_EINVAL, "r_max must be finite and > 0");
-  if (cfg->bin < cfg->r_max || cfg->bin > 45)
-    return gfail(nullptr, RTS_EINVAL, "bin must satisfy r_max <= bin <= 45");
+  if (cfg->bin < cfg->r_max || cfg->bin > kGridMaxBin)
+    return gfail(nullptr, RTS_EINVAL, "bin must satisfy r_max <= bin <= 40");
   const int nbx = (cfg->n_pix + cfg->bin - 1) / cfg->bin;
   if ((int64_t)nbx * nbx > kGridMaxBins) return gfail(nullptr, RTS_EINVAL, "ceil(n_pix / bin)^2 must be <= 8192 bins");
   if (cfg->n_tab < 2 || cfg->n_tab > 4096) return gfail(nullptr, RTS_EINVAL, "n_tab must be in [2, 4096]");
@@ -126,7 +129,10 @@ int rts_grid_run(rts_grid_t* g, const void* d_xy, const void* d_vis, int32_t n_v
     const size_t sort_smem = sizeof(int) * (size_t)kGridWarps * g->n_bins;
     const unsigned sort_grid = (unsigned)((n_chunks + kGridWarps - 1) / kGridWarps);
     k_grid_sort_pass<false><<<sort_grid, kGridWarps * 32, sort_smem, s>>>(a);
-    k_grid_scan<<<1, 1024, 0, s>>>(a);
+    const unsigned bins_grid = (unsigned)((g->n_bins + 255) / 256);
+    k_grid_bin_totals<<<bins_grid, 256, 0, s>>>(a);
+    k_grid_scan_bins<<<1, 1024, 0, s>>>(a);
+    k_grid_offsets<<<bins_grid, 256, 0, s>>>(a);
     k_grid_sort_pass<true><<<sort_grid, kGridWarps * 32, sort_smem, s>>>(a);
   }
   GRID_CUDA(g, cudaGetLastError());
@@ -137,7 +143,7 @@ int rts_grid_run(rts_grid_t* g, const void* d_xy, const void* d_vis, int32_t n_v
   b.r_max = (float)g->r_max; b.r2max = (float)(g->r_max * g->r_max);
   b.tab_scale = (float)((g->n_tab - 1) / g->r_max);
   b.grid = static_cast<float2*>(d_grid);
-  const size_t gsm = sizeof(float2) * (size_t)kGridStage * (1 + g->n_pol) + sizeof(float) * (size_t)(g->n_tab + 1);
+  const size_t gsm = sizeof(float) * (size_t)(g->n_tab + 1);
   const dim3 gg((unsigned)g->n_bins), gb((unsigned)gather_threads(g->bin));
   switch (g->n_pol) {
     case 1: k_grid_gather<1><<<gg, gb, gsm, s>>>(b); break;
