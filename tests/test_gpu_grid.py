@@ -108,3 +108,23 @@ def test_grid_rejects_bad_configurations():
         g.run(torch.zeros((11, 2), dtype=torch.float32, device="cuda"),
               torch.zeros((11, 2), dtype=torch.complex64, device="cuda"))
     g.close()
+
+
+def test_grid_full_size_matches_oracle():
+    """The benchmark's shape for one channel: 1125 x 1125 pixels, r_max 12 in
+    24 x 24 bins, one visibility per baseline of the 512-antenna array (130 816)
+    at the cadence's middle time, 4 polarisations, every pixel against the
+    oracle's FP64 scatter."""
+    import math
+    from synth import config, baseline_pairs
+    cad = config(3)
+    pairs = baseline_pairs(cad.n_ant)
+    uvw = cad.uvw()[cad.n_time // 2]
+    duv = uvw[pairs[:, 0]] - uvw[pairs[:, 1]]
+    xy = (duv[:, :2] * (cad.freqs()[0] / 299792458.0) * math.radians(21.4) + 1125 / 2.0).astype(np.float32)
+    rng = np.random.default_rng(12)
+    vis = (rng.normal(size=(len(xy), 4)) + 1j * rng.normal(size=(len(xy), 4))).astype(np.complex64)
+    gcf = tapered_kb(1025)
+    G = run_gpu(1125, 12.0, gcf, 24, xy, vis)
+    R = oracle.grid(1125, 12.0, gcf, xy.astype(np.float64), vis.astype(np.complex128))
+    assert np.abs(G - R).max() <= 1e-5 * np.abs(R).max()
