@@ -72,6 +72,7 @@ def lib():
             L.orc_peel_taylor.restype = _i32
             L.orc_peel_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _dp, _ip]
             L.orc_grid.argtypes = [_i32, ctypes.c_double, _dp, _i32, _i32, _i32, _dp, _dp, _dp]
+            L.orc_integrate.argtypes = [_i32, ctypes.c_int64, _i32, _ip, _i32, _dp, _dp]
             L.orc_num_threads.restype = _i32
             _lib = L
     return _lib
@@ -255,6 +256,18 @@ def grid(n_pix, r_max, gcf, xy, vis):
     n_vis, n_pol = vis.shape
     out = np.zeros((n_pol, n_pix, n_pix), np.complex128)
     lib().orc_grid(int(n_pix), float(r_max), _d(gcf), gcf.shape[0], n_vis, n_pol, _d(xy), _d(vis), _d(out))
+    return out
+
+
+def integrate(fine, lengths, n_slot):
+    """Per-baseline time averaging: fine [n_fine][n_bl][n_chan][4] complex, lengths [n_bl]
+    (fine samples per output, dividing n_fine) -> [n_slot][n_bl][n_chan][4]; slot s of
+    baseline b is the mean of fine samples s L_b .. (s+1) L_b - 1, zero past n_fine / L_b."""
+    fine = _f64(fine, np.complex128)
+    n_fine, n_bl, n_chan = fine.shape[0], fine.shape[1], fine.shape[2]
+    L = np.ascontiguousarray(lengths, dtype=np.int32)
+    out = np.zeros((n_slot, n_bl, n_chan, 4), np.complex128)
+    lib().orc_integrate(n_fine, n_bl, n_chan, L.ctypes.data_as(_ip), n_slot, _d(fine), _d(out))
     return out
 
 

@@ -696,3 +696,34 @@ void orc_grid(int32_t n_pix, double r_max, const double* gcf, int32_t n_tab, int
       }
   }
 }
+
+/* ---- visibility integrator (Section 3, the first stage of the RTS) ---------
+ * The correlator delivers a sample every dt (0.5 s); the integrator averages
+ * them into longer groups, shorter for baselines between widely separated
+ * tiles (their delays change faster with the Earth's rotation).  Reading R19:
+ * baseline b averages len[b] consecutive fine samples (len[b] divides n_fine),
+ * output slot s of baseline b is the mean of fine samples s len[b] ..
+ * (s + 1) len[b] - 1, for s < n_fine / len[b]; the remaining slots (up to
+ * n_slot) are zero.  fine [n_fine][n_bl][n_chan][4], out [n_slot][n_bl][n_chan][4]. */
+
+void orc_integrate(int32_t n_fine, int64_t n_bl, int32_t n_chan, const int32_t* len, int32_t n_slot,
+                   const double* fine, double* out) {
+  int64_t per_t = n_bl * n_chan * 4;                 /* complex values per time sample */
+  memset(out, 0, sizeof(double) * 2 * per_t * n_slot);
+  for (int64_t b = 0; b < n_bl; ++b) {
+    int32_t L = len[b];
+    for (int32_t s = 0; s < n_fine / L && s < n_slot; ++s)
+      for (int32_t c = 0; c < n_chan; ++c)
+        for (int32_t e = 0; e < 4; ++e) {
+          double re = 0.0, im = 0.0;
+          for (int32_t t = s * L; t < (s + 1) * L; ++t) {
+            const double* x = fine + 2 * ((int64_t)t * per_t + (b * n_chan + c) * 4 + e);
+            re += x[0];
+            im += x[1];
+          }
+          double* o = out + 2 * ((int64_t)s * per_t + (b * n_chan + c) * 4 + e);
+          o[0] = re / L;
+          o[1] = im / L;
+        }
+  }
+}

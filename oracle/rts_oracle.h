@@ -65,6 +65,9 @@ int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const dou
 /* gridder: radial gridding convolution function from a table (reading R18) */
 void orc_grid(int32_t n_pix, double r_max, const double* gcf, int32_t n_tab, int32_t n_vis,
               int32_t n_pol, const double* xy, const double* vis, double* grid);
+/* visibility integrator: per-baseline averaging of len[b] fine samples (reading R19) */
+void orc_integrate(int32_t n_fine, int64_t n_bl, int32_t n_chan, const int32_t* len, int32_t n_slot,
+                   const double* fine, double* out);
 int32_t orc_num_threads(void);
 
 #ifdef __cplusplus
