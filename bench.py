@@ -222,10 +222,11 @@ def main():
                     help="blocked pass: 0 library choice, 1 FP32 FMA pass, 2 mma.sync pass, 3 tcgen05 pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / adjoint / CPU legs")
-    ap.add_argument("--profile-case", choices=["adjoint", "taylor", "grid"], default=None,
+    ap.add_argument("--profile-case", choices=["adjoint", "taylor", "grid", "integrate"], default=None,
                     help="only this workload, twice, at --antennas antennas (small ncu captures; "
                          "adjoint: 300 sources of the config-5 cadence, taylor: --sources sources, "
-                         "grid: the gridder leg on random values); prints its own one-line summary, "
+                         "grid: the gridder leg on random values, integrate: the integrator leg); prints "
+                         "its own one-line summary, "
                          "not the benchmark line")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -445,6 +446,12 @@ def run_profile_case(args):
     __graft_entry__.build()
     from paper_1003_5575_gb300 import Peeler
     from synth import config
+    if args.profile_case == "integrate":
+        c = config(3).with_(n_ant=args.antennas)
+        vals = torch.randn((c.n_time, c.n_bl, c.n_chan, 4), dtype=torch.complex64, device="cuda")
+        res = integrator_leg(c, vals, lambda: torch.cuda.Event(enable_timing=True), reps=1)
+        print(json.dumps({"profile_case": "integrate", "antennas": c.n_ant, "ms": res["ms"]}), flush=True)
+        return 0
     if args.profile_case == "grid":
         c = config(3).with_(n_ant=args.antennas)
         vals = torch.randn((c.n_time, c.n_bl, 12, 4), dtype=torch.complex64, device="cuda")
@@ -475,6 +482,39 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": args.profile_case, "antennas": c.n_ant, "channels": c.n_chan,
                       "times": c.n_time, "sources": c.n_src, **summary}), flush=True)
     return 0
+
+
+def integrator_leg(cad, d_vis, ev, reps=3):
+    """Time the integrator on a 16-sample (0.5 s) cadence built from the bench cube: groups of
+    16, 8 or 4 samples (8, 4, 2 s) by baseline length (cuts 699 m and 1398 m: at most 0.05 turn
+    of fringe drift at the 21.4 deg field edge and 198 MHz over the group)."""
+    import numpy as np
+    import torch
+    from paper_1003_5575_gb300 import Integrator, integration_lengths
+    fine = d_vis.repeat_interleave(2, dim=0)                 # [16][n_bl][n_chan][4]
+    L = integration_lengths(cad.uvw()[cad.n_time // 2], [699.0, 1398.0], [16, 8, 4])
+    ig = Integrator(16, cad.n_chan, L, n_slot=4)
+    out = ig.run(fine)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(reps):
+        ig.run(fine, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    ig.close()
+    nbytes = (16 + 4) * cad.n_bl * cad.n_chan * 32
+    del fine, out
+    torch.cuda.empty_cache()
+    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"workload": f"{cad.n_ant} ant x {cad.n_chan} ch, 16 samples of 0.5 s -> groups of 8/4/2 s "
+                        f"({int(np.sum(L == 16))}/{int(np.sum(L == 8))}/{int(np.sum(L == 4))} baselines), 4 slots",
+            "ms": ms, "visibilities_per_s": 16 * cad.n_bl * cad.n_chan / (ms / 1e3),
+            "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "traffic": None, "algorithmic_bytes_per_launch": nbytes}}
 
 
 def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_deg=21.4, reps=3):
@@ -535,7 +575,8 @@ def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_de
 
 def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
     """One-source-per-pass path, gains Taylor-expanded in frequency, FP64-path
-    comparison, adjoint step, ionospheric offsets, CPU baseline (rank 0 at N=1 only)."""
+    comparison, adjoint step, integrator, gridder, ionospheric offsets, CPU baseline
+    (rank 0 at N=1 only)."""
     import numpy as np
     import torch
     from paper_1003_5575_gb300 import Peeler
@@ -679,6 +720,9 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
     }
     del v64
     pa64.close()
+
+    # visibility integrator (Section 3's first stage) on one 8 s cadence of 0.5 s samples
+    out["integrator"] = integrator_leg(cad, d_vis, ev)
 
     # gridder (Section 6) at the paper's benchmark shape: 1125 x 1125 pixels, a 24 x 24 pixel
     # convolution function (r_max = 12) in 24 x 24 bins, 12 channels of one visibility per

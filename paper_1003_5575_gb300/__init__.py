@@ -24,4 +24,7 @@ def __getattr__(name):
     if name == "Gridder":
         from . import gridder
         return gridder.Gridder
+    if name in ("Integrator", "integration_lengths"):
+        from . import integrator
+        return getattr(integrator, name)
     raise AttributeError(name)

@@ -39,7 +39,9 @@ EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_ca
            "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_barrier_selftest",
            "rts_host_alloc", "rts_host_free",
            "rts_peel_last_error", "rts_peel_destroy",
-           "rts_grid_init", "rts_grid_run", "rts_grid_last_ms", "rts_grid_last_error", "rts_grid_destroy")
+           "rts_grid_init", "rts_grid_run", "rts_grid_last_ms", "rts_grid_last_error", "rts_grid_destroy",
+           "rts_integrate_lengths", "rts_integrate_init", "rts_integrate_run", "rts_integrate_last_error",
+           "rts_integrate_destroy")
 
 
 class rts_peel_config(ctypes.Structure):
@@ -138,6 +140,16 @@ def lib():
             L.rts_grid_last_error.argtypes = [_vp]
             L.rts_grid_destroy.restype = None
             L.rts_grid_destroy.argtypes = [_vp]
+            L.rts_integrate_lengths.restype = ctypes.c_int
+            L.rts_integrate_lengths.argtypes = [_i32, _dp, _i32, _dp, _ip, _ip]
+            L.rts_integrate_init.restype = ctypes.c_int
+            L.rts_integrate_init.argtypes = [_i32, ctypes.c_int64, _i32, _ip, _i32, ctypes.POINTER(_vp)]
+            L.rts_integrate_run.restype = ctypes.c_int
+            L.rts_integrate_run.argtypes = [_vp, _vp, _vp, _vp]
+            L.rts_integrate_last_error.restype = ctypes.c_char_p
+            L.rts_integrate_last_error.argtypes = [_vp]
+            L.rts_integrate_destroy.restype = None
+            L.rts_integrate_destroy.argtypes = [_vp]
             _lib = L
     return _lib
 
@@ -293,3 +305,30 @@ def rts_grid_last_error(h):
 
 def rts_grid_destroy(h):
     lib().rts_grid_destroy(h)
+
+
+# ---- visibility integrator (include/rts_integrate.h) ---------------------------
+
+def _icheck(rc: int, handle) -> int:
+    if rc < 0:
+        msg = lib().rts_integrate_last_error(handle)
+        raise RtsError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def rts_integrate_lengths(n_ant, uvw_ptr, n_cut, cut_ptr, len_for_ptr, len_out_ptr):
+    return _icheck(lib().rts_integrate_lengths(n_ant, uvw_ptr, n_cut, cut_ptr, len_for_ptr, len_out_ptr), None)
+
+
+def rts_integrate_init(n_fine, n_bl, n_chan, len_ptr, n_slot):
+    h = _vp()
+    _icheck(lib().rts_integrate_init(n_fine, n_bl, n_chan, len_ptr, n_slot, ctypes.byref(h)), None)
+    return h
+
+
+def rts_integrate_run(h, d_fine, d_out, stream):
+    return _icheck(lib().rts_integrate_run(h, d_fine, d_out, stream), h)
+
+
+def rts_integrate_destroy(h):
+    lib().rts_integrate_destroy(h)

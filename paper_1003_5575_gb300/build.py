@@ -26,7 +26,7 @@ def sources():
                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
-UNITS = ("rts_peel.cu", "rts_grid.cu")     # translation units, compiled in parallel
+UNITS = ("rts_peel.cu", "rts_grid.cu", "rts_integrate.cu")     # translation units, compiled in parallel
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
