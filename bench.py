@@ -119,7 +119,8 @@ KERNEL_SOURCES = {"k_stream_mixed<true,true>": ("common.cuh", "stream_kernels.cu
                                                  "block_tc_kernels.cuh", "tc05.cuh", "block_t5_kernels.cuh"),
                   "k_grad_sweep_fac<false>": ("common.cuh", "kahan.cuh", "grad_kernels.cuh"),
                   "k_stream_taylor<true,true>": ("common.cuh", "stream_kernels.cuh", "als_kernels.cuh",
-                                                 "taylor_kernels.cuh")}
+                                                 "taylor_kernels.cuh"),
+                  "k_integrate": ("rts_integrate.cu",)}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -514,7 +515,8 @@ def integrator_leg(cad, d_vis, ev, reps=3):
                         f"({int(np.sum(L == 16))}/{int(np.sum(L == 8))}/{int(np.sum(L == 4))} baselines), 4 slots",
             "ms": ms, "visibilities_per_s": 16 * cad.n_bl * cad.n_chan / (ms / 1e3),
             "roofline": {"bound": "hbm", "kernel": "k_integrate", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": gbs / hbm, "traffic": None, "algorithmic_bytes_per_launch": nbytes}}
+                         "frac": gbs / hbm, "traffic": ncu_traffic("k_integrate"),
+                         "algorithmic_bytes_per_launch": nbytes}}
 
 
 def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_deg=21.4, reps=3):
