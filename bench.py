@@ -519,7 +519,7 @@ def integrator_leg(cad, d_vis, ev, reps=3):
                          "algorithmic_bytes_per_launch": nbytes}}
 
 
-def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_deg=21.4, reps=3):
+def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_deg=21.4, reps=3, bin=24):
     """Time the gridder over n_grid_chan channels of the residual cube."""
     import numpy as np
     import torch
@@ -540,7 +540,7 @@ def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_de
         n_in += int(np.sum(np.all((pix >= 0) & (pix < n_pix), axis=1)))
         xy.append(torch.from_numpy(pix.astype(np.float32)).cuda())
         vis.append(d_resid[t_mid, :, c, :].contiguous())
-    g = Gridder(n_pix, r_max, gcf, bin=24, n_pol=4, max_vis=cad.n_bl)
+    g = Gridder(n_pix, r_max, gcf, bin=bin, n_pol=4, max_vis=cad.n_bl)
     grids = torch.empty((n_grid_chan, 4, n_pix, n_pix), dtype=torch.complex64, device="cuda")
     for c in range(n_grid_chan):
         g.run(xy[c], vis[c], out=grids[c])
@@ -562,7 +562,7 @@ def gridder_leg(cad, d_resid, ev, n_pix=1125, r_max=12.0, n_grid_chan=12, fov_de
     g.close()
     flops = n_in * math.pi * r_max * r_max * 16              # 4 complex values x real weight per pair
     peak = fp32_peak_tflops(2070.0)
-    return {"workload": f"{n_pix} x {n_pix} pixels, r_max {r_max:g} (24 x 24 convolution function), 24 x 24 bins, "
+    return {"workload": f"{n_pix} x {n_pix} pixels, r_max {r_max:g} (24 x 24 convolution function), {bin} x {bin} bins, "
                         f"{n_grid_chan} channels x {cad.n_bl} visibilities (one per baseline, middle time), 4 pol, "
                         f"{fov_deg} deg field",
             "ms_per_12_channels": ms, "ms_sort": ms_sort, "ms_gather": ms_gather,

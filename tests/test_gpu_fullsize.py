@@ -133,3 +133,26 @@ def test_fullsize_peel_residual_plus_model_is_input(full, per_pass, kernel):
     assert rms_of(resid) < rms_of(vis)
     del resid, model
     p.close()
+
+
+def test_fullsize_taylor_residual_plus_model_is_input(full):
+    """Gains Taylor-expanded in frequency at full size, 8 sources from the
+    1000-source cube: on sampled baselines the residual plus the oracle's FP64
+    prediction of the solved frequency-linear models (G + x_c H) is the input."""
+    from paper_1003_5575_gb300 import Peeler
+    cad, _, vis, _ = full
+    src = cad.sources()[:8]
+    p = Peeler(cad.uvw(), cad.freqs(), n_iter=20, precision="mixed", max_sources=8, sources_per_pass=1)
+    resid, G, H, st = p.cadence_taylor(vis, src)
+    torch.cuda.synchronize()
+    assert set(np.unique(st).tolist()) <= {0, 1}
+    G, H = G.cpu().numpy().astype(np.complex128), H.cpu().numpy().astype(np.complex128)
+    rms = rms_of(vis)
+    for i, j in sample_baselines(cad.n_ant, 6, 5):
+        bl = bl_index(cad.n_ant, i, j)
+        model = oracle.predict_taylor(sub_array(cad, i, j), cad.freqs(), src, G[:, [i, j], :], H[:, [i, j], :])
+        got = resid[:, bl].cpu().numpy().astype(np.complex128) + model[:, 0]
+        assert np.abs(got - vis[:, bl].cpu().numpy()).max() <= TOL * rms, (i, j)
+    assert rms_of(resid) < rms_of(vis)
+    del resid
+    p.close()
