@@ -94,7 +94,7 @@ int rts_integrate_init(int32_t n_fine, int64_t n_bl, int32_t n_chan, const int32
   if (!out) return ifail(nullptr, RTS_EINVAL, "out is NULL");
   *out = nullptr;
   if (n_fine < 1 || n_fine > 4096) return ifail(nullptr, RTS_EINVAL, "n_fine must be in [1, 4096]");
-  if (n_bl < 1 || n_bl > (int64_t)1 << 31) return ifail(nullptr, RTS_EINVAL, "n_bl must be in [1, 2^31]");
+  if (n_bl < 1 || n_bl >= ((int64_t)1 << 31)) return ifail(nullptr, RTS_EINVAL, "n_bl must be in [1, 2^31 - 1]");
   if (n_chan < 1 || n_chan > 65536) return ifail(nullptr, RTS_EINVAL, "n_chan must be in [1, 65536]");
   if (!h_len) return ifail(nullptr, RTS_EINVAL, "h_len is NULL");
   int min_len = n_fine;
