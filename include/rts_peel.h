@@ -180,14 +180,17 @@ int rts_peel_cadence_host(rts_peel_t* h, const void* h_vis, void* h_resid, int32
  * rts_peel_pipeline_submit enqueues, and returns without waiting:
  *   copy-in stream   h_vis -> one of two library-owned device cubes
  *   compute stream   the peel of that cube in place (after its copy-in)
- *   copy-out stream  residual -> h_resid, Jones -> h_jones [n_src][n_ant][4],
- *                    statuses -> h_status [n_src] (after the peel)
- * so the copies of one cadence overlap the peel of the other.  At most two
+ *   copy-out stream  residual -> h_resid, Jones and statuses -> library-owned
+ *                    page-locked staging (after the peel)
+ * so the copies of one cadence overlap the peel of the other.  The Jones
+ * matrices (h_jones [n_src][n_ant][4]) and statuses (h_status [n_src], may be
+ * NULL) are written to the caller's buffers when the cadence retires: in
+ * rts_peel_pipeline_wait, or in the submit that reuses its slot.  At most two
  * cadences are in flight: a third submit first waits for the oldest one.  The
- * host buffers of a cadence must stay valid and untouched until
- * rts_peel_pipeline_wait returns (or until a later submit has waited for it);
- * page-locked buffers (rts_host_alloc) are required for the copies to overlap.
- * The two device cubes are allocated on the first submit and kept.
+ * host buffers of a cadence must stay valid and untouched until it retires;
+ * h_vis and h_resid must be page-locked (rts_host_alloc) for the copies to
+ * overlap (h_jones and h_status may be ordinary memory).  The two device cubes
+ * and the staging buffers are allocated on the first submit and kept.
  * rts_peel_pipeline_wait waits for every submitted cadence and returns
  * RTS_ENONFINITE if any source of any of them had a non-finite solve. */
 int rts_peel_pipeline_submit(rts_peel_t* h, const void* h_vis, void* h_resid, int32_t n_src,

@@ -85,6 +85,9 @@ struct rts_peel_t {
   cudaEvent_t p_ev_in[2] = {}, p_ev_comp[2] = {}, p_ev_out[2] = {};
   bool p_busy[2] = {false, false};
   int32_t* p_hstatus[2] = {nullptr, nullptr};
+  void* p_hjones[2] = {nullptr, nullptr};       // the caller's Jones buffers, filled at retire
+  void* p_jones_pin[2] = {nullptr, nullptr};    // page-locked Jones staging [max_sources][n_ant][4]
+  int32_t* p_status_pin[2] = {nullptr, nullptr};// page-locked status staging [max_sources]
   int32_t p_nsrc[2] = {0, 0};
   int p_next = 0;
   // tracing: CUDA events around kernel groups, launch counters
@@ -824,6 +827,12 @@ int pipeline_setup(rts_peel_t* h) {
     RTS_CUDA(h, cudaMalloc(&h->p_cube[k], cube));
     RTS_CUDA(h, cudaMalloc(&h->p_jones[k], (size_t)h->max_sources * h->n_ant * 4 * h->elem));
     RTS_CUDA(h, cudaMalloc((void**)&h->p_status[k], (size_t)h->max_sources * sizeof(int32_t)));
+    // Jones and statuses go out through page-locked staging: a copy to pageable
+    // memory would make the submit wait for its own cadence
+    RTS_CUDA(h, cudaHostAlloc(&h->p_jones_pin[k], (size_t)h->max_sources * h->n_ant * 4 * h->elem,
+                              cudaHostAllocDefault));
+    RTS_CUDA(h, cudaHostAlloc((void**)&h->p_status_pin[k], (size_t)h->max_sources * sizeof(int32_t),
+                              cudaHostAllocDefault));
     RTS_CUDA(h, cudaEventCreateWithFlags(&h->p_ev_in[k], cudaEventDisableTiming));
     RTS_CUDA(h, cudaEventCreateWithFlags(&h->p_ev_comp[k], cudaEventDisableTiming));
     RTS_CUDA(h, cudaEventCreateWithFlags(&h->p_ev_out[k], cudaEventDisableTiming));
@@ -834,15 +843,19 @@ int pipeline_setup(rts_peel_t* h) {
   return RTS_OK;
 }
 
-// wait for slot k's cadence; RTS_ENONFINITE if one of its sources failed
+// wait for slot k's cadence, hand its Jones matrices and statuses to the
+// caller's buffers; RTS_ENONFINITE if one of its sources failed
 int pipeline_retire(rts_peel_t* h, int k) {
   if (!h->p_busy[k]) return RTS_OK;
   RTS_CUDA(h, cudaEventSynchronize(h->p_ev_out[k]));
   h->p_busy[k] = false;
-  if (h->p_hstatus[k])
-    for (int i = 0; i < h->p_nsrc[k]; ++i)
-      if (h->p_hstatus[k][i] == RTS_ENONFINITE)
-        return fail(h, RTS_ENONFINITE, "non-finite value in the solve of source " + std::to_string(i));
+  const int n = h->p_nsrc[k];
+  if (n > 0 && h->p_hjones[k])
+    std::memcpy(h->p_hjones[k], h->p_jones_pin[k], (size_t)n * h->n_ant * 4 * h->elem);
+  if (n > 0 && h->p_hstatus[k]) std::memcpy(h->p_hstatus[k], h->p_status_pin[k], sizeof(int32_t) * n);
+  for (int i = 0; i < n; ++i)
+    if (h->p_status_pin[k][i] == RTS_ENONFINITE)
+      return fail(h, RTS_ENONFINITE, "non-finite value in the solve of source " + std::to_string(i));
   return RTS_OK;
 }
 
@@ -873,17 +886,17 @@ int rts_peel_pipeline_submit(rts_peel_t* h, const void* h_vis, void* h_resid, in
   RTS_CUDA(h, cudaStreamWaitEvent(h->p_out, h->p_ev_comp[k], 0));
   RTS_CUDA(h, cudaMemcpyAsync(h_resid, h->p_cube[k], cube, cudaMemcpyDeviceToHost, h->p_out));
   if (n_src > 0) {
-    RTS_CUDA(h, cudaMemcpyAsync(h_jones, h->p_jones[k], (size_t)n_src * h->n_ant * 4 * h->elem,
+    RTS_CUDA(h, cudaMemcpyAsync(h->p_jones_pin[k], h->p_jones[k], (size_t)n_src * h->n_ant * 4 * h->elem,
                                 cudaMemcpyDeviceToHost, h->p_out));
-    if (h_status)
-      RTS_CUDA(h, cudaMemcpyAsync(h_status, h->p_status[k], sizeof(int32_t) * n_src,
-                                  cudaMemcpyDeviceToHost, h->p_out));
+    RTS_CUDA(h, cudaMemcpyAsync(h->p_status_pin[k], h->p_status[k], sizeof(int32_t) * n_src,
+                                cudaMemcpyDeviceToHost, h->p_out));
   }
   RTS_CUDA(h, cudaEventRecord(h->p_ev_out[k], h->p_out));
   // the next cadence's copy-in may not overwrite this slot until its copy-out is done;
   // the next slot's copy-in only needs that slot's previous copy-out (checked at submit)
   h->p_busy[k] = true;
   h->p_hstatus[k] = h_status;
+  h->p_hjones[k] = h_jones;
   h->p_nsrc[k] = n_src;
   h->p_next = 1 - k;
   return RTS_OK;
@@ -1136,6 +1149,8 @@ void rts_peel_destroy(rts_peel_t* h) {
     if (h->p_cube[k]) cudaFree(h->p_cube[k]);
     if (h->p_jones[k]) cudaFree(h->p_jones[k]);
     if (h->p_status[k]) cudaFree(h->p_status[k]);
+    if (h->p_jones_pin[k]) cudaFreeHost(h->p_jones_pin[k]);
+    if (h->p_status_pin[k]) cudaFreeHost(h->p_status_pin[k]);
     if (h->p_ev_in[k]) cudaEventDestroy(h->p_ev_in[k]);
     if (h->p_ev_comp[k]) cudaEventDestroy(h->p_ev_comp[k]);
     if (h->p_ev_out[k]) cudaEventDestroy(h->p_ev_out[k]);
