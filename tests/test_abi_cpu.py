@@ -1,7 +1,8 @@
 """Host-side tests of the C ABI: no GPU needed.
 
-The library loads, exports every symbol include/rts_peel.h declares, and
-rejects bad configurations on the host before touching CUDA.
+The library loads, exports every symbol include/*.h declares (the peel, the
+gridder, the integrator), and rejects bad configurations on the host before
+touching CUDA.
 """
 import ctypes
 import os
@@ -100,3 +101,79 @@ def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_abi, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         _abi.lib()
+
+
+# ---- gridder and integrator: host-side validation (no CUDA call is reached) ----
+
+def _grid_cfg(abi, **kw):
+    gcf = np.asarray(kw.pop("gcf", np.linspace(1.0, 0.0, 33)), np.float64)
+    cfg = abi.rts_grid_config()
+    cfg.n_pix, cfg.bin, cfg.r_max = kw.get("n_pix", 64), kw.get("bin", 8), kw.get("r_max", 4.0)
+    cfg.gcf = gcf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cfg.n_tab = kw.get("n_tab", len(gcf))
+    cfg.n_pol, cfg.max_vis = kw.get("n_pol", 4), kw.get("max_vis", 100)
+    return cfg, gcf
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(n_pix=0), "n_pix"),
+    (dict(r_max=-1.0), "r_max"),
+    (dict(r_max=float("nan")), "r_max"),
+    (dict(bin=3, r_max=4.0), "bin"),
+    (dict(bin=41, r_max=4.0), "bin"),
+    (dict(n_pix=16384, bin=8), "8192"),
+    (dict(n_tab=1), "n_tab"),
+    (dict(gcf=np.array([1.0, np.nan, 0.0])), "non-finite"),
+    (dict(n_pol=5), "n_pol"),
+    (dict(max_vis=0), "max_vis"),
+])
+def test_grid_init_rejects_bad_config_on_host(abi, kw, needle):
+    cfg, keep = _grid_cfg(abi, **kw)
+    h = ctypes.c_void_p()
+    assert abi.lib().rts_grid_init(ctypes.byref(cfg), ctypes.byref(h)) == abi.RTS_EINVAL
+    assert not h.value
+    assert needle in abi.rts_grid_last_error(None)
+
+
+def test_grid_and_integrator_null_handles(abi):
+    L = abi.lib()
+    assert L.rts_grid_run(None, None, None, 0, None, None) == abi.RTS_EINVAL
+    assert L.rts_grid_last_ms(None, None, None) == abi.RTS_EINVAL
+    assert L.rts_integrate_run(None, None, None, None) == abi.RTS_EINVAL
+    L.rts_grid_destroy(None)
+    L.rts_integrate_destroy(None)
+
+
+def test_integration_lengths_on_host(abi):
+    rng = np.random.default_rng(5)
+    pos = rng.uniform(-800.0, 800.0, size=(9, 3))
+    cut = np.array([500.0, 1000.0])
+    lf = np.array([16, 8, 4], np.int32)
+    out = np.zeros(36, np.int32)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = abi.lib().rts_integrate_lengths(9, pos.ctypes.data_as(dp), 2, cut.ctypes.data_as(dp),
+                                         lf.ctypes.data_as(ip), out.ctypes.data_as(ip))
+    assert rc == abi.RTS_OK
+    ref = [16 if d < 500 else (8 if d < 1000 else 4)
+           for d in (np.linalg.norm(pos[i] - pos[j]) for i in range(9) for j in range(i + 1, 9))]
+    np.testing.assert_array_equal(out, ref)
+    bad = np.array([1000.0, 500.0])
+    assert abi.lib().rts_integrate_lengths(9, pos.ctypes.data_as(dp), 2, bad.ctypes.data_as(dp),
+                                           lf.ctypes.data_as(ip), out.ctypes.data_as(ip)) == abi.RTS_EINVAL
+
+
+@pytest.mark.parametrize("n_fine,lens,n_slot,needle", [
+    (16, [3, 4], 4, "divide"),
+    (16, [4, 0], 4, "divide"),
+    (16, [4, 8], 2, "n_slot"),
+    (16, [4, 8], 17, "n_slot"),
+    (0, [1], 1, "n_fine"),
+])
+def test_integrate_init_rejects_bad_lengths_on_host(abi, n_fine, lens, n_slot, needle):
+    L = np.asarray(lens, np.int32)
+    h = ctypes.c_void_p()
+    rc = abi.lib().rts_integrate_init(n_fine, len(L), 8, L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n_slot,
+                                      ctypes.byref(h))
+    assert rc == abi.RTS_EINVAL and not h.value
+    assert needle in abi.lib().rts_integrate_last_error(None).decode()
