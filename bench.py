@@ -669,6 +669,15 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
                                              for k in range(k64))),
         "note": "same input cube; residual error sampled on the first 64 baselines",
     }
+    # FP64 roofline: the complex arithmetic of the subtraction and the average (4 complex
+    # multiply-adds each = 64 flop per update) against the measured FP64 FMA rate; the two FP64
+    # sincospi per visibility are not counted, so the fraction is a lower bound
+    fp64_peak = _abi.rts_fp64_rate()
+    fp64_achieved = 64 * rate64 / 1e12
+    out["fp64_path"]["roofline"] = {"bound": "alu", "kernel": "k_stream_fp64<SUB,ACC>", "achieved": fp64_achieved,
+                                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": fp64_achieved / fp64_peak,
+                                    "peak_source": "measured FP64 FMA rate (rts_fp64_rate), not in MEASURED_PEAKS.json",
+                                    "algorithmic_flops_per_update": 64, "traffic": None}
     del v64, r64
     p64.close()
     p.close()                      # release the pipeline cubes before the adjoint leg

@@ -319,6 +319,13 @@ int rts_peel_timing_read(rts_peel_t* h, double* ms, int64_t* groups, int64_t* la
  * NULL handle. */
 int rts_peel_kernels(const rts_peel_t* h, int32_t* block_kernel, int32_t* solve_kernel);
 
+/* Measured FP64 fused multiply-add rate of the current device in TFLOP/s (no
+ * paper counterpart: the roofline denominator of the RTS_PREC_FP64 path, which
+ * is bound by FP64 arithmetic).  Runs a short kernel of independent FMA chains
+ * on every SM (about a tenth of a second) and waits for it.  RTS_EINVAL for a
+ * NULL pointer, RTS_ECUDA for a failed launch. */
+int rts_fp64_rate(double* h_tflops);
+
 /* Failure-detection self-test of the grid barrier the cooperative block solve
  * uses (no paper counterpart).  Launches n_cta CTAs (1 .. the device's
  * co-resident limit, at most 1024) on the current device, cooperatively, that

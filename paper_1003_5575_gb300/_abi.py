@@ -36,7 +36,7 @@ EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_ca
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad", "rts_peel_offsets",
            "rts_offsets_solve",
            "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
-           "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_barrier_selftest",
+           "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_barrier_selftest", "rts_fp64_rate",
            "rts_host_alloc", "rts_host_free",
            "rts_peel_last_error", "rts_peel_destroy",
            "rts_grid_init", "rts_grid_run", "rts_grid_last_ms", "rts_grid_last_error", "rts_grid_destroy",
@@ -120,6 +120,8 @@ def lib():
                                                ctypes.POINTER(ctypes.c_int64)]
             L.rts_barrier_selftest.restype = ctypes.c_int
             L.rts_barrier_selftest.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _ip]
+            L.rts_fp64_rate.restype = ctypes.c_int
+            L.rts_fp64_rate.argtypes = [_dp]
             L.rts_peel_kernels.restype = ctypes.c_int
             L.rts_peel_kernels.argtypes = [_vp, _ip, _ip]
             L.rts_host_alloc.restype = ctypes.c_int
@@ -228,6 +230,13 @@ def rts_peel_kernels(h):
     bk, sk = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().rts_peel_kernels(h, ctypes.byref(bk), ctypes.byref(sk)), h)
     return bk.value, sk.value
+
+
+def rts_fp64_rate() -> float:
+    """Measured FP64 FMA rate of the current device, TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(lib().rts_fp64_rate(ctypes.byref(v)), None)
+    return v.value
 
 
 def rts_barrier_selftest(n_cta: int, missing: int, rounds: int) -> int:

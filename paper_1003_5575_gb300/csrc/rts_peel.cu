@@ -1162,6 +1162,64 @@ void rts_peel_destroy(rts_peel_t* h) {
   delete h;
 }
 
+}  // extern "C"
+
+namespace {
+
+// FP64 FMA throughput probe: 8 independent chains per thread, so the FP64
+// pipe, not the dependency latency, limits the rate; the result is stored so
+// the loop is kept.
+constexpr int kF64Chains = 8;
+__global__ void __launch_bounds__(256) k_fp64_rate(int iters, double seed, double* out) {
+  double x[kF64Chains];
+  #pragma unroll
+  for (int c = 0; c < kF64Chains; ++c) x[c] = seed + 1e-3 * (threadIdx.x + c);
+  const double a = 0.999999, b = 1e-7;
+  for (int i = 0; i < iters; ++i)
+    #pragma unroll
+    for (int c = 0; c < kF64Chains; ++c) x[c] = fma(x[c], a, b);
+  double s = 0.0;
+  #pragma unroll
+  for (int c = 0; c < kF64Chains; ++c) s += x[c];
+  if (s == 12345.678) out[0] = s;                    // practically never: keeps the work
+}
+
+}  // namespace
+
+extern "C" {
+
+int rts_fp64_rate(double* h_tflops) {
+  g_init_err.clear();
+  if (!h_tflops) return fail(nullptr, RTS_EINVAL, "h_tflops is NULL");
+  int dev = 0, n_sm = 0;
+  RTS_CUDA(nullptr, cudaGetDevice(&dev));
+  RTS_CUDA(nullptr, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  double* d_out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RTS_CUDA(nullptr, cudaMalloc(&d_out, sizeof(double)));
+  auto done = [&](int rc) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d_out);
+    return rc;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return done(fail(nullptr, RTS_ECUDA, "cudaEventCreate"));
+  const int iters = 1 << 14, blocks = 8 * n_sm;
+  k_fp64_rate<<<blocks, 256>>>(iters / 16, 1.0, d_out);    // warm-up
+  cudaEventRecord(e0);
+  k_fp64_rate<<<blocks, 256>>>(iters, 1.0, d_out);
+  cudaEventRecord(e1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return done(fail(nullptr, RTS_ECUDA, std::string("FP64 rate probe: ") + cudaGetErrorString(e)));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  const double flops = 2.0 * kF64Chains * (double)iters * blocks * 256;
+  *h_tflops = flops / (ms * 1e-3) / 1e12;
+  return done(RTS_OK);
+}
+
 int rts_barrier_selftest(int32_t n_cta, int32_t missing, int32_t rounds, int32_t* h_completed) {
   g_init_err.clear();
   if (!h_completed) return fail(nullptr, RTS_EINVAL, "h_completed is NULL");

@@ -89,6 +89,7 @@ def test_null_handle_is_rejected(abi):
     assert abi.lib().rts_peel_grad(None, None, 0, None, None, None, None, None, None) == abi.RTS_EINVAL
     assert abi.lib().rts_peel_kernels(None, None, None) == abi.RTS_EINVAL
     assert abi.lib().rts_peel_cadence_taylor(None, None, None, 0, None, None, None, None, None) == abi.RTS_EINVAL
+    assert abi.lib().rts_fp64_rate(None) == abi.RTS_EINVAL
     out = ctypes.c_int32()
     assert abi.lib().rts_barrier_selftest(0, 0, 1, ctypes.byref(out)) == abi.RTS_EINVAL
     assert abi.lib().rts_barrier_selftest(8, 2, 1, ctypes.byref(out)) == abi.RTS_EINVAL

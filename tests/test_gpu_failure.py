@@ -46,3 +46,10 @@ def test_barrier_selftest_rejects_bad_arguments(abi):
         with pytest.raises(RtsError) as e:
             abi.rts_barrier_selftest(*args)
         assert e.value.code == RTS_EINVAL
+
+
+def test_fp64_rate_probe_is_plausible(abi):
+    """The FP64 FMA rate probe (the FP64 path's roofline denominator) returns a
+    rate between GB300's nominal FP64 figure's order of magnitude bounds."""
+    r = abi.rts_fp64_rate()
+    assert 0.1 < r < 100.0, r
