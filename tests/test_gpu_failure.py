@@ -48,6 +48,7 @@ def test_barrier_selftest_rejects_bad_arguments(abi):
         assert e.value.code == RTS_EINVAL
 
 
+@pytest.mark.gpu
 def test_fp64_rate_probe_is_plausible(abi):
     """The FP64 FMA rate probe (the FP64 path's roofline denominator) returns a
     rate between GB300's nominal FP64 figure's order of magnitude bounds."""
