@@ -71,6 +71,9 @@ def lib():
                                          ctypes.c_double, ctypes.c_double, _i32, _dp, _dp, _dp]
             L.orc_peel_taylor.restype = _i32
             L.orc_peel_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _dp, _ip]
+            L.orc_taylor_moments.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+            L.orc_taylor_dterm.argtypes = [_i32, _i32, _i32, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, _dp]
             L.orc_grid.argtypes = [_i32, ctypes.c_double, _dp, _i32, _i32, _i32, _dp, _dp, _dp]
             L.orc_integrate.argtypes = [_i32, ctypes.c_int64, _i32, _ip, _i32, _dp, _dp]
             L.orc_num_threads.restype = _i32
@@ -243,6 +246,28 @@ def peel_taylor(uvw, freq, vis, lmS, n_iter=20):
     lib().orc_peel_taylor(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(R), n_src, _d(lmS),
                           n_iter, _d(G), _d(H), st.ctypes.data_as(_ip))
     return R, G, H, st[:n_src]
+
+
+def taylor_moments(uvw, freq, vis, l, m):
+    """[3][n_bl][4]: mean_{t,c} x_c^n R exp(+2 pi i phi) of the cube in direction (l, m)."""
+    uvw, freq = _f64(uvw), _f64(freq)
+    vis = _f64(vis, np.complex128)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    nb = n_ant * (n_ant - 1) // 2
+    out = np.zeros((3, nb, 4), np.complex128)
+    lib().orc_taylor_moments(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(vis), float(l), float(m), _d(out))
+    return out
+
+
+def taylor_dterm(uvw, freq, lj, mj, lk, mk):
+    """[5][n_bl]: mean_{t,c} x_c^p exp(2 pi i (phi_k - phi_j)), p = 0..4."""
+    uvw, freq = _f64(uvw), _f64(freq)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    nb = n_ant * (n_ant - 1) // 2
+    out = np.zeros((5, nb), np.complex128)
+    lib().orc_taylor_dterm(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), float(lj), float(mj), float(lk),
+                           float(mk), _d(out))
+    return out
 
 
 def grid(n_pix, r_max, gcf, xy, vis):

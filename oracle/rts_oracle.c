@@ -727,3 +727,60 @@ void orc_integrate(int32_t n_fine, int64_t n_bl, int32_t n_chan, const int32_t* 
         }
   }
 }
+
+/* ---- Taylor-gain moments and pair terms (for the blocked Taylor schedule) ---
+ * mom[n][bl][4] = mean_{t,c} x_c^n R(t,bl,c) exp(+2 pi i phi) (n = 0, 1, 2), the
+ * residual's channel moments in direction (l, m); and, for two directions j
+ * and k, dterm[p][bl] = mean_{t,c} x_c^p exp(2 pi i (phi_k - phi_j)) (p = 0..4),
+ * the plain definitions (direct sums) of the terms that correct source k's
+ * moments for the model of an earlier source j of the same block:
+ *   M_n(k) = M_n^plain(k) - sum_j sum_m P_m,j D^(n+m)_jk,
+ *   P_0 = S G_i G_j^H, P_1 = S (G_i H_j^H + H_i G_j^H), P_2 = S H_i H_j^H.      */
+
+void orc_taylor_moments(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                        const double* freq, const double* vis, double l, double m, double* mom) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  double inv_n = 1.0 / ((double)n_time * n_chan);
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    mat2 acc[3] = {m_zero(), m_zero(), m_zero()};
+    for (int32_t t = 0; t < n_time; ++t) {
+      double tau = orc_delay_m(uvw, n_ant, t, ai[bl], aj[bl], l, m);
+      for (int32_t c = 0; c < n_chan; ++c) {
+        double x = taylor_x(freq, n_chan, c);
+        mat2 y = m_scale(m_load(vis_at((double*)vis, n_bl, n_chan, t, bl, c)), phasor(orc_phase_turns(tau, freq[c]), +1.0));
+        acc[0] = m_add(acc[0], y);
+        acc[1] = m_add(acc[1], m_scale(y, x));
+        acc[2] = m_add(acc[2], m_scale(y, x * x));
+      }
+    }
+    for (int n = 0; n < 3; ++n) m_store(mom + ((int64_t)n * n_bl + bl) * 8, m_scale(acc[n], inv_n));
+  }
+}
+
+void orc_taylor_dterm(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                      const double* freq, double lj, double mj, double lk, double mk, double* dterm) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  double inv_n = 1.0 / ((double)n_time * n_chan);
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    cplx acc[5] = {0, 0, 0, 0, 0};
+    for (int32_t t = 0; t < n_time; ++t) {
+      double tj = orc_delay_m(uvw, n_ant, t, ai[bl], aj[bl], lj, mj);
+      double tk = orc_delay_m(uvw, n_ant, t, ai[bl], aj[bl], lk, mk);
+      for (int32_t c = 0; c < n_chan; ++c) {
+        double x = taylor_x(freq, n_chan, c), xp = 1.0;
+        cplx z = phasor(orc_phase_turns(tk, freq[c]), +1.0) * phasor(orc_phase_turns(tj, freq[c]), -1.0);
+        for (int p = 0; p < 5; ++p, xp *= x) acc[p] += xp * z;
+      }
+    }
+    for (int p = 0; p < 5; ++p) {
+      dterm[2 * ((int64_t)p * n_bl + bl)] = creal(acc[p]) * inv_n;
+      dterm[2 * ((int64_t)p * n_bl + bl) + 1] = cimag(acc[p]) * inv_n;
+    }
+  }
+}

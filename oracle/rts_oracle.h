@@ -62,6 +62,10 @@ int32_t orc_als_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const doub
 int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                         const double* freq, double* vis, int32_t n_src, const double* lmS,
                         int32_t n_iter, double* gain, double* slope, int32_t* status);
+void orc_taylor_moments(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                        const double* freq, const double* vis, double l, double m, double* mom);
+void orc_taylor_dterm(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                      const double* freq, double lj, double mj, double lk, double mk, double* dterm);
 /* gridder: radial gridding convolution function from a table (reading R18) */
 void orc_grid(int32_t n_pix, double r_max, const double* gcf, int32_t n_tab, int32_t n_vis,
               int32_t n_pol, const double* xy, const double* vis, double* grid);

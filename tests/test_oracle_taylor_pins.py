@@ -162,3 +162,55 @@ def test_taylor_als_matches_brute_force_least_squares():
     for xx in x:
         np.testing.assert_allclose(channel_products(G, H, xx, n),
                                    channel_products(Gl.reshape(n, 4), Hl.reshape(n, 4), xx, n), atol=1e-6)
+
+
+def test_taylor_moments_and_pair_terms_reduce_to_pinned_averages():
+    """The Taylor moments are the pinned constant-gain rotate + average of x_c^n V,
+    and the pair terms D^(p)_jk the average in direction k of x_c^p times a unit
+    point source at j (identity gains, S = 1)."""
+    cad = small(n_ant=5, n_chan=10, n_time=2, n_src=2)
+    V = oracle.simulate(cad)
+    x = xc(cad.freqs())
+    l, m = 0.05, -0.08
+    M = oracle.taylor_moments(cad.uvw(), cad.freqs(), V, l, m)
+    for n in range(3):
+        ref = oracle.rotate_average(cad.uvw(), cad.freqs(), V * (x ** n)[None, None, :, None], l, m)
+        np.testing.assert_allclose(M[n], ref, rtol=0, atol=1e-13)
+    lj, mj, lk, mk = -0.1, 0.12, 0.07, 0.02
+    eye = np.zeros((1, cad.n_ant, 4), np.complex128)
+    eye[..., 0] = eye[..., 3] = 1.0
+    unit = oracle.predict(cad.uvw(), cad.freqs(), np.array([[lj, mj, 1.0]]), eye)
+    D = oracle.taylor_dterm(cad.uvw(), cad.freqs(), lj, mj, lk, mk)
+    for p in range(5):
+        ref = oracle.rotate_average(cad.uvw(), cad.freqs(), unit * (x ** p)[None, None, :, None], lk, mk)
+        np.testing.assert_allclose(D[p], ref[:, 0], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(ref[:, 1], 0, atol=1e-15)
+
+
+def test_sequential_taylor_moments_equal_pair_term_corrections():
+    """The identity a blocked Taylor schedule rests on: the moments of source k
+    over the residual of the earlier sources of its block equal the plain
+    moments minus sum_j sum_m P_m,j D^(n+m)_jk, with P_0 = S G_i G_j^H,
+    P_1 = S (G_i H_j^H + H_i G_j^H), P_2 = S H_i H_j^H per baseline."""
+    cad = small(n_ant=6, n_chan=12, n_time=2, n_src=4)
+    src, G, H = cad.sources(), cad.jones(), cad.jones_slope()
+    V = oracle.predict_taylor(cad.uvw(), cad.freqs(), src, G, H) + cad.noise().reshape(cad.n_time, cad.n_bl, cad.n_chan, 4)
+    pairs = baseline_pairs(cad.n_ant)
+    herm_ = lambda a: np.conj(np.swapaxes(a, -1, -2))
+    for k in range(1, cad.n_src):
+        l, m, _ = src[k]
+        neg = src[:k].copy()
+        neg[:, 2] *= -1.0
+        R = oracle.predict_taylor(cad.uvw(), cad.freqs(), neg, G[:k], H[:k], vis=V)
+        got = oracle.taylor_moments(cad.uvw(), cad.freqs(), R, l, m)
+        ref = oracle.taylor_moments(cad.uvw(), cad.freqs(), V, l, m)
+        for j in range(k):
+            Gm, Hm, S = mats(G[j]), mats(H[j]), src[j, 2]
+            P = [S * Gm[pairs[:, 0]] @ herm_(Gm[pairs[:, 1]]),
+                 S * (Gm[pairs[:, 0]] @ herm_(Hm[pairs[:, 1]]) + Hm[pairs[:, 0]] @ herm_(Gm[pairs[:, 1]])),
+                 S * Hm[pairs[:, 0]] @ herm_(Hm[pairs[:, 1]])]
+            D = oracle.taylor_dterm(cad.uvw(), cad.freqs(), src[j, 0], src[j, 1], l, m)
+            for n in range(3):
+                for mm in range(3):
+                    ref[n] -= P[mm].reshape(-1, 4) * D[n + mm][:, None]
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
