@@ -208,9 +208,34 @@ int rts_peel_rotate_average(rts_peel_t* h, const void* d_vis, double l, double m
                             void* d_avg, void* stream);
 
 /* The solve step alone: Jones d_jones[n_ant][4] for a source of flux S from its
- * averaged visibilities d_avg[n_bl][4]; optional *h_status as in rts_peel_cadence. */
+ * averaged visibilities d_avg[n_bl][4]; optional *h_status as in rts_peel_cadence.
+ * d_avg and d_jones start on a 16-byte boundary (else RTS_EINVAL). */
 int rts_peel_solve(rts_peel_t* h, const void* d_avg, double S, void* d_jones,
                    int32_t* h_status, void* stream);
+
+/* The relative change ||J_n - J_(n-1)||_F / ||J_n||_F of each source's last ALS
+ * sweep in the last cadence run on this handle (rts_peel_cadence, _host,
+ * _taylor; slot 0 after rts_peel_solve): the number each status compares with
+ * 1e-6 (Section 3, CML: the per-source solve; the threshold is this library's
+ * reading).  h_rel host [n_src] doubles, n_src <= the cadence's source count.
+ * Copied on `stream` (pass the cadence's stream) and waited for.  RTS_EINVAL
+ * for a NULL handle or pointer or n_src outside [0, max_sources]. */
+int rts_peel_rel(rts_peel_t* h, int32_t n_src, double* h_rel, void* stream);
+
+/* The phase step alone (Section 2: visibilities are Fourier samples of the
+ * sky; the loop's phase rotation to a source direction): for n_pair
+ * (time, baseline) pairs, d_tb DEVICE int32 [n_pair][2] = (t, bl), the phase of
+ * direction (l, m) at every channel, d_phase DEVICE double [n_pair][n_chan], in
+ * turns in [-1/2, 1/2), as the peel's kernels form it: the FP64 delay
+ * tau = u l + v m + w (n - 1), the Q0.64 fixed-point phases A = frac(tau nu_0 / c)
+ * and B = frac(tau dnu / c), and channel c at A + c B modulo one turn (exact
+ * integer arithmetic).  rounded = 0 returns that Q0.64 phase; rounded = 1 the
+ * FP32 value the kernels hand to the hardware sin/cos (rounded to Q0.32 first).
+ * A pair with t or bl out of range gets NaN.  Asynchronous on `stream`.
+ * RTS_EINVAL for a NULL handle or pointer, n_pair < 0, rounded not 0 or 1,
+ * or a direction with l^2 + m^2 >= 1. */
+int rts_peel_phases(rts_peel_t* h, double l, double m, int32_t n_pair, const int32_t* d_tb,
+                    int32_t rounded, double* d_phase, void* stream);
 
 /* The solve step without any allocation, for callers that cannot call
  * cudaMalloc or create a handle: code that runs after a real-time pipeline has
@@ -221,6 +246,7 @@ int rts_peel_solve(rts_peel_t* h, const void* d_avg, double S, void* d_jones,
  *   d_avg    device [n_bl][4] averaged visibilities (complex64 for
  *            RTS_PREC_MIXED, complex128 for RTS_PREC_FP64), as for rts_peel_solve
  *   n_ant    2 .. RTS_NOALLOC_MAX_ANT; larger arrays are rejected with RTS_EINVAL
+ *   d_avg and d_jones start on a 16-byte boundary (else RTS_EINVAL)
  *   d_jones  device [n_ant][4] output, same precision as d_avg
  *   h_status optional host int: as in rts_peel_solve (the call then waits)
  * Scratch: one static device array of about 200 KB (sized for

@@ -60,7 +60,7 @@ def lib():
             L.orc_subtract.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, _dp]
             L.orc_peel.restype = _i32
-            L.orc_peel.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _ip, _dp]
+            L.orc_peel.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _ip, _dp, _dp]
             L.orc_loss_grad.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _dp,
                                         _dp, _dp, _dp, _dp, _dp]
             L.orc_offsets.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _dp, ctypes.c_double,
@@ -161,8 +161,9 @@ def subtract(uvw, freq, vis, l, m, S, jones_k):
     return out
 
 
-def peel(uvw, freq, vis, lmS, n_iter=20, keep_avg=False):
-    """Sequential peel.  Returns (residual, jones [n_src][n_ant][4], status[, avg])."""
+def peel(uvw, freq, vis, lmS, n_iter=20, keep_avg=False, with_rel=False):
+    """Sequential peel.  Returns (residual, jones [n_src][n_ant][4], status[, avg][, rel]),
+    rel [n_src] = each source's last relative change ||J_n - J_(n-1)||_F / ||J_n||_F."""
     uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
     R = _f64(vis, np.complex128).copy()
     n_time, n_ant = uvw.shape[0], uvw.shape[1]
@@ -171,9 +172,15 @@ def peel(uvw, freq, vis, lmS, n_iter=20, keep_avg=False):
     J = np.zeros((n_src, n_ant, 4), np.complex128)
     st = np.zeros(max(n_src, 1), np.int32)
     avg = np.zeros((n_src, nb, 4), np.complex128) if keep_avg else None
+    rel = np.zeros(max(n_src, 1))
     lib().orc_peel(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(R), n_src, _d(lmS),
-                   n_iter, _d(J), st.ctypes.data_as(_ip), _d(avg) if keep_avg else None)
-    return (R, J, st[:n_src], avg) if keep_avg else (R, J, st[:n_src])
+                   n_iter, _d(J), st.ctypes.data_as(_ip), _d(avg) if keep_avg else None, _d(rel))
+    out = (R, J, st[:n_src])
+    if keep_avg:
+        out += (avg,)
+    if with_rel:
+        out += (rel[:n_src],)
+    return out
 
 
 def loss_grad(uvw, freq, vis, lmS, jones):

@@ -292,7 +292,8 @@ void orc_subtract(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* u
 
 int32_t orc_peel(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                  const double* freq, double* vis, int32_t n_src, const double* lmS,
-                 int32_t n_iter, double* jones, int32_t* status, double* avg_per_src) {
+                 int32_t n_iter, double* jones, int32_t* status, double* avg_per_src,
+                 double* rel_per_src) {
   int64_t n_bl = orc_n_baselines(n_ant);
   double* avg = (double*)malloc(sizeof(double) * 8 * (n_bl > 0 ? n_bl : 1));
   int32_t worst = 0;
@@ -301,8 +302,10 @@ int32_t orc_peel(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uv
     double* Jk = jones + (int64_t)k * n_ant * 8;
     orc_rotate_average(n_ant, n_chan, n_time, uvw, freq, vis, l, m, avg);
     if (avg_per_src) memcpy(avg_per_src + (int64_t)k * n_bl * 8, avg, sizeof(double) * 8 * n_bl);
-    int32_t st = orc_als(n_ant, avg, S, n_iter, Jk, NULL);
+    double rel = 0.0;
+    int32_t st = orc_als(n_ant, avg, S, n_iter, Jk, &rel);
     if (status) status[k] = st;
+    if (rel_per_src) rel_per_src[k] = rel;
     if (st < 0) worst = st;
     orc_subtract(n_ant, n_chan, n_time, uvw, freq, vis, l, m, S, Jk);
   }

@@ -43,7 +43,8 @@ void orc_subtract(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* u
                   const double* jones);
 int32_t orc_peel(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                  const double* freq, double* vis, int32_t n_src, const double* lmS,
-                 int32_t n_iter, double* jones, int32_t* status, double* avg_per_src);
+                 int32_t n_iter, double* jones, int32_t* status, double* avg_per_src,
+                 double* rel_per_src);
 void orc_loss_grad(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                    const double* freq, const double* vis, int32_t n_src, const double* lmS,
                    const double* jones, double* loss, double* g_jones, double* g_l,

@@ -35,7 +35,8 @@ EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_ca
            "rts_peel_cadence_taylor",
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad", "rts_peel_offsets",
            "rts_offsets_solve",
-           "rts_peel_solve_noalloc", "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
+           "rts_peel_solve_noalloc", "rts_peel_rel", "rts_peel_phases",
+           "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
            "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_barrier_selftest", "rts_fp64_rate",
            "rts_host_alloc", "rts_host_free",
            "rts_peel_last_error", "rts_peel_destroy",
@@ -102,6 +103,10 @@ def lib():
             L.rts_peel_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp, _ip, _vp]
             L.rts_peel_solve_noalloc.restype = ctypes.c_int
             L.rts_peel_solve_noalloc.argtypes = [_vp, _i32, ctypes.c_double, _i32, _i32, _vp, _ip, _vp]
+            L.rts_peel_rel.restype = ctypes.c_int
+            L.rts_peel_rel.argtypes = [_vp, _i32, _dp, _vp]
+            L.rts_peel_phases.restype = ctypes.c_int
+            L.rts_peel_phases.argtypes = [_vp, ctypes.c_double, ctypes.c_double, _i32, _vp, _i32, _vp, _vp]
             L.rts_peel_pipeline_submit.restype = ctypes.c_int
             L.rts_peel_pipeline_submit.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _ip]
             L.rts_peel_pipeline_wait.restype = ctypes.c_int
@@ -202,6 +207,14 @@ def rts_peel_solve(h, d_avg, S, d_jones, h_status, stream):
 def rts_peel_solve_noalloc(d_avg, n_ant, S, n_iter, precision, d_jones, h_status, stream):
     return _check(lib().rts_peel_solve_noalloc(d_avg, n_ant, S, n_iter, precision, d_jones, h_status,
                                                stream), None)
+
+
+def rts_peel_rel(h, n_src, h_rel, stream):
+    return _check(lib().rts_peel_rel(h, n_src, h_rel, stream), h)
+
+
+def rts_peel_phases(h, l, m, n_pair, d_tb, rounded, d_phase, stream):
+    return _check(lib().rts_peel_phases(h, float(l), float(m), n_pair, d_tb, rounded, d_phase, stream), h)
 
 
 def rts_peel_pipeline_submit(h, h_vis, h_resid, n_src, h_src, h_jones, h_status):

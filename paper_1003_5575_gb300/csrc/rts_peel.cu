@@ -17,6 +17,7 @@
 #include "common.cuh"
 #include "grad_kernels.cuh"
 #include "offset_kernels.cuh"
+#include "phase_kernels.cuh"
 #include "predict_kernels.cuh"
 #include "solve_kernels.cuh"
 #include "stream_kernels.cuh"
@@ -967,6 +968,8 @@ int rts_peel_solve(rts_peel_t* h, const void* d_avg, double S, void* d_jones, in
                    void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (!d_avg || !d_jones) return fail(h, RTS_EINVAL, "d_avg and d_jones are required");
+  if (misaligned(d_avg) || misaligned(d_jones))
+    return fail(h, RTS_EINVAL, "d_avg and d_jones must start on a 16-byte boundary");
   if (!std::isfinite(S) || !(S > 0.0)) return fail(h, RTS_EINVAL, "S must be finite and > 0");
   cudaStream_t s = as_stream(stream);
   int rc = launch_als(h, d_avg, S, d_jones, 0, s);
@@ -1114,6 +1117,34 @@ int rts_peel_kernels(const rts_peel_t* h, int32_t* block_kernel, int32_t* solve_
   if (solve_kernel)
     *solve_kernel = h->b_avg ? (h->bs_ok ? RTS_SOLVE_AUTO : RTS_SOLVE_LAUNCHES) : h->solve_kernel;
   return RTS_OK;
+}
+
+int rts_peel_rel(rts_peel_t* h, int32_t n_src, double* h_rel, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (n_src < 0 || n_src > h->max_sources) return fail(h, RTS_EINVAL, "n_src must be in [0, max_sources]");
+  if (n_src == 0) return RTS_OK;
+  if (!h_rel) return fail(h, RTS_EINVAL, "h_rel is NULL");
+  cudaStream_t s = as_stream(stream);
+  RTS_CUDA(h, cudaMemcpyAsync(h_rel, h->d_rel, sizeof(double) * n_src, cudaMemcpyDeviceToHost, s));
+  RTS_CUDA(h, cudaStreamSynchronize(s));
+  return RTS_OK;
+}
+
+int rts_peel_phases(rts_peel_t* h, double l, double m, int32_t n_pair, const int32_t* d_tb, int32_t rounded,
+                    double* d_phase, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!std::isfinite(l) || !std::isfinite(m) || !(l * l + m * m < 1.0))
+    return fail(h, RTS_EINVAL, "direction must be finite with l^2 + m^2 < 1");
+  if (n_pair < 0) return fail(h, RTS_EINVAL, "n_pair must be >= 0");
+  if (rounded != 0 && rounded != 1) return fail(h, RTS_EINVAL, "rounded must be 0 or 1");
+  if (n_pair == 0) return RTS_OK;
+  if (!d_tb || !d_phase) return fail(h, RTS_EINVAL, "d_tb and d_phase are required");
+  const int64_t n = (int64_t)n_pair * h->n_chan;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_phase_table<<<grid, 256, 0, as_stream(stream)>>>(h->d_uvw, h->d_bl_ant, h->n_ant, h->n_chan, h->n_time, h->n_bl,
+                                                      make_dir(l, m, 1.0), h->nu0 / kCLight, h->dnu / kCLight,
+                                                      n_pair, d_tb, rounded, d_phase);
+  return check_launch(h, "phase table launch");
 }
 
 const char* rts_peel_last_error(const rts_peel_t* h) {
@@ -1291,6 +1322,8 @@ extern "C" int rts_peel_solve_noalloc(const void* d_avg, int32_t n_ant, double S
                                       void* stream) {
   g_init_err.clear();
   if (!d_avg || !d_jones) return fail(nullptr, RTS_EINVAL, "d_avg and d_jones are required");
+  if (misaligned(d_avg) || misaligned(d_jones))
+    return fail(nullptr, RTS_EINVAL, "d_avg and d_jones must start on a 16-byte boundary");
   if (n_ant < 2 || n_ant > RTS_NOALLOC_MAX_ANT)
     return fail(nullptr, RTS_EINVAL, "rts_peel_solve_noalloc: n_ant must be in [2, " +
                                          std::to_string(RTS_NOALLOC_MAX_ANT) + "] (static scratch limit)");

@@ -26,7 +26,11 @@
 //     are added in FP32 in a fixed order, the sum over the 8 lane positions of
 //     an antenna is FP64 (the normal-equation accumulation, spread over four
 //     warps), and the 2x2 solve, the iterate, its averaging and the
-//     convergence norms are FP32 (per-source status sums FP64).
+//     convergence norms are FP32 in sweeps 1 .. n_iter-1.  The last sweep
+//     solves from the FP64 totals in FP64 and takes the relative change of its
+//     FP64 iterate against the FP32 previous one in FP64: the status compares
+//     that change with 1e-6, and the FP32 rounding of a solve (a few 1e-7 of
+//     each entry) would move it by several per cent near the threshold.
 //
 // FP64 arithmetic runs at 1/64 of the FP32 rate on GB300, a warp instruction
 // costs the same with 4 or 32 lanes active, and each dependent FP64 step
@@ -74,10 +78,30 @@ struct BlockSolveArgs {
 
 // dynamic shared memory: rows [apc][2][n_ant] float4, iterate [n_ant][4] float2,
 // previous iterate of the CTA's antennas [apc][4] float2, per-slot convergence
-// sums [apc][3] double, normal-equation totals [apc][12] float
+// sums [apc][3] double, FP64 normal-equation totals of the last sweep [apc][12]
+// double, normal-equation totals [apc][12] float
 inline size_t block_solve_smem(int n_ant, int apc) {
   return (size_t)apc * n_ant * 4 * sizeof(float2) + (size_t)n_ant * 4 * sizeof(float2) +
-         (size_t)apc * 4 * sizeof(float2) + (size_t)apc * 3 * sizeof(double) + (size_t)apc * 12 * sizeof(float);
+         (size_t)apc * 4 * sizeof(float2) + (size_t)apc * 3 * sizeof(double) + (size_t)apc * 12 * sizeof(double) +
+         (size_t)apc * 12 * sizeof(float);
+}
+
+// J_p = A C^-1 / S, entry e (row r = e >> 1, column c = e & 1), from the 12
+// normal-equation totals (A: 8 reals row-major, C: c00, c11, re c01, im c01),
+// C = [c00 c01; conj(c01) c11], C^-1 = [c11 -c01; -conj(c01) c00] / det
+template <typename T>
+__device__ __forceinline__ typename cplx_of<T>::type solve_entry(const T* tot, T S, int e) {
+  using C = typename cplx_of<T>::type;
+  const int r = e >> 1, c = e & 1;
+  const T c00 = tot[8], c11 = tot[9];
+  const C c01 = cmk<C>(tot[10], tot[11]);
+  const T det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);
+  const T sc = T(1) / (det * S);
+  const C i0c = c == 0 ? cmk<C>(c11 * sc, 0) : cmk<C>(-c01.x * sc, -c01.y * sc);
+  const C i1c = c == 0 ? cmk<C>(-c01.x * sc, c01.y * sc) : cmk<C>(c00 * sc, 0);
+  const C Ar0 = cmk<C>(tot[4 * r], tot[4 * r + 1]);
+  const C Ar1 = cmk<C>(tot[4 * r + 2], tot[4 * r + 3]);
+  return cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
 }
 
 // Sum 16 doubles over the 8 lanes of a lane group (lanes 8i .. 8i+7): lane j of
@@ -177,7 +201,8 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
   float2* Js = rows + (size_t)a.apc * a.n_ant * 4;                       // [n_ant][4]
   float2* Jold = Js + (size_t)a.n_ant * 4;                               // [apc][4]
   double* s_norm = reinterpret_cast<double*>(Jold + (size_t)a.apc * 4);  // [apc][3]
-  float* s_tot = reinterpret_cast<float*>(s_norm + (size_t)a.apc * 3);   // [apc][12]
+  double* s_tot64 = s_norm + (size_t)a.apc * 3;                          // [apc][12]
+  float* s_tot = reinterpret_cast<float*>(s_tot64 + (size_t)a.apc * 12); // [apc][12]
   __shared__ float s_p32[kSolveWarps][12][32];   // FP32 partials of every lane
   __shared__ int s_flag;
 
@@ -354,50 +379,50 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
               v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
             }
           }
-          const float tot = (float)(v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1));   // lane j: slot j >> 1
+          const double tot = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);   // lane j: slot j >> 1
           const int j = lane & 7;
-          if (live && (j & 1) == 0 && j < 6) s_tot[s * 12 + 3 * wq + (j >> 1)] = tot;
+          if (live && (j & 1) == 0 && j < 6) {
+            s_tot[s * 12 + 3 * wq + (j >> 1)] = (float)tot;
+            if (last) s_tot64[s * 12 + 3 * wq + (j >> 1)] = tot;
+          }
         }
         __syncthreads();
         if (wq == 0 && g < nquad) {
           const int j = lane & 7;
           const unsigned m4 = __ballot_sync(0xffffffffu, live && j < 4);   // solving lanes
           if (live && j < 4) {
-            // J_p = A C^-1 / S in FP32 from the FP64 sums, C = [c00 c01; conj(c01) c11];
-            // lane j: entry e = j.  Iterate, averaging and convergence norms FP32:
-            // on GB300 each dependent FP64 step of this tail cost ~100 cycles
-            const float* tot = s_tot + s * 12;
-            const int e = j, r = e >> 1, c = e & 1;
-            const float c00 = tot[8], c11 = tot[9];
-            const float2 c01 = make_float2(tot[10], tot[11]);
-            const float det = c00 * c11 - (c01.x * c01.x + c01.y * c01.y);
-            const float sc = 1.0f / (det * Sf);
-            const float2 i0c = c == 0 ? make_float2(c11 * sc, 0.f) : make_float2(-c01.x * sc, -c01.y * sc);
-            const float2 i1c = c == 0 ? make_float2(-c01.x * sc, c01.y * sc) : make_float2(c00 * sc, 0.f);
-            const float2 Ar0 = make_float2(tot[4 * r], tot[4 * r + 1]);
-            const float2 Ar1 = make_float2(tot[4 * r + 2], tot[4 * r + 3]);
-            float2 Jn = cadd(cmul(Ar0, i0c), cmul(Ar1, i1c));
+            // lane j: entry e = j.  Sweeps before the last: solve, iterate and
+            // averaging in FP32 (on GB300 each dependent FP64 step of this tail cost
+            // ~100 cycles); the last sweep in FP64, with its relative change (the
+            // status) against the FP32 previous iterate
+            const int e = j;
             const float2 Jo = Jold[s * 4 + e];
-            if (average) Jn = make_float2(0.5f * (Jn.x + Jo.x), 0.5f * (Jn.y + Jo.y));
-            const float dx = Jn.x - Jo.x, dy = Jn.y - Jo.y;
-            float dn = dx * dx + dy * dy, nn = Jn.x * Jn.x + Jn.y * Jn.y;
-            int bad = !(isfinite(Jn.x) && isfinite(Jn.y));
-            #pragma unroll
-            for (int o = 1; o <= 2; o <<= 1) {
-              dn += __shfl_xor_sync(m4, dn, o);
-              nn += __shfl_xor_sync(m4, nn, o);
-              bad |= __shfl_xor_sync(m4, bad, o);
-            }
-            Jold[s * 4 + e] = Jn;
-            Jf_new[(size_t)p * 4 + e] = Jn;
-            if (last) {
+            float2 Jn;
+            if (!last) {
+              Jn = solve_entry<float>(s_tot + s * 12, Sf, e);
+              if (average) Jn = make_float2(0.5f * (Jn.x + Jo.x), 0.5f * (Jn.y + Jo.y));
+            } else {
+              double2 Jd = solve_entry<double>(s_tot64 + s * 12, a.src[3 * k + 2], e);
+              if (average) Jd = make_double2(0.5 * (Jd.x + (double)Jo.x), 0.5 * (Jd.y + (double)Jo.y));
+              const double dx = Jd.x - (double)Jo.x, dy = Jd.y - (double)Jo.y;
+              double dn = dx * dx + dy * dy, nn = Jd.x * Jd.x + Jd.y * Jd.y;
+              int bad = !(isfinite(Jd.x) && isfinite(Jd.y));
+              #pragma unroll
+              for (int o = 1; o <= 2; o <<= 1) {
+                dn += __shfl_xor_sync(m4, dn, o);
+                nn += __shfl_xor_sync(m4, nn, o);
+                bad |= __shfl_xor_sync(m4, bad, o);
+              }
+              Jn = make_float2((float)Jd.x, (float)Jd.y);
               a.jones[((size_t)k * a.n_ant + p) * 4 + e] = Jn;
               if (e == 0) {
-                s_norm[3 * s] = (double)dn;
-                s_norm[3 * s + 1] = (double)nn;
+                s_norm[3 * s] = dn;
+                s_norm[3 * s + 1] = nn;
                 s_norm[3 * s + 2] = (double)bad;
               }
             }
+            Jold[s * 4 + e] = Jn;
+            Jf_new[(size_t)p * 4 + e] = Jn;
           }
         }
         __syncthreads();                     // partials read before the next quad round

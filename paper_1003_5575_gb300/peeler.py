@@ -177,6 +177,21 @@ class Peeler:
         _abi.rts_peel_solve(self.h, _ptr(avg), float(S), _ptr(J), st.ctypes.data_as(_ip), _stream(stream))
         return J, int(st[0])
 
+    def rel(self, n_src: int, stream=None) -> np.ndarray:
+        """Last relative change of each source's ALS solve in the last cadence
+        (the number its status compares with 1e-6), float64[n_src]."""
+        out = np.zeros(max(n_src, 1))
+        _abi.rts_peel_rel(self.h, n_src, out.ctypes.data_as(_dp), _stream(stream))
+        return out[:n_src]
+
+    def phases(self, l: float, m: float, tb, rounded: bool = False, stream=None) -> torch.Tensor:
+        """The peel's per-channel phase of direction (l, m), in turns, on the
+        (time, baseline) pairs tb ([n][2] int): float64 [n][n_chan]."""
+        tb = torch.as_tensor(np.ascontiguousarray(tb, dtype=np.int32).reshape(-1, 2), device=self.device)
+        out = torch.empty((tb.shape[0], self.n_chan), dtype=torch.float64, device=self.device)
+        _abi.rts_peel_phases(self.h, l, m, tb.shape[0], _ptr(tb), int(rounded), _ptr(out), _stream(stream))
+        return out
+
     def grad(self, vis: torch.Tensor, jones: torch.Tensor, src: torch.Tensor,
              want_grad: bool = True, stream=None):
         """(loss, dL/dJ, dL/d(l, m, S)) with loss and gradients as cuda tensors."""

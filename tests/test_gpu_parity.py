@@ -7,10 +7,11 @@ CUDA path's output).  Tolerances (written here, from the stated targets):
               averages |dA| <= 1e-5 x rms, loss <= 1e-5 relative,
               gradients <= 1e-4 relative (vs the oracle's analytic gradient);
   FP64 path   1e-10 on all of these.
-Integer/index work (baseline order, status codes) is exact.
+Integer/index work (baseline order, status codes) is exact: a source's status
+is compared wherever the oracle's last relative change is farther from the 1e-6
+threshold than the tolerance on that change (rel_tol), and the change itself is
+compared with the oracle's.
 """
-import math
-
 import numpy as np
 import pytest
 
@@ -18,10 +19,10 @@ import oracle
 from synth import Cadence, config
 
 torch = pytest.importorskip("torch")
-pytestmark = pytest.mark.gpu
+from _parity import (CDT, TOL, check_status, jones_rel, make_peeler, oracle_case, rms_of,  # noqa: E402
+                     to_dev)
 
-TOL = {"mixed": 1e-5, "fp64": 1e-10}
-CDT = {"mixed": (np.complex64, torch.complex64), "fp64": (np.complex128, torch.complex128)}
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,40 +31,6 @@ def _built():
         pytest.skip("no CUDA device")
     from paper_1003_5575_gb300 import build
     build.build()
-
-
-def rms_of(V):
-    return math.sqrt(float(np.mean(V.real.astype(np.float64) ** 2 + V.imag.astype(np.float64) ** 2) / 2))
-
-
-def to_dev(V, prec):
-    return torch.from_numpy(np.ascontiguousarray(V.astype(CDT[prec][0]))).cuda()
-
-
-def jones_rel(Jg, Jr):
-    return max(np.linalg.norm(Jg[k] - Jr[k]) / np.linalg.norm(Jr[k]) for k in range(len(Jr)))
-
-
-_cache = {}
-
-
-def oracle_case(cad, n_iter=20):
-    key = (cad, n_iter)
-    if key not in _cache:
-        V = oracle.simulate(cad)
-        if cad.precision == "mixed":
-            V = V.astype(np.complex64).astype(np.complex128)   # what the GPU sees
-        R, J, st = oracle.peel(cad.uvw(), cad.freqs(), V, cad.sources(), n_iter=n_iter)
-        _cache[key] = (V, R, J, st)
-    return _cache[key]
-
-
-def make_peeler(cad, prec, n_iter=20, max_sources=None, per_pass=0, block_kernel=0, solve_kernel=0,
-                grad_kernel=0):
-    from paper_1003_5575_gb300 import Peeler
-    return Peeler(cad.uvw(), cad.freqs(), n_iter=n_iter, precision=prec,
-                  max_sources=max_sources or max(cad.n_src, 1), sources_per_pass=per_pass,
-                  block_kernel=block_kernel, solve_kernel=solve_kernel, grad_kernel=grad_kernel)
 
 
 # ---------------------------------------------------------------------------
@@ -83,11 +50,12 @@ PEEL_CASES = [
 
 @pytest.mark.parametrize("name,cad,prec", PEEL_CASES, ids=[c[0] for c in PEEL_CASES])
 def test_peel_matches_oracle(name, cad, prec):
-    V, R_ref, J_ref, st_ref = oracle_case(cad)
+    V, R_ref, J_ref, st_ref, rel_ref = oracle_case(cad)
     p = make_peeler(cad, prec, per_pass=1)
     vis = to_dev(V, prec)
     resid, jones, st = p.cadence(vis, cad.sources())
     torch.cuda.synchronize()
+    rel = p.rel(cad.n_src)
     R = resid.cpu().numpy()
     J = jones.cpu().numpy()
     tol = TOL[prec]
@@ -96,7 +64,7 @@ def test_peel_matches_oracle(name, cad, prec):
     print(f"{name}: residual {err_r:.2e} x rms, Jones {err_j:.2e} relative")
     assert err_r <= tol
     assert err_j <= tol
-    assert set(st.tolist()) <= {0, 1}
+    check_status(name, st, st_ref, rel, rel_ref, prec)
     # input untouched by the out-of-place call
     np.testing.assert_array_equal(vis.cpu().numpy(), V.astype(CDT[prec][0]))
     p.close()
@@ -106,10 +74,11 @@ def test_peel_matches_oracle(name, cad, prec):
 # Jones matrices move by well under 1e-6 when its input is perturbed by
 # 1e-7 x rms, so a 1e-5 parity bound is meaningful.  Narrow-band cases with many
 # sources on few antennas amplify FP32-level perturbations beyond 1e-5 whatever
-# the pass structure (64 antennas x 96 channels x 150 sources amplifies 1e-7 to
-# 1.4e-6 and both the one-source and the blocked GPU paths land at 2-4e-5 there;
-# 9 antennas x 37 channels x 70 sources amplifies it to 4e-3), and are left out.
+# the pass structure; test_gpu_conditioning.py checks one of them against a
+# bound scaled by its measured conditioning.
 BLOCK_CASES = [
+    ("wide768-block64", Cadence(64, 768, 4, 150, freq0_hz=167e6, seed=101), 64),  # the bench's 768-channel
+    #   strip: two 128-row subtraction tiles and N = 192 in the tcgen05 pass; 64, 64, 22
     ("cfg2-blocked", config(2), 16),                                # 50 sources: blocks of 16
     ("cfg2-block64", config(2), 64),                                # one block of 50
     ("wide-blocked", Cadence(64, 384, 4, 150, freq0_hz=167e6, seed=98), 16),
@@ -133,17 +102,18 @@ def test_blocked_peel_matches_sequential_oracle(name, cad, per_pass, kernel):
     same results as the oracle's one-source-at-a-time peel."""
     if kernel[0] == 3 and cad.n_chan > 768:
         pytest.skip("the tcgen05 pass holds at most 768 channels")
-    V, R_ref, J_ref, st_ref = oracle_case(cad)
+    V, R_ref, J_ref, st_ref, rel_ref = oracle_case(cad)
     p = make_peeler(cad, "mixed", per_pass=per_pass, block_kernel=kernel[0], solve_kernel=kernel[1])
     vis = to_dev(V, "mixed")
     resid, jones, st = p.cadence(vis, cad.sources())
     torch.cuda.synchronize()
+    rel = p.rel(cad.n_src)
     err_r = np.abs(resid.cpu().numpy() - R_ref).max() / rms_of(V)
     err_j = jones_rel(jones.cpu().numpy(), J_ref)
     print(f"{name}: residual {err_r:.2e} x rms, Jones {err_j:.2e} relative")
     assert err_r <= TOL["mixed"]
     assert err_j <= TOL["mixed"]
-    assert set(st.tolist()) <= {0, 1}
+    check_status(name, st, st_ref, rel, rel_ref)
     # in place gives the same bits
     work = vis.clone()
     r2, j2, _ = p.cadence(work, cad.sources(), resid=work)
@@ -155,7 +125,7 @@ def test_blocked_peel_matches_sequential_oracle(name, cad, per_pass, kernel):
 
 def test_in_place_equals_out_of_place_and_is_deterministic():
     cad = config(2).with_(n_src=6)
-    V, _, _, _ = oracle_case(config(2))
+    V = oracle_case(config(2))[0]
     p = make_peeler(cad, "mixed", per_pass=1)
     vis = to_dev(V, "mixed")
     r1, j1, _ = p.cadence(vis, cad.sources())
@@ -204,12 +174,12 @@ def test_solve_matches_oracle_on_oracle_average(prec):
     l, m, S = cad.sources()[0]
     avg = oracle.rotate_average(cad.uvw(), cad.freqs(), V, l, m)
     avg_in = avg.astype(CDT[prec][0]).astype(np.complex128)
-    J_ref, st_ref, rel = oracle.als(avg_in, S, cad.n_ant, n_iter=20)
+    J_ref, st_ref, rel_ref = oracle.als(avg_in, S, cad.n_ant, n_iter=20)
     p = make_peeler(cad, prec)
     J, st = p.solve(torch.from_numpy(avg_in.astype(CDT[prec][0])).cuda(), S)
     J = J.cpu().numpy()
     assert np.linalg.norm(J - J_ref) / np.linalg.norm(J_ref) <= TOL[prec]
-    assert st in (0, 1)
+    check_status(f"solve-{prec}", [st], [st_ref], p.rel(1), [rel_ref], prec)
     p.close()
 
 
@@ -437,7 +407,7 @@ def test_tcgen05_pass_channel_limit():
     with pytest.raises(RtsError) as e:
         make_peeler(cad, "mixed", per_pass=64, block_kernel=3)
     assert e.value.code == RTS_EINVAL
-    V, R_ref, J_ref, _ = oracle_case(cad)
+    V, R_ref, J_ref, _, _ = oracle_case(cad)
     p = make_peeler(cad, "mixed", per_pass=64)
     resid, jones, _ = p.cadence(to_dev(V, "mixed"), cad.sources())
     torch.cuda.synchronize()
@@ -454,7 +424,7 @@ def test_tensor_pass_channel_limit():
     with pytest.raises(RtsError) as e:
         make_peeler(cad, "mixed", per_pass=64, block_kernel=2)
     assert e.value.code == RTS_EINVAL
-    V, R_ref, J_ref, _ = oracle_case(cad)
+    V, R_ref, J_ref, _, _ = oracle_case(cad)
     p = make_peeler(cad, "mixed", per_pass=64)
     resid, jones, _ = p.cadence(to_dev(V, "mixed"), cad.sources())
     torch.cuda.synchronize()
@@ -476,10 +446,12 @@ def test_persistent_solve_equals_per_step_launches():
         p = make_peeler(cad, "mixed", per_pass=64, block_kernel=2, solve_kernel=solve)
         r, j, st = p.cadence(vis, cad.sources())
         torch.cuda.synchronize()
-        out.append((r.cpu().numpy(), j.cpu().numpy(), st))
+        out.append((r.cpu().numpy(), j.cpu().numpy(), st, p.rel(cad.n_src)))
         p.close()
-    (r0, j0, s0), (r1, j1, s1) = out
+    (r0, j0, s0, rel0), (r1, j1, s1, rel1) = out
     assert jones_rel(j0, j1) <= 3e-6
     assert np.abs(r0 - r1).max() <= 3e-6 * rms_of(V)
-    assert np.mean(s0 == s1) >= 0.95
+    # the per-step launches solve in FP64 from FP64 iterates: their changes
+    # stand in for the reference
+    check_status("coop-vs-launches", s0, s1, rel0, rel1)
 

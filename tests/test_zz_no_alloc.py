@@ -4,9 +4,10 @@ It serves callers that may not allocate device memory or create a handle (a
 pipeline whose memory is fixed at start-up, code running inside another
 framework's memory pool, code inside a stream-capture region).  It keeps its
 scratch in one static device array, so this file checks that it gives the
-same Jones matrices as the handle-based rts_peel_solve, through the C ABI, on
-two calls in a row (the second call reuses the scratch the first one left),
-and that arrays larger than the static limit are refused.  The file name
+same Jones matrices as the handle-based rts_peel_solve and as the oracle's
+solve, through the C ABI, on two calls in a row (the second call reuses the
+scratch the first one left), and that arrays larger than the static limit and
+misaligned buffers are refused.  The file name
 makes pytest collect it last.
 """
 import ctypes
@@ -53,6 +54,9 @@ def test_noalloc_solve_matches_handle_solve_on_two_calls(built, prec):
         Jr, Jn = J_ref.cpu().numpy(), J.cpu().numpy()
         assert np.linalg.norm(Jn - Jr) / np.linalg.norm(Jr) <= TOL[prec]
         assert int(st[0]) == st_ref
+        # and the oracle's solve of the same (rounded) average
+        Jo, _, _ = oracle.als(avg.astype(np.complex128), S, cad.n_ant, n_iter=20)
+        assert np.linalg.norm(Jn - Jo) / np.linalg.norm(Jo) <= TOL[prec]
     p.close()
 
 
@@ -65,3 +69,17 @@ def test_noalloc_solve_rejects_arrays_above_the_static_limit(built):
                                   ctypes.c_void_p(dummy.data_ptr()), None, None)
     assert rc == _abi.RTS_EINVAL
     assert "static scratch limit" in _abi.rts_peel_last_error(None)
+
+
+@pytest.mark.gpu
+def test_noalloc_solve_rejects_misaligned_buffers(built):
+    """A buffer that does not start on a 16-byte boundary is refused on the host
+    (nothing is launched with it)."""
+    from paper_1003_5575_gb300 import _abi
+    L = _abi.lib()
+    buf = torch.zeros(64, dtype=torch.complex64, device="cuda")
+    good, odd = buf.data_ptr(), buf.data_ptr() + 8
+    for d_avg, d_jones in ((odd, good), (good, odd)):
+        rc = L.rts_peel_solve_noalloc(ctypes.c_void_p(d_avg), 4, 1.0, 20, 0, ctypes.c_void_p(d_jones), None, None)
+        assert rc == _abi.RTS_EINVAL
+        assert "16-byte" in _abi.rts_peel_last_error(None)
