@@ -28,9 +28,17 @@
  *
  * Ownership: the caller owns every pointer it passes; "d_" pointers are
  * device memory, "h_" pointers host memory.  The handle owns the device
- * workspace it allocates in rts_peel_init (the paper's advice in Section 5
- * to pre-allocate all workspace at initialisation) and frees it in
- * rts_peel_destroy.  Calls are asynchronous on `stream` (a cudaStream_t, NULL
+ * workspace and frees it in rts_peel_destroy.  rts_peel_init allocates the
+ * workspace of the peel (the paper's advice in Section 5 to pre-allocate all
+ * workspace at initialisation): the per-source buffers, the blocked
+ * schedule's geometry tables, streams and solve set-up, and the Taylor
+ * cadence's moments, so rts_peel_cadence, _cadence_taylor, _cadence_host,
+ * _predict, _rotate_average and _solve allocate nothing.  Two workspaces whose
+ * size depends on how the handle is used are allocated on first use and kept:
+ * the adjoint's (first rts_peel_grad or rts_peel_offsets: 88 bytes per
+ * baseline for each of max_sources sources) and the pipeline's two
+ * device cubes and page-locked staging (first rts_peel_pipeline_submit); a
+ * warm-up call before real-time use moves that allocation out of the loop.  Calls are asynchronous on `stream` (a cudaStream_t, NULL
  * = legacy default stream) unless an h_status pointer is given, which makes
  * the call wait for its stream.  A handle must not be used from two host
  * threads at once.
@@ -160,8 +168,7 @@ int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_
  *   d_gain   [n_src][n_ant][4] complex64 receives G (the gain at the band centre).
  *   d_slope  [n_src][n_ant][4] complex64 receives H (the change of the gain
  *            across one band width).
- * RTS_PREC_MIXED handles only, n_chan >= 2 (else RTS_EINVAL).  The first call
- * allocates the moments and iterates (3 n_bl x 32 B + 192 B per antenna). */
+ * RTS_PREC_MIXED handles only, n_chan >= 2 (else RTS_EINVAL). */
 int rts_peel_cadence_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
                             const double* h_src, void* d_gain, void* d_slope, int32_t* h_status,
                             void* stream);
@@ -339,10 +346,8 @@ int rts_peel_timing_read(rts_peel_t* h, double* ms, int64_t* groups, int64_t* la
  * for benchmarks and tests).  *block_kernel: 0 when the handle peels one source
  * per pass, else RTS_BLOCK_FMA, RTS_BLOCK_TENSOR or RTS_BLOCK_TCGEN05 (the
  * choice RTS_BLOCK_AUTO made).  *solve_kernel: RTS_SOLVE_AUTO when the blocked
- * peel solves each block in one cooperative launch, else RTS_SOLVE_LAUNCHES
- * (known once the first blocked cadence has set up its workspace; before
- * that, the requested value).  Either pointer may be NULL.  RTS_EINVAL for a
- * NULL handle. */
+ * peel solves each block in one cooperative launch, else RTS_SOLVE_LAUNCHES.
+ * Either pointer may be NULL.  RTS_EINVAL for a NULL handle. */
 int rts_peel_kernels(const rts_peel_t* h, int32_t* block_kernel, int32_t* solve_kernel);
 
 /* Measured FP64 fused multiply-add rate of the current device in TFLOP/s (no

@@ -770,6 +770,17 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   if ((e = cudaMemset(h->d_flag, 0, sizeof(int))) != cudaSuccess) return bail(e, "clear flag");
   if ((e = cudaMemset(h->d_status, 0, (size_t)h->max_sources * sizeof(int))) != cudaSuccess)
     return bail(e, "clear status");
+  // the blocked schedule's tables, streams and solve set-up, and the Taylor
+  // cadence's moments and iterates, are allocated here too (the paper's Section 5
+  // advice), so a cadence allocates nothing
+  int rc = RTS_OK;
+  if (h->per_pass > 1) rc = ensure_block_workspace(h);
+  if (rc == RTS_OK && h->precision == RTS_PREC_MIXED) rc = taylor_setup(h);
+  if (rc != RTS_OK) {
+    const std::string m = h->err;
+    rts_peel_destroy(h);
+    return fail(nullptr, rc, m);
+  }
   *out = h;
   return RTS_OK;
 }
