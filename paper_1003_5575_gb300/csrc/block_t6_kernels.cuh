@@ -1,0 +1,528 @@
+// Blocked peel pass on the 5th-generation tensor cores, transposed form: the
+// same pass as k_block_pass (subtract the solved sources of block b from one
+// (baseline, time step) strip of channels, average the directions of block b+1),
+// with both contractions as tcgen05.mma kind::tf32 GEMMs whose operands the
+// CUDA cores form in O(sources x 16) or O(sources x channels / 16) work.
+//
+// The phasor of source k at channel c = 16 q + r factors as
+//   P_k(c) = T1_k[q] T2_k[r],  T1_k[q] = e^{2 pi i (A_k + 16 q B_k)},  T2_k[r] = e^{2 pi i r B_k}.
+//
+// subtraction  R(16 q + r, e) -= sum_k [M_k(e) conj(T2_k[r])] conj(T1_k[q])
+//   GEMM D_s[m, q] = sum_K A_s[m, K] B_s[q, K], M = 128 rows m = 8 r + 2 e + o
+//   (o: real or imaginary part of the output), K = 128 = (source k, re/im),
+//   N = NQ (the 16-channel tiles, rounded up to 16).  A_s = the real form of
+//   a_k(r, e) = M_k(e) conj(T2_k[r]) (rows o = 0: (a_re, -a_im), o = 1:
+//   (a_im, a_re)), written by the threads into TMEM; B_s = conj(T1) as
+//   (re, im) pairs along K in shared memory.  One 128-row tile whatever the
+//   channel count, and 64 x 16 x 4 operand products per step.
+// average      A_k(e) += sum_r T2_k[r] H_k(r, e),  H_k(r, e) = sum_q T1_k[q] R(16 q + r, e)
+//   GEMM D_a[m', n] = sum_K' A_a[m', K'] B_a[n, K'], M = 128 rows m' = 2 k + o,
+//   K' = 2 NQ = (q, re/im), N = 64 columns n = 4 r + e.  A_a = the real form
+//   of T1 (rows o = 0: (t_re, -t_im), o = 1: (t_im, t_re)) in TMEM; B_a = the
+//   new residual, written by the subtraction's epilogue in shared memory.
+//   The 16-term T2 contraction of H runs on the CUDA cores (32 FMAs a thread),
+//   summed over time steps with compensation.
+//
+// TF32 keeps 11 significand bits, so every operand is split x = hi + lo and
+// each product takes three MMAs, hi*hi + lo*hi + hi*lo.  The tensor cores'
+// FP32 accumulation does not round to nearest, so the hi*hi products go to
+// accumulators of 4 k-steps each and the (2^-11 smaller) cross terms to one
+// more; the epilogues add them in FP32 with round-to-nearest.
+//
+// One CTA of 16 warps per baseline (1 per SM: ~170 KB of shared memory, all 512
+// TMEM columns), looping over the time steps.  The strip of a time step
+// arrives by a bulk asynchronous copy one step ahead and the residual leaves
+// by one, so the CUDA cores move no visibility data to or from HBM.  A step:
+//   P1  subtraction MMAs   | beside them: T1 and T2 of the averaged sources
+//   P2  subtraction epilogue (residual into the strip and B_a), A_a into TMEM
+//   P3  average MMAs       | beside them: the residual's store, the next
+//                            step's B_s and T2 of the subtracted sources
+//   P4  average epilogue, the next step's A_s into TMEM
+// MMAs are issued by one lane in each of several warps that each commit to
+// the phase's mbarrier; warp 0 waits with bounded polls (a wait that runs out
+// sets *err and stops the pass, which the status read reports, after the
+// copies in flight have been waited for and TMEM is freed).
+// Limits: at most 64 sources per role, n_chan <= kT6MaxChan.
+#pragma once
+#include "block_kernels.cuh"
+#include "tc05.cuh"
+
+namespace rts {
+
+constexpr int kT6Threads = 512;
+constexpr int kT6Src = 64;                  // sources per role
+constexpr int kT6MaxChan = 768;             // NQ <= 48: 5 NQ accumulator columns beside A_s
+constexpr uint32_t kT6MaxPolls = 1u << 17;  // mbarrier polls (each up to 20 us) before giving up
+constexpr int kT6T2Row = 17;                // T2 table row stride (float2): conflict-free column reads
+// TMEM columns.  Subtraction: A_s hi [0, 128), lo [128, 256); hi*hi accumulators
+// g = 0..3 at 256 + g NQ, cross terms at 256 + 4 NQ.  Average: A_a hi [0, 2 NQ),
+// lo [2 NQ, 4 NQ); hi*hi accumulators g < NQ / 16 at 192 + 64 g, cross terms
+// after them.  Each phase starts once every read of the other's columns is done.
+constexpr uint32_t kT6ColSub = 256;
+constexpr uint32_t kT6ColAvg = 192;
+constexpr uint32_t kT6Cols = 512;
+
+// shared-memory layout (byte offsets) for NQ 16-channel tiles (16, 32 or 48)
+struct T6Smem {
+  int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, bar, total;
+  __host__ __device__ explicit T6Smem(int NQ) {
+    int o = 0;
+    strip = o; o += 2 * 16 * NQ * 32;            // two strips [16 NQ channels][4 pol][re, im]
+    bs_hi = o; o += NQ * 128 * 4;                // B_s [NQ rows][128 K], K-major
+    bs_lo = o; o += NQ * 128 * 4;
+    ba_hi = o; o += 64 * 2 * NQ * 4;             // B_a [64 rows][2 NQ K], K-major
+    ba_lo = o; o += 64 * 2 * NQ * 4;
+    t2s = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the subtracted sources [64][17] float2
+    t2a = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the averaged sources
+    mtab = o;  o += kT6Src * 4 * 8;              // model matrices [64][4] float2
+    ph = o;    o += 2 * kT6Src * 16;             // phases of the time step, both roles
+    bar = o;   o += 64;                          // mbarriers (sub, avg, load 0, load 1), TMEM address
+    total = o;
+  }
+};
+
+inline int t6_nq(int n_chan) { return (((n_chan + 15) >> 4) + 15) & ~15; }
+inline size_t t6_pass_smem(int n_chan) { return (size_t)T6Smem(t6_nq(n_chan)).total; }
+
+// TF32 rounding (to nearest, ties away from zero, as cvt.rna.tf32.f32 for
+// finite x below the FP32 maximum) by two integer operations
+__device__ __forceinline__ uint32_t t6_tf32(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+// x = hi + lo, hi the TF32 rounding of x, lo the exact remainder (the MMA reads
+// lo truncated to TF32: error below 2^-21 |x|)
+__device__ __forceinline__ float2 t6_split(float x) {
+  const float hi = __uint_as_float(t6_tf32(x));
+  return make_float2(hi, x - hi);
+}
+
+template <bool SUB, bool ACC>
+__global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a, int bk, int* err) {
+  using namespace tc05;
+  const int nq = (a.n_chan + 15) >> 4;
+  const int NQ = (nq + 15) & ~15;           // 16, 32 or 48
+  const int QW = NQ >> 2;                   // tiles per column-group warp: 4, 8 or 12
+  const int nmain_a = NQ >> 4;              // the average's hi*hi accumulators: 1, 2 or 3
+  const int n16 = 16 * NQ;
+  const uint32_t strip_bytes = (uint32_t)a.n_chan * 32u;
+  const T6Smem L(NQ);
+  extern __shared__ __align__(1024) unsigned char t6_smem[];
+  float* strip0 = reinterpret_cast<float*>(t6_smem + L.strip);
+  unsigned char* bs_hi = t6_smem + L.bs_hi;
+  unsigned char* bs_lo = t6_smem + L.bs_lo;
+  unsigned char* ba_hi = t6_smem + L.ba_hi;
+  unsigned char* ba_lo = t6_smem + L.ba_lo;
+  float2* t2s = reinterpret_cast<float2*>(t6_smem + L.t2s);
+  float2* t2a = reinterpret_cast<float2*>(t6_smem + L.t2a);
+  float2* mtab = reinterpret_cast<float2*>(t6_smem + L.mtab);
+  PhaseAB* ph = reinterpret_cast<PhaseAB*>(t6_smem + L.ph);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(t6_smem + L.bar);      // sub, avg, load 0, load 1
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 32);
+  float* part = reinterpret_cast<float*>(ba_hi);    // [4 cg][64 k][8]: B_a is free in P4
+
+  const int64_t bl = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qtr = warp & 3, cg = warp >> 2;
+  const uint32_t lane_base = (uint32_t)(32 * qtr) << 16;
+
+  if (warp == 0) tmem_alloc(tslot, kT6Cols);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 5);                 // the subtraction's 5 issuing lanes
+    mbar_init(&mbar[1], nmain_a + 1);       // the average's issuing lanes
+    mbar_init(&mbar[2], 1);                 // strip loads into buffer 0 and 1
+    mbar_init(&mbar[3], 1);
+  }
+  // padding channels of both strips stay zero (the copies never write them)
+  for (int i = tid; i < (n16 - a.n_chan) * 8; i += kT6Threads) {
+    strip0[a.n_chan * 8 + i] = 0.f;
+    strip0[(n16 + a.n_chan) * 8 + i] = 0.f;
+  }
+  if (SUB)
+    for (int i = tid; i < kT6Src * 4; i += kT6Threads) {
+      const int s = i >> 2, e = i & 3;
+      mtab[i] = s < a.n_sub ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
+    }
+  // a pass in which some CTA's wait already ran out does no more work
+  __shared__ int s_bad;
+  if (tid == 0) s_bad = *reinterpret_cast<volatile int*>(err);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  const uint64_t dbs_hi = desc_kmajor(smem_u32(bs_hi), 128, 4096), dbs_lo = desc_kmajor(smem_u32(bs_lo), 128, 4096);
+  const uint64_t dba_hi = desc_kmajor(smem_u32(ba_hi), 128, 64 * NQ), dba_lo = desc_kmajor(smem_u32(ba_lo), 128, 64 * NQ);
+
+  // strip of time step t -> buffer t & 1 (thread 0)
+  auto issue_load = [&](int t) {
+    const int b = t & 1;
+    mbar_expect_tx(&mbar[2 + b], strip_bytes);
+    bulk_load(strip0 + (size_t)b * n16 * 8, a.src + ((size_t)t * a.n_bl + bl) * a.n_chan * 2, strip_bytes,
+              &mbar[2 + b]);
+  };
+  // the phases of one role at time t (64 threads)
+  auto load_ph = [&](int t, bool sub) {
+    const int base = sub ? 0 : kT6Src;
+    if (tid >= base && tid < base + kT6Src) {
+      const int k = tid - base;
+      PhaseAB p;
+      p.a = 0; p.b = 0;
+      if (sub ? (SUB && k < a.n_sub) : (ACC && k < a.n_acc))
+        p = (sub ? a.ph_sub : a.ph_acc)[((size_t)bl * a.n_time + t) * bk + k];
+      ph[tid] = p;
+    }
+  };
+  // T2_k[r] of one role: [64][kT6T2Row]
+  auto t2_fill = [&](float2* t2, int base) {
+    for (int i = tid; i < kT6Src * 16; i += kT6Threads) {
+      const int k = i >> 4, r = i & 15;
+      t2[k * kT6T2Row + r] = phasor_hw((unsigned long long)r * ph[base + k].b);
+    }
+  };
+  // B_s = conj(T1_k[q]) of the subtracted sources: thread (q & 7 = lane & 7,
+  // k = (lane >> 3) + 4 warp) steps q by 8 with an exact 64-bit phase increment;
+  // its 8-byte (re, im) stores cover 16 distinct slots of each 128-byte line
+  auto bs_fill = [&]() {
+    const int ql = tid & 7, k = ((tid >> 3) & 3) + 4 * warp;
+    const PhaseAB p = ph[k];
+    const unsigned long long step = 128ull * p.b;
+    unsigned long long x = p.a + (unsigned long long)(16 * ql) * p.b;
+    for (int q = ql; q < NQ; q += 8, x += step) {
+      const float2 z = phasor_hw(x);
+      const float hr = __uint_as_float(t6_tf32(z.x)), hi = __uint_as_float(t6_tf32(-z.y));
+      const int o = kmaj_byte(q, 2 * k, 128);
+      *reinterpret_cast<float2*>(bs_hi + o) = make_float2(hr, hi);
+      *reinterpret_cast<float2*>(bs_lo + o) = make_float2(__uint_as_float(t6_tf32(z.x - hr)),
+                                                          __uint_as_float(t6_tf32(-z.y - hi)));
+    }
+  };
+  // A_s -> TMEM: warp (qtr, cg) writes rows m = 32 qtr + lane = 8 r + 2 e + o,
+  // sources 16 cg .. 16 cg + 15 (columns 32 cg .. 32 cg + 31, hi and lo)
+  auto as_store = [&]() {
+    const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1;
+    #pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t vh[16], vl[16];
+      #pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = 16 * cg + 8 * h + j;
+        const float2 m = mtab[4 * k + e], z = t2s[k * kT6T2Row + r];
+        const float ar = fmaf(m.x, z.x, m.y * z.y), ai = fmaf(m.y, z.x, -m.x * z.y);   // m conj(z)
+        const float v0 = o ? ai : ar, v1 = o ? ar : -ai;
+        const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
+        vh[2 * j] = h0;
+        vh[2 * j + 1] = h1;
+        vl[2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
+        vl[2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
+      }
+      const uint32_t col = 32 * cg + 16 * h;
+      tmem_st16(tmem + lane_base + col, vh);
+      tmem_st16(tmem + lane_base + 128 + col, vl);
+    }
+  };
+  // T1_k[q] of the averaged source k = 16 qtr + lane / 2 for the warp's tiles
+  // q = cg QW .. cg QW + QW - 1: the lane pair (o = 0, 1) computes even and odd
+  // tiles and exchanges them
+  auto aa_compute = [&](float2 (&t1v)[12]) {
+    const int k = 16 * qtr + (lane >> 1), o = lane & 1, q0 = cg * QW;
+    const PhaseAB p = ph[kT6Src + k];
+    const unsigned long long step = 32ull * p.b;
+    unsigned long long x = p.a + (unsigned long long)(16 * (q0 + o)) * p.b;
+    #pragma unroll
+    for (int jj = 0; jj < 6; ++jj) {
+      float2 mine = make_float2(0.f, 0.f);
+      if (2 * jj < QW) {
+        mine = phasor_hw(x);
+        x += step;
+      }
+      const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, 1), __shfl_xor_sync(0xffffffffu, mine.y, 1));
+      t1v[2 * jj] = o ? other : mine;
+      t1v[2 * jj + 1] = o ? mine : other;
+    }
+  };
+  // A_a -> TMEM: rows m' = 2 k + o, columns 2 q + i of the warp's tiles
+  auto aa_store = [&](const float2 (&t1v)[12]) {
+    const int o = lane & 1, q0 = cg * QW;
+    #pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      if (4 * ch < QW) {
+        uint32_t vh[8], vl[8];
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 t = t1v[4 * ch + u];
+          const float v0 = o ? t.y : t.x, v1 = o ? t.x : -t.y;
+          const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
+          vh[2 * u] = h0;
+          vh[2 * u + 1] = h1;
+          vl[2 * u] = __float_as_uint(v0 - __uint_as_float(h0));
+          vl[2 * u + 1] = __float_as_uint(v1 - __uint_as_float(h1));
+        }
+        const uint32_t col = 2 * (q0 + 4 * ch);
+        tmem_st8(tmem + lane_base + col, vh);
+        tmem_st8(tmem + lane_base + 2 * NQ + col, vl);
+      }
+    }
+  };
+  // the residual value x = R(16 q + r, e).o into B_a at (n = 4 r + e, K' = 2 q + o)
+  auto ba_put = [&](int n, int q, int o, float x) {
+    const float2 s2 = t6_split(x);
+    const int off = kmaj_byte(n, 2 * q + o, 2 * NQ);
+    *reinterpret_cast<float*>(ba_hi + off) = s2.x;
+    *reinterpret_cast<float*>(ba_lo + off) = s2.y;
+  };
+  // subtraction epilogue: warp (qtr, cg), rows m = 8 r + 2 e + o of lane, tiles
+  // q = cg QW .. ; the strip word (16 q + r) 8 + 2 e + o of the 32 lanes is 32
+  // consecutive words (conflict-free)
+  auto sub_epilogue = [&](float* strip) {
+    const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1, n = 4 * r + e, q0 = cg * QW;
+    const uint32_t base = tmem + lane_base + kT6ColSub + q0;
+    #pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      if (4 * ch < QW) {
+        float v[5][4];
+        #pragma unroll
+        for (int g = 0; g < 5; ++g) tmem_ld4(base + g * NQ + 4 * ch, v[g]);
+        tmem_wait_ld();
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + 4 * ch + u, c = 16 * q + r;
+          const float d = (((v[4][u] + v[0][u]) + v[1][u]) + v[2][u]) + v[3][u];
+          float x = 0.f;
+          if (c < a.n_chan) {
+            float* sp = strip + c * 8 + 2 * e + o;
+            x = *sp - d;
+            *sp = x;
+          }
+          if (ACC) ba_put(n, q, o, x);
+        }
+      }
+    }
+  };
+  // first pass: B_a straight from the strip
+  auto ba_from_strip = [&](const float* strip) {
+    const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1, n = 4 * r + e, q0 = cg * QW;
+    for (int j = 0; j < QW; ++j) {
+      const int q = q0 + j;
+      ba_put(n, q, o, strip[(16 * q + r) * 8 + 2 * e + o]);
+    }
+  };
+
+  // compensated sums of the averages across time steps: warps 0..3, lanes with
+  // o = 0 own source k = 16 qtr + lane / 2, values (re, im) of the 4 pols
+  float ks[8], kc[8];
+  #pragma unroll
+  for (int i = 0; i < 8; ++i) ks[i] = kc[i] = 0.f;
+  uint32_t par_sub = 0, par_avg = 0;
+  // thread 0: strip loads issued into / landed in buffers 0 and 1 (uses of each mbarrier)
+  int issued0 = 0, issued1 = 0, landed0 = 0, landed1 = 0;
+
+  if (tid == 0) {
+    issue_load(0);
+    issued0 = 1;
+  }
+  if (SUB) {                                 // the first step's subtraction operands
+    load_ph(0, true);
+    __syncthreads();
+    bs_fill();
+    t2_fill(t2s, 0);
+    __syncthreads();
+    as_store();
+    tmem_wait_st();
+    fence_smem_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+  }
+
+  for (int t = 0; t < a.n_time && !s_bad; ++t) {
+    const int buf = t & 1;
+    float* strip = strip0 + (size_t)buf * n16 * 8;
+    // ---- P1: subtraction MMAs; T1 and T2 of the averaged sources beside them
+    if (SUB && warp < 5 && lane == 0) {
+      const uint32_t id = idesc_tf32(128, NQ);
+      if (warp < 4) {                        // hi*hi, k-steps 4 warp .. 4 warp + 3
+        const uint32_t d = tmem + kT6ColSub + warp * NQ;
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int s = 4 * warp + u;
+          mma_ts(d, tmem + 8 * s, dbs_hi + 16 * s, id, u != 0);
+        }
+      } else {                               // lo*hi, then hi*lo, all 16 k-steps
+        const uint32_t d = tmem + kT6ColSub + 4 * NQ;
+        #pragma unroll
+        for (int s = 0; s < 16; ++s) mma_ts(d, tmem + 128 + 8 * s, dbs_hi + 16 * s, id, s != 0);
+        #pragma unroll
+        for (int s = 0; s < 16; ++s) mma_ts(d, tmem + 8 * s, dbs_lo + 16 * s, id, 1);
+      }
+      commit(&mbar[0]);
+    }
+    if (tid == 0 && t + 1 < a.n_time) {
+      if (SUB && t >= 1) bulk_wait_read();   // the residual store of step t - 1 has left buffer (t + 1) & 1
+      issue_load(t + 1);
+      if ((t + 1) & 1) ++issued1;
+      else ++issued0;
+    }
+    float2 t1v[12];
+    if (ACC) {
+      load_ph(t, false);
+      __syncthreads();
+      aa_compute(t1v);
+      t2_fill(t2a, kT6Src);
+    }
+    // ---- this step's strip has landed, the subtraction MMAs are complete
+    if (warp == 0) {
+      bool ok = mbar_wait(&mbar[2 + buf], (uint32_t)(t >> 1) & 1u, kT6MaxPolls);
+      if (ok && lane == 0) {
+        if (buf) landed1 = (t >> 1) + 1;
+        else landed0 = (t >> 1) + 1;
+      }
+      if (ok && SUB) ok = mbar_wait(&mbar[0], par_sub, kT6MaxPolls);
+      if (!ok && lane == 0) s_bad = 1;
+      fence_before_sync();
+    }
+    if (SUB) par_sub ^= 1;
+    __syncthreads();
+    fence_after_sync();
+    if (s_bad) break;
+    // ---- P2: residual into the strip and B_a; A_a into TMEM (A_s is done with)
+    if (SUB) sub_epilogue(strip);
+    else if (ACC) ba_from_strip(strip);
+    if (ACC) {
+      aa_store(t1v);
+      tmem_wait_st();
+    }
+    fence_smem_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    // ---- P3: average MMAs; the residual's store and the next step's
+    // subtraction tables beside them
+    if (ACC && warp <= nmain_a && lane == 0) {
+      const uint32_t id = idesc_tf32(128, 64);
+      const int nks = NQ >> 2;               // k-steps over K' = 2 NQ
+      if (warp < nmain_a) {                  // hi*hi, k-steps 4 warp .. 4 warp + 3
+        const uint32_t d = tmem + kT6ColAvg + 64 * warp;
+        #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int s = 4 * warp + u;
+          mma_ts(d, tmem + 8 * s, dba_hi + 16 * s, id, u != 0);
+        }
+      } else {
+        const uint32_t d = tmem + kT6ColAvg + 64 * nmain_a;
+        for (int s = 0; s < nks; ++s) mma_ts(d, tmem + 2 * NQ + 8 * s, dba_hi + 16 * s, id, s != 0);
+        for (int s = 0; s < nks; ++s) mma_ts(d, tmem + 8 * s, dba_lo + 16 * s, id, 1);
+      }
+      commit(&mbar[1]);
+    }
+    if (SUB && tid == 0) {
+      bulk_store(a.dst + ((size_t)t * a.n_bl + bl) * a.n_chan * 2, strip, strip_bytes);
+      bulk_commit();
+    }
+    const bool next_sub = SUB && t + 1 < a.n_time;
+    if (next_sub) {
+      load_ph(t + 1, true);
+      __syncthreads();
+      bs_fill();
+      t2_fill(t2s, 0);
+    }
+    // ---- P4: average epilogue; the next step's A_s into TMEM
+    if (ACC) {
+      if (warp == 0) {
+        if (!mbar_wait(&mbar[1], par_avg, kT6MaxPolls) && lane == 0) s_bad = 1;
+        fence_before_sync();
+      }
+      par_avg ^= 1;
+      __syncthreads();
+      fence_after_sync();
+      {
+        // warp (qtr, cg): rows m' = 2 k + o of lane, columns n = 4 r + e of
+        // r = 4 cg .. 4 cg + 3; G = H_o(r, e) summed over the accumulators
+        const int k = 16 * qtr + (lane >> 1), o = lane & 1;
+        const uint32_t base = tmem + lane_base + kT6ColAvg + 16 * cg;
+        float h[4][16];
+        tmem_ld16(base + 64 * nmain_a, h[0]);
+        #pragma unroll
+        for (int g = 0; g < 3; ++g)
+          if (g < nmain_a) tmem_ld16(base + 64 * g, h[1 + g]);
+        tmem_wait_ld();
+        float pr[4] = {0.f, 0.f, 0.f, 0.f}, pi[4] = {0.f, 0.f, 0.f, 0.f};
+        #pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          const float2 z = t2a[k * kT6T2Row + 4 * cg + rr];
+          // o = 0 holds Re H: A += T2 Re H; o = 1 holds Im H: A += i T2 Im H
+          const float wr = o ? -z.y : z.x, wi = o ? z.x : z.y;
+          #pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float H = h[0][4 * rr + e];
+            #pragma unroll
+            for (int g = 0; g < 3; ++g)
+              if (g < nmain_a) H += h[1 + g][4 * rr + e];
+            pr[e] = fmaf(wr, H, pr[e]);
+            pi[e] = fmaf(wi, H, pi[e]);
+          }
+        }
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          pr[e] += __shfl_xor_sync(0xffffffffu, pr[e], 1);
+          pi[e] += __shfl_xor_sync(0xffffffffu, pi[e], 1);
+        }
+        if (o == 0) {
+          float4* dst = reinterpret_cast<float4*>(part + (cg * kT6Src + k) * 8);
+          dst[0] = make_float4(pr[0], pi[0], pr[1], pi[1]);
+          dst[1] = make_float4(pr[2], pi[2], pr[3], pi[3]);
+        }
+      }
+      fence_before_sync();
+      __syncthreads();                       // accumulators read by every warp; parts written
+      fence_after_sync();
+      if (cg == 0 && (lane & 1) == 0) {
+        const int k = 16 * qtr + (lane >> 1);
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float x = part[k * 8 + i];
+          #pragma unroll
+          for (int c = 1; c < 4; ++c) x += part[(c * kT6Src + k) * 8 + i];
+          const float y = x - kc[i];
+          const float tt = ks[i] + y;
+          kc[i] = (tt - ks[i]) - y;
+          ks[i] = tt;
+        }
+      }
+    } else if (next_sub) {
+      __syncthreads();                       // T2 of the next step's subtraction ready
+    }
+    if (next_sub) {
+      as_store();
+      tmem_wait_st();
+    }
+    fence_smem_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (s_bad) break;
+  }
+
+  if (ACC && !s_bad && cg == 0 && (lane & 1) == 0) {
+    const int k = 16 * qtr + (lane >> 1);
+    if (k < a.n_acc)
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const double re = (double)ks[2 * e] - (double)kc[2 * e];
+        const double im = (double)ks[2 * e + 1] - (double)kc[2 * e + 1];
+        a.avg[((size_t)k * a.n_bl + bl) * 4 + e] = make_float2((float)(re * a.inv_n), (float)(im * a.inv_n));
+      }
+  }
+  if (tid == 0) {
+    // a load still in flight after a failed wait must land before the CTA's
+    // shared memory goes away (bounded); stores are waited for unconditionally
+    for (int u = landed0; u < issued0; ++u)
+      if (!mbar_wait(&mbar[2], (uint32_t)u & 1u, kT6MaxPolls)) break;
+    for (int u = landed1; u < issued1; ++u)
+      if (!mbar_wait(&mbar[3], (uint32_t)u & 1u, kT6MaxPolls)) break;
+    bulk_wait_all();
+    if (s_bad) atomicExch(err, 1);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 0) tmem_dealloc(tmem, kT6Cols);
+}
+
+}  // namespace rts
