@@ -17,11 +17,13 @@
 //   channel count, and 64 x 16 x 4 operand products per step.
 // average      A_k(e) += sum_r T2_k[r] H_k(r, e),  H_k(r, e) = sum_q T1_k[q] R(16 q + r, e)
 //   GEMM D_a[m', n] = sum_K' A_a[m', K'] B_a[n, K'], M = 128 rows m' = 2 k + o,
-//   K' = 2 NQ = (q, re/im), N = 64 columns n = 4 r + e.  A_a = the real form
-//   of T1 (rows o = 0: (t_re, -t_im), o = 1: (t_im, t_re)) in TMEM; B_a = the
-//   new residual, written by the subtraction's epilogue in shared memory.
-//   The 16-term T2 contraction of H runs on the CUDA cores (32 FMAs a thread),
-//   summed over time steps with compensation.
+//   K' = 2 NQ = (re/im i, q) at i NQ + q, N = 64 columns n = 4 r + e.  A_a =
+//   the real form of T1 (row o = 0: t_re at i = 0, -t_im at i = 1; row o = 1:
+//   t_im, t_re) in TMEM; B_a = the new residual, written by the subtraction's
+//   epilogue in shared memory (4 consecutive tiles of one part per 16-byte
+//   store).  The 16-term T2 contraction of H runs on the CUDA cores (32 FMAs a
+//   thread) beside the next step's subtraction MMAs, summed over time steps
+//   with compensation.
 //
 // TF32 keeps 11 significand bits, so every operand is split x = hi + lo and
 // each product takes three MMAs, hi*hi + lo*hi + hi*lo.  The tensor cores'
@@ -33,11 +35,12 @@
 // TMEM columns), looping over the time steps.  The strip of a time step
 // arrives by a bulk asynchronous copy one step ahead and the residual leaves
 // by one, so the CUDA cores move no visibility data to or from HBM.  A step:
-//   P1  subtraction MMAs   | beside them: T1 and T2 of the averaged sources
+//   P1  subtraction MMAs   | beside them: the previous step's T2 contraction,
+//                            T1 and T2 of the averaged sources
 //   P2  subtraction epilogue (residual into the strip and B_a), A_a into TMEM
 //   P3  average MMAs       | beside them: the residual's store, the next
 //                            step's B_s and T2 of the subtracted sources
-//   P4  average epilogue, the next step's A_s into TMEM
+//   P4  the average's accumulators into registers, the next step's A_s into TMEM
 // MMAs are issued by one lane in each of several warps that each commit to
 // the phase's mbarrier; warp 0 waits with bounded polls (a wait that runs out
 // sets *err and stops the pass, which the status read reports, after the
@@ -64,7 +67,7 @@ constexpr uint32_t kT6Cols = 512;
 
 // shared-memory layout (byte offsets) for NQ 16-channel tiles (16, 32 or 48)
 struct T6Smem {
-  int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, bar, total;
+  int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, kahan, bar, total;
   __host__ __device__ explicit T6Smem(int NQ) {
     int o = 0;
     strip = o; o += 2 * 16 * NQ * 32;            // two strips [16 NQ channels][4 pol][re, im]
@@ -76,6 +79,7 @@ struct T6Smem {
     t2a = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the averaged sources
     mtab = o;  o += kT6Src * 4 * 8;              // model matrices [64][4] float2
     ph = o;    o += 2 * kT6Src * 16;             // phases of the time step, both roles
+    kahan = o; o += kT6Src * 17 * 4;             // compensated sums of the averages [64][8 sums, 8 compensations, pad]
     bar = o;   o += 64;                          // mbarriers (sub, avg, load 0, load 1), TMEM address
     total = o;
   }
@@ -117,6 +121,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   uint64_t* mbar = reinterpret_cast<uint64_t*>(t6_smem + L.bar);      // sub, avg, load 0, load 1
   uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 32);
   float* part = reinterpret_cast<float*>(ba_hi);    // [4 cg][64 k][8]: B_a is free in P4
+  float* kahan = reinterpret_cast<float*>(t6_smem + L.kahan);
 
   const int64_t bl = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qtr = warp & 3, cg = warp >> 2;
@@ -139,6 +144,8 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       const int s = i >> 2, e = i & 3;
       mtab[i] = s < a.n_sub ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
     }
+  if (ACC)
+    for (int i = tid; i < kT6Src * 17; i += kT6Threads) kahan[i] = 0.f;
   // a pass in which some CTA's wait already ran out does no more work
   __shared__ int s_bad;
   if (tid == 0) s_bad = *reinterpret_cast<volatile int*>(err);
@@ -193,28 +200,36 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
                                                           __uint_as_float(t6_tf32(-z.y - hi)));
     }
   };
-  // A_s -> TMEM: warp (qtr, cg) writes rows m = 32 qtr + lane = 8 r + 2 e + o,
-  // sources 16 cg .. 16 cg + 15 (columns 32 cg .. 32 cg + 31, hi and lo)
-  auto as_store = [&]() {
+  // A_s of warp (qtr, cg): rows m = 32 qtr + lane = 8 r + 2 e + o, sources
+  // 16 cg .. 16 cg + 15 (columns 32 cg .. 32 cg + 31), hi and lo, formed in
+  // registers (beside the average's MMAs) and then written to TMEM
+  auto as_compute = [&](uint32_t (&vh)[32], uint32_t (&vl)[32]) {
     const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1;
     #pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = 16 * cg + j;
+      const float2 m = mtab[4 * k + e], z = t2s[k * kT6T2Row + r];
+      const float ar = fmaf(m.x, z.x, m.y * z.y), ai = fmaf(m.y, z.x, -m.x * z.y);   // m conj(z)
+      const float v0 = o ? ai : ar, v1 = o ? ar : -ai;
+      const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
+      vh[2 * j] = h0;
+      vh[2 * j + 1] = h1;
+      vl[2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
+      vl[2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
+    }
+  };
+  auto as_write = [&](const uint32_t (&vh)[32], const uint32_t (&vl)[32]) {
+    #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      uint32_t vh[16], vl[16];
+      uint32_t x[16], y[16];
       #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int k = 16 * cg + 8 * h + j;
-        const float2 m = mtab[4 * k + e], z = t2s[k * kT6T2Row + r];
-        const float ar = fmaf(m.x, z.x, m.y * z.y), ai = fmaf(m.y, z.x, -m.x * z.y);   // m conj(z)
-        const float v0 = o ? ai : ar, v1 = o ? ar : -ai;
-        const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
-        vh[2 * j] = h0;
-        vh[2 * j + 1] = h1;
-        vl[2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
-        vl[2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
+      for (int i = 0; i < 16; ++i) {
+        x[i] = vh[16 * h + i];
+        y[i] = vl[16 * h + i];
       }
       const uint32_t col = 32 * cg + 16 * h;
-      tmem_st16(tmem + lane_base + col, vh);
-      tmem_st16(tmem + lane_base + 128 + col, vl);
+      tmem_st16(tmem + lane_base + col, x);
+      tmem_st16(tmem + lane_base + 128 + col, y);
     }
   };
   // T1_k[q] of the averaged source k = 16 qtr + lane / 2 for the warp's tiles
@@ -237,35 +252,41 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       t1v[2 * jj + 1] = o ? mine : other;
     }
   };
-  // A_a -> TMEM: rows m' = 2 k + o, columns 2 q + i of the warp's tiles
+  // A_a -> TMEM: rows m' = 2 k + o, columns i NQ + q of the warp's tiles
   auto aa_store = [&](const float2 (&t1v)[12]) {
     const int o = lane & 1, q0 = cg * QW;
     #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       if (4 * ch < QW) {
-        uint32_t vh[8], vl[8];
+        uint32_t h0[4], l0[4], h1[4], l1[4];
         #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float2 t = t1v[4 * ch + u];
-          const float v0 = o ? t.y : t.x, v1 = o ? t.x : -t.y;
-          const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
-          vh[2 * u] = h0;
-          vh[2 * u + 1] = h1;
-          vl[2 * u] = __float_as_uint(v0 - __uint_as_float(h0));
-          vl[2 * u + 1] = __float_as_uint(v1 - __uint_as_float(h1));
+          const float v0 = o ? t.y : t.x, v1 = o ? t.x : -t.y;     // i = 0, i = 1
+          h0[u] = t6_tf32(v0);
+          h1[u] = t6_tf32(v1);
+          l0[u] = __float_as_uint(v0 - __uint_as_float(h0[u]));
+          l1[u] = __float_as_uint(v1 - __uint_as_float(h1[u]));
         }
-        const uint32_t col = 2 * (q0 + 4 * ch);
-        tmem_st8(tmem + lane_base + col, vh);
-        tmem_st8(tmem + lane_base + 2 * NQ + col, vl);
+        const uint32_t col = q0 + 4 * ch;
+        tmem_st4(tmem + lane_base + col, h0);
+        tmem_st4(tmem + lane_base + NQ + col, h1);
+        tmem_st4(tmem + lane_base + 2 * NQ + col, l0);
+        tmem_st4(tmem + lane_base + 3 * NQ + col, l1);
       }
     }
   };
-  // the residual value x = R(16 q + r, e).o into B_a at (n = 4 r + e, K' = 2 q + o)
-  auto ba_put = [&](int n, int q, int o, float x) {
-    const float2 s2 = t6_split(x);
-    const int off = kmaj_byte(n, 2 * q + o, 2 * NQ);
-    *reinterpret_cast<float*>(ba_hi + off) = s2.x;
-    *reinterpret_cast<float*>(ba_lo + off) = s2.y;
+  // residual values x[u] = R(16 (q + u) + r, e).o, u = 0..3, into B_a at
+  // (n = 4 r + e, K' = o NQ + q + u): one 16-byte store each for hi and lo
+  auto ba_put4 = [&](int n, int q, int o, const float (&x)[4]) {
+    float4 h, l;
+    float2 s2 = t6_split(x[0]); h.x = s2.x; l.x = s2.y;
+    s2 = t6_split(x[1]); h.y = s2.x; l.y = s2.y;
+    s2 = t6_split(x[2]); h.z = s2.x; l.z = s2.y;
+    s2 = t6_split(x[3]); h.w = s2.x; l.w = s2.y;
+    const int off = kmaj_byte(n, o * NQ + q, 2 * NQ);
+    *reinterpret_cast<float4*>(ba_hi + off) = h;
+    *reinterpret_cast<float4*>(ba_lo + off) = l;
   };
   // subtraction epilogue: warp (qtr, cg), rows m = 8 r + 2 e + o of lane, tiles
   // q = cg QW .. ; the strip word (16 q + r) 8 + 2 e + o of the 32 lanes is 32
@@ -280,35 +301,80 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
         #pragma unroll
         for (int g = 0; g < 5; ++g) tmem_ld4(base + g * NQ + 4 * ch, v[g]);
         tmem_wait_ld();
+        float x[4];
         #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int q = q0 + 4 * ch + u, c = 16 * q + r;
+          const int c = 16 * (q0 + 4 * ch + u) + r;
           const float d = (((v[4][u] + v[0][u]) + v[1][u]) + v[2][u]) + v[3][u];
-          float x = 0.f;
+          x[u] = 0.f;
           if (c < a.n_chan) {
             float* sp = strip + c * 8 + 2 * e + o;
-            x = *sp - d;
-            *sp = x;
+            x[u] = *sp - d;
+            *sp = x[u];
           }
-          if (ACC) ba_put(n, q, o, x);
         }
+        if (ACC) ba_put4(n, q0 + 4 * ch, o, x);
       }
     }
   };
   // first pass: B_a straight from the strip
   auto ba_from_strip = [&](const float* strip) {
     const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1, n = 4 * r + e, q0 = cg * QW;
-    for (int j = 0; j < QW; ++j) {
-      const int q = q0 + j;
-      ba_put(n, q, o, strip[(16 * q + r) * 8 + 2 * e + o]);
+    for (int j = 0; j < QW; j += 4) {
+      float x[4];
+      #pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = strip[(16 * (q0 + j + u) + r) * 8 + 2 * e + o];
+      ba_put4(n, q0 + j, o, x);
+    }
+  };
+  // the T2 contraction of one step's H (rows m' = 2 k + o of lane, columns
+  // n = 4 r + e of r = 4 cg .. 4 cg + 3): o = 0 holds Re H (A += T2 Re H), o = 1
+  // Im H (A += i T2 Im H); the lane pair's sums meet by a shuffle and the four
+  // column groups' in part[cg][k]
+  auto avg_contract = [&](const float (&H)[16]) {
+    const int k = 16 * qtr + (lane >> 1), o = lane & 1;
+    float pr[4] = {0.f, 0.f, 0.f, 0.f}, pi[4] = {0.f, 0.f, 0.f, 0.f};
+    #pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const float2 z = t2a[k * kT6T2Row + 4 * cg + rr];
+      const float wr = o ? -z.y : z.x, wi = o ? z.x : z.y;
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        pr[e] = fmaf(wr, H[4 * rr + e], pr[e]);
+        pi[e] = fmaf(wi, H[4 * rr + e], pi[e]);
+      }
+    }
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      pr[e] += __shfl_xor_sync(0xffffffffu, pr[e], 1);
+      pi[e] += __shfl_xor_sync(0xffffffffu, pi[e], 1);
+    }
+    if (o == 0) {
+      float4* dst = reinterpret_cast<float4*>(part + (cg * kT6Src + k) * 8);
+      dst[0] = make_float4(pr[0], pi[0], pr[1], pi[1]);
+      dst[1] = make_float4(pr[2], pi[2], pr[3], pi[3]);
+    }
+  };
+  // compensated accumulation of the four column groups' sums (fixed order)
+  // into kahan[17 k ..] = (8 sums, 8 compensations): warps 0..3, even lanes
+  auto avg_accumulate = [&]() {
+    if (cg == 0 && (lane & 1) == 0) {
+      const int k = 16 * qtr + (lane >> 1);
+      float* ks = kahan + 17 * k;
+      #pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float x = part[k * 8 + i];
+        #pragma unroll
+        for (int c = 1; c < 4; ++c) x += part[(c * kT6Src + k) * 8 + i];
+        const float y = x - ks[8 + i];
+        const float tt = ks[i] + y;
+        ks[8 + i] = (tt - ks[i]) - y;
+        ks[i] = tt;
+      }
     }
   };
 
-  // compensated sums of the averages across time steps: warps 0..3, lanes with
-  // o = 0 own source k = 16 qtr + lane / 2, values (re, im) of the 4 pols
-  float ks[8], kc[8];
-  #pragma unroll
-  for (int i = 0; i < 8; ++i) ks[i] = kc[i] = 0.f;
+  float H[16];                               // the average's H of the last step, this thread's columns
   uint32_t par_sub = 0, par_avg = 0;
   // thread 0: strip loads issued into / landed in buffers 0 and 1 (uses of each mbarrier)
   int issued0 = 0, issued1 = 0, landed0 = 0, landed1 = 0;
@@ -317,13 +383,15 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     issue_load(0);
     issued0 = 1;
   }
+  uint32_t as_hi[32], as_lo[32];             // the next step's A_s (subtraction passes)
   if (SUB) {                                 // the first step's subtraction operands
     load_ph(0, true);
     __syncthreads();
     bs_fill();
     t2_fill(t2s, 0);
     __syncthreads();
-    as_store();
+    as_compute(as_hi, as_lo);
+    as_write(as_hi, as_lo);
     tmem_wait_st();
     fence_smem_async();
     fence_before_sync();
@@ -361,8 +429,10 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     }
     float2 t1v[12];
     if (ACC) {
+      if (t > 0) avg_contract(H);            // the previous step's H with its T2 (still in t2a)
       load_ph(t, false);
-      __syncthreads();
+      __syncthreads();                       // parts written; t2a free
+      if (t > 0) avg_accumulate();
       aa_compute(t1v);
       t2_fill(t2a, kT6Src);
     }
@@ -396,7 +466,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     // subtraction tables beside them
     if (ACC && warp <= nmain_a && lane == 0) {
       const uint32_t id = idesc_tf32(128, 64);
-      const int nks = NQ >> 2;               // k-steps over K' = 2 NQ
+      const int nks = NQ >> 2;               // k-steps over K' = 2 NQ (i NQ + q)
       if (warp < nmain_a) {                  // hi*hi, k-steps 4 warp .. 4 warp + 3
         const uint32_t d = tmem + kT6ColAvg + 64 * warp;
         #pragma unroll
@@ -421,8 +491,11 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       __syncthreads();
       bs_fill();
       t2_fill(t2s, 0);
+      __syncthreads();
+      as_compute(as_hi, as_lo);
     }
-    // ---- P4: average epilogue; the next step's A_s into TMEM
+    // ---- P4: the average's accumulators into registers (H = the sum of its
+    // hi*hi and cross-term accumulators); the next step's A_s into TMEM
     if (ACC) {
       if (warp == 0) {
         if (!mbar_wait(&mbar[1], par_avg, kT6MaxPolls) && lane == 0) s_bad = 1;
@@ -431,65 +504,25 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       par_avg ^= 1;
       __syncthreads();
       fence_after_sync();
-      {
-        // warp (qtr, cg): rows m' = 2 k + o of lane, columns n = 4 r + e of
-        // r = 4 cg .. 4 cg + 3; G = H_o(r, e) summed over the accumulators
-        const int k = 16 * qtr + (lane >> 1), o = lane & 1;
-        const uint32_t base = tmem + lane_base + kT6ColAvg + 16 * cg;
-        float h[4][16];
-        tmem_ld16(base + 64 * nmain_a, h[0]);
-        #pragma unroll
-        for (int g = 0; g < 3; ++g)
-          if (g < nmain_a) tmem_ld16(base + 64 * g, h[1 + g]);
-        tmem_wait_ld();
-        float pr[4] = {0.f, 0.f, 0.f, 0.f}, pi[4] = {0.f, 0.f, 0.f, 0.f};
-        #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          const float2 z = t2a[k * kT6T2Row + 4 * cg + rr];
-          // o = 0 holds Re H: A += T2 Re H; o = 1 holds Im H: A += i T2 Im H
-          const float wr = o ? -z.y : z.x, wi = o ? z.x : z.y;
+      const uint32_t base = tmem + lane_base + kT6ColAvg + 16 * cg;
+      tmem_ld16(base + 64 * nmain_a, H);
+      #pragma unroll
+      for (int g = 0; g < 3; ++g) {
+        if (g < nmain_a) {
+          float h[16];
+          tmem_ld16(base + 64 * g, h);
+          tmem_wait_ld();
           #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float H = h[0][4 * rr + e];
-            #pragma unroll
-            for (int g = 0; g < 3; ++g)
-              if (g < nmain_a) H += h[1 + g][4 * rr + e];
-            pr[e] = fmaf(wr, H, pr[e]);
-            pi[e] = fmaf(wi, H, pi[e]);
-          }
-        }
-        #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          pr[e] += __shfl_xor_sync(0xffffffffu, pr[e], 1);
-          pi[e] += __shfl_xor_sync(0xffffffffu, pi[e], 1);
-        }
-        if (o == 0) {
-          float4* dst = reinterpret_cast<float4*>(part + (cg * kT6Src + k) * 8);
-          dst[0] = make_float4(pr[0], pi[0], pr[1], pi[1]);
-          dst[1] = make_float4(pr[2], pi[2], pr[3], pi[3]);
+          for (int i = 0; i < 16; ++i) H[i] += h[i];
         }
       }
+      tmem_wait_ld();
       fence_before_sync();
-      __syncthreads();                       // accumulators read by every warp; parts written
+      __syncthreads();                       // every warp has read its accumulator columns
       fence_after_sync();
-      if (cg == 0 && (lane & 1) == 0) {
-        const int k = 16 * qtr + (lane >> 1);
-        #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float x = part[k * 8 + i];
-          #pragma unroll
-          for (int c = 1; c < 4; ++c) x += part[(c * kT6Src + k) * 8 + i];
-          const float y = x - kc[i];
-          const float tt = ks[i] + y;
-          kc[i] = (tt - ks[i]) - y;
-          ks[i] = tt;
-        }
-      }
-    } else if (next_sub) {
-      __syncthreads();                       // T2 of the next step's subtraction ready
     }
     if (next_sub) {
-      as_store();
+      as_write(as_hi, as_lo);
       tmem_wait_st();
     }
     fence_smem_async();
@@ -499,13 +532,19 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     if (s_bad) break;
   }
 
+  if (ACC && !s_bad) {                       // the last step's contraction
+    avg_contract(H);
+    __syncthreads();
+    avg_accumulate();
+  }
   if (ACC && !s_bad && cg == 0 && (lane & 1) == 0) {
     const int k = 16 * qtr + (lane >> 1);
+    const float* ks = kahan + 17 * k;
     if (k < a.n_acc)
       #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const double re = (double)ks[2 * e] - (double)kc[2 * e];
-        const double im = (double)ks[2 * e + 1] - (double)kc[2 * e + 1];
+        const double re = (double)ks[2 * e] - (double)ks[8 + 2 * e];
+        const double im = (double)ks[2 * e + 1] - (double)ks[8 + 2 * e + 1];
         a.avg[((size_t)k * a.n_bl + bl) * 4 + e] = make_float2((float)(re * a.inv_n), (float)(im * a.inv_n));
       }
   }
