@@ -41,10 +41,12 @@
 //   P3  average MMAs       | beside them: the residual's store, the next
 //                            step's B_s and T2 of the subtracted sources
 //   P4  the average's accumulators into registers, the next step's A_s into TMEM
-// MMAs are issued by one lane in each of several warps that each commit to
-// the phase's mbarrier; warp 0 waits with bounded polls (a wait that runs out
-// sets *err and stops the pass, which the status read reports, after the
-// copies in flight have been waited for and TMEM is freed).
+// A 17th warp issues every MMA: an issuing thread stalls while the tensor
+// core's queue drains (a few tens of cycles per MMA), so the 16 compute warps,
+// which meet at a named barrier of their own, never wait for it; operands-ready
+// and MMAs-done mbarriers hand each phase between them.  Every wait is bounded
+// (a wait that runs out sets *err and stops the pass, which the status read
+// reports, after the copies in flight have been waited for and TMEM is freed).
 // Limits: at most 64 sources per role, n_chan <= kT6MaxChan.
 #pragma once
 #include "block_kernels.cuh"
@@ -52,7 +54,8 @@
 
 namespace rts {
 
-constexpr int kT6Threads = 512;
+constexpr int kT6Compute = 512;             // 16 compute warps (4 per TMEM lane quarter)
+constexpr int kT6Threads = kT6Compute + 32;  // and one warp whose lane 0 issues every MMA
 constexpr int kT6Src = 64;                  // sources per role
 constexpr int kT6MaxChan = 768;             // NQ <= 48: 5 NQ accumulator columns beside A_s
 constexpr uint32_t kT6MaxPolls = 1u << 17;  // mbarrier polls (each up to 20 us) before giving up
@@ -80,7 +83,8 @@ struct T6Smem {
     mtab = o;  o += kT6Src * 4 * 8;              // model matrices [64][4] float2
     ph = o;    o += 2 * kT6Src * 16;             // phases of the time step, both roles
     kahan = o; o += kT6Src * 17 * 4;             // compensated sums of the averages [64][8 sums, 8 compensations, pad]
-    bar = o;   o += 64;                          // mbarriers (sub, avg, load 0, load 1), TMEM address
+    bar = o;   o += 64;                          // mbarriers (sub done, avg done, load 0, load 1, sub
+                                                 // operands ready, avg operands ready), TMEM address
     total = o;
   }
 };
@@ -118,8 +122,8 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   float2* t2a = reinterpret_cast<float2*>(t6_smem + L.t2a);
   float2* mtab = reinterpret_cast<float2*>(t6_smem + L.mtab);
   PhaseAB* ph = reinterpret_cast<PhaseAB*>(t6_smem + L.ph);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(t6_smem + L.bar);      // sub, avg, load 0, load 1
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 32);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(t6_smem + L.bar);      // see T6Smem::bar
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 48);
   float* part = reinterpret_cast<float*>(ba_hi);    // [4 cg][64 k][8]: B_a is free in P4
   float* kahan = reinterpret_cast<float*>(t6_smem + L.kahan);
 
@@ -129,23 +133,21 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
 
   if (warp == 0) tmem_alloc(tslot, kT6Cols);
   if (tid == 0) {
-    mbar_init(&mbar[0], 5);                 // the subtraction's 5 issuing lanes
-    mbar_init(&mbar[1], nmain_a + 1);       // the average's issuing lanes
-    mbar_init(&mbar[2], 1);                 // strip loads into buffer 0 and 1
-    mbar_init(&mbar[3], 1);
+    for (int i = 0; i < 6; ++i) mbar_init(&mbar[i], 1);   // each completed by one arrival (or commit)
   }
+  const bool compute = tid < kT6Compute;
   // padding channels of both strips stay zero (the copies never write them)
-  for (int i = tid; i < (n16 - a.n_chan) * 8; i += kT6Threads) {
+  for (int i = tid; compute && i < (n16 - a.n_chan) * 8; i += kT6Compute) {
     strip0[a.n_chan * 8 + i] = 0.f;
     strip0[(n16 + a.n_chan) * 8 + i] = 0.f;
   }
   if (SUB)
-    for (int i = tid; i < kT6Src * 4; i += kT6Threads) {
+    for (int i = tid; compute && i < kT6Src * 4; i += kT6Compute) {
       const int s = i >> 2, e = i & 3;
       mtab[i] = s < a.n_sub ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
     }
   if (ACC)
-    for (int i = tid; i < kT6Src * 17; i += kT6Threads) kahan[i] = 0.f;
+    for (int i = tid; compute && i < kT6Src * 17; i += kT6Compute) kahan[i] = 0.f;
   // a pass in which some CTA's wait already ran out does no more work
   __shared__ int s_bad;
   if (tid == 0) s_bad = *reinterpret_cast<volatile int*>(err);
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   };
   // T2_k[r] of one role: [64][kT6T2Row]
   auto t2_fill = [&](float2* t2, int base) {
-    for (int i = tid; i < kT6Src * 16; i += kT6Threads) {
+    for (int i = tid; i < kT6Src * 16; i += kT6Compute) {
       const int k = i >> 4, r = i & 15;
       t2[k * kT6T2Row + r] = phasor_hw((unsigned long long)r * ph[base + k].b);
     }
@@ -200,36 +202,28 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
                                                           __uint_as_float(t6_tf32(-z.y - hi)));
     }
   };
-  // A_s of warp (qtr, cg): rows m = 32 qtr + lane = 8 r + 2 e + o, sources
-  // 16 cg .. 16 cg + 15 (columns 32 cg .. 32 cg + 31), hi and lo, formed in
-  // registers (beside the average's MMAs) and then written to TMEM
-  auto as_compute = [&](uint32_t (&vh)[32], uint32_t (&vl)[32]) {
+  // A_s -> TMEM: warp (qtr, cg) writes rows m = 32 qtr + lane = 8 r + 2 e + o,
+  // sources 16 cg .. 16 cg + 15 (columns 32 cg .. 32 cg + 31, hi and lo)
+  auto as_store = [&]() {
     const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1;
     #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int k = 16 * cg + j;
-      const float2 m = mtab[4 * k + e], z = t2s[k * kT6T2Row + r];
-      const float ar = fmaf(m.x, z.x, m.y * z.y), ai = fmaf(m.y, z.x, -m.x * z.y);   // m conj(z)
-      const float v0 = o ? ai : ar, v1 = o ? ar : -ai;
-      const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
-      vh[2 * j] = h0;
-      vh[2 * j + 1] = h1;
-      vl[2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
-      vl[2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
-    }
-  };
-  auto as_write = [&](const uint32_t (&vh)[32], const uint32_t (&vl)[32]) {
-    #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      uint32_t x[16], y[16];
+      uint32_t vh[16], vl[16];
       #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        x[i] = vh[16 * h + i];
-        y[i] = vl[16 * h + i];
+      for (int j = 0; j < 8; ++j) {
+        const int k = 16 * cg + 8 * h + j;
+        const float2 m = mtab[4 * k + e], z = t2s[k * kT6T2Row + r];
+        const float ar = fmaf(m.x, z.x, m.y * z.y), ai = fmaf(m.y, z.x, -m.x * z.y);   // m conj(z)
+        const float v0 = o ? ai : ar, v1 = o ? ar : -ai;
+        const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
+        vh[2 * j] = h0;
+        vh[2 * j + 1] = h1;
+        vl[2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
+        vl[2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
       }
       const uint32_t col = 32 * cg + 16 * h;
-      tmem_st16(tmem + lane_base + col, x);
-      tmem_st16(tmem + lane_base + 128 + col, y);
+      tmem_st16(tmem + lane_base + col, vh);
+      tmem_st16(tmem + lane_base + 128 + col, vl);
     }
   };
   // T1_k[q] of the averaged source k = 16 qtr + lane / 2 for the warp's tiles
@@ -374,189 +368,194 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     }
   };
 
-  float H[16];                               // the average's H of the last step, this thread's columns
-  uint32_t par_sub = 0, par_avg = 0;
-  // thread 0: strip loads issued into / landed in buffers 0 and 1 (uses of each mbarrier)
-  int issued0 = 0, issued1 = 0, landed0 = 0, landed1 = 0;
+  // the 16 compute warps' own barrier (the MMA-issuing warp is not in it)
+  auto csync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(kT6Compute) : "memory"); };
+  // a bounded mbarrier wait that also gives up once another thread has raised s_bad
+  auto wait_or_bad = [&](uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kT6MaxPolls / 64; ++it) {
+      if (mbar_wait(bar, parity, 64, 20000)) return true;
+      if (*reinterpret_cast<volatile int*>(&s_bad)) return false;
+    }
+    return false;
+  };
 
-  if (tid == 0) {
-    issue_load(0);
-    issued0 = 1;
-  }
-  uint32_t as_hi[32], as_lo[32];             // the next step's A_s (subtraction passes)
-  if (SUB) {                                 // the first step's subtraction operands
-    load_ph(0, true);
-    __syncthreads();
-    bs_fill();
-    t2_fill(t2s, 0);
-    __syncthreads();
-    as_compute(as_hi, as_lo);
-    as_write(as_hi, as_lo);
-    tmem_wait_st();
-    fence_smem_async();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-  }
+  if (!compute) {
+    // ---- the MMA-issuing warp: per step, the subtraction's 48 MMAs once its
+    // operands are ready, then the average's 4 NQ / 16 x 3 ... once its are
+    if (lane == 0) {
+      uint32_t p_sub = 0, p_avg = 0;
+      const uint32_t id_s = idesc_tf32(128, NQ), id_a = idesc_tf32(128, 64);
+      const int nks = NQ >> 2;               // the average's k-steps over K' = 2 NQ
+      for (int t = 0; t < a.n_time; ++t) {
+        if (SUB) {
+          if (!wait_or_bad(&mbar[4], p_sub)) break;
+          p_sub ^= 1;
+          fence_after_sync();
+          // k-step s: hi*hi into accumulator s / 4, lo*hi and hi*lo into the cross-term one
+          #pragma unroll
+          for (int s = 0; s < 16; ++s) {
+            mma_ts(tmem + kT6ColSub + (s >> 2) * NQ, tmem + 8 * s, dbs_hi + 16 * s, id_s, (s & 3) != 0);
+            mma_ts(tmem + kT6ColSub + 4 * NQ, tmem + 128 + 8 * s, dbs_hi + 16 * s, id_s, s != 0);
+            mma_ts(tmem + kT6ColSub + 4 * NQ, tmem + 8 * s, dbs_lo + 16 * s, id_s, 1);
+          }
+          commit(&mbar[0]);
+        }
+        if (ACC) {
+          if (!wait_or_bad(&mbar[5], p_avg)) break;
+          p_avg ^= 1;
+          fence_after_sync();
+          for (int s = 0; s < nks; ++s) {
+            mma_ts(tmem + kT6ColAvg + 64 * (s >> 2), tmem + 8 * s, dba_hi + 16 * s, id_a, (s & 3) != 0);
+            mma_ts(tmem + kT6ColAvg + 64 * nmain_a, tmem + 2 * NQ + 8 * s, dba_hi + 16 * s, id_a, s != 0);
+            mma_ts(tmem + kT6ColAvg + 64 * nmain_a, tmem + 8 * s, dba_lo + 16 * s, id_a, 1);
+          }
+          commit(&mbar[1]);
+        }
+      }
+    }
+  } else {
+    // ---- the compute warps
+    float H[16];                             // the average's H of the last step, this thread's columns
+    uint32_t par_sub = 0, par_avg = 0;
+    // thread 0: strip loads issued into / landed in buffers 0 and 1 (uses of each mbarrier)
+    int issued0 = 0, issued1 = 0, landed0 = 0, landed1 = 0;
 
-  for (int t = 0; t < a.n_time && !s_bad; ++t) {
-    const int buf = t & 1;
-    float* strip = strip0 + (size_t)buf * n16 * 8;
-    // ---- P1: subtraction MMAs; T1 and T2 of the averaged sources beside them
-    if (SUB && warp < 5 && lane == 0) {
-      const uint32_t id = idesc_tf32(128, NQ);
-      if (warp < 4) {                        // hi*hi, k-steps 4 warp .. 4 warp + 3
-        const uint32_t d = tmem + kT6ColSub + warp * NQ;
-        #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int s = 4 * warp + u;
-          mma_ts(d, tmem + 8 * s, dbs_hi + 16 * s, id, u != 0);
-        }
-      } else {                               // lo*hi, then hi*lo, all 16 k-steps
-        const uint32_t d = tmem + kT6ColSub + 4 * NQ;
-        #pragma unroll
-        for (int s = 0; s < 16; ++s) mma_ts(d, tmem + 128 + 8 * s, dbs_hi + 16 * s, id, s != 0);
-        #pragma unroll
-        for (int s = 0; s < 16; ++s) mma_ts(d, tmem + 8 * s, dbs_lo + 16 * s, id, 1);
-      }
-      commit(&mbar[0]);
+    if (tid == 0) {
+      issue_load(0);
+      issued0 = 1;
     }
-    if (tid == 0 && t + 1 < a.n_time) {
-      if (SUB && t >= 1) bulk_wait_read();   // the residual store of step t - 1 has left buffer (t + 1) & 1
-      issue_load(t + 1);
-      if ((t + 1) & 1) ++issued1;
-      else ++issued0;
-    }
-    float2 t1v[12];
-    if (ACC) {
-      if (t > 0) avg_contract(H);            // the previous step's H with its T2 (still in t2a)
-      load_ph(t, false);
-      __syncthreads();                       // parts written; t2a free
-      if (t > 0) avg_accumulate();
-      aa_compute(t1v);
-      t2_fill(t2a, kT6Src);
-    }
-    // ---- this step's strip has landed, the subtraction MMAs are complete
-    if (warp == 0) {
-      bool ok = mbar_wait(&mbar[2 + buf], (uint32_t)(t >> 1) & 1u, kT6MaxPolls);
-      if (ok && lane == 0) {
-        if (buf) landed1 = (t >> 1) + 1;
-        else landed0 = (t >> 1) + 1;
-      }
-      if (ok && SUB) ok = mbar_wait(&mbar[0], par_sub, kT6MaxPolls);
-      if (!ok && lane == 0) s_bad = 1;
-      fence_before_sync();
-    }
-    if (SUB) par_sub ^= 1;
-    __syncthreads();
-    fence_after_sync();
-    if (s_bad) break;
-    // ---- P2: residual into the strip and B_a; A_a into TMEM (A_s is done with)
-    if (SUB) sub_epilogue(strip);
-    else if (ACC) ba_from_strip(strip);
-    if (ACC) {
-      aa_store(t1v);
-      tmem_wait_st();
-    }
-    fence_smem_async();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    // ---- P3: average MMAs; the residual's store and the next step's
-    // subtraction tables beside them
-    if (ACC && warp <= nmain_a && lane == 0) {
-      const uint32_t id = idesc_tf32(128, 64);
-      const int nks = NQ >> 2;               // k-steps over K' = 2 NQ (i NQ + q)
-      if (warp < nmain_a) {                  // hi*hi, k-steps 4 warp .. 4 warp + 3
-        const uint32_t d = tmem + kT6ColAvg + 64 * warp;
-        #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int s = 4 * warp + u;
-          mma_ts(d, tmem + 8 * s, dba_hi + 16 * s, id, u != 0);
-        }
-      } else {
-        const uint32_t d = tmem + kT6ColAvg + 64 * nmain_a;
-        for (int s = 0; s < nks; ++s) mma_ts(d, tmem + 2 * NQ + 8 * s, dba_hi + 16 * s, id, s != 0);
-        for (int s = 0; s < nks; ++s) mma_ts(d, tmem + 8 * s, dba_lo + 16 * s, id, 1);
-      }
-      commit(&mbar[1]);
-    }
-    if (SUB && tid == 0) {
-      bulk_store(a.dst + ((size_t)t * a.n_bl + bl) * a.n_chan * 2, strip, strip_bytes);
-      bulk_commit();
-    }
-    const bool next_sub = SUB && t + 1 < a.n_time;
-    if (next_sub) {
-      load_ph(t + 1, true);
-      __syncthreads();
+    if (SUB) {                               // the first step's subtraction operands
+      load_ph(0, true);
+      csync();
       bs_fill();
       t2_fill(t2s, 0);
-      __syncthreads();
-      as_compute(as_hi, as_lo);
-    }
-    // ---- P4: the average's accumulators into registers (H = the sum of its
-    // hi*hi and cross-term accumulators); the next step's A_s into TMEM
-    if (ACC) {
-      if (warp == 0) {
-        if (!mbar_wait(&mbar[1], par_avg, kT6MaxPolls) && lane == 0) s_bad = 1;
-        fence_before_sync();
-      }
-      par_avg ^= 1;
-      __syncthreads();
-      fence_after_sync();
-      const uint32_t base = tmem + lane_base + kT6ColAvg + 16 * cg;
-      tmem_ld16(base + 64 * nmain_a, H);
-      #pragma unroll
-      for (int g = 0; g < 3; ++g) {
-        if (g < nmain_a) {
-          float h[16];
-          tmem_ld16(base + 64 * g, h);
-          tmem_wait_ld();
-          #pragma unroll
-          for (int i = 0; i < 16; ++i) H[i] += h[i];
-        }
-      }
-      tmem_wait_ld();
-      fence_before_sync();
-      __syncthreads();                       // every warp has read its accumulator columns
-      fence_after_sync();
-    }
-    if (next_sub) {
-      as_write(as_hi, as_lo);
+      csync();
+      as_store();
       tmem_wait_st();
+      fence_smem_async();
+      fence_before_sync();
+      csync();
+      if (tid == 0) mbar_arrive(&mbar[4]);
     }
-    fence_smem_async();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    if (s_bad) break;
-  }
 
-  if (ACC && !s_bad) {                       // the last step's contraction
-    avg_contract(H);
-    __syncthreads();
-    avg_accumulate();
-  }
-  if (ACC && !s_bad && cg == 0 && (lane & 1) == 0) {
-    const int k = 16 * qtr + (lane >> 1);
-    const float* ks = kahan + 17 * k;
-    if (k < a.n_acc)
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const double re = (double)ks[2 * e] - (double)ks[8 + 2 * e];
-        const double im = (double)ks[2 * e + 1] - (double)ks[8 + 2 * e + 1];
-        a.avg[((size_t)k * a.n_bl + bl) * 4 + e] = make_float2((float)(re * a.inv_n), (float)(im * a.inv_n));
+    for (int t = 0; t < a.n_time && !s_bad; ++t) {
+      const int buf = t & 1;
+      float* strip = strip0 + (size_t)buf * n16 * 8;
+      // ---- C1 (beside the subtraction MMAs): the next strip's load, the
+      // previous step's T2 contraction, T1 and T2 of the averaged sources
+      if (tid == 0 && t + 1 < a.n_time) {
+        if (SUB && t >= 1) bulk_wait_read();   // the residual store of step t - 1 has left buffer (t + 1) & 1
+        issue_load(t + 1);
+        if ((t + 1) & 1) ++issued1;
+        else ++issued0;
       }
-  }
-  if (tid == 0) {
-    // a load still in flight after a failed wait must land before the CTA's
-    // shared memory goes away (bounded); stores are waited for unconditionally
-    for (int u = landed0; u < issued0; ++u)
-      if (!mbar_wait(&mbar[2], (uint32_t)u & 1u, kT6MaxPolls)) break;
-    for (int u = landed1; u < issued1; ++u)
-      if (!mbar_wait(&mbar[3], (uint32_t)u & 1u, kT6MaxPolls)) break;
-    bulk_wait_all();
-    if (s_bad) atomicExch(err, 1);
+      float2 t1v[12];
+      if (ACC) {
+        if (t > 0) avg_contract(H);          // the previous step's H with its T2 (still in t2a)
+        load_ph(t, false);
+        csync();                             // parts written; t2a free
+        if (t > 0) avg_accumulate();
+        aa_compute(t1v);
+        t2_fill(t2a, kT6Src);
+      }
+      // this step's strip has landed; the subtraction MMAs are complete
+      {
+        bool ok = wait_or_bad(&mbar[2 + buf], (uint32_t)(t >> 1) & 1u);
+        if (ok && tid == 0) {
+          if (buf) landed1 = (t >> 1) + 1;
+          else landed0 = (t >> 1) + 1;
+        }
+        if (ok && SUB) ok = wait_or_bad(&mbar[0], par_sub);
+        if (!ok) s_bad = 1;
+      }
+      if (SUB) par_sub ^= 1;
+      fence_after_sync();
+      csync();
+      if (s_bad) break;
+      // ---- C2: residual into the strip and B_a; A_a into TMEM (A_s is done with)
+      if (SUB) sub_epilogue(strip);
+      else if (ACC) ba_from_strip(strip);
+      if (ACC) {
+        aa_store(t1v);
+        tmem_wait_st();
+      }
+      fence_smem_async();
+      fence_before_sync();
+      csync();
+      if (ACC && tid == 0) mbar_arrive(&mbar[5]);
+      if (SUB && tid == 0) {
+        bulk_store(a.dst + ((size_t)t * a.n_bl + bl) * a.n_chan * 2, strip, strip_bytes);
+        bulk_commit();
+      }
+      // ---- C3 (beside the average MMAs): the next step's subtraction tables
+      const bool next_sub = SUB && t + 1 < a.n_time;
+      if (next_sub) {
+        load_ph(t + 1, true);
+        csync();
+        bs_fill();
+        t2_fill(t2s, 0);
+      }
+      // ---- C4: the average's accumulators into registers (H = the sum of its
+      // hi*hi and cross-term accumulators); the next step's A_s into TMEM
+      if (ACC) {
+        if (!wait_or_bad(&mbar[1], par_avg)) s_bad = 1;
+        par_avg ^= 1;
+        fence_after_sync();
+        const uint32_t base = tmem + lane_base + kT6ColAvg + 16 * cg;
+        tmem_ld16(base + 64 * nmain_a, H);
+        #pragma unroll
+        for (int g = 0; g < 3; ++g) {
+          if (g < nmain_a) {
+            float h[16];
+            tmem_ld16(base + 64 * g, h);
+            tmem_wait_ld();
+            #pragma unroll
+            for (int i = 0; i < 16; ++i) H[i] += h[i];
+          }
+        }
+        tmem_wait_ld();
+        fence_before_sync();
+        csync();                             // every warp has read its accumulator columns
+        fence_after_sync();
+      }
+      if (next_sub) {
+        as_store();
+        tmem_wait_st();
+        fence_smem_async();
+        fence_before_sync();
+        csync();
+        if (tid == 0 && !s_bad) mbar_arrive(&mbar[4]);
+      }
+      csync();
+      if (s_bad) break;
+    }
+
+    if (ACC && !s_bad) {                     // the last step's contraction
+      avg_contract(H);
+      csync();
+      avg_accumulate();
+    }
+    if (ACC && !s_bad && cg == 0 && (lane & 1) == 0) {
+      const int k = 16 * qtr + (lane >> 1);
+      const float* ks = kahan + 17 * k;
+      if (k < a.n_acc)
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const double re = (double)ks[2 * e] - (double)ks[8 + 2 * e];
+          const double im = (double)ks[2 * e + 1] - (double)ks[8 + 2 * e + 1];
+          a.avg[((size_t)k * a.n_bl + bl) * 4 + e] = make_float2((float)(re * a.inv_n), (float)(im * a.inv_n));
+        }
+    }
+    if (tid == 0) {
+      // a load still in flight after a failed wait must land before the CTA's
+      // shared memory goes away (bounded); stores are waited for unconditionally
+      for (int u = landed0; u < issued0; ++u)
+        if (!mbar_wait(&mbar[2], (uint32_t)u & 1u, kT6MaxPolls)) break;
+      for (int u = landed1; u < issued1; ++u)
+        if (!mbar_wait(&mbar[3], (uint32_t)u & 1u, kT6MaxPolls)) break;
+      bulk_wait_all();
+      if (s_bad) atomicExch(err, 1);
+    }
   }
   fence_before_sync();
   __syncthreads();

@@ -67,6 +67,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// one arrival on an mbarrier (release semantics for this thread's prior writes)
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
 // wait for completion of the mbarrier phase with the given parity; each poll
 // may suspend the thread for up to suspend_ns (until the phase completes);
 // gives up after max_polls polls and returns false
