@@ -81,10 +81,11 @@ struct T6Smem {
     t2s = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the subtracted sources [64][17] float2
     t2a = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the averaged sources
     mtab = o;  o += kT6Src * 4 * 8;              // model matrices [64][4] float2
-    ph = o;    o += 2 * kT6Src * 16;             // phases of the time step, both roles
+    ph = o;    o += 2 * 2 * kT6Src * 16;         // phases of two time steps [2][sub 64, avg 64]
     kahan = o; o += kT6Src * 17 * 4;             // compensated sums of the averages [64][8 sums, 8 compensations, pad]
-    bar = o;   o += 64;                          // mbarriers (sub done, avg done, load 0, load 1, sub
-                                                 // operands ready, avg operands ready), TMEM address
+    bar = o;   o += 80;                          // mbarriers (sub done, avg done, strip 0, strip 1, sub
+                                                 // operands ready, avg operands ready, phases 0, phases 1),
+                                                 // TMEM address
     total = o;
   }
 };
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   float2* mtab = reinterpret_cast<float2*>(t6_smem + L.mtab);
   PhaseAB* ph = reinterpret_cast<PhaseAB*>(t6_smem + L.ph);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(t6_smem + L.bar);      // see T6Smem::bar
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 48);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 64);
   float* part = reinterpret_cast<float*>(ba_hi);    // [4 cg][64 k][8]: B_a is free in P4
   float* kahan = reinterpret_cast<float*>(t6_smem + L.kahan);
 
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
 
   if (warp == 0) tmem_alloc(tslot, kT6Cols);
   if (tid == 0) {
-    for (int i = 0; i < 6; ++i) mbar_init(&mbar[i], 1);   // each completed by one arrival (or commit)
+    for (int i = 0; i < 8; ++i) mbar_init(&mbar[i], 1);   // each completed by one arrival (or commit)
   }
   const bool compute = tid < kT6Compute;
   // padding channels of both strips stay zero (the copies never write them)
@@ -148,6 +149,12 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     }
   if (ACC)
     for (int i = tid; compute && i < kT6Src * 17; i += kT6Compute) kahan[i] = 0.f;
+  // phases of sources beyond bk stay zero (the copies bring bk per role)
+  for (int i = tid; compute && i < 4 * kT6Src; i += kT6Compute) {
+    ph[i].a = 0;
+    ph[i].b = 0;
+  }
+  fence_smem_async();                      // the zero fills precede the bulk copies into the same words
   // a pass in which some CTA's wait already ran out does no more work
   __shared__ int s_bad;
   if (tid == 0) s_bad = *reinterpret_cast<volatile int*>(err);
@@ -166,31 +173,29 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     bulk_load(strip0 + (size_t)b * n16 * 8, a.src + ((size_t)t * a.n_bl + bl) * a.n_chan * 2, strip_bytes,
               &mbar[2 + b]);
   };
-  // the phases of one role at time t (64 threads)
-  auto load_ph = [&](int t, bool sub) {
-    const int base = sub ? 0 : kT6Src;
-    if (tid >= base && tid < base + kT6Src) {
-      const int k = tid - base;
-      PhaseAB p;
-      p.a = 0; p.b = 0;
-      if (sub ? (SUB && k < a.n_sub) : (ACC && k < a.n_acc))
-        p = (sub ? a.ph_sub : a.ph_acc)[((size_t)bl * a.n_time + t) * bk + k];
-      ph[tid] = p;
-    }
+  // the phases of both roles at time step t -> ring slot t & 1 (thread 0): one
+  // bulk copy of bk entries per role, completing on mbarrier 6 + (t & 1)
+  auto issue_ph = [&](int t) {
+    const int b = t & 1;
+    const uint32_t bytes = (uint32_t)bk * sizeof(PhaseAB);
+    mbar_expect_tx(&mbar[6 + b], (SUB ? bytes : 0u) + (ACC ? bytes : 0u));
+    const size_t at = ((size_t)bl * a.n_time + t) * bk;
+    if (SUB) bulk_load(ph + 2 * kT6Src * b, a.ph_sub + at, bytes, &mbar[6 + b]);
+    if (ACC) bulk_load(ph + 2 * kT6Src * b + kT6Src, a.ph_acc + at, bytes, &mbar[6 + b]);
   };
-  // T2_k[r] of one role: [64][kT6T2Row]
-  auto t2_fill = [&](float2* t2, int base) {
+  // T2_k[r] of one role from its phases p[64]: [64][kT6T2Row]
+  auto t2_fill = [&](float2* t2, const PhaseAB* p) {
     for (int i = tid; i < kT6Src * 16; i += kT6Compute) {
       const int k = i >> 4, r = i & 15;
-      t2[k * kT6T2Row + r] = phasor_hw((unsigned long long)r * ph[base + k].b);
+      t2[k * kT6T2Row + r] = phasor_hw((unsigned long long)r * p[k].b);
     }
   };
   // B_s = conj(T1_k[q]) of the subtracted sources: thread (q & 7 = lane & 7,
   // k = (lane >> 3) + 4 warp) steps q by 8 with an exact 64-bit phase increment;
   // its 8-byte (re, im) stores cover 16 distinct slots of each 128-byte line
-  auto bs_fill = [&]() {
+  auto bs_fill = [&](const PhaseAB* ps) {
     const int ql = tid & 7, k = ((tid >> 3) & 3) + 4 * warp;
-    const PhaseAB p = ph[k];
+    const PhaseAB p = ps[k];
     const unsigned long long step = 128ull * p.b;
     unsigned long long x = p.a + (unsigned long long)(16 * ql) * p.b;
     for (int q = ql; q < NQ; q += 8, x += step) {
@@ -229,9 +234,9 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   // T1_k[q] of the averaged source k = 16 qtr + lane / 2 for the warp's tiles
   // q = cg QW .. cg QW + QW - 1: the lane pair (o = 0, 1) computes even and odd
   // tiles and exchanges them
-  auto aa_compute = [&](float2 (&t1v)[12]) {
+  auto aa_compute = [&](float2 (&t1v)[12], const PhaseAB* pa) {
     const int k = 16 * qtr + (lane >> 1), o = lane & 1, q0 = cg * QW;
-    const PhaseAB p = ph[kT6Src + k];
+    const PhaseAB p = pa[k];
     const unsigned long long step = 32ull * p.b;
     unsigned long long x = p.a + (unsigned long long)(16 * (q0 + o)) * p.b;
     #pragma unroll
@@ -291,15 +296,15 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       if (4 * ch < QW) {
-        float v[5][4];
+        float v[4][4];
         #pragma unroll
-        for (int g = 0; g < 5; ++g) tmem_ld4(base + g * NQ + 4 * ch, v[g]);
+        for (int g = 0; g < 4; ++g) tmem_ld4(base + g * NQ + 4 * ch, v[g]);
         tmem_wait_ld();
         float x[4];
         #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int c = 16 * (q0 + 4 * ch + u) + r;
-          const float d = (((v[4][u] + v[0][u]) + v[1][u]) + v[2][u]) + v[3][u];
+          const float d = ((v[0][u] + v[1][u]) + v[2][u]) + v[3][u];
           x[u] = 0.f;
           if (c < a.n_chan) {
             float* sp = strip + c * 8 + 2 * e + o;
@@ -380,23 +385,27 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   };
 
   if (!compute) {
-    // ---- the MMA-issuing warp: per step, the subtraction's 48 MMAs once its
-    // operands are ready, then the average's 4 NQ / 16 x 3 ... once its are
+    // ---- the MMA-issuing warp.  Each accumulator takes the cross terms
+    // (lo*hi, hi*lo) of its 4 k-steps first, then their hi*hi products; the
+    // accumulators are issued round-robin, so consecutive MMAs never depend
+    // on each other (a dependent MMA waits for the previous one to finish)
     if (lane == 0) {
       uint32_t p_sub = 0, p_avg = 0;
       const uint32_t id_s = idesc_tf32(128, NQ), id_a = idesc_tf32(128, 64);
-      const int nks = NQ >> 2;               // the average's k-steps over K' = 2 NQ
       for (int t = 0; t < a.n_time; ++t) {
         if (SUB) {
           if (!wait_or_bad(&mbar[4], p_sub)) break;
           p_sub ^= 1;
           fence_after_sync();
-          // k-step s: hi*hi into accumulator s / 4, lo*hi and hi*lo into the cross-term one
           #pragma unroll
-          for (int s = 0; s < 16; ++s) {
-            mma_ts(tmem + kT6ColSub + (s >> 2) * NQ, tmem + 8 * s, dbs_hi + 16 * s, id_s, (s & 3) != 0);
-            mma_ts(tmem + kT6ColSub + 4 * NQ, tmem + 128 + 8 * s, dbs_hi + 16 * s, id_s, s != 0);
-            mma_ts(tmem + kT6ColSub + 4 * NQ, tmem + 8 * s, dbs_lo + 16 * s, id_s, 1);
+          for (int j = 0; j < 12; ++j) {
+            #pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const int s = 4 * g + (j & 3);
+              const uint32_t acol = tmem + (j < 4 ? 128 : 0) + 8 * s;       // lo(A) for j < 4, else hi(A)
+              const uint64_t bd = (j >= 4 && j < 8 ? dbs_lo : dbs_hi) + 16 * s;
+              mma_ts(tmem + kT6ColSub + g * NQ, acol, bd, id_s, j != 0);
+            }
           }
           commit(&mbar[0]);
         }
@@ -404,11 +413,13 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
           if (!wait_or_bad(&mbar[5], p_avg)) break;
           p_avg ^= 1;
           fence_after_sync();
-          for (int s = 0; s < nks; ++s) {
-            mma_ts(tmem + kT6ColAvg + 64 * (s >> 2), tmem + 8 * s, dba_hi + 16 * s, id_a, (s & 3) != 0);
-            mma_ts(tmem + kT6ColAvg + 64 * nmain_a, tmem + 2 * NQ + 8 * s, dba_hi + 16 * s, id_a, s != 0);
-            mma_ts(tmem + kT6ColAvg + 64 * nmain_a, tmem + 8 * s, dba_lo + 16 * s, id_a, 1);
-          }
+          for (int j = 0; j < 12; ++j)
+            for (int g = 0; g < nmain_a; ++g) {
+              const int s = 4 * g + (j & 3);
+              const uint32_t acol = tmem + (j < 4 ? 2 * NQ : 0) + 8 * s;
+              const uint64_t bd = (j >= 4 && j < 8 ? dba_lo : dba_hi) + 16 * s;
+              mma_ts(tmem + kT6ColAvg + 64 * g, acol, bd, id_a, j != 0);
+            }
           commit(&mbar[1]);
         }
       }
@@ -419,32 +430,36 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     uint32_t par_sub = 0, par_avg = 0;
     // thread 0: strip loads issued into / landed in buffers 0 and 1 (uses of each mbarrier)
     int issued0 = 0, issued1 = 0, landed0 = 0, landed1 = 0;
+    auto ph_slot = [&](int t) { return ph + 2 * kT6Src * (t & 1); };   // [sub 64][avg 64]
+    auto wait_ph = [&](int t) { return wait_or_bad(&mbar[6 + (t & 1)], (uint32_t)(t >> 1) & 1u); };
 
     if (tid == 0) {
+      issue_ph(0);
       issue_load(0);
       issued0 = 1;
     }
     if (SUB) {                               // the first step's subtraction operands
-      load_ph(0, true);
-      csync();
-      bs_fill();
-      t2_fill(t2s, 0);
+      if (!wait_ph(0)) s_bad = 1;
+      bs_fill(ph_slot(0));
+      t2_fill(t2s, ph_slot(0));
       csync();
       as_store();
       tmem_wait_st();
       fence_smem_async();
       fence_before_sync();
       csync();
-      if (tid == 0) mbar_arrive(&mbar[4]);
+      if (tid == 0 && !s_bad) mbar_arrive(&mbar[4]);
     }
 
     for (int t = 0; t < a.n_time && !s_bad; ++t) {
       const int buf = t & 1;
       float* strip = strip0 + (size_t)buf * n16 * 8;
-      // ---- C1 (beside the subtraction MMAs): the next strip's load, the
-      // previous step's T2 contraction, T1 and T2 of the averaged sources
+      // ---- C1 (beside the subtraction MMAs): the next step's strip and
+      // phases, the previous step's T2 contraction, T1 and T2 of the averaged
+      // sources
       if (tid == 0 && t + 1 < a.n_time) {
         if (SUB && t >= 1) bulk_wait_read();   // the residual store of step t - 1 has left buffer (t + 1) & 1
+        issue_ph(t + 1);
         issue_load(t + 1);
         if ((t + 1) & 1) ++issued1;
         else ++issued0;
@@ -452,11 +467,11 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       float2 t1v[12];
       if (ACC) {
         if (t > 0) avg_contract(H);          // the previous step's H with its T2 (still in t2a)
-        load_ph(t, false);
+        if (!wait_ph(t)) s_bad = 1;
         csync();                             // parts written; t2a free
         if (t > 0) avg_accumulate();
-        aa_compute(t1v);
-        t2_fill(t2a, kT6Src);
+        aa_compute(t1v, ph_slot(t) + kT6Src);
+        t2_fill(t2a, ph_slot(t) + kT6Src);
       }
       // this step's strip has landed; the subtraction MMAs are complete
       {
@@ -490,21 +505,20 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       // ---- C3 (beside the average MMAs): the next step's subtraction tables
       const bool next_sub = SUB && t + 1 < a.n_time;
       if (next_sub) {
-        load_ph(t + 1, true);
-        csync();
-        bs_fill();
-        t2_fill(t2s, 0);
+        if (!wait_ph(t + 1)) s_bad = 1;
+        bs_fill(ph_slot(t + 1));
+        t2_fill(t2s, ph_slot(t + 1));
       }
       // ---- C4: the average's accumulators into registers (H = the sum of its
-      // hi*hi and cross-term accumulators); the next step's A_s into TMEM
+      // accumulators); the next step's A_s into TMEM
       if (ACC) {
         if (!wait_or_bad(&mbar[1], par_avg)) s_bad = 1;
         par_avg ^= 1;
         fence_after_sync();
         const uint32_t base = tmem + lane_base + kT6ColAvg + 16 * cg;
-        tmem_ld16(base + 64 * nmain_a, H);
+        tmem_ld16(base, H);
         #pragma unroll
-        for (int g = 0; g < 3; ++g) {
+        for (int g = 1; g < 3; ++g) {
           if (g < nmain_a) {
             float h[16];
             tmem_ld16(base + 64 * g, h);
@@ -515,16 +529,16 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
         }
         tmem_wait_ld();
         fence_before_sync();
-        csync();                             // every warp has read its accumulator columns
-        fence_after_sync();
       }
-      if (next_sub) {
+      csync();                               // accumulators read by every warp; T2 of the next step ready
+      fence_after_sync();
+      if (next_sub && !s_bad) {
         as_store();
         tmem_wait_st();
         fence_smem_async();
         fence_before_sync();
         csync();
-        if (tid == 0 && !s_bad) mbar_arrive(&mbar[4]);
+        if (tid == 0) mbar_arrive(&mbar[4]);
       }
       csync();
       if (s_bad) break;
