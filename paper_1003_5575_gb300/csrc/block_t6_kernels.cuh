@@ -41,10 +41,10 @@
 //   P3  average MMAs       | beside them: the residual's store, the next
 //                            step's B_s and T2 of the subtracted sources
 //   P4  the average's accumulators into registers, the next step's A_s into TMEM
-// A 17th warp issues every MMA: an issuing thread stalls while the tensor
-// core's queue drains (a few tens of cycles per MMA), so the 16 compute warps,
-// which meet at a named barrier of their own, never wait for it; operands-ready
-// and MMAs-done mbarriers hand each phase between them.  Every wait is bounded
+// Four more warps issue the MMAs, one accumulator each: an issuing thread
+// stalls while its MMAs are accepted (a few tens of cycles each), so the 16
+// compute warps, which meet at a named barrier of their own, never wait for
+// it; operands-ready and MMAs-done mbarriers hand each phase between them.  Every wait is bounded
 // (a wait that runs out sets *err and stops the pass, which the status read
 // reports, after the copies in flight have been waited for and TMEM is freed).
 // Limits: at most 64 sources per role, n_chan <= kT6MaxChan.
@@ -55,22 +55,25 @@
 namespace rts {
 
 constexpr int kT6Compute = 512;             // 16 compute warps (4 per TMEM lane quarter)
-constexpr int kT6Threads = kT6Compute + 32;  // and one warp whose lane 0 issues every MMA
+constexpr int kT6Issuers = 4;               // and 4 warps whose lane 0 issues one accumulator's MMAs
+constexpr int kT6Threads = kT6Compute + 32 * kT6Issuers;
 constexpr int kT6Src = 64;                  // sources per role
 constexpr int kT6MaxChan = 768;             // NQ <= 48: 5 NQ accumulator columns beside A_s
 constexpr uint32_t kT6MaxPolls = 1u << 17;  // mbarrier polls (each up to 20 us) before giving up
 constexpr int kT6T2Row = 17;                // T2 table row stride (float2): conflict-free column reads
-// TMEM columns.  Subtraction: A_s hi [0, 128), lo [128, 256); hi*hi accumulators
-// g = 0..3 at 256 + g NQ, cross terms at 256 + 4 NQ.  Average: A_a hi [0, 2 NQ),
-// lo [2 NQ, 4 NQ); hi*hi accumulators g < NQ / 16 at 192 + 64 g, cross terms
-// after them.  Each phase starts once every read of the other's columns is done.
-constexpr uint32_t kT6ColSub = 256;
-constexpr uint32_t kT6ColAvg = 192;
+// TMEM columns.  Subtraction: accumulators g = 0..3 at g NQ (< 192), A_s lo at
+// [192, 320), A_s hi at [384, 512).  Average: accumulators g < NQ / 16 at 64 g
+// (< 192), A_a hi at [192, 192 + 2 NQ), lo after it (< 384).  So the next step's
+// A_s hi can be written while the average's MMAs run, and its lo once they are
+// done, beside the reads of the average's accumulators.
+constexpr uint32_t kT6ColAcc = 0;
+constexpr uint32_t kT6ColALo = 192;         // A_s lo; A_a (hi then lo)
+constexpr uint32_t kT6ColAHi = 384;         // A_s hi
 constexpr uint32_t kT6Cols = 512;
 
 // shared-memory layout (byte offsets) for NQ 16-channel tiles (16, 32 or 48)
 struct T6Smem {
-  int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, kahan, bar, total;
+  int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, bar, total;
   __host__ __device__ explicit T6Smem(int NQ) {
     int o = 0;
     strip = o; o += 2 * 16 * NQ * 32;            // two strips [16 NQ channels][4 pol][re, im]
@@ -82,7 +85,6 @@ struct T6Smem {
     t2a = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the averaged sources
     mtab = o;  o += kT6Src * 4 * 8;              // model matrices [64][4] float2
     ph = o;    o += 2 * 2 * kT6Src * 16;         // phases of two time steps [2][sub 64, avg 64]
-    kahan = o; o += kT6Src * 17 * 4;             // compensated sums of the averages [64][8 sums, 8 compensations, pad]
     bar = o;   o += 80;                          // mbarriers (sub done, avg done, strip 0, strip 1, sub
                                                  // operands ready, avg operands ready, phases 0, phases 1),
                                                  // TMEM address
@@ -126,7 +128,6 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   uint64_t* mbar = reinterpret_cast<uint64_t*>(t6_smem + L.bar);      // see T6Smem::bar
   uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 64);
   float* part = reinterpret_cast<float*>(ba_hi);    // [4 cg][64 k][8]: B_a is free in P4
-  float* kahan = reinterpret_cast<float*>(t6_smem + L.kahan);
 
   const int64_t bl = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qtr = warp & 3, cg = warp >> 2;
@@ -134,7 +135,9 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
 
   if (warp == 0) tmem_alloc(tslot, kT6Cols);
   if (tid == 0) {
-    for (int i = 0; i < 8; ++i) mbar_init(&mbar[i], 1);   // each completed by one arrival (or commit)
+    mbar_init(&mbar[0], kT6Issuers);        // subtraction MMAs done: one commit per issuer
+    mbar_init(&mbar[1], nmain_a);           // average MMAs done: one commit per accumulator
+    for (int i = 2; i < 8; ++i) mbar_init(&mbar[i], 1);   // each completed by one arrival
   }
   const bool compute = tid < kT6Compute;
   // padding channels of both strips stay zero (the copies never write them)
@@ -147,8 +150,6 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       const int s = i >> 2, e = i & 3;
       mtab[i] = s < a.n_sub ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
     }
-  if (ACC)
-    for (int i = tid; compute && i < kT6Src * 17; i += kT6Compute) kahan[i] = 0.f;
   // phases of sources beyond bk stay zero (the copies bring bk per role)
   for (int i = tid; compute && i < 4 * kT6Src; i += kT6Compute) {
     ph[i].a = 0;
@@ -207,13 +208,14 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
                                                           __uint_as_float(t6_tf32(-z.y - hi)));
     }
   };
-  // A_s -> TMEM: warp (qtr, cg) writes rows m = 32 qtr + lane = 8 r + 2 e + o,
-  // sources 16 cg .. 16 cg + 15 (columns 32 cg .. 32 cg + 31, hi and lo)
-  auto as_store = [&]() {
+  // A_s of warp (qtr, cg): rows m = 32 qtr + lane = 8 r + 2 e + o, sources
+  // 16 cg .. 16 cg + 15 (columns 32 cg .. 32 cg + 31): the hi parts go to TMEM
+  // here, the lo parts stay in lo[] for as_store_lo
+  auto as_store_hi = [&](uint32_t (&lo)[32]) {
     const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1;
     #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      uint32_t vh[16], vl[16];
+      uint32_t vh[16];
       #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int k = 16 * cg + 8 * h + j;
@@ -223,12 +225,19 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
         const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
         vh[2 * j] = h0;
         vh[2 * j + 1] = h1;
-        vl[2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
-        vl[2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
+        lo[16 * h + 2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
+        lo[16 * h + 2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
       }
-      const uint32_t col = 32 * cg + 16 * h;
-      tmem_st16(tmem + lane_base + col, vh);
-      tmem_st16(tmem + lane_base + 128 + col, vl);
+      tmem_st16(tmem + lane_base + kT6ColAHi + 32 * cg + 16 * h, vh);
+    }
+  };
+  auto as_store_lo = [&](const uint32_t (&lo)[32]) {
+    #pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t vl[16];
+      #pragma unroll
+      for (int i = 0; i < 16; ++i) vl[i] = lo[16 * h + i];
+      tmem_st16(tmem + lane_base + kT6ColALo + 32 * cg + 16 * h, vl);
     }
   };
   // T1_k[q] of the averaged source k = 16 qtr + lane / 2 for the warp's tiles
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
           l0[u] = __float_as_uint(v0 - __uint_as_float(h0[u]));
           l1[u] = __float_as_uint(v1 - __uint_as_float(h1[u]));
         }
-        const uint32_t col = q0 + 4 * ch;
+        const uint32_t col = kT6ColALo + q0 + 4 * ch;
         tmem_st4(tmem + lane_base + col, h0);
         tmem_st4(tmem + lane_base + NQ + col, h1);
         tmem_st4(tmem + lane_base + 2 * NQ + col, l0);
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   // consecutive words (conflict-free)
   auto sub_epilogue = [&](float* strip) {
     const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1, n = 4 * r + e, q0 = cg * QW;
-    const uint32_t base = tmem + lane_base + kT6ColSub + q0;
+    const uint32_t base = tmem + lane_base + kT6ColAcc + q0;
     #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       if (4 * ch < QW) {
@@ -354,23 +363,18 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       dst[1] = make_float4(pr[2], pi[2], pr[3], pi[3]);
     }
   };
-  // compensated accumulation of the four column groups' sums (fixed order)
-  // into kahan[17 k ..] = (8 sums, 8 compensations): warps 0..3, even lanes
+  // compensated accumulation of the four column groups' sums (fixed order):
+  // compute thread tid owns value i = tid & 7 of source k = tid >> 3
+  float ks = 0.f, kc = 0.f;
   auto avg_accumulate = [&]() {
-    if (cg == 0 && (lane & 1) == 0) {
-      const int k = 16 * qtr + (lane >> 1);
-      float* ks = kahan + 17 * k;
-      #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float x = part[k * 8 + i];
-        #pragma unroll
-        for (int c = 1; c < 4; ++c) x += part[(c * kT6Src + k) * 8 + i];
-        const float y = x - ks[8 + i];
-        const float tt = ks[i] + y;
-        ks[8 + i] = (tt - ks[i]) - y;
-        ks[i] = tt;
-      }
-    }
+    const int k = tid >> 3, i = tid & 7;
+    float x = part[k * 8 + i];
+    #pragma unroll
+    for (int c = 1; c < 4; ++c) x += part[(c * kT6Src + k) * 8 + i];
+    const float y = x - kc;
+    const float tt = ks + y;
+    kc = (tt - ks) - y;
+    ks = tt;
   };
 
   // the 16 compute warps' own barrier (the MMA-issuing warp is not in it)
@@ -385,10 +389,12 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   };
 
   if (!compute) {
-    // ---- the MMA-issuing warp.  Each accumulator takes the cross terms
-    // (lo*hi, hi*lo) of its 4 k-steps first, then their hi*hi products; the
-    // accumulators are issued round-robin, so consecutive MMAs never depend
-    // on each other (a dependent MMA waits for the previous one to finish)
+    // ---- the MMA-issuing warps: lane 0 of warp 16 + g issues accumulator g's
+    // MMAs (a thread's MMAs are accepted one at a time, so one thread issuing
+    // them all leaves the tensor core half idle).  Each accumulator takes the
+    // cross terms (lo*hi, hi*lo) of its 4 k-steps first, then their hi*hi
+    // products
+    const int g = warp - kT6Compute / 32;
     if (lane == 0) {
       uint32_t p_sub = 0, p_avg = 0;
       const uint32_t id_s = idesc_tf32(128, NQ), id_a = idesc_tf32(128, 64);
@@ -399,27 +405,24 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
           fence_after_sync();
           #pragma unroll
           for (int j = 0; j < 12; ++j) {
-            #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const int s = 4 * g + (j & 3);
-              const uint32_t acol = tmem + (j < 4 ? 128 : 0) + 8 * s;       // lo(A) for j < 4, else hi(A)
-              const uint64_t bd = (j >= 4 && j < 8 ? dbs_lo : dbs_hi) + 16 * s;
-              mma_ts(tmem + kT6ColSub + g * NQ, acol, bd, id_s, j != 0);
-            }
+            const int s = 4 * g + (j & 3);
+            const uint32_t acol = tmem + (j < 4 ? kT6ColALo : kT6ColAHi) + 8 * s;   // lo(A) for j < 4, else hi(A)
+            const uint64_t bd = (j >= 4 && j < 8 ? dbs_lo : dbs_hi) + 16 * s;
+            mma_ts(tmem + kT6ColAcc + g * NQ, acol, bd, id_s, j != 0);
           }
           commit(&mbar[0]);
         }
-        if (ACC) {
+        if (ACC && g < nmain_a) {
           if (!wait_or_bad(&mbar[5], p_avg)) break;
           p_avg ^= 1;
           fence_after_sync();
-          for (int j = 0; j < 12; ++j)
-            for (int g = 0; g < nmain_a; ++g) {
-              const int s = 4 * g + (j & 3);
-              const uint32_t acol = tmem + (j < 4 ? 2 * NQ : 0) + 8 * s;
-              const uint64_t bd = (j >= 4 && j < 8 ? dba_lo : dba_hi) + 16 * s;
-              mma_ts(tmem + kT6ColAvg + 64 * g, acol, bd, id_a, j != 0);
-            }
+          #pragma unroll
+          for (int j = 0; j < 12; ++j) {
+            const int s = 4 * g + (j & 3);
+            const uint32_t acol = tmem + kT6ColALo + (j < 4 ? 2 * NQ : 0) + 8 * s;
+            const uint64_t bd = (j >= 4 && j < 8 ? dba_lo : dba_hi) + 16 * s;
+            mma_ts(tmem + kT6ColAcc + 64 * g, acol, bd, id_a, j != 0);
+          }
           commit(&mbar[1]);
         }
       }
@@ -438,12 +441,14 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       issue_load(0);
       issued0 = 1;
     }
+    uint32_t as_lo[32];                      // the next step's A_s lo, between C3 and C4
     if (SUB) {                               // the first step's subtraction operands
       if (!wait_ph(0)) s_bad = 1;
       bs_fill(ph_slot(0));
       t2_fill(t2s, ph_slot(0));
       csync();
-      as_store();
+      as_store_hi(as_lo);
+      as_store_lo(as_lo);
       tmem_wait_st();
       fence_smem_async();
       fence_before_sync();
@@ -503,19 +508,22 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
         bulk_commit();
       }
       // ---- C3 (beside the average MMAs): the next step's subtraction tables
+      // and A_s hi (its TMEM columns are free of the average)
       const bool next_sub = SUB && t + 1 < a.n_time;
       if (next_sub) {
         if (!wait_ph(t + 1)) s_bad = 1;
         bs_fill(ph_slot(t + 1));
         t2_fill(t2s, ph_slot(t + 1));
+        csync();
+        as_store_hi(as_lo);
       }
       // ---- C4: the average's accumulators into registers (H = the sum of its
-      // accumulators); the next step's A_s into TMEM
+      // accumulators); the next step's A_s lo into the columns A_a has left
       if (ACC) {
         if (!wait_or_bad(&mbar[1], par_avg)) s_bad = 1;
         par_avg ^= 1;
         fence_after_sync();
-        const uint32_t base = tmem + lane_base + kT6ColAvg + 16 * cg;
+        const uint32_t base = tmem + lane_base + kT6ColAcc + 16 * cg;
         tmem_ld16(base, H);
         #pragma unroll
         for (int g = 1; g < 3; ++g) {
@@ -528,19 +536,14 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
           }
         }
         tmem_wait_ld();
-        fence_before_sync();
       }
-      csync();                               // accumulators read by every warp; T2 of the next step ready
+      if (next_sub) as_store_lo(as_lo);
+      tmem_wait_st();
+      fence_smem_async();
+      fence_before_sync();
+      csync();                               // accumulators read by every warp; the next A_s and B_s ready
       fence_after_sync();
-      if (next_sub && !s_bad) {
-        as_store();
-        tmem_wait_st();
-        fence_smem_async();
-        fence_before_sync();
-        csync();
-        if (tid == 0) mbar_arrive(&mbar[4]);
-      }
-      csync();
+      if (next_sub && !s_bad && tid == 0) mbar_arrive(&mbar[4]);
       if (s_bad) break;
     }
 
@@ -549,16 +552,11 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       csync();
       avg_accumulate();
     }
-    if (ACC && !s_bad && cg == 0 && (lane & 1) == 0) {
-      const int k = 16 * qtr + (lane >> 1);
-      const float* ks = kahan + 17 * k;
+    if (ACC && !s_bad) {
+      const int k = tid >> 3, i = tid & 7;   // value i = (re, im) of pol i / 2
       if (k < a.n_acc)
-        #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const double re = (double)ks[2 * e] - (double)ks[8 + 2 * e];
-          const double im = (double)ks[2 * e + 1] - (double)ks[8 + 2 * e + 1];
-          a.avg[((size_t)k * a.n_bl + bl) * 4 + e] = make_float2((float)(re * a.inv_n), (float)(im * a.inv_n));
-        }
+        reinterpret_cast<float*>(a.avg)[((size_t)k * a.n_bl + bl) * 8 + i] =
+            (float)(((double)ks - (double)kc) * a.inv_n);
     }
     if (tid == 0) {
       // a load still in flight after a failed wait must land before the CTA's
