@@ -115,8 +115,8 @@ class Clocks:
 
 KERNEL_SOURCES = {"k_stream_mixed<true,true>": ("common.cuh", "stream_kernels.cuh"),
                   "k_block_pass<64,true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh"),
-                  "k_block_pass_t5<true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh",
-                                                 "block_tc_kernels.cuh", "tc05.cuh", "block_t5_kernels.cuh"),
+                  "k_block_pass_tc05<true,true>": ("common.cuh", "stream_kernels.cuh", "block_kernels.cuh",
+                                                   "tc05.cuh", "block_tc05_kernels.cuh"),
                   "k_grad_sweep_fac<false>": ("common.cuh", "kahan.cuh", "grad_kernels.cuh"),
                   "k_stream_taylor<true,true>": ("common.cuh", "stream_kernels.cuh", "als_kernels.cuh",
                                                  "taylor_kernels.cuh"),
@@ -143,8 +143,10 @@ def ncu_traffic(kernel: str):
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
-    """FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    """FP32 (non-tensor) peak: the device's SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -318,10 +320,10 @@ def main():
         achieved = flops / (ms_bp / 1e3) / 1e12
         sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         name = {1: "k_block_pass<64,SUB,ACC> (FP32 FMA)", 2: "k_block_pass_tc<SUB,ACC> (TF32 mma.sync)",
-                3: "k_block_pass_t5<SUB,ACC> (tcgen05.mma kind::tf32, TMEM accumulators)"}[block_kernel]
+                3: "k_block_pass_tc05<SUB,ACC> (tcgen05.mma kind::tf32, TMEM accumulators)"}[block_kernel]
         if block_kernel == 1:
             peak = fp32_peak_tflops(sm_mhz)
-            bound, peak_source = "alu", (f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
+            bound, peak_source = "alu", (f"derived: the device's SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
                                          "(median SM clock under load)")
         else:
             # TF32 dense peak: measured bf16 (sustained: the pass runs inside a long step)
@@ -334,13 +336,13 @@ def main():
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
                     "traffic": (ncu_traffic("k_block_pass<64,true,true>") if block_kernel == 1 else
-                                ncu_traffic("k_block_pass_t5<true,true>") if block_kernel == 3 else None),
+                                ncu_traffic("k_block_pass_tc05<true,true>") if block_kernel == 3 else None),
                     "kernel": name + ": subtract 64 solved sources + average the next 64",
                     "algorithmic_flops_per_update": FLOPS_PER_UPDATE,
                     "algorithmic_flops_note": ("32 FP32 flop per source x visibility for each of the subtraction and "
                                                "the average (4 complex multiply-adds); the tensor-core passes execute "
                                                "3 TF32 MMAs per product (split operands), so the tensor pipes do 3x "
-                                               "(subtraction 4x: its second 128-row tile is half padding)"),
+                                               "the algorithmic work"),
                     "algorithmic_bytes_per_launch": cad.n_vis * BYTES_PER_UPDATE,
                     "avg_launch_ms": ms_bp / n_bp,
                     "hbm_GBps_of_the_pass": cad.n_vis * BYTES_PER_UPDATE / (ms_bp / n_bp / 1e3) / 1e9,

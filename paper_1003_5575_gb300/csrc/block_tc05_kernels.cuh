@@ -47,44 +47,44 @@
 // it; operands-ready and MMAs-done mbarriers hand each phase between them.  Every wait is bounded
 // (a wait that runs out sets *err and stops the pass, which the status read
 // reports, after the copies in flight have been waited for and TMEM is freed).
-// Limits: at most 64 sources per role, n_chan <= kT6MaxChan.
+// Limits: at most 64 sources per role, n_chan <= kTc5MaxChan.
 #pragma once
 #include "block_kernels.cuh"
 #include "tc05.cuh"
 
 namespace rts {
 
-constexpr int kT6Compute = 512;             // 16 compute warps (4 per TMEM lane quarter)
-constexpr int kT6Issuers = 4;               // and 4 warps whose lane 0 issues one accumulator's MMAs
-constexpr int kT6Threads = kT6Compute + 32 * kT6Issuers;
-constexpr int kT6Src = 64;                  // sources per role
-constexpr int kT6MaxChan = 768;             // NQ <= 48: 5 NQ accumulator columns beside A_s
-constexpr uint32_t kT6MaxPolls = 1u << 17;  // mbarrier polls (each up to 20 us) before giving up
-constexpr int kT6T2Row = 17;                // T2 table row stride (float2): conflict-free column reads
+constexpr int kTc5Compute = 512;             // 16 compute warps (4 per TMEM lane quarter)
+constexpr int kTc5Issuers = 4;               // and 4 warps whose lane 0 issues one accumulator's MMAs
+constexpr int kTc5Threads = kTc5Compute + 32 * kTc5Issuers;
+constexpr int kTc5Src = 64;                  // sources per role
+constexpr int kTc5MaxChan = 768;             // NQ <= 48: 5 NQ accumulator columns beside A_s
+constexpr uint32_t kTc5MaxPolls = 1u << 17;  // mbarrier polls (each up to 20 us) before giving up
+constexpr int kTc5T2Row = 17;                // T2 table row stride (float2): conflict-free column reads
 // TMEM columns.  Subtraction: accumulators g = 0..3 at g NQ (< 192), A_s lo at
 // [192, 320), A_s hi at [384, 512).  Average: accumulators g < NQ / 16 at 64 g
 // (< 192), A_a hi at [192, 192 + 2 NQ), lo after it (< 384).  So the next step's
 // A_s hi can be written while the average's MMAs run, and its lo once they are
 // done, beside the reads of the average's accumulators.
-constexpr uint32_t kT6ColAcc = 0;
-constexpr uint32_t kT6ColALo = 192;         // A_s lo; A_a (hi then lo)
-constexpr uint32_t kT6ColAHi = 384;         // A_s hi
-constexpr uint32_t kT6Cols = 512;
+constexpr uint32_t kTc5ColAcc = 0;
+constexpr uint32_t kTc5ColALo = 192;         // A_s lo; A_a (hi then lo)
+constexpr uint32_t kTc5ColAHi = 384;         // A_s hi
+constexpr uint32_t kTc5Cols = 512;
 
 // shared-memory layout (byte offsets) for NQ 16-channel tiles (16, 32 or 48)
-struct T6Smem {
+struct Tc05Smem {
   int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, bar, total;
-  __host__ __device__ explicit T6Smem(int NQ) {
+  __host__ __device__ explicit Tc05Smem(int NQ) {
     int o = 0;
     strip = o; o += 2 * 16 * NQ * 32;            // two strips [16 NQ channels][4 pol][re, im]
     bs_hi = o; o += NQ * 128 * 4;                // B_s [NQ rows][128 K], K-major
     bs_lo = o; o += NQ * 128 * 4;
     ba_hi = o; o += 64 * 2 * NQ * 4;             // B_a [64 rows][2 NQ K], K-major
     ba_lo = o; o += 64 * 2 * NQ * 4;
-    t2s = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the subtracted sources [64][17] float2
-    t2a = o;   o += kT6Src * kT6T2Row * 8;       // T2 of the averaged sources
-    mtab = o;  o += kT6Src * 4 * 8;              // model matrices [64][4] float2
-    ph = o;    o += 2 * 2 * kT6Src * 16;         // phases of two time steps [2][sub 64, avg 64]
+    t2s = o;   o += kTc5Src * kTc5T2Row * 8;       // T2 of the subtracted sources [64][17] float2
+    t2a = o;   o += kTc5Src * kTc5T2Row * 8;       // T2 of the averaged sources
+    mtab = o;  o += kTc5Src * 4 * 8;              // model matrices [64][4] float2
+    ph = o;    o += 2 * 2 * kTc5Src * 16;         // phases of two time steps [2][sub 64, avg 64]
     bar = o;   o += 80;                          // mbarriers (sub done, avg done, strip 0, strip 1, sub
                                                  // operands ready, avg operands ready, phases 0, phases 1),
                                                  // TMEM address
@@ -92,21 +92,21 @@ struct T6Smem {
   }
 };
 
-inline int t6_nq(int n_chan) { return (((n_chan + 15) >> 4) + 15) & ~15; }
-inline size_t t6_pass_smem(int n_chan) { return (size_t)T6Smem(t6_nq(n_chan)).total; }
+inline int tc05_nq(int n_chan) { return (((n_chan + 15) >> 4) + 15) & ~15; }
+inline size_t tc05_pass_smem(int n_chan) { return (size_t)Tc05Smem(tc05_nq(n_chan)).total; }
 
 // TF32 rounding (to nearest, ties away from zero, as cvt.rna.tf32.f32 for
 // finite x below the FP32 maximum) by two integer operations
-__device__ __forceinline__ uint32_t t6_tf32(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ uint32_t tc05_tf32(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 // x = hi + lo, hi the TF32 rounding of x, lo the exact remainder (the MMA reads
 // lo truncated to TF32: error below 2^-21 |x|)
-__device__ __forceinline__ float2 t6_split(float x) {
-  const float hi = __uint_as_float(t6_tf32(x));
+__device__ __forceinline__ float2 tc05_split(float x) {
+  const float hi = __uint_as_float(tc05_tf32(x));
   return make_float2(hi, x - hi);
 }
 
 template <bool SUB, bool ACC>
-__global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a, int bk, int* err) {
+__global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArgs a, int bk, int* err) {
   using namespace tc05;
   const int nq = (a.n_chan + 15) >> 4;
   const int NQ = (nq + 15) & ~15;           // 16, 32 or 48
@@ -114,44 +114,44 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   const int nmain_a = NQ >> 4;              // the average's hi*hi accumulators: 1, 2 or 3
   const int n16 = 16 * NQ;
   const uint32_t strip_bytes = (uint32_t)a.n_chan * 32u;
-  const T6Smem L(NQ);
-  extern __shared__ __align__(1024) unsigned char t6_smem[];
-  float* strip0 = reinterpret_cast<float*>(t6_smem + L.strip);
-  unsigned char* bs_hi = t6_smem + L.bs_hi;
-  unsigned char* bs_lo = t6_smem + L.bs_lo;
-  unsigned char* ba_hi = t6_smem + L.ba_hi;
-  unsigned char* ba_lo = t6_smem + L.ba_lo;
-  float2* t2s = reinterpret_cast<float2*>(t6_smem + L.t2s);
-  float2* t2a = reinterpret_cast<float2*>(t6_smem + L.t2a);
-  float2* mtab = reinterpret_cast<float2*>(t6_smem + L.mtab);
-  PhaseAB* ph = reinterpret_cast<PhaseAB*>(t6_smem + L.ph);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(t6_smem + L.bar);      // see T6Smem::bar
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(t6_smem + L.bar + 64);
+  const Tc05Smem L(NQ);
+  extern __shared__ __align__(1024) unsigned char tc05_smem[];
+  float* strip0 = reinterpret_cast<float*>(tc05_smem + L.strip);
+  unsigned char* bs_hi = tc05_smem + L.bs_hi;
+  unsigned char* bs_lo = tc05_smem + L.bs_lo;
+  unsigned char* ba_hi = tc05_smem + L.ba_hi;
+  unsigned char* ba_lo = tc05_smem + L.ba_lo;
+  float2* t2s = reinterpret_cast<float2*>(tc05_smem + L.t2s);
+  float2* t2a = reinterpret_cast<float2*>(tc05_smem + L.t2a);
+  float2* mtab = reinterpret_cast<float2*>(tc05_smem + L.mtab);
+  PhaseAB* ph = reinterpret_cast<PhaseAB*>(tc05_smem + L.ph);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tc05_smem + L.bar);      // see Tc05Smem::bar
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tc05_smem + L.bar + 64);
   float* part = reinterpret_cast<float*>(ba_hi);    // [4 cg][64 k][8]: B_a is free in P4
 
   const int64_t bl = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qtr = warp & 3, cg = warp >> 2;
   const uint32_t lane_base = (uint32_t)(32 * qtr) << 16;
 
-  if (warp == 0) tmem_alloc(tslot, kT6Cols);
+  if (warp == 0) tmem_alloc(tslot, kTc5Cols);
   if (tid == 0) {
-    mbar_init(&mbar[0], kT6Issuers);        // subtraction MMAs done: one commit per issuer
+    mbar_init(&mbar[0], kTc5Issuers);        // subtraction MMAs done: one commit per issuer
     mbar_init(&mbar[1], nmain_a);           // average MMAs done: one commit per accumulator
     for (int i = 2; i < 8; ++i) mbar_init(&mbar[i], 1);   // each completed by one arrival
   }
-  const bool compute = tid < kT6Compute;
+  const bool compute = tid < kTc5Compute;
   // padding channels of both strips stay zero (the copies never write them)
-  for (int i = tid; compute && i < (n16 - a.n_chan) * 8; i += kT6Compute) {
+  for (int i = tid; compute && i < (n16 - a.n_chan) * 8; i += kTc5Compute) {
     strip0[a.n_chan * 8 + i] = 0.f;
     strip0[(n16 + a.n_chan) * 8 + i] = 0.f;
   }
   if (SUB)
-    for (int i = tid; compute && i < kT6Src * 4; i += kT6Compute) {
+    for (int i = tid; compute && i < kTc5Src * 4; i += kTc5Compute) {
       const int s = i >> 2, e = i & 3;
       mtab[i] = s < a.n_sub ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
     }
   // phases of sources beyond bk stay zero (the copies bring bk per role)
-  for (int i = tid; compute && i < 4 * kT6Src; i += kT6Compute) {
+  for (int i = tid; compute && i < 4 * kTc5Src; i += kTc5Compute) {
     ph[i].a = 0;
     ph[i].b = 0;
   }
@@ -181,14 +181,14 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     const uint32_t bytes = (uint32_t)bk * sizeof(PhaseAB);
     mbar_expect_tx(&mbar[6 + b], (SUB ? bytes : 0u) + (ACC ? bytes : 0u));
     const size_t at = ((size_t)bl * a.n_time + t) * bk;
-    if (SUB) bulk_load(ph + 2 * kT6Src * b, a.ph_sub + at, bytes, &mbar[6 + b]);
-    if (ACC) bulk_load(ph + 2 * kT6Src * b + kT6Src, a.ph_acc + at, bytes, &mbar[6 + b]);
+    if (SUB) bulk_load(ph + 2 * kTc5Src * b, a.ph_sub + at, bytes, &mbar[6 + b]);
+    if (ACC) bulk_load(ph + 2 * kTc5Src * b + kTc5Src, a.ph_acc + at, bytes, &mbar[6 + b]);
   };
-  // T2_k[r] of one role from its phases p[64]: [64][kT6T2Row]
+  // T2_k[r] of one role from its phases p[64]: [64][kTc5T2Row]
   auto t2_fill = [&](float2* t2, const PhaseAB* p) {
-    for (int i = tid; i < kT6Src * 16; i += kT6Compute) {
+    for (int i = tid; i < kTc5Src * 16; i += kTc5Compute) {
       const int k = i >> 4, r = i & 15;
-      t2[k * kT6T2Row + r] = phasor_hw((unsigned long long)r * p[k].b);
+      t2[k * kTc5T2Row + r] = phasor_hw((unsigned long long)r * p[k].b);
     }
   };
   // B_s = conj(T1_k[q]) of the subtracted sources: thread (q & 7 = lane & 7,
@@ -201,11 +201,11 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     unsigned long long x = p.a + (unsigned long long)(16 * ql) * p.b;
     for (int q = ql; q < NQ; q += 8, x += step) {
       const float2 z = phasor_hw(x);
-      const float hr = __uint_as_float(t6_tf32(z.x)), hi = __uint_as_float(t6_tf32(-z.y));
+      const float hr = __uint_as_float(tc05_tf32(z.x)), hi = __uint_as_float(tc05_tf32(-z.y));
       const int o = kmaj_byte(q, 2 * k, 128);
       *reinterpret_cast<float2*>(bs_hi + o) = make_float2(hr, hi);
-      *reinterpret_cast<float2*>(bs_lo + o) = make_float2(__uint_as_float(t6_tf32(z.x - hr)),
-                                                          __uint_as_float(t6_tf32(-z.y - hi)));
+      *reinterpret_cast<float2*>(bs_lo + o) = make_float2(__uint_as_float(tc05_tf32(z.x - hr)),
+                                                          __uint_as_float(tc05_tf32(-z.y - hi)));
     }
   };
   // A_s of warp (qtr, cg): rows m = 32 qtr + lane = 8 r + 2 e + o, sources
@@ -219,16 +219,16 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int k = 16 * cg + 8 * h + j;
-        const float2 m = mtab[4 * k + e], z = t2s[k * kT6T2Row + r];
+        const float2 m = mtab[4 * k + e], z = t2s[k * kTc5T2Row + r];
         const float ar = fmaf(m.x, z.x, m.y * z.y), ai = fmaf(m.y, z.x, -m.x * z.y);   // m conj(z)
         const float v0 = o ? ai : ar, v1 = o ? ar : -ai;
-        const uint32_t h0 = t6_tf32(v0), h1 = t6_tf32(v1);
+        const uint32_t h0 = tc05_tf32(v0), h1 = tc05_tf32(v1);
         vh[2 * j] = h0;
         vh[2 * j + 1] = h1;
         lo[16 * h + 2 * j] = __float_as_uint(v0 - __uint_as_float(h0));
         lo[16 * h + 2 * j + 1] = __float_as_uint(v1 - __uint_as_float(h1));
       }
-      tmem_st16(tmem + lane_base + kT6ColAHi + 32 * cg + 16 * h, vh);
+      tmem_st16(tmem + lane_base + kTc5ColAHi + 32 * cg + 16 * h, vh);
     }
   };
   auto as_store_lo = [&](const uint32_t (&lo)[32]) {
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       uint32_t vl[16];
       #pragma unroll
       for (int i = 0; i < 16; ++i) vl[i] = lo[16 * h + i];
-      tmem_st16(tmem + lane_base + kT6ColALo + 32 * cg + 16 * h, vl);
+      tmem_st16(tmem + lane_base + kTc5ColALo + 32 * cg + 16 * h, vl);
     }
   };
   // T1_k[q] of the averaged source k = 16 qtr + lane / 2 for the warp's tiles
@@ -271,12 +271,12 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
         for (int u = 0; u < 4; ++u) {
           const float2 t = t1v[4 * ch + u];
           const float v0 = o ? t.y : t.x, v1 = o ? t.x : -t.y;     // i = 0, i = 1
-          h0[u] = t6_tf32(v0);
-          h1[u] = t6_tf32(v1);
+          h0[u] = tc05_tf32(v0);
+          h1[u] = tc05_tf32(v1);
           l0[u] = __float_as_uint(v0 - __uint_as_float(h0[u]));
           l1[u] = __float_as_uint(v1 - __uint_as_float(h1[u]));
         }
-        const uint32_t col = kT6ColALo + q0 + 4 * ch;
+        const uint32_t col = kTc5ColALo + q0 + 4 * ch;
         tmem_st4(tmem + lane_base + col, h0);
         tmem_st4(tmem + lane_base + NQ + col, h1);
         tmem_st4(tmem + lane_base + 2 * NQ + col, l0);
@@ -288,10 +288,10 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   // (n = 4 r + e, K' = o NQ + q + u): one 16-byte store each for hi and lo
   auto ba_put4 = [&](int n, int q, int o, const float (&x)[4]) {
     float4 h, l;
-    float2 s2 = t6_split(x[0]); h.x = s2.x; l.x = s2.y;
-    s2 = t6_split(x[1]); h.y = s2.x; l.y = s2.y;
-    s2 = t6_split(x[2]); h.z = s2.x; l.z = s2.y;
-    s2 = t6_split(x[3]); h.w = s2.x; l.w = s2.y;
+    float2 s2 = tc05_split(x[0]); h.x = s2.x; l.x = s2.y;
+    s2 = tc05_split(x[1]); h.y = s2.x; l.y = s2.y;
+    s2 = tc05_split(x[2]); h.z = s2.x; l.z = s2.y;
+    s2 = tc05_split(x[3]); h.w = s2.x; l.w = s2.y;
     const int off = kmaj_byte(n, o * NQ + q, 2 * NQ);
     *reinterpret_cast<float4*>(ba_hi + off) = h;
     *reinterpret_cast<float4*>(ba_lo + off) = l;
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   // consecutive words (conflict-free)
   auto sub_epilogue = [&](float* strip) {
     const int r = 4 * qtr + (lane >> 3), e = (lane >> 1) & 3, o = lane & 1, n = 4 * r + e, q0 = cg * QW;
-    const uint32_t base = tmem + lane_base + kT6ColAcc + q0;
+    const uint32_t base = tmem + lane_base + kTc5ColAcc + q0;
     #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       if (4 * ch < QW) {
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     float pr[4] = {0.f, 0.f, 0.f, 0.f}, pi[4] = {0.f, 0.f, 0.f, 0.f};
     #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
-      const float2 z = t2a[k * kT6T2Row + 4 * cg + rr];
+      const float2 z = t2a[k * kTc5T2Row + 4 * cg + rr];
       const float wr = o ? -z.y : z.x, wi = o ? z.x : z.y;
       #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       pi[e] += __shfl_xor_sync(0xffffffffu, pi[e], 1);
     }
     if (o == 0) {
-      float4* dst = reinterpret_cast<float4*>(part + (cg * kT6Src + k) * 8);
+      float4* dst = reinterpret_cast<float4*>(part + (cg * kTc5Src + k) * 8);
       dst[0] = make_float4(pr[0], pi[0], pr[1], pi[1]);
       dst[1] = make_float4(pr[2], pi[2], pr[3], pi[3]);
     }
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     const int k = tid >> 3, i = tid & 7;
     float x = part[k * 8 + i];
     #pragma unroll
-    for (int c = 1; c < 4; ++c) x += part[(c * kT6Src + k) * 8 + i];
+    for (int c = 1; c < 4; ++c) x += part[(c * kTc5Src + k) * 8 + i];
     const float y = x - kc;
     const float tt = ks + y;
     kc = (tt - ks) - y;
@@ -378,10 +378,10 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   };
 
   // the 16 compute warps' own barrier (the MMA-issuing warp is not in it)
-  auto csync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(kT6Compute) : "memory"); };
+  auto csync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(kTc5Compute) : "memory"); };
   // a bounded mbarrier wait that also gives up once another thread has raised s_bad
   auto wait_or_bad = [&](uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kT6MaxPolls / 64; ++it) {
+    for (uint32_t it = 0; it < kTc5MaxPolls / 64; ++it) {
       if (mbar_wait(bar, parity, 64, 20000)) return true;
       if (*reinterpret_cast<volatile int*>(&s_bad)) return false;
     }
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     // them all leaves the tensor core half idle).  Each accumulator takes the
     // cross terms (lo*hi, hi*lo) of its 4 k-steps first, then their hi*hi
     // products
-    const int g = warp - kT6Compute / 32;
+    const int g = warp - kTc5Compute / 32;
     if (lane == 0) {
       uint32_t p_sub = 0, p_avg = 0;
       const uint32_t id_s = idesc_tf32(128, NQ), id_a = idesc_tf32(128, 64);
@@ -406,9 +406,9 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
           #pragma unroll
           for (int j = 0; j < 12; ++j) {
             const int s = 4 * g + (j & 3);
-            const uint32_t acol = tmem + (j < 4 ? kT6ColALo : kT6ColAHi) + 8 * s;   // lo(A) for j < 4, else hi(A)
+            const uint32_t acol = tmem + (j < 4 ? kTc5ColALo : kTc5ColAHi) + 8 * s;   // lo(A) for j < 4, else hi(A)
             const uint64_t bd = (j >= 4 && j < 8 ? dbs_lo : dbs_hi) + 16 * s;
-            mma_ts(tmem + kT6ColAcc + g * NQ, acol, bd, id_s, j != 0);
+            mma_ts(tmem + kTc5ColAcc + g * NQ, acol, bd, id_s, j != 0);
           }
           commit(&mbar[0]);
         }
@@ -419,9 +419,9 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
           #pragma unroll
           for (int j = 0; j < 12; ++j) {
             const int s = 4 * g + (j & 3);
-            const uint32_t acol = tmem + kT6ColALo + (j < 4 ? 2 * NQ : 0) + 8 * s;
+            const uint32_t acol = tmem + kTc5ColALo + (j < 4 ? 2 * NQ : 0) + 8 * s;
             const uint64_t bd = (j >= 4 && j < 8 ? dba_lo : dba_hi) + 16 * s;
-            mma_ts(tmem + kT6ColAcc + 64 * g, acol, bd, id_a, j != 0);
+            mma_ts(tmem + kTc5ColAcc + 64 * g, acol, bd, id_a, j != 0);
           }
           commit(&mbar[1]);
         }
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
     uint32_t par_sub = 0, par_avg = 0;
     // thread 0: strip loads issued into / landed in buffers 0 and 1 (uses of each mbarrier)
     int issued0 = 0, issued1 = 0, landed0 = 0, landed1 = 0;
-    auto ph_slot = [&](int t) { return ph + 2 * kT6Src * (t & 1); };   // [sub 64][avg 64]
+    auto ph_slot = [&](int t) { return ph + 2 * kTc5Src * (t & 1); };   // [sub 64][avg 64]
     auto wait_ph = [&](int t) { return wait_or_bad(&mbar[6 + (t & 1)], (uint32_t)(t >> 1) & 1u); };
 
     if (tid == 0) {
@@ -475,8 +475,8 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
         if (!wait_ph(t)) s_bad = 1;
         csync();                             // parts written; t2a free
         if (t > 0) avg_accumulate();
-        aa_compute(t1v, ph_slot(t) + kT6Src);
-        t2_fill(t2a, ph_slot(t) + kT6Src);
+        aa_compute(t1v, ph_slot(t) + kTc5Src);
+        t2_fill(t2a, ph_slot(t) + kTc5Src);
       }
       // this step's strip has landed; the subtraction MMAs are complete
       {
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
         if (!wait_or_bad(&mbar[1], par_avg)) s_bad = 1;
         par_avg ^= 1;
         fence_after_sync();
-        const uint32_t base = tmem + lane_base + kT6ColAcc + 16 * cg;
+        const uint32_t base = tmem + lane_base + kTc5ColAcc + 16 * cg;
         tmem_ld16(base, H);
         #pragma unroll
         for (int g = 1; g < 3; ++g) {
@@ -562,9 +562,9 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
       // a load still in flight after a failed wait must land before the CTA's
       // shared memory goes away (bounded); stores are waited for unconditionally
       for (int u = landed0; u < issued0; ++u)
-        if (!mbar_wait(&mbar[2], (uint32_t)u & 1u, kT6MaxPolls)) break;
+        if (!mbar_wait(&mbar[2], (uint32_t)u & 1u, kTc5MaxPolls)) break;
       for (int u = landed1; u < issued1; ++u)
-        if (!mbar_wait(&mbar[3], (uint32_t)u & 1u, kT6MaxPolls)) break;
+        if (!mbar_wait(&mbar[3], (uint32_t)u & 1u, kTc5MaxPolls)) break;
       bulk_wait_all();
       if (s_bad) atomicExch(err, 1);
     }
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kT6Threads, 1) k_block_pass_t6(BlockPassArgs a
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  if (warp == 0) tmem_dealloc(tmem, kT6Cols);
+  if (warp == 0) tmem_dealloc(tmem, kTc5Cols);
 }
 
 }  // namespace rts

@@ -12,8 +12,7 @@
 
 #include "als_kernels.cuh"
 #include "block_kernels.cuh"
-#include "block_t5_kernels.cuh"
-#include "block_t6_kernels.cuh"
+#include "block_tc05_kernels.cuh"
 #include "block_tc_kernels.cuh"
 #include "common.cuh"
 #include "grad_kernels.cuh"
@@ -30,8 +29,7 @@ struct rts_peel_t {
   int n_ant = 0, n_chan = 0, n_time = 0, n_iter = 0, precision = 0, max_sources = 0;
   int per_pass = 1;                // sources per streaming pass (1 or RTS_BLOCK)
   bool block_tc = false;           // blocked passes as TF32 mma.sync (k_block_pass_tc)
-  bool block_t5 = false;           // blocked passes as tcgen05 MMAs (k_block_pass_t6)
-  bool block_t5v1 = false;         // the first tcgen05 pass (k_block_pass_t5), for comparison
+  bool block_tc05 = false;           // blocked passes as tcgen05 MMAs (k_block_pass_tc05)
   int* d_perr = nullptr;           // [1] set by a tcgen05 pass whose mbarrier wait ran out
   int64_t n_bl = 0;
   double nu0 = 0, dnu = 0;
@@ -285,8 +283,7 @@ int setup_block_solve(rts_peel_t* h);
 
 // the tcgen05 pass holds all 512 TMEM columns: at least 116 KB of shared memory
 // keeps it at one CTA per SM (a second CTA would wait in its TMEM allocation)
-size_t t5_launch_smem(const rts_peel_t* h) { return std::max<size_t>(t5_pass_smem(h->n_chan), 116 * 1024); }
-size_t t6_launch_smem(const rts_peel_t* h) { return std::max<size_t>(t6_pass_smem(h->n_chan), 116 * 1024); }
+size_t tc05_launch_smem(const rts_peel_t* h) { return std::max<size_t>(tc05_pass_smem(h->n_chan), 116 * 1024); }
 
 int ensure_block_workspace(rts_peel_t* h) {
   if (h->b_avg) return RTS_OK;
@@ -313,18 +310,11 @@ int ensure_block_workspace(rts_peel_t* h) {
   if (rc) return rc;
   RTS_CUDA(h, cudaMalloc((void**)&h->d_perr, sizeof(int)));
   RTS_CUDA(h, cudaMemset(h->d_perr, 0, sizeof(int)));
-  if (h->block_t5 && !h->block_t5v1) {
-    const int tsm = (int)t6_launch_smem(h);
-    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t6<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
-    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t6<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
-    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t6<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
-    return RTS_OK;
-  }
-  if (h->block_t5) {
-    const int tsm = (int)t5_launch_smem(h);
-    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t5<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
-    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t5<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
-    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_t5<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+  if (h->block_tc05) {
+    const int tsm = (int)tc05_launch_smem(h);
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
     return RTS_OK;
   }
   if (h->block_tc) {
@@ -406,19 +396,11 @@ void block_pass_t(bool sub, bool acc, const BlockPassArgs& a, unsigned grid, siz
 int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a, cudaStream_t s) {
   Span span(h, RTS_K_BLOCK_PASS, s);
   const unsigned grid = (unsigned)h->n_bl;
-  if (h->block_t5 && !h->block_t5v1) {
-    const size_t tsm = t6_launch_smem(h);
-    if (sub && acc) k_block_pass_t6<true, true><<<grid, kT6Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
-    else if (sub) k_block_pass_t6<true, false><<<grid, kT6Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
-    else k_block_pass_t6<false, true><<<grid, kT6Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
-    span.end(1);
-    return check_launch(h, "block pass launch");
-  }
-  if (h->block_t5) {
-    const size_t tsm = t5_launch_smem(h);
-    if (sub && acc) k_block_pass_t5<true, true><<<grid, kT5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
-    else if (sub) k_block_pass_t5<true, false><<<grid, kT5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
-    else k_block_pass_t5<false, true><<<grid, kT5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
+  if (h->block_tc05) {
+    const size_t tsm = tc05_launch_smem(h);
+    if (sub && acc) k_block_pass_tc05<true, true><<<grid, kTc5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
+    else if (sub) k_block_pass_tc05<true, false><<<grid, kTc5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
+    else k_block_pass_tc05<false, true><<<grid, kTc5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
     span.end(1);
     return check_launch(h, "block pass launch");
   }
@@ -717,12 +699,12 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   if (per_pass > 1 && (size_t)cfg->n_chan * 32 + 2048 + 32768 > 200 * 1024)
     return fail(nullptr, RTS_EINVAL, "the blocked peel needs n_chan*32 + 34 KB <= 200 KB of shared memory "
                                      "(n_chan <= 5300); use sources_per_pass = 1");
-  if (cfg->block_kernel < RTS_BLOCK_AUTO || cfg->block_kernel > RTS_BLOCK_TCGEN05 + 1)
+  if (cfg->block_kernel < RTS_BLOCK_AUTO || cfg->block_kernel > RTS_BLOCK_TCGEN05)
     return fail(nullptr, RTS_EINVAL,
                 "block_kernel must be RTS_BLOCK_AUTO, RTS_BLOCK_FMA, RTS_BLOCK_TENSOR or RTS_BLOCK_TCGEN05");
   if (cfg->block_kernel == RTS_BLOCK_TENSOR && cfg->n_chan > kTcMaxChan)
     return fail(nullptr, RTS_EINVAL, "the tensor-core blocked pass needs n_chan <= 960");
-  if (cfg->block_kernel >= RTS_BLOCK_TCGEN05 && cfg->n_chan > kT6MaxChan)
+  if (cfg->block_kernel == RTS_BLOCK_TCGEN05 && cfg->n_chan > kTc5MaxChan)
     return fail(nullptr, RTS_EINVAL, "the tcgen05 blocked pass needs n_chan <= 768");
 
   if (cfg->solve_kernel != RTS_SOLVE_AUTO && cfg->solve_kernel != RTS_SOLVE_LAUNCHES)
@@ -737,9 +719,8 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   {
     int bk = cfg->block_kernel;
     if (bk == RTS_BLOCK_AUTO)
-      bk = cfg->n_chan <= kT6MaxChan ? RTS_BLOCK_TCGEN05 : (cfg->n_chan <= kTcMaxChan ? RTS_BLOCK_TENSOR : RTS_BLOCK_FMA);
-    h->block_t5 = per_pass > 1 && bk >= RTS_BLOCK_TCGEN05;
-    h->block_t5v1 = per_pass > 1 && bk == RTS_BLOCK_TCGEN05 + 1;
+      bk = cfg->n_chan <= kTc5MaxChan ? RTS_BLOCK_TCGEN05 : (cfg->n_chan <= kTcMaxChan ? RTS_BLOCK_TENSOR : RTS_BLOCK_FMA);
+    h->block_tc05 = per_pass > 1 && bk == RTS_BLOCK_TCGEN05;
     h->block_tc = per_pass > 1 && bk == RTS_BLOCK_TENSOR;
   }
   h->n_ant = cfg->n_ant; h->n_chan = cfg->n_chan; h->n_time = cfg->n_time;
@@ -1144,7 +1125,7 @@ int rts_host_free(void* p) {
 int rts_peel_kernels(const rts_peel_t* h, int32_t* block_kernel, int32_t* solve_kernel) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (block_kernel)
-    *block_kernel = h->per_pass == 1 ? 0 : (h->block_t5 ? RTS_BLOCK_TCGEN05 : (h->block_tc ? RTS_BLOCK_TENSOR : RTS_BLOCK_FMA));
+    *block_kernel = h->per_pass == 1 ? 0 : (h->block_tc05 ? RTS_BLOCK_TCGEN05 : (h->block_tc ? RTS_BLOCK_TENSOR : RTS_BLOCK_FMA));
   if (solve_kernel)
     *solve_kernel = h->b_avg ? (h->bs_ok ? RTS_SOLVE_AUTO : RTS_SOLVE_LAUNCHES) : h->solve_kernel;
   return RTS_OK;

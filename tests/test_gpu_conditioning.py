@@ -6,15 +6,20 @@ Jones matrices move by ~1e-6 relative when its input moves by 1e-7 x rms.  A
 path that holds the residual in FP32 perturbs it at that level on every pass
 (each element rounded to 2^-24 of itself, each FP32 sum carrying a few such
 roundings), so its agreement with the oracle is bounded by that
-amplification, not by 1e-5.  The bound here is max(1e-5, 30 x the oracle's
-response to a 1e-7 x rms perturbation), i.e. an FP32 path is allowed the
-oracle's own response to ~3e-6 x rms of input error, for both schedules (one
-source per pass, blocks of 64).  Statuses and relative changes are compared
-as everywhere else.
+amplification, not by 1e-5.  The bound here is max(1e-5, 30 x g x the
+oracle's response to a 1e-7 x rms perturbation): an FP32 path is allowed the
+oracle's own response to ~3e-6 x rms of input error, times g, how much larger
+the data its averages are taken over are than the sequential peel's.  One
+source per pass: g = 1.  Blocks of 64: each block's averages are taken over the
+residual that still holds the whole block, so its FP32 rounding is larger by
+g = max over blocks of rms(residual at the block's start) / rms(residual after
+the block), from the oracle's own peel.  Statuses and relative changes are
+compared as everywhere else.
 """
 import numpy as np
 import pytest
 
+import oracle
 from synth import Cadence
 
 torch = pytest.importorskip("torch")
@@ -34,13 +39,25 @@ def built():
     build.build()
 
 
+def block_growth(cad, V, block):
+    """max over blocks of rms(oracle residual at the block's start) / rms(after it)."""
+    src = cad.sources()
+    starts = list(range(0, cad.n_src, block)) + [cad.n_src]
+    rms_at = [rms_of(V)]
+    for s in starts[1:]:
+        R, _, _ = oracle.peel(cad.uvw(), cad.freqs(), V, src[:s])
+        rms_at.append(rms_of(R))
+    return max(a / b for a, b in zip(rms_at[:-1], rms_at[1:]))
+
+
 @pytest.mark.parametrize("per_pass", [1, 64], ids=["one-source-per-pass", "blocks-of-64"])
 def test_ill_conditioned_cadence_within_its_conditioning_bound(built, per_pass):
     cad = ILL
     V, R_ref, J_ref, st_ref, rel_ref = oracle_case(cad)
     dj, dr = conditioning(cad, V)
-    bound_j = max(TOL["mixed"], AMPLIFICATION * dj)
-    bound_r = max(TOL["mixed"], AMPLIFICATION * dr)
+    g = 1.0 if per_pass == 1 else block_growth(cad, V, per_pass)
+    bound_j = max(TOL["mixed"], AMPLIFICATION * g * dj)
+    bound_r = max(TOL["mixed"], AMPLIFICATION * g * dr)
     p = make_peeler(cad, "mixed", per_pass=per_pass)
     resid, jones, st = p.cadence(to_dev(V, "mixed"), cad.sources())
     torch.cuda.synchronize()
@@ -49,7 +66,7 @@ def test_ill_conditioned_cadence_within_its_conditioning_bound(built, per_pass):
     err_r = np.abs(resid.cpu().numpy() - R_ref).max() / rms_of(V)
     err_j = jones_rel(jones.cpu().numpy(), J_ref)
     print(f"64x96x150 per_pass={per_pass}: residual {err_r:.2e} (bound {bound_r:.2e}), Jones {err_j:.2e} "
-          f"(bound {bound_j:.2e}); oracle response to 1e-7 x rms: {dj:.2e} / {dr:.2e}")
+          f"(bound {bound_j:.2e}); oracle response to 1e-7 x rms: {dj:.2e} / {dr:.2e}; growth {g:.2f}")
     assert err_r <= bound_r
     assert err_j <= bound_j
     check_status(f"ill-{per_pass}", st, st_ref, rel, rel_ref)
