@@ -34,6 +34,7 @@ struct rts_peel_t {
   int64_t n_bl = 0;
   double nu0 = 0, dnu = 0;
   int device = 0;
+  int n_sm = 1;                    // multiprocessors of the device (grid sizing)
   size_t elem = 8;                 // bytes per complex element of the cube
   // device workspace, allocated once in rts_peel_init
   double* d_uvw = nullptr;         // [n_time][n_ant][3]
@@ -250,7 +251,7 @@ void launch_block_geometry(rts_peel_t* h, int b, int n_src, cudaStream_t ps) {
   const int BK = h->per_pass, s0 = b * BK, nblk = std::min(BK, n_src - s0);
   const int r = b % rts_peel_t::kRing;
   const double* src = h->d_src + 3 * (size_t)s0;
-  const unsigned g = 4 * 152;
+  const unsigned g = 4 * (unsigned)h->n_sm;
   const double nu0_c = h->nu0 / kCLight, dnu_c = h->dnu / kCLight;
   const unsigned grid = (unsigned)h->n_bl;
   PhaseAB* ph = h->b_ph[r];
@@ -735,6 +736,8 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   };
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+    return bail(e, "cudaDeviceGetAttribute");
   std::vector<int2> map((size_t)n_bl);
   {
     int64_t b = 0;
@@ -1152,7 +1155,7 @@ int rts_peel_phases(rts_peel_t* h, double l, double m, int32_t n_pair, const int
   if (n_pair == 0) return RTS_OK;
   if (!d_tb || !d_phase) return fail(h, RTS_EINVAL, "d_tb and d_phase are required");
   const int64_t n = (int64_t)n_pair * h->n_chan;
-  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)h->n_sm * 16);
   k_phase_table<<<grid, 256, 0, as_stream(stream)>>>(h->d_uvw, h->d_bl_ant, h->n_ant, h->n_chan, h->n_time, h->n_bl,
                                                       make_dir(l, m, 1.0), h->nu0 / kCLight, h->dnu / kCLight,
                                                       n_pair, d_tb, rounded, d_phase);
