@@ -236,13 +236,17 @@ int rts_peel_rel(rts_peel_t* h, int32_t n_src, double* h_rel, void* stream);
  * turns in [-1/2, 1/2), as the peel's kernels form it: the FP64 delay
  * tau = u l + v m + w (n - 1), the Q0.64 fixed-point phases A = frac(tau nu_0 / c)
  * and B = frac(tau dnu / c), and channel c at A + c B modulo one turn (exact
- * integer arithmetic).  rounded = 0 returns that Q0.64 phase; rounded = 1 the
- * FP32 value the kernels hand to the hardware sin/cos (rounded to Q0.32 first).
- * A pair with t or bl out of range gets NaN.  Asynchronous on `stream`.
- * RTS_EINVAL for a NULL handle or pointer, n_pair < 0, rounded not 0 or 1,
- * or a direction with l^2 + m^2 >= 1. */
+ * integer arithmetic).  form = 0 returns that Q0.64 phase (the streaming,
+ * predict and adjoint kernels); form = 1 the FP32 value the kernels hand to the
+ * hardware sin/cos (rounded to Q0.32 first); form = 2 the Q0.64 phase as the
+ * blocked schedule forms it, from the two antennas' delays
+ * tau_i = u_i l + v_i m + w_i (n - 1) (the same geometry: uvw_ij = uvw_i - uvw_j)
+ * as the difference of their Q0.64 phases modulo one turn.  A pair with t or
+ * bl out of range gets NaN.  Asynchronous on `stream`.  RTS_EINVAL for a NULL
+ * handle or pointer, n_pair < 0, form not 0, 1 or 2, or a direction with
+ * l^2 + m^2 >= 1. */
 int rts_peel_phases(rts_peel_t* h, double l, double m, int32_t n_pair, const int32_t* d_tb,
-                    int32_t rounded, double* d_phase, void* stream);
+                    int32_t form, double* d_phase, void* stream);
 
 /* The solve step without any allocation, for callers that cannot call
  * cudaMalloc or create a handle: code that runs after a real-time pipeline has

@@ -213,8 +213,8 @@ def rts_peel_rel(h, n_src, h_rel, stream):
     return _check(lib().rts_peel_rel(h, n_src, h_rel, stream), h)
 
 
-def rts_peel_phases(h, l, m, n_pair, d_tb, rounded, d_phase, stream):
-    return _check(lib().rts_peel_phases(h, float(l), float(m), n_pair, d_tb, rounded, d_phase, stream), h)
+def rts_peel_phases(h, l, m, n_pair, d_tb, form, d_phase, stream):
+    return _check(lib().rts_peel_phases(h, float(l), float(m), n_pair, d_tb, form, d_phase, stream), h)
 
 
 def rts_peel_pipeline_submit(h, h_vis, h_resid, n_src, h_src, h_jones, h_status):

@@ -232,15 +232,44 @@ __device__ inline unsigned long long pair_mid_phase(unsigned long long dA, long 
 
 // ---------------------------------------------------------------------------
 // geometry of one block (no visibility data): Q0.64 phases of its sources,
-//   ph[bl][t][k] = (frac(tau nu_0 / c), frac(tau dnu / c))
+//   ph[bl][t][k] = (frac(tau nu_0 / c), frac(tau dnu / c)).
+// The array's baselines are antenna pairs with (u, v, w)_ij = uvw_i - uvw_j, so
+// tau_ij = tau_i - tau_j with the antenna delay tau_i = u_i l + v_i m + w_i (n - 1),
+// and the Q0.64 phases of a baseline are the differences of its antennas'
+// phases modulo one turn (2^64: exact integer arithmetic).  The FP64 work is
+// per (time, antenna, source) instead of per (time, baseline, source); the
+// result differs from the per-baseline FP64 evaluation by the rounding of the
+// antenna products (~1e-16 of tau nu / c, below 1e-12 turns).
+
+// aph[t][i][k] = (frac(tau_i nu_0 / c), frac(tau_i dnu / c)) for the block's sources
+template <int BK>
+__global__ void __launch_bounds__(256) k_block_ant_phases(const double* __restrict__ src, int n_blk,
+                                                         const double* __restrict__ uvw, int n_ant, int n_time,
+                                                         double nu0_c, double dnu_c, PhaseAB* __restrict__ aph) {
+  const int64_t n = (int64_t)n_time * n_ant * BK;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q % BK);
+    const int64_t ti = q / BK;                  // t * n_ant + i
+    PhaseAB p;
+    p.a = 0; p.b = 0;
+    if (k < n_blk) {
+      const double l = src[3 * k], m = src[3 * k + 1];
+      const double r2 = l * l + m * m;
+      const double nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
+      const double* x = uvw + ti * 3;
+      const double tau = x[0] * l + x[1] * m + x[2] * nm1;
+      p.a = frac_q64(tau * nu0_c);
+      p.b = frac_q64(tau * dnu_c);
+    }
+    aph[q] = p;
+  }
+}
 
 template <int BK>
-__global__ void __launch_bounds__(256) k_block_phases(const double* __restrict__ src, int n_blk,
-                                                     const double* __restrict__ uvw,
+__global__ void __launch_bounds__(256) k_block_phases(const PhaseAB* __restrict__ aph, int n_blk,
                                                      const int2* __restrict__ bl_ant, int n_ant,
-                                                     int n_time, int n_chan, int64_t n_bl, double nu0_c,
-                                                     double dnu_c, PhaseAB* __restrict__ ph,
-                                                     GeoTrig* __restrict__ trig) {
+                                                     int n_time, int n_chan, int64_t n_bl,
+                                                     PhaseAB* __restrict__ ph, GeoTrig* __restrict__ trig) {
   const int64_t n = n_bl * n_time * BK;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(q % BK);
@@ -249,14 +278,10 @@ __global__ void __launch_bounds__(256) k_block_phases(const double* __restrict__
     const int t = (int)(r % n_time);
     const int64_t bl = r / n_time;
     const int2 ij = bl_ant[bl];
-    SrcDir d;
-    d.l = src[3 * k]; d.m = src[3 * k + 1]; d.S = src[3 * k + 2];
-    const double r2 = d.l * d.l + d.m * d.m;
-    d.nm1 = -r2 / (1.0 + sqrt(1.0 - r2));
-    const double tau = delay_m(uvw, n_ant, t, ij.x, ij.y, d);
+    const PhaseAB pi = aph[((int64_t)t * n_ant + ij.x) * BK + k], pj = aph[((int64_t)t * n_ant + ij.y) * BK + k];
     PhaseAB p;
-    p.a = frac_q64(tau * nu0_c);
-    p.b = frac_q64(tau * dnu_c);
+    p.a = pi.a - pj.a;                          // modulo 2^64
+    p.b = pi.b - pj.b;
     ph[q] = p;
     GeoTrig g;
     const long long bs = (long long)p.b;                           // signed B

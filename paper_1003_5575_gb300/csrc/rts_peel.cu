@@ -61,6 +61,7 @@ struct rts_peel_t {
   PhaseAB* b_ph[kRing] = {};       // [n_bl][n_time][BK] phases of a block
   GeoTrig* b_trig[kRing] = {};     // [n_bl][n_time][BK] trigonometry for D_jk
   float2* b_dir[kRing] = {};       // [n_bl][BK(BK-1)/2] in-block closed-form averages D_jk
+  PhaseAB* b_aph = nullptr;        // [n_time][n_ant][BK] antenna phases of the block being prepared
   float2* b_avg = nullptr;         // [BK][n_bl][4] plain averages of a block
   float2* b_model = nullptr;       // [BK][n_bl][4] model matrices of a block
   // persistent block solve (k_block_solve, one cooperative launch per block)
@@ -258,8 +259,10 @@ void launch_block_geometry(rts_peel_t* h, int b, int n_src, cudaStream_t ps) {
   GeoTrig* tg = h->b_trig[r];
   float2* Dt = h->b_dir[r];
 #define RTS_GEOM(BKV)                                                                                   \
-  k_block_phases<BKV><<<g, 256, 0, ps>>>(src, nblk, h->d_uvw, h->d_bl_ant, h->n_ant, h->n_time,     \
-                                         h->n_chan, h->n_bl, nu0_c, dnu_c, ph, tg);                     \
+  k_block_ant_phases<BKV><<<g, 256, 0, ps>>>(src, nblk, h->d_uvw, h->n_ant, h->n_time, nu0_c, dnu_c,   \
+                                             h->b_aph);                                                 \
+  k_block_phases<BKV><<<g, 256, 0, ps>>>(h->b_aph, nblk, h->d_bl_ant, h->n_ant, h->n_time, h->n_chan,  \
+                                         h->n_bl, ph, tg);                                              \
   if (nblk > 1)                                                                                          \
     k_block_dirichlet<BKV><<<grid, 256, 0, ps>>>(ph, tg, nblk, Dt, h->n_bl, h->n_time, h->n_chan);
   switch (BK) {
@@ -269,7 +272,7 @@ void launch_block_geometry(rts_peel_t* h, int b, int n_src, cudaStream_t ps) {
     default: RTS_GEOM(64) break;
   }
 #undef RTS_GEOM
-  h->launches[RTS_K_BLOCK_FIX] += nblk > 1 ? 2 : 1;
+  h->launches[RTS_K_BLOCK_FIX] += nblk > 1 ? 3 : 2;
 }
 
 template <int BK>
@@ -297,6 +300,7 @@ int ensure_block_workspace(rts_peel_t* h) {
     RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_ready[r], cudaEventDisableTiming));
     RTS_CUDA(h, cudaEventCreateWithFlags(&h->b_ev_free[r], cudaEventDisableTiming));
   }
+  RTS_CUDA(h, cudaMalloc((void**)&h->b_aph, (size_t)h->n_time * h->n_ant * BK * sizeof(PhaseAB)));
   RTS_CUDA(h, cudaMalloc((void**)&h->b_avg, (size_t)BK * h->n_bl * 4 * sizeof(float2)));
   RTS_CUDA(h, cudaMalloc((void**)&h->b_model, (size_t)BK * h->n_bl * 4 * sizeof(float2)));
   int lo_prio = 0, hi_prio = 0;
@@ -1145,20 +1149,20 @@ int rts_peel_rel(rts_peel_t* h, int32_t n_src, double* h_rel, void* stream) {
   return RTS_OK;
 }
 
-int rts_peel_phases(rts_peel_t* h, double l, double m, int32_t n_pair, const int32_t* d_tb, int32_t rounded,
+int rts_peel_phases(rts_peel_t* h, double l, double m, int32_t n_pair, const int32_t* d_tb, int32_t form,
                     double* d_phase, void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (!std::isfinite(l) || !std::isfinite(m) || !(l * l + m * m < 1.0))
     return fail(h, RTS_EINVAL, "direction must be finite with l^2 + m^2 < 1");
   if (n_pair < 0) return fail(h, RTS_EINVAL, "n_pair must be >= 0");
-  if (rounded != 0 && rounded != 1) return fail(h, RTS_EINVAL, "rounded must be 0 or 1");
+  if (form < 0 || form > 2) return fail(h, RTS_EINVAL, "form must be 0, 1 or 2");
   if (n_pair == 0) return RTS_OK;
   if (!d_tb || !d_phase) return fail(h, RTS_EINVAL, "d_tb and d_phase are required");
   const int64_t n = (int64_t)n_pair * h->n_chan;
   const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)h->n_sm * 16);
   k_phase_table<<<grid, 256, 0, as_stream(stream)>>>(h->d_uvw, h->d_bl_ant, h->n_ant, h->n_chan, h->n_time, h->n_bl,
                                                       make_dir(l, m, 1.0), h->nu0 / kCLight, h->dnu / kCLight,
-                                                      n_pair, d_tb, rounded, d_phase);
+                                                      n_pair, d_tb, form, d_phase);
   return check_launch(h, "phase table launch");
 }
 
@@ -1172,7 +1176,7 @@ void rts_peel_destroy(rts_peel_t* h) {
   if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
   void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
                   h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage,
-                  h->b_avg, h->b_model, h->b_sync, h->b_part, h->d_perr, h->t_mom, h->t_X[0],
+                  h->b_avg, h->b_aph, h->b_model, h->b_sync, h->b_part, h->d_perr, h->t_mom, h->t_X[0],
                   h->t_X[1], h->t_Xf[0], h->t_Xf[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -184,12 +184,14 @@ class Peeler:
         _abi.rts_peel_rel(self.h, n_src, out.ctypes.data_as(_dp), _stream(stream))
         return out[:n_src]
 
-    def phases(self, l: float, m: float, tb, rounded: bool = False, stream=None) -> torch.Tensor:
+    def phases(self, l: float, m: float, tb, form: int = 0, stream=None) -> torch.Tensor:
         """The peel's per-channel phase of direction (l, m), in turns, on the
-        (time, baseline) pairs tb ([n][2] int): float64 [n][n_chan]."""
+        (time, baseline) pairs tb ([n][2] int): float64 [n][n_chan].  form 0:
+        Q0.64 phase of the baseline delay; 1: its FP32 sin/cos argument; 2: the
+        blocked schedule's difference of antenna phases."""
         tb = torch.as_tensor(np.ascontiguousarray(tb, dtype=np.int32).reshape(-1, 2), device=self.device)
         out = torch.empty((tb.shape[0], self.n_chan), dtype=torch.float64, device=self.device)
-        _abi.rts_peel_phases(self.h, l, m, tb.shape[0], _ptr(tb), int(rounded), _ptr(out), _stream(stream))
+        _abi.rts_peel_phases(self.h, l, m, tb.shape[0], _ptr(tb), int(form), _ptr(out), _stream(stream))
         return out
 
     def grad(self, vis: torch.Tensor, jones: torch.Tensor, src: torch.Tensor,
