@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x;
+  const int64_t gstride = (int64_t)G * kSolveThreads;
   const int nquad = (a.apc + 3) >> 2;
   // warps per quad: all 16 share the terms when the CTA has one quad (n_ant <= 4 G)
   const int wpq = nquad <= 1 ? 16 : (nquad == 2 ? 8 : 4);
@@ -218,19 +219,12 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
     // ---- per baseline: model matrix of source q-1, corrected average of source q
     const bool model = q > 0, corr = q < a.n_blk;
     const float Sprev = model ? (float)a.src[3 * (k - 1) + 2] : 0.f;
-    // 8 lanes per baseline: lane l of the group sums the terms j = l, l + 8, ...
-    // (coalesced reads of the baseline's D row; M_j recomputed from the solved
-    // Jones matrices in L1/L2 with the arithmetic that stored it, instead of read
-    // back from HBM), the group's partial sums meet by shuffles, lane 0 writes;
-    // a CTA's groups take consecutive baselines (mostly one first antenna)
-    const int sl = tid & 7;
-    for (int64_t b0 = (int64_t)blockIdx.x * (kSolveThreads / 8); b0 < a.n_bl;
-         b0 += (int64_t)G * (kSolveThreads / 8)) {   // CTA-uniform trip count (the shuffles need whole warps)
-      const int64_t bl = b0 + (tid >> 3);
-      const bool live = bl < a.n_bl;
-      const int2 ij = live ? a.bl_ant[bl] : make_int2(0, 1);
-      if (live && model && sl == 0) {
-        float2 Mp[4];
+    // a CTA's threads take consecutive baselines (mostly one first antenna), so
+    // the Jones rows they read come from L1
+    for (int64_t bl = blockIdx.x * (int64_t)kSolveThreads + tid; bl < a.n_bl; bl += gstride) {
+      const int2 ij = a.bl_ant[bl];
+      float2 Mp[4];
+      if (model) {
         block_model_f(a.jones + (size_t)(k - 1) * a.n_ant * 4, ij, Sprev, Mp);
         #pragma unroll
         for (int e = 0; e < 4; ++e) a.M[((size_t)(q - 1) * a.n_bl + bl) * 4 + e] = Mp[e];
@@ -238,26 +232,25 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs
       if (corr) {
         float2 v[4];
         #pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
-        const float2* D = a.Dtab + (size_t)(live ? bl : 0) * a.n_pairs + q * (q - 1) / 2;
-        for (int j = sl; live && j < q; j += 8) {
+        for (int e = 0; e < 4; ++e) v[e] = __ldg(a.Ablk + ((size_t)q * a.n_bl + bl) * 4 + e);
+        const float2* D = a.Dtab + (size_t)bl * a.n_pairs + q * (q - 1) / 2;
+        // M_j recomputed from the solved Jones matrices (L1/L2) with the arithmetic
+        // that stored it, instead of read back from the [BK][n_bl][4] array in HBM
+        #pragma unroll 2
+        for (int j = 0; j < q; ++j) {
           const float2 d = __ldg(D + j);
           float2 mj[4];
-          block_model_f(a.jones + (size_t)(a.s0 + j) * a.n_ant * 4, ij, (float)a.src[3 * (a.s0 + j) + 2], mj);
+          if (j == q - 1) {
+            #pragma unroll
+            for (int e = 0; e < 4; ++e) mj[e] = Mp[e];
+          } else {
+            block_model_f(a.jones + (size_t)(a.s0 + j) * a.n_ant * 4, ij, (float)a.src[3 * (a.s0 + j) + 2], mj);
+          }
           #pragma unroll
-          for (int e = 0; e < 4; ++e) v[e] = cadd(v[e], cmul(mj[e], d));
+          for (int e = 0; e < 4; ++e) v[e] = csub(v[e], cmul(mj[e], d));
         }
         #pragma unroll
-        for (int o = 4; o >= 1; o >>= 1)
-          #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            v[e].x += __shfl_xor_sync(0xffffffffu, v[e].x, o);
-            v[e].y += __shfl_xor_sync(0xffffffffu, v[e].y, o);
-          }
-        if (live && sl == 0)
-          #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            a.avg[(size_t)bl * 4 + e] = csub(__ldg(a.Ablk + ((size_t)q * a.n_bl + bl) * 4 + e), v[e]);
+        for (int e = 0; e < 4; ++e) a.avg[(size_t)bl * 4 + e] = v[e];
       }
     }
     if (!corr) break;
