@@ -108,6 +108,16 @@ typedef struct rts_peel_config {
                            GB300; otherwise as RTS_GRAD_DIRECT), RTS_GRAD_DIRECT (1: one
                            hardware sin/cos per source and sample).  FP32-level accuracy
                            either way; RTS_PREC_FP64 always evaluates every phasor in FP64. */
+  int32_t band_n_chan;   /* channel sharding (Section 3.1: channel groups on separate
+                           workers, combined centrally): 0 = the handle's channels are the
+                           whole band; else the band has band_n_chan uniform channels and
+                           freq_hz are its channels band_chan0 .. band_chan0 + n_chan - 1.
+                           A shard's averages are normalised by the whole band's sample
+                           count and its in-block corrections are taken over the whole
+                           band, so the shards' partial averages add up to the band's.
+                           Shard handles peel only through the rts_peel_shard_* calls
+                           (blocked peel, RTS_PREC_MIXED, sources_per_pass > 1). */
+  int32_t band_chan0;    /* this handle's first channel in the band (0 when band_n_chan = 0) */
 } rts_peel_config;
 
 #define RTS_GRAD_AUTO   0
@@ -172,6 +182,32 @@ int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_
 int rts_peel_cadence_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
                             const double* h_src, void* d_gain, void* d_slope, int32_t* h_status,
                             void* stream);
+
+/* One cadence of a channel shard, step by step (Section 3.1: channel groups are
+ * processed by separate workers and their numbers combined centrally).  Every
+ * shard of the band runs the same calls with the same source list; between
+ * the calls the caller sums the shards' partial averages, in place, across the
+ * shards (an all-reduce of n_float floats per block of sources, e.g. NCCL on
+ * `stream`), so every shard solves the same Jones matrices from the whole
+ * band's averages and subtracts them from its own channels:
+ *   rts_peel_shard_begin(h, ...)         first pass: partial averages of block 0
+ *   loop: rts_peel_shard_partials(h, &p, &n); sum p[0..n) over the shards;
+ *         rc = rts_peel_shard_step(h, h_status, stream)
+ *         (solve the block, subtract it, partial averages of the next block;
+ *          rc = 1: sum again and step again; rc = 0: the cadence is done)
+ * d_vis, d_resid, n_src (>= 1), h_src, d_jones: as rts_peel_cadence, the cube
+ * holding this handle's n_chan channels.  The source list is copied at begin.
+ * d_partial: float [n_blk][n_bl][4][re, im] of the library's workspace, valid
+ * until the next step.  All calls of a cadence use the same stream; the
+ * partials are ready on it when begin / step return, and step orders its work
+ * after what the caller enqueued on it.  h_status (may be NULL) is filled by the
+ * final step, as in rts_peel_cadence.  Errors: RTS_EINVAL (a one-source-per-pass
+ * handle, a call out of order, another stream), or as rts_peel_cadence; an
+ * error ends the cadence. */
+int rts_peel_shard_begin(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src, const double* h_src,
+                         void* d_jones, void* stream);
+int rts_peel_shard_partials(rts_peel_t* h, float** d_partial, int64_t* n_float);
+int rts_peel_shard_step(rts_peel_t* h, int32_t* h_status, void* stream);
 
 /* rts_peel_cadence on host buffers: copies h_vis to the caller's device buffer
  * d_work (cube-sized), peels it in place, copies the residual to h_resid and

@@ -36,6 +36,7 @@ EXPORTS = ("rts_peel_init", "rts_peel_set_uvw", "rts_peel_cadence", "rts_peel_ca
            "rts_peel_predict", "rts_peel_rotate_average", "rts_peel_solve", "rts_peel_grad", "rts_peel_offsets",
            "rts_offsets_solve",
            "rts_peel_solve_noalloc", "rts_peel_rel", "rts_peel_phases",
+           "rts_peel_shard_begin", "rts_peel_shard_partials", "rts_peel_shard_step",
            "rts_peel_pipeline_submit", "rts_peel_pipeline_wait",
            "rts_peel_timing", "rts_peel_timing_read", "rts_peel_kernels", "rts_barrier_selftest", "rts_fp64_rate",
            "rts_host_alloc", "rts_host_free",
@@ -52,7 +53,8 @@ class rts_peel_config(ctypes.Structure):
                 ("uvw", ctypes.POINTER(ctypes.c_double)),
                 ("freq_hz", ctypes.POINTER(ctypes.c_double)),
                 ("sources_per_pass", ctypes.c_int32), ("block_kernel", ctypes.c_int32),
-                ("solve_kernel", ctypes.c_int32), ("grad_kernel", ctypes.c_int32)]
+                ("solve_kernel", ctypes.c_int32), ("grad_kernel", ctypes.c_int32),
+                ("band_n_chan", ctypes.c_int32), ("band_chan0", ctypes.c_int32)]
 
 
 class rts_grid_config(ctypes.Structure):
@@ -103,6 +105,13 @@ def lib():
             L.rts_peel_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp, _ip, _vp]
             L.rts_peel_solve_noalloc.restype = ctypes.c_int
             L.rts_peel_solve_noalloc.argtypes = [_vp, _i32, ctypes.c_double, _i32, _i32, _vp, _ip, _vp]
+            L.rts_peel_shard_begin.restype = ctypes.c_int
+            L.rts_peel_shard_begin.argtypes = [_vp, _vp, _vp, _i32, _dp, _vp, _vp]
+            L.rts_peel_shard_partials.restype = ctypes.c_int
+            L.rts_peel_shard_partials.argtypes = [_vp, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)),
+                                                  ctypes.POINTER(ctypes.c_int64)]
+            L.rts_peel_shard_step.restype = ctypes.c_int
+            L.rts_peel_shard_step.argtypes = [_vp, _ip, _vp]
             L.rts_peel_rel.restype = ctypes.c_int
             L.rts_peel_rel.argtypes = [_vp, _i32, _dp, _vp]
             L.rts_peel_phases.restype = ctypes.c_int
@@ -207,6 +216,23 @@ def rts_peel_solve(h, d_avg, S, d_jones, h_status, stream):
 def rts_peel_solve_noalloc(d_avg, n_ant, S, n_iter, precision, d_jones, h_status, stream):
     return _check(lib().rts_peel_solve_noalloc(d_avg, n_ant, S, n_iter, precision, d_jones, h_status,
                                                stream), None)
+
+
+def rts_peel_shard_begin(h, d_vis, d_resid, n_src, h_src, d_jones, stream):
+    return _check(lib().rts_peel_shard_begin(h, d_vis, d_resid, n_src, h_src, d_jones, stream), h)
+
+
+def rts_peel_shard_partials(h):
+    """(device address, float count) of the current block's partial averages."""
+    p = ctypes.POINTER(ctypes.c_float)()
+    n = ctypes.c_int64()
+    _check(lib().rts_peel_shard_partials(h, ctypes.byref(p), ctypes.byref(n)), h)
+    return ctypes.cast(p, ctypes.c_void_p).value, n.value
+
+
+def rts_peel_shard_step(h, h_status, stream) -> int:
+    """1 while another exchange of partial averages is needed, 0 when done."""
+    return _check(lib().rts_peel_shard_step(h, h_status, stream), h)
 
 
 def rts_peel_rel(h, n_src, h_rel, stream):

@@ -265,10 +265,13 @@ __global__ void __launch_bounds__(256) k_block_ant_phases(const double* __restri
   }
 }
 
+// ph: the phases of this handle's first channel; trig: the band-centre phasor
+// and sin/cos(pi N B) of the whole band of n_band channels, whose channel c0 is
+// this handle's first (A_band = A - c0 B, exactly)
 template <int BK>
 __global__ void __launch_bounds__(256) k_block_phases(const PhaseAB* __restrict__ aph, int n_blk,
                                                      const int2* __restrict__ bl_ant, int n_ant,
-                                                     int n_time, int n_chan, int64_t n_bl,
+                                                     int n_time, int n_chan, int c0, int64_t n_bl,
                                                      PhaseAB* __restrict__ ph, GeoTrig* __restrict__ trig) {
   const int64_t n = n_bl * n_time * BK;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(256) k_block_phases(const PhaseAB* __restrict_
     ph[q] = p;
     GeoTrig g;
     const long long bs = (long long)p.b;                           // signed B
-    g.u = phasor_q64_fine(pair_mid_phase(p.a, bs, n_chan));
+    g.u = phasor_q64_fine(pair_mid_phase(p.a - (unsigned long long)c0 * p.b, bs, n_chan));
     // pi N B: N B = hi + lo 2^-64 = (hi + [lo_s < 0]) + lo_s 2^-64 with lo_s in [-1/2, 1/2)
     const long long nn = n_chan;
     const unsigned long long lo = (unsigned long long)nn * (unsigned long long)bs;

@@ -58,6 +58,16 @@ struct rts_peel_t {
   // and D_jk tables depend on geometry only; a second stream fills a ring of
   // kRing block slots ahead of the main stream (events order the reuse).
   static constexpr int kRing = 4;
+  int n_band = 0, band_chan0 = 0;   // the whole band's channel count, this handle's first channel in it
+  // a blocked cadence in progress (between rts_peel_shard_begin and the last rts_peel_shard_step)
+  struct BlockRun {
+    const void* vis = nullptr; void* resid = nullptr; void* jones = nullptr;
+    int n_src = 0, b = 0, nb = 0;
+    std::vector<double> src;       // host copy of the source list
+    cudaStream_t user = nullptr;
+    BlockPassArgs a;
+    bool active = false;
+  } br;
   PhaseAB* b_ph[kRing] = {};       // [n_bl][n_time][BK] phases of a block
   GeoTrig* b_trig[kRing] = {};     // [n_bl][n_time][BK] trigonometry for D_jk
   float2* b_dir[kRing] = {};       // [n_bl][BK(BK-1)/2] in-block closed-form averages D_jk
@@ -261,10 +271,10 @@ void launch_block_geometry(rts_peel_t* h, int b, int n_src, cudaStream_t ps) {
 #define RTS_GEOM(BKV)                                                                                   \
   k_block_ant_phases<BKV><<<g, 256, 0, ps>>>(src, nblk, h->d_uvw, h->n_ant, h->n_time, nu0_c, dnu_c,   \
                                              h->b_aph);                                                 \
-  k_block_phases<BKV><<<g, 256, 0, ps>>>(h->b_aph, nblk, h->d_bl_ant, h->n_ant, h->n_time, h->n_chan,  \
-                                         h->n_bl, ph, tg);                                              \
+  k_block_phases<BKV><<<g, 256, 0, ps>>>(h->b_aph, nblk, h->d_bl_ant, h->n_ant, h->n_time, h->n_band,  \
+                                         h->band_chan0, h->n_bl, ph, tg);                               \
   if (nblk > 1)                                                                                          \
-    k_block_dirichlet<BKV><<<grid, 256, 0, ps>>>(ph, tg, nblk, Dt, h->n_bl, h->n_time, h->n_chan);
+    k_block_dirichlet<BKV><<<grid, 256, 0, ps>>>(ph, tg, nblk, Dt, h->n_bl, h->n_time, h->n_band);
   switch (BK) {
     case 8: RTS_GEOM(8) break;
     case 16: RTS_GEOM(16) break;
@@ -430,33 +440,41 @@ int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a,
 
 // The blocked cadence: one HBM pass per block of BK sources (see block_kernels.cuh).
 // Main stream: passes, in-block corrections, solves.  Prep stream: the
-// geometry tables of the blocks, up to kRing blocks ahead.
-int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
-                 const double* h_src, void* d_jones, int32_t* h_status, cudaStream_t s) {
+// geometry tables of the blocks, up to kRing blocks ahead.  The cadence runs as
+// blocked_begin (the first pass: block 0's averages), blocked_block for every
+// block (its solve, then the pass that subtracts it and averages the next
+// block) and blocked_end; rts_peel_cadence runs them back to back, the
+// channel-shard calls return to the caller before each solve so that the
+// averages of all shards can be summed.
+int blocked_begin(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src, const double* h_src,
+                  void* d_jones, cudaStream_t user) {
   int rc = ensure_block_workspace(h);
   if (rc) return rc;
   constexpr int R = rts_peel_t::kRing;
-  const int BK = h->per_pass, n_pairs = BK * (BK - 1) / 2;
+  const int BK = h->per_pass;
+  rts_peel_t::BlockRun& br = h->br;
+  br = rts_peel_t::BlockRun();
+  br.vis = d_vis; br.resid = d_resid; br.jones = d_jones; br.n_src = n_src;
+  br.src.assign(h_src, h_src + 3 * (size_t)n_src);
+  br.nb = (n_src + BK - 1) / BK;
+  br.b = 0;
+  br.user = user;
   // work on the library's high-priority stream, ordered after the caller's stream
-  cudaStream_t user = s;
+  cudaStream_t s = h->b_main;
   RTS_CUDA(h, cudaEventRecord(h->b_ev_in, user));
-  s = h->b_main;
   RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_in, 0));
   RTS_CUDA(h, cudaMemsetAsync(h->d_perr, 0, sizeof(int), s));      // the pass's wait-timeout flag
-  RTS_CUDA(h, cudaMemcpyAsync(h->d_src, h_src, sizeof(double) * 3 * n_src, cudaMemcpyHostToDevice, s));
+  RTS_CUDA(h, cudaMemcpyAsync(h->d_src, br.src.data(), sizeof(double) * 3 * n_src, cudaMemcpyHostToDevice, s));
   RTS_CUDA(h, cudaEventRecord(h->b_ev_src, s));
   RTS_CUDA(h, cudaStreamWaitEvent(h->b_prep, h->b_ev_src, 0));
-  const size_t jstride = (size_t)h->n_ant * 4 * h->elem;
-  const unsigned bl_grid = (unsigned)((h->n_bl + 255) / 256);
-  const int nb = (n_src + BK - 1) / BK;
-  for (int b = 0; b < std::min(nb, R); ++b) {
+  for (int b = 0; b < std::min(br.nb, R); ++b) {
     launch_block_geometry(h, b, n_src, h->b_prep);
     RTS_CUDA(h, cudaEventRecord(h->b_ev_ready[b % R], h->b_prep));
   }
-  BlockPassArgs a;
+  BlockPassArgs& a = br.a;
   std::memset(&a, 0, sizeof(a));
   a.n_ant = h->n_ant; a.n_chan = h->n_chan; a.n_time = h->n_time; a.n_bl = h->n_bl;
-  a.inv_n = 1.0 / ((double)h->n_time * h->n_chan);
+  a.inv_n = 1.0 / ((double)h->n_time * h->n_band);     // the whole band's samples: shards' averages add up
   a.M_sub = h->b_model; a.avg = h->b_avg;
   // first pass: plain averages of block 0 from the input
   RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_ready[0], 0));
@@ -464,59 +482,98 @@ int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
   a.n_acc = std::min(BK, (int)n_src); a.ph_acc = h->b_ph[0];
   rc = launch_block_pass(h, false, true, a, s);
   if (rc) return rc;
-  for (int b = 0; b < nb; ++b) {
-    const int s0 = b * BK, nblk = std::min(BK, (int)n_src - s0);
-    const float2* Dt = h->b_dir[b % R];
-    if (h->bs_ok) {
-      rc = launch_block_solve(h, s0, nblk, Dt, d_jones, s);
-      if (rc) return rc;
-    }
-    for (int q = 0; q < nblk && !h->bs_ok; ++q) {
-      const int k = s0 + q;
-      {
-        Span span(h, RTS_K_BLOCK_FIX, s);
-        if (q > 0)
-          k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (k - 1) + 2], h->d_bl_ant, h->n_bl,
-                                                 h->b_model + (size_t)(q - 1) * h->n_bl * 4);
-        k_block_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, Dt, n_pairs, h->n_bl,
-                                                static_cast<float2*>(h->d_avg));
-        span.end(q > 0 ? 2 : 1);
-      }
-      rc = launch_als(h, h->d_avg, h_src[3 * k + 2], static_cast<char*>(d_jones) + k * jstride, k, s);
-      if (rc) return rc;
-    }
-    if (!h->bs_ok) {
-      Span span(h, RTS_K_BLOCK_FIX, s);
-      k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (s0 + nblk - 1) + 2], h->d_bl_ant,
-                                             h->n_bl, h->b_model + (size_t)(nblk - 1) * h->n_bl * 4);
-      span.end(1);
-    }
-    // subtract block b (input -> residual on the first block), average block b+1
-    const bool more = b + 1 < nb;
-    if (more) RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_ready[(b + 1) % R], 0));
-    a.src = static_cast<const float4*>(b == 0 ? d_vis : d_resid);
-    a.dst = static_cast<float4*>(d_resid);
-    a.n_sub = nblk; a.ph_sub = h->b_ph[b % R];
-    a.n_acc = more ? std::min(BK, (int)n_src - s0 - BK) : 0;
-    a.ph_acc = h->b_ph[(b + 1) % R];
-    rc = launch_block_pass(h, true, more, a, s);
+  br.active = true;
+  return RTS_OK;
+}
+
+// block br.b: its solve from the (summed) averages in b_avg, then the pass that
+// subtracts it and averages block br.b + 1
+int blocked_block(rts_peel_t* h) {
+  constexpr int R = rts_peel_t::kRing;
+  rts_peel_t::BlockRun& br = h->br;
+  const int BK = h->per_pass, n_pairs = BK * (BK - 1) / 2, b = br.b;
+  const int n_src = br.n_src, s0 = b * BK, nblk = std::min(BK, n_src - s0);
+  const double* h_src = br.src.data();
+  cudaStream_t s = h->b_main;
+  const size_t jstride = (size_t)h->n_ant * 4 * h->elem;
+  const unsigned bl_grid = (unsigned)((h->n_bl + 255) / 256);
+  const float2* Dt = h->b_dir[b % R];
+  int rc;
+  if (h->bs_ok) {
+    rc = launch_block_solve(h, s0, nblk, Dt, br.jones, s);
     if (rc) return rc;
-    // slot b is free once that pass has run: the prep stream may fill it with block b + R
-    RTS_CUDA(h, cudaEventRecord(h->b_ev_free[b % R], s));
-    if (b + R < nb) {
-      RTS_CUDA(h, cudaStreamWaitEvent(h->b_prep, h->b_ev_free[b % R], 0));
-      launch_block_geometry(h, b + R, n_src, h->b_prep);
-      RTS_CUDA(h, cudaEventRecord(h->b_ev_ready[b % R], h->b_prep));
-    }
   }
+  for (int q = 0; q < nblk && !h->bs_ok; ++q) {
+    const int k = s0 + q;
+    {
+      Span span(h, RTS_K_BLOCK_FIX, s);
+      if (q > 0)
+        k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (k - 1) + 2], h->d_bl_ant, h->n_bl,
+                                               h->b_model + (size_t)(q - 1) * h->n_bl * 4);
+      k_block_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, Dt, n_pairs, h->n_bl,
+                                              static_cast<float2*>(h->d_avg));
+      span.end(q > 0 ? 2 : 1);
+    }
+    rc = launch_als(h, h->d_avg, h_src[3 * k + 2], static_cast<char*>(br.jones) + k * jstride, k, s);
+    if (rc) return rc;
+  }
+  if (!h->bs_ok) {
+    Span span(h, RTS_K_BLOCK_FIX, s);
+    k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (s0 + nblk - 1) + 2], h->d_bl_ant,
+                                           h->n_bl, h->b_model + (size_t)(nblk - 1) * h->n_bl * 4);
+    span.end(1);
+  }
+  // subtract block b (input -> residual on the first block), average block b+1
+  BlockPassArgs& a = br.a;
+  const bool more = b + 1 < br.nb;
+  if (more) RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_ready[(b + 1) % R], 0));
+  a.src = static_cast<const float4*>(b == 0 ? br.vis : br.resid);
+  a.dst = static_cast<float4*>(br.resid);
+  a.n_sub = nblk; a.ph_sub = h->b_ph[b % R];
+  a.n_acc = more ? std::min(BK, n_src - s0 - BK) : 0;
+  a.ph_acc = h->b_ph[(b + 1) % R];
+  rc = launch_block_pass(h, true, more, a, s);
+  if (rc) return rc;
+  // slot b is free once that pass has run: the prep stream may fill it with block b + R
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_free[b % R], s));
+  if (b + R < br.nb) {
+    RTS_CUDA(h, cudaStreamWaitEvent(h->b_prep, h->b_ev_free[b % R], 0));
+    launch_block_geometry(h, b + R, n_src, h->b_prep);
+    RTS_CUDA(h, cudaEventRecord(h->b_ev_ready[b % R], h->b_prep));
+  }
+  ++br.b;
+  return RTS_OK;
+}
+
+// the caller's stream waits for the library's (outputs or partial averages ready)
+int blocked_to_user(rts_peel_t* h) {
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_out, h->b_main));
+  RTS_CUDA(h, cudaStreamWaitEvent(h->br.user, h->b_ev_out, 0));
+  return RTS_OK;
+}
+
+int blocked_end(rts_peel_t* h, int32_t* h_status) {
+  rts_peel_t::BlockRun& br = h->br;
+  br.active = false;
   RTS_CUDA(h, cudaEventRecord(h->b_ev_done, h->b_prep));
-  RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_done, 0));
-  RTS_CUDA(h, cudaEventRecord(h->b_ev_out, s));
-  RTS_CUDA(h, cudaStreamWaitEvent(user, h->b_ev_out, 0));
+  RTS_CUDA(h, cudaStreamWaitEvent(h->b_main, h->b_ev_done, 0));
+  int rc = blocked_to_user(h);
+  if (rc) return rc;
   rc = check_launch(h, "block geometry launch");
   if (rc) return rc;
-  if (h_status) return read_status(h, n_src, h_status, user);
+  if (h_status) return read_status(h, br.n_src, h_status, br.user);
   return RTS_OK;
+}
+
+int peel_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
+                 const double* h_src, void* d_jones, int32_t* h_status, cudaStream_t s) {
+  int rc = blocked_begin(h, d_vis, d_resid, n_src, h_src, d_jones, s);
+  while (rc == RTS_OK && h->br.b < h->br.nb) rc = blocked_block(h);
+  if (rc) {
+    h->br.active = false;
+    return rc;
+  }
+  return blocked_end(h, h_status);
 }
 
 int peel_device(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
@@ -656,6 +713,8 @@ int rts_peel_cadence_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int
                             void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
   if (h->precision != RTS_PREC_MIXED) return fail(h, RTS_EINVAL, "Taylor gains need an RTS_PREC_MIXED handle");
+  if (h->n_band != h->n_chan || h->br.active)
+    return fail(h, RTS_EINVAL, "Taylor gains need a handle that holds the whole band and no cadence in progress");
   if (h->n_chan < 2) return fail(h, RTS_EINVAL, "Taylor gains need n_chan >= 2");
   if (!d_vis || !d_resid) return fail(h, RTS_EINVAL, "d_vis and d_resid are required");
   if (misaligned(d_vis) || misaligned(d_resid))
@@ -712,6 +771,13 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   if (cfg->block_kernel == RTS_BLOCK_TCGEN05 && cfg->n_chan > kTc5MaxChan)
     return fail(nullptr, RTS_EINVAL, "the tcgen05 blocked pass needs n_chan <= 768");
 
+  const int n_band = cfg->band_n_chan > 0 ? cfg->band_n_chan : cfg->n_chan;
+  if (cfg->band_n_chan < 0 || cfg->band_chan0 < 0 || cfg->band_chan0 + cfg->n_chan > n_band ||
+      (cfg->band_n_chan == 0 && cfg->band_chan0 != 0))
+    return fail(nullptr, RTS_EINVAL, "band_chan0 .. band_chan0 + n_chan - 1 must lie in the band's band_n_chan channels");
+  if (n_band != cfg->n_chan && per_pass == 1)
+    return fail(nullptr, RTS_EINVAL, "a channel shard (band_n_chan > n_chan) needs the blocked peel "
+                                     "(RTS_PREC_MIXED, sources_per_pass > 1)");
   if (cfg->solve_kernel != RTS_SOLVE_AUTO && cfg->solve_kernel != RTS_SOLVE_LAUNCHES)
     return fail(nullptr, RTS_EINVAL, "solve_kernel must be RTS_SOLVE_AUTO or RTS_SOLVE_LAUNCHES");
   if (cfg->grad_kernel != RTS_GRAD_AUTO && cfg->grad_kernel != RTS_GRAD_DIRECT)
@@ -731,6 +797,7 @@ int rts_peel_init(const rts_peel_config* cfg, rts_peel_t** out) {
   h->n_ant = cfg->n_ant; h->n_chan = cfg->n_chan; h->n_time = cfg->n_time;
   h->n_iter = cfg->n_iter; h->precision = cfg->precision; h->max_sources = cfg->max_sources;
   h->n_bl = n_bl; h->nu0 = nu0; h->dnu = dnu;
+  h->n_band = n_band; h->band_chan0 = cfg->band_chan0;
   h->elem = cfg->precision == RTS_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   auto bail = [&](cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
@@ -804,9 +871,19 @@ int rts_peel_set_uvw(rts_peel_t* h, const double* h_uvw, void* stream) {
   return RTS_OK;
 }
 
+namespace {
+int not_a_shard(rts_peel_t* h) {
+  if (h->n_band != h->n_chan)
+    return fail(h, RTS_EINVAL, "this handle holds a channel shard of a wider band: use the rts_peel_shard_* calls");
+  if (h->br.active) return fail(h, RTS_EINVAL, "a channel-shard cadence is in progress on this handle");
+  return RTS_OK;
+}
+}  // namespace
+
 int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src,
                      const double* h_src, void* d_jones, int32_t* h_status, void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (int rc0 = not_a_shard(h)) return rc0;
   if (!d_vis || !d_resid) return fail(h, RTS_EINVAL, "d_vis and d_resid are required");
   if (misaligned(d_vis) || misaligned(d_resid))
     return fail(h, RTS_EINVAL, "d_vis and d_resid must start on a 16-byte boundary");
@@ -816,10 +893,61 @@ int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_
   return peel_device(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, as_stream(stream));
 }
 
+int rts_peel_shard_begin(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src, const double* h_src,
+                         void* d_jones, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (h->per_pass == 1) return fail(h, RTS_EINVAL, "channel-shard cadences need the blocked peel (sources_per_pass > 1)");
+  if (h->br.active) return fail(h, RTS_EINVAL, "a channel-shard cadence is already in progress on this handle");
+  if (!d_vis || !d_resid) return fail(h, RTS_EINVAL, "d_vis and d_resid are required");
+  if (misaligned(d_vis) || misaligned(d_resid))
+    return fail(h, RTS_EINVAL, "d_vis and d_resid must start on a 16-byte boundary");
+  int rc = validate_sources(h, n_src, h_src);
+  if (rc) return rc;
+  if (n_src < 1) return fail(h, RTS_EINVAL, "a channel-shard cadence needs n_src >= 1");
+  if (!d_jones) return fail(h, RTS_EINVAL, "d_jones is NULL");
+  rc = blocked_begin(h, d_vis, d_resid, n_src, h_src, d_jones, as_stream(stream));
+  if (rc) {
+    h->br.active = false;
+    return rc;
+  }
+  return blocked_to_user(h);
+}
+
+int rts_peel_shard_partials(rts_peel_t* h, float** d_partial, int64_t* n_float) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!d_partial || !n_float) return fail(h, RTS_EINVAL, "d_partial and n_float are required");
+  if (!h->br.active) return fail(h, RTS_EINVAL, "no channel-shard cadence is in progress");
+  const int nblk = std::min(h->per_pass, h->br.n_src - h->br.b * h->per_pass);
+  *d_partial = reinterpret_cast<float*>(h->b_avg);
+  *n_float = (int64_t)nblk * h->n_bl * 8;
+  return RTS_OK;
+}
+
+int rts_peel_shard_step(rts_peel_t* h, int32_t* h_status, void* stream) {
+  if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (!h->br.active) return fail(h, RTS_EINVAL, "no channel-shard cadence is in progress");
+  if (as_stream(stream) != h->br.user)
+    return fail(h, RTS_EINVAL, "rts_peel_shard_step must use the stream of rts_peel_shard_begin");
+  // the library's stream waits for the caller's exchange of the partial averages
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_in, h->br.user));
+  RTS_CUDA(h, cudaStreamWaitEvent(h->b_main, h->b_ev_in, 0));
+  int rc = blocked_block(h);
+  if (rc) {
+    h->br.active = false;
+    return rc;
+  }
+  if (h->br.b < h->br.nb) {
+    rc = blocked_to_user(h);
+    return rc ? rc : 1;
+  }
+  return blocked_end(h, h_status);
+}
+
 int rts_peel_cadence_host(rts_peel_t* h, const void* h_vis, void* h_resid, int32_t n_src,
                           const double* h_src, void* h_jones, int32_t* h_status,
                           void* d_work, void* stream) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (int rc0 = not_a_shard(h)) return rc0;
   if (!h_vis || !h_resid || !d_work) return fail(h, RTS_EINVAL, "h_vis, h_resid and d_work are required");
   int rc = validate_sources(h, n_src, h_src);
   if (rc) return rc;
@@ -884,6 +1012,7 @@ int pipeline_retire(rts_peel_t* h, int k) {
 int rts_peel_pipeline_submit(rts_peel_t* h, const void* h_vis, void* h_resid, int32_t n_src,
                              const double* h_src, void* h_jones, int32_t* h_status) {
   if (!h) return fail(nullptr, RTS_EINVAL, "handle is NULL");
+  if (int rc0 = not_a_shard(h)) return rc0;
   if (!h_vis || !h_resid) return fail(h, RTS_EINVAL, "h_vis and h_resid are required");
   int rc = validate_sources(h, n_src, h_src);
   if (rc) return rc;

@@ -33,12 +33,20 @@ def _host_f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+class _DeviceFloats:
+    """A float32 device buffer of the library, seen by torch without a copy."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f4", "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
 class Peeler:
     """One array configuration (antennas, channels, times) on the current CUDA device."""
 
     def __init__(self, uvw, freq_hz, n_iter: int = 20, precision: str = "mixed",
                  max_sources: int = 1024, sources_per_pass: int = 0, block_kernel: int = 0,
-                 solve_kernel: int = 0, grad_kernel: int = 0):
+                 solve_kernel: int = 0, grad_kernel: int = 0, band_n_chan: int = 0, band_chan0: int = 0):
         uvw = _host_f64(uvw)
         freq = _host_f64(freq_hz)
         if uvw.ndim != 3 or uvw.shape[2] != 3:
@@ -62,8 +70,12 @@ class Peeler:
         cfg.block_kernel = int(block_kernel)
         cfg.solve_kernel = int(solve_kernel)
         cfg.grad_kernel = int(grad_kernel)
+        cfg.band_n_chan = int(band_n_chan)
+        cfg.band_chan0 = int(band_chan0)
         self.sources_per_pass = int(sources_per_pass)
         self._keep = (uvw, freq)
+        self._shard_status = np.zeros(1, np.int32)
+        self._shard_k = 0
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.h = _abi.rts_peel_init(cfg)
 
@@ -115,6 +127,53 @@ class Peeler:
         _abi.rts_peel_cadence(self.h, _ptr(vis), _ptr(resid), k, src.ctypes.data_as(_dp),
                               _ptr(jones), st.ctypes.data_as(_ip) if status else None, _stream(stream))
         return resid, jones, (st[:k] if status else None)
+
+    # -- channel shards (band_n_chan > 0) --------------------------------------
+    def shard_begin(self, vis: torch.Tensor, sources, resid: torch.Tensor | None = None, stream=None):
+        """Start a channel-shard cadence (first pass: the partial averages of the
+        first block).  Returns (resid, jones [K][n_ant][4]), filled as it runs."""
+        self._check_cube(vis)
+        src = _host_f64(sources).reshape(-1, 3)
+        k = src.shape[0]
+        if resid is None:
+            resid = self.empty_cube()
+        self._check_cube(resid, "resid")
+        jones = torch.empty((k, self.n_ant, 4), dtype=self.cdtype, device=self.device)
+        self._shard_status = np.zeros(max(k, 1), np.int32)
+        self._shard_k = k
+        _abi.rts_peel_shard_begin(self.h, _ptr(vis), _ptr(resid), k, src.ctypes.data_as(_dp), _ptr(jones),
+                                  _stream(stream))
+        return resid, jones
+
+    def shard_partials(self) -> torch.Tensor:
+        """The current block's partial averages (float32, a view of the
+        library's workspace, valid until the next shard_step)."""
+        ptr, n = _abi.rts_peel_shard_partials(self.h)
+        self._shard_view = _DeviceFloats(ptr, n)
+        return torch.as_tensor(self._shard_view, device=self.device)
+
+    def shard_step(self, stream=None) -> int:
+        """Solve the block from the summed partials, subtract it, leave the next
+        block's partials: 1 while another exchange is needed, 0 when the cadence
+        is done (shard_status() then holds the statuses)."""
+        return _abi.rts_peel_shard_step(self.h, self._shard_status.ctypes.data_as(_ip), _stream(stream))
+
+    def shard_status(self) -> np.ndarray:
+        return self._shard_status[:self._shard_k]
+
+    def cadence_sharded(self, vis: torch.Tensor, sources, exchange, resid: torch.Tensor | None = None):
+        """One cadence of this handle's channel shard.  Before each block's
+        solve, exchange(partial) must sum the float32 tensor `partial` in place
+        over all shards of the band, on the current stream (e.g.
+        replicas.sum_over_ranks).  Returns (resid, jones, status, exchanges)."""
+        from .replicas import run_sharded_cadence
+        out = {}
+
+        def begin():
+            out["r"], out["j"] = self.shard_begin(vis, sources, resid)
+
+        n = run_sharded_cadence(begin, self.shard_partials, self.shard_step, exchange)
+        return out["r"], out["j"], self.shard_status(), n
 
     def cadence_taylor(self, vis: torch.Tensor, sources, resid: torch.Tensor | None = None,
                        status: bool = True, stream=None):

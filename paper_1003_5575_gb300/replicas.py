@@ -5,9 +5,12 @@ paper's per-GPU channel sets, weak scaling across GPUs) and needs no data-path
 collective.  What the ranks share is bookkeeping: a per-rank seed, a barrier
 around the timed region, the slowest rank's time and the job total.
 
-For a cadence split by channel across GPUs, the one exchange per source would
-be a sum of the per-rank partial averages (each rank's samples-weighted mean
-over its channels); `combine_partial_averages` is that reduction.  The
+For a cadence split by channel across GPUs (Section 3.1: channel groups on
+separate workers, combined centrally), every rank peels its channels with the
+library's channel-shard calls and the ranks sum their partial averages once
+per block of sources before the block's solve: `run_sharded_cadence` drives
+that loop with any in-place sum (`sum_over_ranks`: an all-reduce over the
+process group); `combine_partial_averages` scales and sums a per-rank mean.  The
 ionospheric offset fit is the exchange the paper itself plans (Section 3.1:
 six numbers per source from every worker, two-number solution built
 centrally): `combine_offset_statistics` sums the six numbers over ranks.
@@ -70,3 +73,24 @@ def combine_offset_statistics(six: torch.Tensor) -> torch.Tensor:
     if world()[1] > 1:
         dist.all_reduce(six, op=dist.ReduceOp.SUM)
     return six
+
+
+def sum_over_ranks(t: torch.Tensor) -> torch.Tensor:
+    """In-place sum over ranks (the exchange of a channel-sharded cadence)."""
+    if world()[1] > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
+def run_sharded_cadence(begin, partials, step, exchange) -> int:
+    """One channel-shard cadence: begin(); then, until step() returns 0, the
+    current partial averages (partials(), a tensor) are summed in place over
+    the band's shards by exchange() and step() solves and subtracts a block and
+    leaves the next block's partials.  Returns the number of exchanges."""
+    begin()
+    n = 0
+    while True:
+        exchange(partials())
+        n += 1
+        if step() == 0:
+            return n
