@@ -173,6 +173,41 @@ def time_oracle(cad, V, reps=1):
     return cad.n_src * cad.n_vis / dt, dt
 
 
+def run_cpu_baselines():
+    """The CPU-baseline plan: the FP64 oracle on the machine's host cores, all cores and
+    one core; configurations 1, 2 and 4 peeled in full, the full-size
+    configuration 3 on its first 20 sources and extrapolated linearly to 1000
+    (labelled so).  One JSON line; minutes of CPU time."""
+    import numpy as np
+    import oracle
+    from synth import config
+    oracle.build()
+    n_all = oracle.num_threads()
+    rows = []
+    plan = [("config 1", config(1), None, True), ("config 2", config(2), None, True),
+            ("config 4", config(4).with_(pos_sigma_rad=0.0), None, False),
+            ("config 3, first 20 sources", config(3), 20, False)]
+    for label, cad, k, single in plan:
+        run = cad.with_(n_src=k) if k else cad
+        V = oracle.simulate(run)
+        if run.precision == "mixed":
+            V = V.astype(np.complex64).astype(np.complex128)
+        row = {"workload": label, "n_ant": run.n_ant, "n_chan": run.n_chan, "n_time": run.n_time,
+               "sources_timed": run.n_src}
+        for threads in ([n_all, 1] if single else [n_all]):
+            oracle.set_num_threads(threads)
+            rate, dt = time_oracle(run, V)
+            row[f"{threads}_cores"] = {"s": dt, "updates_per_s": rate}
+        oracle.set_num_threads(n_all)
+        if k:
+            row["extrapolated_to_sources"] = cad.n_src
+            row["extrapolated_s"] = row[f"{n_all}_cores"]["s"] * cad.n_src / k
+        rows.append(row)
+    print(json.dumps({"cpu_baselines": rows, "cores": n_all, "os_cpu_count": os.cpu_count(),
+                      "kind": "oracle (plain FP64 C, OpenMP over baselines)"}), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -213,6 +248,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-baselines", action="store_true",
+                    help="time the FP64 CPU oracle on configurations 1, 2, 4 and 3 (first 20 sources) instead")
     ap.add_argument("--sources", type=int, default=1000, help="sources peeled per cadence")
     ap.add_argument("--n-iter", type=int, default=20)
     ap.add_argument("--antennas", type=int, default=512,
@@ -234,6 +271,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_baselines:
+        return run_cpu_baselines()
     if args.profile_case:
         return run_profile_case(args)
 
@@ -847,6 +886,15 @@ def extra_legs(args, p, cad, d_vis, d_resid, src, rank, mixed_rate, sm_mhz):
         out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                                "sample": (f"512 ant, 8 t, first {oc.n_chan} of 768 channels, {oc.n_src} "
                                           f"sources, FP64 C oracle, {dt:.1f} s")}
+        # one core on a smaller sample of the same workload
+        n_all = oracle.num_threads()
+        oracle.set_num_threads(1)
+        oc1, V1 = oracle_sample(n_chan=8, n_src=2)
+        val1, dt1 = time_oracle(oc1, V1)
+        oracle.set_num_threads(n_all)
+        out["cpu_baseline"]["single_core"] = {
+            "value": val1, "unit": UNIT, "cores": 1,
+            "sample": f"512 ant, 8 t, first 8 of 768 channels, 2 sources, {dt1:.1f} s"}
     return out
 
 

@@ -77,6 +77,7 @@ def lib():
             L.orc_grid.argtypes = [_i32, ctypes.c_double, _dp, _i32, _i32, _i32, _dp, _dp, _dp]
             L.orc_integrate.argtypes = [_i32, ctypes.c_int64, _i32, _ip, _i32, _dp, _dp]
             L.orc_num_threads.restype = _i32
+            L.orc_set_num_threads.argtypes = [_i32]
             _lib = L
     return _lib
 
@@ -91,6 +92,11 @@ def _f64(a, dtype=np.float64):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the oracle's later calls (results do not depend on it)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def n_baselines(n_ant: int) -> int:

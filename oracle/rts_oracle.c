@@ -108,6 +108,10 @@ static int m_finite(mat2 a) {
   return 1;
 }
 
+void orc_set_num_threads(int32_t n) {
+  if (n > 0) omp_set_num_threads(n);
+}
+
 int32_t orc_num_threads(void) {
 #ifdef _OPENMP
   return (int32_t)omp_get_max_threads();

@@ -74,6 +74,7 @@ void orc_grid(int32_t n_pix, double r_max, const double* gcf, int32_t n_tab, int
 void orc_integrate(int32_t n_fine, int64_t n_bl, int32_t n_chan, const int32_t* len, int32_t n_slot,
                    const double* fine, double* out);
 int32_t orc_num_threads(void);
+void    orc_set_num_threads(int32_t n);   /* OpenMP threads of the later calls (timing only) */
 
 #ifdef __cplusplus
 }
