@@ -44,6 +44,7 @@ struct BlockPassArgs {
   const PhaseAB* ph_acc;    // [n_bl][n_time][BK] their phases (precomputed)
   float2* avg;              // [BK][n_bl][4] plain averages of R_s in their directions
   double inv_n;
+  float tx0, tdx;           // gains Taylor-expanded in frequency: x_c = tx0 + c tdx (tcgen05 pass only)
 };
 
 // a Q0.64 phase read as a signed fraction of a turn, x 2^-64, in FP32: the high

@@ -48,6 +48,19 @@
 // (a wait that runs out sets *err and stops the pass, which the status read
 // reports, after the copies in flight have been waited for and TMEM is freed).
 // Limits: at most 64 sources per role, n_chan <= kTc5MaxChan.
+//
+// Gains Taylor-expanded in frequency (TAY): a source's model on a baseline is
+// (P0 + x_c P1 + x_c^2 P2) e^{-2 pi i phi} and its averages are the three
+// moments mean x_c^n R e^{+2 pi i phi}.  With x_c = u_q + v_r (u_q = x_0 + 16 q dx,
+// v_r = r dx) the same two GEMMs carry them when each source takes three of
+// the 64 operand slots, s = 3 k + m (21 sources per block):
+//   subtraction  slot (k, m): A_s = [sum_{n >= m} C(n, m) v_r^{n-m} P_n] conj(T2_k[r])
+//                             B_s = u_q^m conj(T1_k[q])
+//   average      slot (k, m): A_a rows = u_q^m T1_k[q] (real form), so the GEMM gives
+//                             H_km(r, e) = sum_q u_q^m T1_k[q] R(16 q + r, e), and
+//                M_kn = sum_{m <= n} C(n, m) sum_r v_r^{n-m} T2_k[r] H_km(r, e).
+// The CUDA cores form the coefficient table once per CTA, the u_q^m weights
+// beside the phasors, and three v_r-weighted T2 sums per slot.
 #pragma once
 #include "block_kernels.cuh"
 #include "tc05.cuh"
@@ -72,9 +85,12 @@ constexpr uint32_t kTc5ColAHi = 384;         // A_s hi
 constexpr uint32_t kTc5Cols = 512;
 
 // shared-memory layout (byte offsets) for NQ 16-channel tiles (16, 32 or 48)
+constexpr int kTayBlk = 21;                  // Taylor sources per block: 3 slots each
+constexpr int kTayOut = 6 * kTayBlk;         // v_r-weighted T2 sums per block (6 per source)
+
 struct Tc05Smem {
-  int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, bar, total;
-  __host__ __device__ explicit Tc05Smem(int NQ) {
+  int strip, bs_hi, bs_lo, ba_hi, ba_lo, t2s, t2a, mtab, ph, bar, cf, total;
+  __host__ __device__ explicit Tc05Smem(int NQ, bool tay = false) {
     int o = 0;
     strip = o; o += 2 * 16 * NQ * 32;            // two strips [16 NQ channels][4 pol][re, im]
     bs_hi = o; o += NQ * 128 * 4;                // B_s [NQ rows][128 K], K-major
@@ -88,12 +104,13 @@ struct Tc05Smem {
     bar = o;   o += 80;                          // mbarriers (sub done, avg done, strip 0, strip 1, sub
                                                  // operands ready, avg operands ready, phases 0, phases 1),
                                                  // TMEM address
+    cf = o;    o += tay ? kTc5Src * 16 * 4 * 8 : 0;  // Taylor A_s coefficients [64 slots][16 r][4 e] float2
     total = o;
   }
 };
 
 inline int tc05_nq(int n_chan) { return (((n_chan + 15) >> 4) + 15) & ~15; }
-inline size_t tc05_pass_smem(int n_chan) { return (size_t)Tc05Smem(tc05_nq(n_chan)).total; }
+inline size_t tc05_pass_smem(int n_chan, bool tay = false) { return (size_t)Tc05Smem(tc05_nq(n_chan), tay).total; }
 
 // TF32 rounding (to nearest, ties away from zero, as cvt.rna.tf32.f32 for
 // finite x below the FP32 maximum) by two integer operations
@@ -105,7 +122,7 @@ __device__ __forceinline__ float2 tc05_split(float x) {
   return make_float2(hi, x - hi);
 }
 
-template <bool SUB, bool ACC>
+template <bool SUB, bool ACC, bool TAY = false>
 __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArgs a, int bk, int* err) {
   using namespace tc05;
   const int nq = (a.n_chan + 15) >> 4;
@@ -114,7 +131,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   const int nmain_a = NQ >> 4;              // the average's hi*hi accumulators: 1, 2 or 3
   const int n16 = 16 * NQ;
   const uint32_t strip_bytes = (uint32_t)a.n_chan * 32u;
-  const Tc05Smem L(NQ);
+  const Tc05Smem L(NQ, TAY);
   extern __shared__ __align__(1024) unsigned char tc05_smem[];
   float* strip0 = reinterpret_cast<float*>(tc05_smem + L.strip);
   unsigned char* bs_hi = tc05_smem + L.bs_hi;
@@ -127,7 +144,18 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   PhaseAB* ph = reinterpret_cast<PhaseAB*>(tc05_smem + L.ph);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tc05_smem + L.bar);      // see Tc05Smem::bar
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tc05_smem + L.bar + 64);
-  float* part = reinterpret_cast<float*>(ba_hi);    // [4 cg][64 k][8]: B_a is free in P4
+  float2* cf = reinterpret_cast<float2*>(tc05_smem + L.cf);             // Taylor only
+  // [4 cg][64 slots][8] (Taylor: [4 cg][128 sums][8], B_a hi and lo): B_a is free in P4
+  constexpr int kPartRows = TAY ? 2 * kTc5Src : kTc5Src;
+  float* part = reinterpret_cast<float*>(ba_hi);
+  // slot -> source, and the slot's power m of u_q (Taylor: slot 3 k + m)
+  auto src_of = [](int s) { return TAY ? s / 3 : s; };
+  auto pow_of = [](int s) { return TAY ? s % 3 : 0; };
+  // u_q^m, u_q = x_0 + 16 q dx the offset of tile q's channel 0 from the band centre
+  auto upow = [&](int q, int m) {
+    const float u = fmaf((float)(16 * q), a.tdx, a.tx0);
+    return m == 0 ? 1.f : (m == 1 ? u : u * u);
+  };
 
   const int64_t bl = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qtr = warp & 3, cg = warp >> 2;
@@ -145,11 +173,35 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
     strip0[a.n_chan * 8 + i] = 0.f;
     strip0[(n16 + a.n_chan) * 8 + i] = 0.f;
   }
+  const int n_sub_slots = TAY ? 3 * a.n_sub : a.n_sub;
   if (SUB)
     for (int i = tid; compute && i < kTc5Src * 4; i += kTc5Compute) {
       const int s = i >> 2, e = i & 3;
-      mtab[i] = s < a.n_sub ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
+      mtab[i] = s < n_sub_slots ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
     }
+  if (SUB && TAY) {
+    // the Taylor subtraction's A_s coefficients, slot (k, m), channel offset r:
+    // sum_{n >= m} C(n, m) v_r^{n-m} P_n, v_r = r dx (from the model table mtab)
+    __syncthreads();
+    for (int i = tid; compute && i < kTc5Src * 64; i += kTc5Compute) {
+      const int s = i >> 6, r = (i >> 2) & 15, e = i & 3, k = s / 3, m = s - 3 * k;
+      float2 c = make_float2(0.f, 0.f);
+      if (k < a.n_sub) {
+        const float v = (float)r * a.tdx;
+        const float2 p2 = mtab[4 * (3 * k + 2) + e];
+        if (m == 2) {
+          c = p2;
+        } else if (m == 1) {
+          const float2 p1 = mtab[4 * (3 * k + 1) + e];
+          c = make_float2(fmaf(2.f * v, p2.x, p1.x), fmaf(2.f * v, p2.y, p1.y));
+        } else {
+          const float2 p1 = mtab[4 * (3 * k + 1) + e], p0 = mtab[4 * (3 * k) + e];
+          c = make_float2(fmaf(v, fmaf(v, p2.x, p1.x), p0.x), fmaf(v, fmaf(v, p2.y, p1.y), p0.y));
+        }
+      }
+      cf[i] = c;
+    }
+  }
   // phases of sources beyond bk stay zero (the copies bring bk per role)
   for (int i = tid; compute && i < 4 * kTc5Src; i += kTc5Compute) {
     ph[i].a = 0;
@@ -188,19 +240,23 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   auto t2_fill = [&](float2* t2, const PhaseAB* p) {
     for (int i = tid; i < kTc5Src * 16; i += kTc5Compute) {
       const int k = i >> 4, r = i & 15;
-      t2[k * kTc5T2Row + r] = phasor_hw((unsigned long long)r * p[k].b);
+      t2[k * kTc5T2Row + r] = phasor_hw((unsigned long long)r * p[src_of(k)].b);
     }
   };
   // B_s = conj(T1_k[q]) of the subtracted sources: thread (q & 7 = lane & 7,
   // k = (lane >> 3) + 4 warp) steps q by 8 with an exact 64-bit phase increment;
   // its 8-byte (re, im) stores cover 16 distinct slots of each 128-byte line
   auto bs_fill = [&](const PhaseAB* ps) {
-    const int ql = tid & 7, k = ((tid >> 3) & 3) + 4 * warp;
-    const PhaseAB p = ps[k];
+    const int ql = tid & 7, k = ((tid >> 3) & 3) + 4 * warp, m = pow_of(k);
+    const PhaseAB p = ps[src_of(k)];
     const unsigned long long step = 128ull * p.b;
     unsigned long long x = p.a + (unsigned long long)(16 * ql) * p.b;
     for (int q = ql; q < NQ; q += 8, x += step) {
-      const float2 z = phasor_hw(x);
+      float2 z = phasor_hw(x);
+      if (TAY) {
+        const float w = upow(q, m);
+        z = make_float2(z.x * w, z.y * w);
+      }
       const float hr = __uint_as_float(tc05_tf32(z.x)), hi = __uint_as_float(tc05_tf32(-z.y));
       const int o = kmaj_byte(q, 2 * k, 128);
       *reinterpret_cast<float2*>(bs_hi + o) = make_float2(hr, hi);
@@ -219,7 +275,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int k = 16 * cg + 8 * h + j;
-        const float2 m = mtab[4 * k + e], z = t2s[k * kTc5T2Row + r];
+        const float2 m = TAY ? cf[(k * 16 + r) * 4 + e] : mtab[4 * k + e], z = t2s[k * kTc5T2Row + r];
         const float ar = fmaf(m.x, z.x, m.y * z.y), ai = fmaf(m.y, z.x, -m.x * z.y);   // m conj(z)
         const float v0 = o ? ai : ar, v1 = o ? ar : -ai;
         const uint32_t h0 = tc05_tf32(v0), h1 = tc05_tf32(v1);
@@ -244,8 +300,8 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   // q = cg QW .. cg QW + QW - 1: the lane pair (o = 0, 1) computes even and odd
   // tiles and exchanges them
   auto aa_compute = [&](float2 (&t1v)[12], const PhaseAB* pa) {
-    const int k = 16 * qtr + (lane >> 1), o = lane & 1, q0 = cg * QW;
-    const PhaseAB p = pa[k];
+    const int k = 16 * qtr + (lane >> 1), o = lane & 1, q0 = cg * QW, m = pow_of(k);
+    const PhaseAB p = pa[src_of(k)];
     const unsigned long long step = 32ull * p.b;
     unsigned long long x = p.a + (unsigned long long)(16 * (q0 + o)) * p.b;
     #pragma unroll
@@ -253,6 +309,10 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       float2 mine = make_float2(0.f, 0.f);
       if (2 * jj < QW) {
         mine = phasor_hw(x);
+        if (TAY) {
+          const float w = upow(q0 + 2 * jj + o, m);
+          mine = make_float2(mine.x * w, mine.y * w);
+        }
         x += step;
       }
       const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, mine.x, 1), __shfl_xor_sync(0xffffffffu, mine.y, 1));
@@ -339,7 +399,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   // n = 4 r + e of r = 4 cg .. 4 cg + 3): o = 0 holds Re H (A += T2 Re H), o = 1
   // Im H (A += i T2 Im H); the lane pair's sums meet by a shuffle and the four
   // column groups' in part[cg][k]
-  auto avg_contract = [&](const float (&H)[16]) {
+  auto avg_contract_plain = [&](const float (&H)[16]) {
     const int k = 16 * qtr + (lane >> 1), o = lane & 1;
     float pr[4] = {0.f, 0.f, 0.f, 0.f}, pi[4] = {0.f, 0.f, 0.f, 0.f};
     #pragma unroll
@@ -358,23 +418,76 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       pi[e] += __shfl_xor_sync(0xffffffffu, pi[e], 1);
     }
     if (o == 0) {
-      float4* dst = reinterpret_cast<float4*>(part + (cg * kTc5Src + k) * 8);
+      float4* dst = reinterpret_cast<float4*>(part + (cg * kPartRows + k) * 8);
       dst[0] = make_float4(pr[0], pi[0], pr[1], pi[1]);
       dst[1] = make_float4(pr[2], pi[2], pr[3], pi[3]);
     }
   };
-  // compensated accumulation of the four column groups' sums (fixed order):
-  // compute thread tid owns value i = tid & 7 of source k = tid >> 3
-  float ks = 0.f, kc = 0.f;
-  auto avg_accumulate = [&]() {
-    const int k = tid >> 3, i = tid & 7;
-    float x = part[k * 8 + i];
+  // Taylor: slot s = 3 k + m gives Q_{k,m,d}(e) = sum_r v_r^d T2_k[r] H_km(r, e) for
+  // d = 0 .. 2 - m, sum index 6 k + {0, 3, 5}[m] + d (the moments combine them at the end)
+  auto avg_contract_tay = [&](const float (&H)[16]) {
+    const int s = 16 * qtr + (lane >> 1), o = lane & 1, k = s / 3, m = s - 3 * k;
+    float pr[3][4], pi[3][4];
     #pragma unroll
-    for (int c = 1; c < 4; ++c) x += part[(c * kTc5Src + k) * 8 + i];
-    const float y = x - kc;
-    const float tt = ks + y;
-    kc = (tt - ks) - y;
-    ks = tt;
+    for (int d = 0; d < 3; ++d)
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) { pr[d][e] = 0.f; pi[d][e] = 0.f; }
+    #pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const float2 z = t2a[s * kTc5T2Row + 4 * cg + rr];
+      const float v = (float)(4 * cg + rr) * a.tdx;
+      float wr = o ? -z.y : z.x, wi = o ? z.x : z.y;
+      #pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          pr[d][e] = fmaf(wr, H[4 * rr + e], pr[d][e]);
+          pi[d][e] = fmaf(wi, H[4 * rr + e], pi[d][e]);
+        }
+        wr *= v;
+        wi *= v;
+      }
+    }
+    #pragma unroll
+    for (int d = 0; d < 3; ++d)
+      #pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        pr[d][e] += __shfl_xor_sync(0xffffffffu, pr[d][e], 1);
+        pi[d][e] += __shfl_xor_sync(0xffffffffu, pi[d][e], 1);
+      }
+    if (o == 0) {
+      const int base = 6 * k + (m == 0 ? 0 : (m == 1 ? 3 : 5));
+      #pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (m + d <= 2 && base + d < kTayOut) {
+          float4* dst = reinterpret_cast<float4*>(part + (cg * kPartRows + base + d) * 8);
+          dst[0] = make_float4(pr[d][0], pi[d][0], pr[d][1], pi[d][1]);
+          dst[1] = make_float4(pr[d][2], pi[d][2], pr[d][3], pi[d][3]);
+        }
+      }
+    }
+  };
+  auto avg_contract = [&](const float (&H)[16]) {
+    if (TAY) avg_contract_tay(H);
+    else avg_contract_plain(H);
+  };
+  // compensated accumulation of the four column groups' sums (fixed order):
+  // compute thread tid owns value i = tid & 7 of row k = tid >> 3 (Taylor: and
+  // of row k + 64)
+  float ks[2] = {0.f, 0.f}, kc[2] = {0.f, 0.f};
+  auto avg_accumulate = [&]() {
+    #pragma unroll
+    for (int u = 0; u < (TAY ? 2 : 1); ++u) {
+      const int k = (tid >> 3) + 64 * u, i = tid & 7;
+      if (TAY && k >= kTayOut) continue;
+      float x = part[k * 8 + i];
+      #pragma unroll
+      for (int c = 1; c < 4; ++c) x += part[(c * kPartRows + k) * 8 + i];
+      const float y = x - kc[u];
+      const float tt = ks[u] + y;
+      kc[u] = (tt - ks[u]) - y;
+      ks[u] = tt;
+    }
   };
 
   // the 16 compute warps' own barrier (the MMA-issuing warp is not in it)
@@ -552,11 +665,34 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       csync();
       avg_accumulate();
     }
-    if (ACC && !s_bad) {
+    if (ACC && !s_bad && !TAY) {
       const int k = tid >> 3, i = tid & 7;   // value i = (re, im) of pol i / 2
       if (k < a.n_acc)
         reinterpret_cast<float*>(a.avg)[((size_t)k * a.n_bl + bl) * 8 + i] =
-            (float)(((double)ks - (double)kc) * a.inv_n);
+            (float)(((double)ks[0] - (double)kc[0]) * a.inv_n);
+    }
+    if (ACC && !s_bad && TAY) {
+      // the moments M_kn = sum_{m <= n} C(n, m) Q_{k,m,n-m} from the compensated sums
+      // (the coefficient table is no longer read: its words hold them)
+      float* qs = reinterpret_cast<float*>(cf);  // [128][8][2]: sum, compensation
+      #pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = (tid >> 3) + 64 * u, i = tid & 7;
+        if (k < kTayOut) {
+          qs[(k * 8 + i) * 2] = ks[u];
+          qs[(k * 8 + i) * 2 + 1] = kc[u];
+        }
+      }
+      csync();
+      const int s = tid >> 3, i = tid & 7, k = s / 3, n = s - 3 * k;
+      if (k < a.n_acc) {
+        auto val = [&](int j) {
+          const int w = ((6 * k + j) * 8 + i) * 2;
+          return (double)qs[w] - (double)qs[w + 1];
+        };
+        const double V = n == 0 ? val(0) : (n == 1 ? val(1) + val(3) : val(2) + 2.0 * val(4) + val(5));
+        reinterpret_cast<float*>(a.avg)[((size_t)s * a.n_bl + bl) * 8 + i] = (float)(V * a.inv_n);
+      }
     }
     if (tid == 0) {
       // a load still in flight after a failed wait must land before the CTA's

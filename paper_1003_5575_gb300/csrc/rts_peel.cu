@@ -22,6 +22,7 @@
 #include "solve_kernels.cuh"
 #include "stream_kernels.cuh"
 #include "taylor_kernels.cuh"
+#include "taylor_block_kernels.cuh"
 
 using namespace rts;
 
@@ -298,6 +299,9 @@ int setup_block_solve(rts_peel_t* h);
 // the tcgen05 pass holds all 512 TMEM columns: at least 116 KB of shared memory
 // keeps it at one CTA per SM (a second CTA would wait in its TMEM allocation)
 size_t tc05_launch_smem(const rts_peel_t* h) { return std::max<size_t>(tc05_pass_smem(h->n_chan), 116 * 1024); }
+size_t tc05_tay_launch_smem(const rts_peel_t* h) {
+  return std::max<size_t>(tc05_pass_smem(h->n_chan, true), 116 * 1024);
+}
 
 int ensure_block_workspace(rts_peel_t* h) {
   if (h->b_avg) return RTS_OK;
@@ -330,6 +334,10 @@ int ensure_block_workspace(rts_peel_t* h) {
     RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
     RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
     RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    const int tay = (int)tc05_tay_launch_smem(h);
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tay));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tay));
+    RTS_CUDA(h, cudaFuncSetAttribute(k_block_pass_tc05<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tay));
     return RTS_OK;
   }
   if (h->block_tc) {
@@ -704,6 +712,144 @@ int peel_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src, 
   return RTS_OK;
 }
 
+// ---- gains Taylor-expanded in frequency, blocked (taylor_block_kernels.cuh) ----
+// kTayBlk sources per pass through the tcgen05 pass's Taylor form; needs the
+// tcgen05 blocked workspace of 64-source blocks (its tables hold a Taylor
+// block: phases of 21 <= 32 sources, 210 x 5 <= 2016 D terms, 63 slots)
+bool taylor_blocked(const rts_peel_t* h) {
+  return h->block_tc05 && h->per_pass == kTc5Src && h->n_band == h->n_chan;
+}
+
+// mu_j = mean_c x_c^j, x_c = (c - (N - 1)/2) / N, in FP64 (odd j: zero by symmetry)
+TayMu taylor_mu(const rts_peel_t* h) {
+  const int n = h->n_chan;
+  double acc[kTayMu] = {};
+  for (int c = 0; c < n; ++c) {
+    const double x = (c - 0.5 * (n - 1)) / n;
+    double xp = 1.0;
+    for (int j = 0; j < kTayMu; ++j, xp *= x) acc[j] += xp;
+  }
+  TayMu mu;
+  for (int j = 0; j < kTayMu; ++j) mu.mu[j] = (j & 1) ? 0.f : (float)(acc[j] / n);
+  return mu;
+}
+
+// geometry of Taylor block b (phases with a stride of 32 sources, D^(0..4)) into
+// ring slot b % kRing, on the prep stream
+void launch_taylor_geometry(rts_peel_t* h, int b, int n_src, cudaStream_t ps) {
+  constexpr int BKG = 32;
+  const int s0 = b * kTayBlk, nblk = std::min(kTayBlk, n_src - s0);
+  const int r = b % rts_peel_t::kRing;
+  const unsigned g = 4 * (unsigned)h->n_sm;
+  const double nu0_c = h->nu0 / kCLight, dnu_c = h->dnu / kCLight;
+  k_block_ant_phases<BKG><<<g, 256, 0, ps>>>(h->d_src + 3 * (size_t)s0, nblk, h->d_uvw, h->n_ant, h->n_time,
+                                             nu0_c, dnu_c, h->b_aph);
+  k_block_phases<BKG><<<g, 256, 0, ps>>>(h->b_aph, nblk, h->d_bl_ant, h->n_ant, h->n_time, h->n_band,
+                                         h->band_chan0, h->n_bl, h->b_ph[r], h->b_trig[r]);
+  if (nblk > 1)
+    k_block_dirichlet_taylor<BKG><<<(unsigned)h->n_bl, 256, 0, ps>>>(h->b_ph[r], h->b_trig[r], nblk, h->b_dir[r],
+                                                                     h->n_bl, h->n_time, h->n_chan, taylor_mu(h));
+  h->launches[RTS_K_BLOCK_FIX] += nblk > 1 ? 3 : 2;
+}
+
+int launch_taylor_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a, cudaStream_t s) {
+  Span span(h, RTS_K_BLOCK_PASS, s);
+  const unsigned grid = (unsigned)h->n_bl;
+  const size_t tsm = tc05_tay_launch_smem(h);
+  if (sub && acc) k_block_pass_tc05<true, true, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, h->d_perr);
+  else if (sub) k_block_pass_tc05<true, false, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, h->d_perr);
+  else k_block_pass_tc05<false, true, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, h->d_perr);
+  span.end(1);
+  return check_launch(h, "Taylor block pass launch");
+}
+
+// The blocked Taylor cadence: a pass subtracts block b's models and takes the
+// plain moments of block b + 1; inside a block each source's moments are
+// corrected with D^(0..4) (k_taylor_correct), solved by the Taylor ALS, and its
+// P0, P1, P2 go to the block's model table (k_taylor_model)
+int peel_taylor_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src, const double* h_src,
+                        void* d_gain, void* d_slope, int32_t* h_status, cudaStream_t user) {
+  const size_t cube = (size_t)h->n_time * h->n_bl * h->n_chan * 4 * h->elem;
+  if (n_src == 0) {
+    if (d_resid != d_vis) RTS_CUDA(h, cudaMemcpyAsync(d_resid, d_vis, cube, cudaMemcpyDeviceToDevice, user));
+    return RTS_OK;
+  }
+  constexpr int R = rts_peel_t::kRing;
+  const int nb = (n_src + kTayBlk - 1) / kTayBlk;
+  const size_t jstride = (size_t)h->n_ant * 4;
+  const unsigned bl_grid = (unsigned)((h->n_bl + 255) / 256);
+  cudaStream_t s = h->b_main;
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_in, user));
+  RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_in, 0));
+  RTS_CUDA(h, cudaMemsetAsync(h->d_perr, 0, sizeof(int), s));
+  std::vector<double> src(h_src, h_src + 3 * (size_t)n_src);
+  RTS_CUDA(h, cudaMemcpyAsync(h->d_src, src.data(), sizeof(double) * 3 * n_src, cudaMemcpyHostToDevice, s));
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_src, s));
+  RTS_CUDA(h, cudaStreamWaitEvent(h->b_prep, h->b_ev_src, 0));
+  for (int b = 0; b < std::min(nb, R); ++b) {
+    launch_taylor_geometry(h, b, n_src, h->b_prep);
+    RTS_CUDA(h, cudaEventRecord(h->b_ev_ready[b % R], h->b_prep));
+  }
+  float x0, dx;
+  double mu[5];
+  taylor_axis(h, &x0, &dx, mu);
+  BlockPassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n_ant = h->n_ant; a.n_chan = h->n_chan; a.n_time = h->n_time; a.n_bl = h->n_bl;
+  a.inv_n = 1.0 / ((double)h->n_time * h->n_chan);
+  a.M_sub = h->b_model; a.avg = h->b_avg;
+  a.tx0 = x0; a.tdx = dx;
+  RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_ready[0], 0));
+  a.src = static_cast<const float4*>(d_vis);
+  a.n_acc = std::min(kTayBlk, (int)n_src); a.ph_acc = h->b_ph[0];
+  int rc = launch_taylor_pass(h, false, true, a, s);
+  if (rc) return rc;
+  for (int b = 0; b < nb; ++b) {
+    const int s0 = b * kTayBlk, nblk = std::min(kTayBlk, n_src - s0);
+    const float2* Dt = h->b_dir[b % R];
+    for (int q = 0; q < nblk; ++q) {
+      const int k = s0 + q;
+      {
+        Span span(h, RTS_K_BLOCK_FIX, s);
+        k_taylor_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, Dt, h->n_bl, h->t_mom);
+        span.end(1);
+      }
+      rc = launch_als_taylor(h, src[3 * k + 2], static_cast<float2*>(d_gain) + k * jstride,
+                             static_cast<float2*>(d_slope) + k * jstride, k, s);
+      if (rc) return rc;
+      {
+        Span span(h, RTS_K_BLOCK_FIX, s);
+        k_taylor_model<<<bl_grid, 256, 0, s>>>(h->t_X[h->n_iter & 1], src[3 * k + 2], h->d_bl_ant, h->n_bl,
+                                               h->b_model + (size_t)(3 * q) * h->n_bl * 4);
+        span.end(1);
+      }
+    }
+    const bool more = b + 1 < nb;
+    if (more) RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_ready[(b + 1) % R], 0));
+    a.src = static_cast<const float4*>(b == 0 ? d_vis : d_resid);
+    a.dst = static_cast<float4*>(d_resid);
+    a.n_sub = nblk; a.ph_sub = h->b_ph[b % R];
+    a.n_acc = more ? std::min(kTayBlk, n_src - s0 - kTayBlk) : 0;
+    a.ph_acc = h->b_ph[(b + 1) % R];
+    rc = launch_taylor_pass(h, true, more, a, s);
+    if (rc) return rc;
+    RTS_CUDA(h, cudaEventRecord(h->b_ev_free[b % R], s));
+    if (b + R < nb) {
+      RTS_CUDA(h, cudaStreamWaitEvent(h->b_prep, h->b_ev_free[b % R], 0));
+      launch_taylor_geometry(h, b + R, n_src, h->b_prep);
+      RTS_CUDA(h, cudaEventRecord(h->b_ev_ready[b % R], h->b_prep));
+    }
+  }
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_done, h->b_prep));
+  RTS_CUDA(h, cudaStreamWaitEvent(s, h->b_ev_done, 0));
+  RTS_CUDA(h, cudaEventRecord(h->b_ev_out, s));
+  RTS_CUDA(h, cudaStreamWaitEvent(user, h->b_ev_out, 0));
+  rc = check_launch(h, "Taylor block geometry launch");
+  if (rc) return rc;
+  if (h_status) return read_status(h, n_src, h_status, user);
+  return RTS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -722,6 +868,8 @@ int rts_peel_cadence_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int
   int rc = validate_sources(h, n_src, h_src);
   if (rc) return rc;
   if (n_src > 0 && (!d_gain || !d_slope)) return fail(h, RTS_EINVAL, "d_gain and d_slope are required");
+  if (taylor_blocked(h))
+    return peel_taylor_blocked(h, d_vis, d_resid, n_src, h_src, d_gain, d_slope, h_status, as_stream(stream));
   return peel_taylor(h, d_vis, d_resid, n_src, h_src, d_gain, d_slope, h_status, as_stream(stream));
 }
 
