@@ -72,6 +72,9 @@ def lib():
             L.orc_peel_taylor.restype = _i32
             L.orc_peel_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _dp, _ip]
             L.orc_taylor_moments.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+            L.orc_taylor_rotation.restype = _i32
+            L.orc_taylor_rotation.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, _dp, _dp, _dp, _dp]
             L.orc_taylor_dterm.argtypes = [_i32, _i32, _i32, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, _dp]
             L.orc_grid.argtypes = [_i32, ctypes.c_double, _dp, _i32, _i32, _i32, _dp, _dp, _dp]
@@ -259,6 +262,21 @@ def peel_taylor(uvw, freq, vis, lmS, n_iter=20):
     lib().orc_peel_taylor(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(R), n_src, _d(lmS),
                           n_iter, _d(G), _d(H), st.ctypes.data_as(_ip))
     return R, G, H, st[:n_src]
+
+
+def taylor_rotation(uvw, freq, vis, l, m, S, gain, slope):
+    """One common slope-rotation Newton step at the iterate (gain, slope)
+    [n_ant][4]: (new slope, taken, g [4], h [4][4])."""
+    uvw, freq = _f64(uvw), _f64(freq)
+    vis = _f64(vis, np.complex128)
+    n_time, n_ant = uvw.shape[0], uvw.shape[1]
+    G = np.ascontiguousarray(np.asarray(gain, np.complex128).reshape(n_ant, 4))
+    H = np.ascontiguousarray(np.asarray(slope, np.complex128).reshape(n_ant, 4)).copy()
+    g = np.zeros(4)
+    h = np.zeros(16)
+    taken = lib().orc_taylor_rotation(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(vis), float(l),
+                                      float(m), float(S), _d(G), _d(H), _d(g), _d(h))
+    return H, bool(taken), g, h.reshape(4, 4)
 
 
 def taylor_moments(uvw, freq, vis, l, m):

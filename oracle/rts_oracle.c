@@ -529,6 +529,103 @@ static int c_inverse(int n, const cplx* a, cplx* inv) {
   return 1;
 }
 
+/* The common slope rotation (reading R27).  Rotating every slope by the same
+ * Hermitian K, H_p -> H_p + i G_p K, changes the model
+ * S (G_i + x H_i)(G_j + x H_j)^H only at second order in x (the first-order
+ * terms cancel), so the Jacobi sweeps, which move one antenna at a time, barely
+ * move the iterate along it.  After every sweep from the second on, one Newton
+ * step from K = 0 on the least-squares cost restricted to that direction,
+ *   f(K) = sum_{i<j} sum_{t,c} || R~_ij - S (G_i + x (H_i + i G_i K))(G_j + x (H_j + i G_j K))^H ||^2,
+ * with K = sum_a k_a B_a over the Hermitian basis
+ *   B_0 = [1 0; 0 0], B_1 = [0 0; 0 1], B_2 = [0 1; 1 0], B_3 = [0 -i; i 0].
+ * With r the residual at K = 0 and <X, Y> = tr(X^H Y):
+ *   dm/dk_a         = S x^2 i (G_i B_a H_j^H - H_i B_a G_j^H)
+ *   d2m/dk_a dk_b   = S x^2 G_i (B_a B_b + B_b B_a) G_j^H
+ *   g_a  = -2 Re sum <r, dm/dk_a>
+ *   h_ab =  2 Re sum <dm/dk_a, dm/dk_b> - 2 Re sum <r, d2m/dk_a dk_b>
+ * and k = -h^-1 g when every Cholesky pivot of h exceeds 1e-6 of its largest
+ * diagonal entry (else no step: along a flat direction the step is not
+ * defined).  Returns 1 when the step was taken.  The solve takes the step only
+ * with three channels or more: with two, x_c^2 is the same at both, the change
+ * along K is one that G can absorb, and the direction is part of a flat set.  g_out [4], h_out [16]
+ * (optional) receive g and h. */
+static const cplx kRotB[4][4] = {{1, 0, 0, 0}, {0, 0, 0, 1}, {0, 1, 1, 0}, {0, -I, I, 0}};
+
+static int rotation_step(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* freq,
+                         const mat2* Rr, double S, const mat2* G, mat2* H, double* g_out, double* h_out) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int64_t n_s = (int64_t)n_time * n_chan;
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  mat2 B[4], W[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 4; ++k) B[a].e[k] = kRotB[a][k];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) W[a][b] = m_add(m_mul(B[a], B[b]), m_mul(B[b], B[a]));
+  double g[4] = {0, 0, 0, 0}, h[16] = {0};
+#pragma omp parallel for schedule(static) reduction(+ : g[:4], h[:16])
+  for (int64_t bl = 0; bl < n_bl; ++bl) {
+    int32_t p = ai[bl], q = aj[bl];
+    mat2 D[4], E[4][4];
+    for (int a = 0; a < 4; ++a)
+      D[a] = m_scale(m_sub(m_mul(m_mul(G[p], B[a]), m_herm(H[q])), m_mul(m_mul(H[p], B[a]), m_herm(G[q]))),
+                     I * S);
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) E[a][b] = m_scale(m_mul(m_mul(G[p], W[a][b]), m_herm(G[q])), S);
+    for (int32_t t = 0; t < n_time; ++t)
+      for (int32_t c = 0; c < n_chan; ++c) {
+        double x = taylor_x(freq, n_chan, c), x2 = x * x, x4 = x2 * x2;
+        mat2 Ap = m_add(G[p], m_scale(H[p], x)), Aq = m_add(G[q], m_scale(H[q], x));
+        mat2 r = m_sub(Rr[bl * n_s + (int64_t)t * n_chan + c], m_scale(m_mul(Ap, m_herm(Aq)), S));
+        for (int a = 0; a < 4; ++a) {
+          cplx rd = 0;
+          for (int k = 0; k < 4; ++k) rd += conj(r.e[k]) * D[a].e[k];
+          g[a] += -2.0 * x2 * creal(rd);
+          for (int b = 0; b < 4; ++b) {
+            cplx dd = 0, re = 0;
+            for (int k = 0; k < 4; ++k) {
+              dd += conj(D[a].e[k]) * D[b].e[k];
+              re += conj(r.e[k]) * E[a][b].e[k];
+            }
+            h[4 * a + b] += 2.0 * x4 * creal(dd) - 2.0 * x2 * creal(re);
+          }
+        }
+      }
+  }
+  if (g_out) memcpy(g_out, g, sizeof(g));
+  if (h_out) memcpy(h_out, h, sizeof(h));
+  /* Cholesky h = L L^T with the pivot test, then k = -h^-1 g */
+  double L[4][4] = {{0}}, dmax = 0.0;
+  for (int a = 0; a < 4; ++a) dmax = fmax(dmax, h[5 * a]);
+  if (!(dmax > 0.0)) return 0;
+  for (int j = 0; j < 4; ++j) {
+    double d = h[5 * j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 1e-6 * dmax)) return 0;
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < 4; ++i) {
+      double v = h[4 * i + j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  double y[4], k[4];
+  for (int i = 0; i < 4; ++i) {
+    double v = -g[i];
+    for (int j = 0; j < i; ++j) v -= L[i][j] * y[j];
+    y[i] = v / L[i][i];
+  }
+  for (int i = 3; i >= 0; --i) {
+    double v = y[i];
+    for (int j = i + 1; j < 4; ++j) v -= L[j][i] * k[j];
+    k[i] = v / L[i][i];
+  }
+  mat2 K = m_zero();
+  for (int a = 0; a < 4; ++a) K = m_add(K, m_scale(B[a], k[a]));
+  for (int32_t p = 0; p < n_ant; ++p) H[p] = m_add(H[p], m_scale(m_mul(G[p], K), I));
+  return 1;
+}
+
 void orc_predict_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                         const double* freq, int32_t n_src, const double* lmS, const double* gain,
                         const double* slope, double* vis, int32_t accumulate) {
@@ -621,6 +718,7 @@ int32_t orc_als_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const doub
         Gn[p] = m_scale(m_add(Gn[p], G[p]), 0.5);
         Hn[p] = m_scale(m_add(Hn[p], H[p]), 0.5);
       }
+    if (it >= 2 && n_chan >= 3) rotation_step(n_ant, n_chan, n_time, freq, Rr, S, Gn, Hn, NULL, NULL);
     double dn = 0.0, nn = 0.0;
     for (int32_t p = 0; p < n_ant; ++p) {
       dn += m_norm2(m_sub(Gn[p], G[p])) + m_norm2(m_sub(Hn[p], H[p]));
@@ -639,6 +737,38 @@ int32_t orc_als_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const doub
   if (rel_change) *rel_change = rel;
   if (!finite || !isfinite(rel)) return -4;
   return rel > 1e-6 ? 1 : 0;
+}
+
+/* One slope-rotation step (rotation_step above) of source (l, m, S) on the
+ * cube vis at the iterate (gain, slope), exposed for the tests: slope is
+ * updated in place when the step is taken (returns 1), g [4] and h [16]
+ * receive the gradient and Hessian of f at K = 0. */
+int32_t orc_taylor_rotation(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
+                            const double* freq, const double* vis, double l, double m, double S,
+                            const double* gain, double* slope, double* g, double* h) {
+  int64_t n_bl = orc_n_baselines(n_ant);
+  int64_t n_s = (int64_t)n_time * n_chan;
+  int32_t *ai, *aj;
+  antenna_map(n_ant, &ai, &aj);
+  mat2* Rr = (mat2*)malloc(sizeof(mat2) * (size_t)(n_bl * n_s > 0 ? n_bl * n_s : 1));
+#pragma omp parallel for schedule(static)
+  for (int64_t bl = 0; bl < n_bl; ++bl)
+    for (int32_t t = 0; t < n_time; ++t) {
+      double tau = orc_delay_m(uvw, n_ant, t, ai[bl], aj[bl], l, m);
+      for (int32_t c = 0; c < n_chan; ++c)
+        Rr[bl * n_s + (int64_t)t * n_chan + c] =
+            m_scale(m_load(vis_at((double*)vis, n_bl, n_chan, t, bl, c)), phasor(orc_phase_turns(tau, freq[c]), +1.0));
+    }
+  mat2* G = (mat2*)malloc(sizeof(mat2) * n_ant);
+  mat2* H = (mat2*)malloc(sizeof(mat2) * n_ant);
+  for (int32_t p = 0; p < n_ant; ++p) {
+    G[p] = m_load(gain + (int64_t)p * 8);
+    H[p] = m_load(slope + (int64_t)p * 8);
+  }
+  int taken = rotation_step(n_ant, n_chan, n_time, freq, Rr, S, G, H, g, h);
+  for (int32_t p = 0; p < n_ant; ++p) m_store(slope + (int64_t)p * 8, H[p]);
+  free(Rr); free(G); free(H);
+  return taken;
 }
 
 int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,

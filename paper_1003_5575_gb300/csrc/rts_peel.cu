@@ -55,6 +55,10 @@ struct rts_peel_t {
   float2* t_mom = nullptr;         // [3][n_bl][4] channel moments of the averaged source
   double2* t_X[2] = {nullptr, nullptr};   // [n_ant][8] FP64 iterates (G then H)
   float2* t_Xf[2] = {nullptr, nullptr};   // FP32 copies
+  double* t_rot_part = nullptr;    // [t_rot_grid][kRotVals] slope-rotation sums per CTA
+  unsigned* t_rot_count = nullptr; // [1] CTAs done (zero between launches)
+  double* t_rot_step = nullptr;    // [5] the step (k_0..k_3, taken)
+  int t_rot_grid = 0;
   // blocked peel workspace (allocated on the first blocked cadence).  The phase
   // and D_jk tables depend on geometry only; a second stream fills a ring of
   // kRing block slots ahead of the main stream (events order the reuse).
@@ -621,6 +625,13 @@ int taylor_setup(rts_peel_t* h) {
     if (!h->t_X[k]) RTS_CUDA(h, cudaMalloc(&h->t_X[k], (size_t)h->n_ant * 8 * sizeof(double2)));
     if (!h->t_Xf[k]) RTS_CUDA(h, cudaMalloc(&h->t_Xf[k], (size_t)h->n_ant * 8 * sizeof(float2)));
   }
+  h->t_rot_grid = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)h->n_sm, (h->n_bl + 255) / 256));
+  if (!h->t_rot_part) RTS_CUDA(h, cudaMalloc(&h->t_rot_part, (size_t)h->t_rot_grid * kRotVals * sizeof(double)));
+  if (!h->t_rot_step) RTS_CUDA(h, cudaMalloc(&h->t_rot_step, 5 * sizeof(double)));
+  if (!h->t_rot_count) {
+    RTS_CUDA(h, cudaMalloc(&h->t_rot_count, sizeof(unsigned)));
+    RTS_CUDA(h, cudaMemset(h->t_rot_count, 0, sizeof(unsigned)));
+  }
   return RTS_OK;
 }
 
@@ -669,9 +680,19 @@ int launch_als_taylor(rts_peel_t* h, double S, float2* gain_out, float2* slope_o
     for (int k = 0; k < 5; ++k) a.mu[k] = mu[k];
     a.first = it == 1; a.average = (it % 2) == 0;
     k_als_taylor_sweep<<<(unsigned)h->n_ant, kAlsThreads, 0, s>>>(a);
+    if (it >= 2 && h->n_chan >= 3) {         // the common slope-rotation step (three channels or more)
+      TaylorRotArgs r;
+      r.mom = h->t_mom; r.Xf = h->t_Xf[it & 1]; r.bl_ant = h->d_bl_ant; r.n_bl = h->n_bl;
+      r.S = (float)S; r.mu2 = (float)mu[2]; r.mu3 = (float)mu[3]; r.mu4 = (float)mu[4];
+      r.part = h->t_rot_part; r.count = h->t_rot_count; r.step = h->t_rot_step;
+      k_taylor_rot_sums<<<(unsigned)h->t_rot_grid, 256, 0, s>>>(r);
+      k_taylor_rot_apply<<<(unsigned)((8 * h->n_ant + 255) / 256), 256, 0, s>>>(
+          h->t_rot_step, h->t_X[it & 1], h->t_X[(it - 1) & 1], h->t_Xf[it & 1], h->d_norms, h->d_flag,
+          a.gain_out, a.slope_out, h->n_ant);
+    }
   }
   k_als_finalize<<<1, 256, 0, s>>>(h->d_norms, h->n_ant, h->d_flag, h->d_status + slot, h->d_rel + slot);
-  span.end(h->n_iter + 1);
+  span.end(h->n_chan >= 3 ? 3 * h->n_iter - 1 : h->n_iter + 1);
   return check_launch(h, "Taylor ALS kernel launch");
 }
 
@@ -1454,7 +1475,7 @@ void rts_peel_destroy(rts_peel_t* h) {
   void* ptrs[] = {h->d_uvw, h->d_bl_ant, h->d_freq_c, h->d_avg, h->d_J[0], h->d_J[1], h->d_Jf[0],
                   h->d_Jf[1], h->d_norms, h->d_flag, h->d_status, h->d_rel, h->d_src, h->d_jones_stage,
                   h->b_avg, h->b_aph, h->b_model, h->b_sync, h->b_part, h->d_perr, h->t_mom, h->t_X[0],
-                  h->t_X[1], h->t_Xf[0], h->t_Xf[1]};
+                  h->t_X[1], h->t_Xf[0], h->t_Xf[1], h->t_rot_part, h->t_rot_count, h->t_rot_step};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int r = 0; r < rts_peel_t::kRing; ++r) {

@@ -410,4 +410,226 @@ __global__ void __launch_bounds__(kAlsThreads) k_als_taylor_sweep(TaylorAlsArgs 
   }
 }
 
+// ---- the common slope rotation (reading R27) ------------------------------------
+// Rotating every slope by the same Hermitian K, H_p -> H_p + i G_p K, changes
+// the model only at second order in x_c, so the Jacobi sweeps barely move the
+// iterate along it.  After each sweep from the second on: one Newton step from
+// K = 0 on the cost along that direction, K = sum_a k_a B_a over
+// B = [1 0; 0 0], [0 0; 0 1], [0 1; 1 0], [0 -i; i 0].  From the moments, per
+// baseline (p, q), with rho = M2 - S (mu2 P0 + mu3 P1 + mu4 P2) the
+// x_c^2-weighted mean residual, F_a = G_p B_a G_q^H and
+// D_a = i (G_p B_a H_q^H - H_p B_a G_q^H) (<X, Y> = tr X^H Y):
+//   g_a  = -2 S sum Re<rho, D_a>
+//   h_ab =  2 S^2 mu4 sum Re<D_a, D_b> - 2 S sum Re<rho, G_p (B_a B_b + B_b B_a) G_q^H>,
+// B_a B_b + B_b B_a being 2 B_0, 2 B_1, 2 I, 2 I on the diagonal, B_2 at (0, 2)
+// and (1, 2), B_3 at (0, 3) and (1, 3), 0 at (0, 1) and (2, 3).  The sums over
+// all samples carry a common factor (the sample count) that drops out of
+// k = -h^-1 g.  The step is taken when every Cholesky pivot of h exceeds 1e-6
+// of its largest diagonal entry, and only with three channels or more (with
+// two, x_c^2 is the same at both and G absorbs the change along K).
+
+constexpr int kRotVals = 18;   // per baseline: Re<rho,F_a> (4), Re<rho,D_a> (4), Re<D_a,D_b> a <= b (10)
+
+struct TaylorRotArgs {
+  const float2* mom;        // [3][n_bl][4] moments (M2 is used)
+  const float2* Xf;         // [n_ant][8] FP32 iterate after the sweep (G then H)
+  const int2* bl_ant;
+  int64_t n_bl;
+  float S, mu2, mu3, mu4;
+  double* part;             // [gridDim.x][kRotVals] per-CTA sums
+  unsigned* count;          // CTAs done (zero between launches: the last CTA resets it)
+  double* step;             // [5]: k_0 .. k_3, then 1 when the step is taken, else 0
+};
+
+// X B_a Y^H, a = 0..3, from the outer products O_kl[r][c] = X[r][k] conj(Y[c][l]):
+// O_00, O_11, O_01 + O_10, i (O_10 - O_01)
+__device__ inline void basis_products(const float2 (&X)[4], const float2 (&Y)[4], float2 (&out)[4][4]) {
+  #pragma unroll
+  for (int r = 0; r < 2; ++r)
+    #pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int e = 2 * r + c;
+      const float2 o00 = cmulc(X[2 * r], Y[2 * c]), o11 = cmulc(X[2 * r + 1], Y[2 * c + 1]);
+      const float2 o01 = cmulc(X[2 * r], Y[2 * c + 1]), o10 = cmulc(X[2 * r + 1], Y[2 * c]);
+      out[0][e] = o00;
+      out[1][e] = o11;
+      out[2][e] = cadd(o01, o10);
+      out[3][e] = make_float2(o01.y - o10.y, o10.x - o01.x);
+    }
+}
+
+__device__ inline float re_inner(const float2 (&a)[4], const float2 (&b)[4]) {
+  float s = 0.f;
+  #pragma unroll
+  for (int e = 0; e < 4; ++e) s += a[e].x * b[e].x + a[e].y * b[e].y;
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_taylor_rot_sums(TaylorRotArgs a) {
+  __shared__ double s_w[8][kRotVals];
+  __shared__ double s_tot[kRotVals];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float acc[kRotVals];
+  #pragma unroll
+  for (int i = 0; i < kRotVals; ++i) acc[i] = 0.f;
+  for (int64_t bl = blockIdx.x * (int64_t)blockDim.x + tid; bl < a.n_bl; bl += (int64_t)gridDim.x * blockDim.x) {
+    const int2 ij = a.bl_ant[bl];
+    float2 Gp[4], Hp[4], Gq[4], Hq[4], M2[4];
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      Gp[e] = a.Xf[(size_t)ij.x * 8 + e]; Hp[e] = a.Xf[(size_t)ij.x * 8 + 4 + e];
+      Gq[e] = a.Xf[(size_t)ij.y * 8 + e]; Hq[e] = a.Xf[(size_t)ij.y * 8 + 4 + e];
+      M2[e] = a.mom[((size_t)2 * a.n_bl + bl) * 4 + e];
+    }
+    float2 F[4][4], DA[4][4], DB[4][4];
+    basis_products(Gp, Gq, F);
+    basis_products(Gp, Hq, DA);
+    basis_products(Hp, Gq, DB);
+    float2 rho[4], D[4][4];
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = e >> 1, c = e & 1;
+      const float2 P0 = cadd(F[0][e], F[1][e]);
+      const float2 P1 = cadd(cadd(DA[0][e], DA[1][e]), cadd(DB[0][e], DB[1][e]));
+      const float2 P2 = cadd(cmulc(Hp[2 * r], Hq[2 * c]), cmulc(Hp[2 * r + 1], Hq[2 * c + 1]));
+      rho[e] = make_float2(M2[e].x - a.S * (a.mu2 * P0.x + a.mu3 * P1.x + a.mu4 * P2.x),
+                           M2[e].y - a.S * (a.mu2 * P0.y + a.mu3 * P1.y + a.mu4 * P2.y));
+      #pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float2 d = csub(DA[b][e], DB[b][e]);
+        D[b][e] = make_float2(-d.y, d.x);                  // i (G_p B H_q^H - H_p B G_q^H)
+      }
+    }
+    #pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc[b] += re_inner(rho, F[b]);
+      acc[4 + b] += re_inner(rho, D[b]);
+    }
+    int k = 8;
+    #pragma unroll
+    for (int b0 = 0; b0 < 4; ++b0)
+      #pragma unroll
+      for (int b1 = b0; b1 < 4; ++b1) acc[k++] += re_inner(D[b0], D[b1]);
+  }
+  // FP64 sums: warps, then the CTA, then (last CTA) the grid in a fixed order
+  #pragma unroll
+  for (int i = 0; i < kRotVals; ++i) {
+    double v = (double)acc[i];
+    #pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_w[warp][i] = v;
+  }
+  __syncthreads();
+  if (tid < kRotVals) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_w[w][tid];
+    a.part[(size_t)blockIdx.x * kRotVals + tid] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid < kRotVals) {
+    double v = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(a.part + (size_t)b * kRotVals + tid);
+    s_tot[tid] = v;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  *a.count = 0u;
+  const double S = a.S, r0 = s_tot[0], r1 = s_tot[1], r2 = s_tot[2], r3 = s_tot[3];
+  double g[4], h[4][4];
+  #pragma unroll
+  for (int b = 0; b < 4; ++b) g[b] = -2.0 * S * s_tot[4 + b];
+  {
+    int k = 8;
+    for (int b0 = 0; b0 < 4; ++b0)
+      for (int b1 = b0; b1 < 4; ++b1) {
+        h[b0][b1] = 2.0 * S * S * (double)a.mu4 * s_tot[k++];
+        h[b1][b0] = h[b0][b1];
+      }
+  }
+  const double rt[4][4] = {{2 * r0, 0, r2, r3}, {0, 2 * r1, r2, r3}, {r2, r2, 2 * (r0 + r1), 0},
+                           {r3, r3, 0, 2 * (r0 + r1)}};
+  for (int b0 = 0; b0 < 4; ++b0)
+    for (int b1 = 0; b1 < 4; ++b1) h[b0][b1] -= 2.0 * S * rt[b0][b1];
+  double L[4][4] = {{0}}, dmax = 0.0;
+  for (int b = 0; b < 4; ++b) dmax = fmax(dmax, h[b][b]);
+  bool ok = dmax > 0.0;
+  for (int j = 0; j < 4 && ok; ++j) {
+    double d = h[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 1e-6 * dmax)) { ok = false; break; }
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < 4; ++i) {
+      double v = h[i][j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  double kk[4] = {0, 0, 0, 0};
+  if (ok) {
+    double y[4];
+    for (int i = 0; i < 4; ++i) {
+      double v = -g[i];
+      for (int j = 0; j < i; ++j) v -= L[i][j] * y[j];
+      y[i] = v / L[i][i];
+    }
+    for (int i = 3; i >= 0; --i) {
+      double v = y[i];
+      for (int j = i + 1; j < 4; ++j) v -= L[j][i] * kk[j];
+      kk[i] = v / L[i][i];
+    }
+  }
+  for (int i = 0; i < 4; ++i) a.step[i] = kk[i];
+  a.step[4] = ok ? 1.0 : 0.0;
+}
+
+// H_p += i G_p K for every antenna (FP64 iterate and its FP32 copy), then the
+// convergence norms of the rotated iterate against the previous one; the
+// last sweep's G and H to gain_out / slope_out.  8 threads per antenna.
+__global__ void __launch_bounds__(256) k_taylor_rot_apply(const double* __restrict__ step, double2* X_new,
+                                                         const double2* __restrict__ X_old, float2* Xf_new,
+                                                         double* norms, int* flag, float2* gain_out,
+                                                         float2* slope_out, int n_ant) {
+  if (step[4] == 0.0) return;                // no step: the sweep's iterate, norms and outputs stand
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = t >> 3, e = t & 7;
+  const bool live = p < n_ant;
+  double2 Xn = make_double2(0.0, 0.0), Xo = Xn;
+  if (live) {
+    Xn = X_new[(size_t)p * 8 + e];
+    Xo = X_old[(size_t)p * 8 + e];
+    if (e >= 4) {
+      const int r = (e - 4) >> 1, c = e & 1;
+      // K = [k0, k2 - i k3; k2 + i k3, k1], column c
+      const double2 K0c = c == 0 ? make_double2(step[0], 0.0) : make_double2(step[2], -step[3]);
+      const double2 K1c = c == 0 ? make_double2(step[2], step[3]) : make_double2(step[1], 0.0);
+      const double2 gk = cadd(cmul(X_new[(size_t)p * 8 + 2 * r], K0c), cmul(X_new[(size_t)p * 8 + 2 * r + 1], K1c));
+      Xn = make_double2(Xn.x - gk.y, Xn.y + gk.x);
+      X_new[(size_t)p * 8 + e] = Xn;
+      Xf_new[(size_t)p * 8 + e] = make_float2((float)Xn.x, (float)Xn.y);
+    }
+  }
+  const double dx = Xn.x - Xo.x, dy = Xn.y - Xo.y;
+  double dn = dx * dx + dy * dy, nn = Xn.x * Xn.x + Xn.y * Xn.y;
+  int bad = live && !(isfinite(Xn.x) && isfinite(Xn.y));
+  #pragma unroll
+  for (int o = 1; o <= 4; o <<= 1) {
+    dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (!live) return;
+  if (e == 0) {
+    norms[2 * p] = dn;
+    norms[2 * p + 1] = nn;
+    if (bad) *flag = 1;
+  }
+  if (gain_out && e >= 4) slope_out[(size_t)p * 4 + (e - 4)] = make_float2((float)Xn.x, (float)Xn.y);
+}
+
 }  // namespace rts
