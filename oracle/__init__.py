@@ -70,7 +70,7 @@ def lib():
             L.orc_als_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, _i32, _dp, _dp, _dp]
             L.orc_peel_taylor.restype = _i32
-            L.orc_peel_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _dp, _ip]
+            L.orc_peel_taylor.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, _i32, _dp, _i32, _dp, _dp, _ip, _dp]
             L.orc_taylor_moments.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
             L.orc_taylor_rotation.restype = _i32
             L.orc_taylor_rotation.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
@@ -250,8 +250,9 @@ def als_taylor(uvw, freq, vis, l, m, S, n_iter=20):
     return G, H, int(st), rel.value
 
 
-def peel_taylor(uvw, freq, vis, lmS, n_iter=20):
-    """Sequential peel with gains linear in frequency: (residual, G, H, status)."""
+def peel_taylor(uvw, freq, vis, lmS, n_iter=20, with_rel=False):
+    """Sequential peel with gains linear in frequency: (residual, G, H, status[, rel]),
+    rel [n_src] = each source's last relative change ||X_n - X_(n-1)||_F / ||X_n||_F."""
     uvw, freq, lmS = _f64(uvw), _f64(freq), _f64(lmS)
     R = _f64(vis, np.complex128).copy()
     n_time, n_ant = uvw.shape[0], uvw.shape[1]
@@ -259,9 +260,11 @@ def peel_taylor(uvw, freq, vis, lmS, n_iter=20):
     G = np.zeros((n_src, n_ant, 4), np.complex128)
     H = np.zeros((n_src, n_ant, 4), np.complex128)
     st = np.zeros(max(n_src, 1), np.int32)
+    rel = np.zeros(max(n_src, 1))
     lib().orc_peel_taylor(n_ant, freq.shape[0], n_time, _d(uvw), _d(freq), _d(R), n_src, _d(lmS),
-                          n_iter, _d(G), _d(H), st.ctypes.data_as(_ip))
-    return R, G, H, st[:n_src]
+                          n_iter, _d(G), _d(H), st.ctypes.data_as(_ip), _d(rel))
+    out = (R, G, H, st[:n_src])
+    return out + (rel[:n_src],) if with_rel else out
 
 
 def taylor_rotation(uvw, freq, vis, l, m, S, gain, slope):

@@ -773,13 +773,15 @@ int32_t orc_taylor_rotation(int32_t n_ant, int32_t n_chan, int32_t n_time, const
 
 int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                         const double* freq, double* vis, int32_t n_src, const double* lmS,
-                        int32_t n_iter, double* gain, double* slope, int32_t* status) {
+                        int32_t n_iter, double* gain, double* slope, int32_t* status,
+                        double* rel_per_src) {
   int32_t worst = 0;
   for (int32_t k = 0; k < n_src; ++k) {
     double l = lmS[3 * k], m = lmS[3 * k + 1], S = lmS[3 * k + 2];
     double* Gk = gain + (int64_t)k * n_ant * 8;
     double* Hk = slope + (int64_t)k * n_ant * 8;
-    int32_t st = orc_als_taylor(n_ant, n_chan, n_time, uvw, freq, vis, l, m, S, n_iter, Gk, Hk, NULL);
+    int32_t st = orc_als_taylor(n_ant, n_chan, n_time, uvw, freq, vis, l, m, S, n_iter, Gk, Hk,
+                                rel_per_src ? rel_per_src + k : NULL);
     if (status) status[k] = st;
     if (st < 0) worst = st;
     /* subtract S (G_i + x H_i)(G_j + x H_j)^H exp(-2 pi i phi) */

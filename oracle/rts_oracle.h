@@ -62,7 +62,8 @@ int32_t orc_als_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const doub
                        int32_t n_iter, double* gain, double* slope, double* rel_change);
 int32_t orc_peel_taylor(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                         const double* freq, double* vis, int32_t n_src, const double* lmS,
-                        int32_t n_iter, double* gain, double* slope, int32_t* status);
+                        int32_t n_iter, double* gain, double* slope, int32_t* status,
+                        double* rel_per_src);
 int32_t orc_taylor_rotation(int32_t n_ant, int32_t n_chan, int32_t n_time, const double* uvw,
                             const double* freq, const double* vis, double l, double m, double S,
                             const double* gain, double* slope, double* g, double* h);

@@ -625,7 +625,7 @@ int taylor_setup(rts_peel_t* h) {
     if (!h->t_X[k]) RTS_CUDA(h, cudaMalloc(&h->t_X[k], (size_t)h->n_ant * 8 * sizeof(double2)));
     if (!h->t_Xf[k]) RTS_CUDA(h, cudaMalloc(&h->t_Xf[k], (size_t)h->n_ant * 8 * sizeof(float2)));
   }
-  h->t_rot_grid = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)h->n_sm, (h->n_bl + 255) / 256));
+  h->t_rot_grid = (int)std::max<int64_t>(1, std::min<int64_t>(kRotMaxGrid, (h->n_bl + kRotThreads - 1) / kRotThreads));
   if (!h->t_rot_part) RTS_CUDA(h, cudaMalloc(&h->t_rot_part, (size_t)h->t_rot_grid * kRotVals * sizeof(double)));
   if (!h->t_rot_step) RTS_CUDA(h, cudaMalloc(&h->t_rot_step, 5 * sizeof(double)));
   if (!h->t_rot_count) {
@@ -685,7 +685,7 @@ int launch_als_taylor(rts_peel_t* h, double S, float2* gain_out, float2* slope_o
       r.mom = h->t_mom; r.Xf = h->t_Xf[it & 1]; r.bl_ant = h->d_bl_ant; r.n_bl = h->n_bl;
       r.S = (float)S; r.mu2 = (float)mu[2]; r.mu3 = (float)mu[3]; r.mu4 = (float)mu[4];
       r.part = h->t_rot_part; r.count = h->t_rot_count; r.step = h->t_rot_step;
-      k_taylor_rot_sums<<<(unsigned)h->t_rot_grid, 256, 0, s>>>(r);
+      k_taylor_rot_sums<<<(unsigned)h->t_rot_grid, kRotThreads, 0, s>>>(r);
       k_taylor_rot_apply<<<(unsigned)((8 * h->n_ant + 255) / 256), 256, 0, s>>>(
           h->t_rot_step, h->t_X[it & 1], h->t_X[(it - 1) & 1], h->t_Xf[it & 1], h->d_norms, h->d_flag,
           a.gain_out, a.slope_out, h->n_ant);
@@ -840,8 +840,8 @@ int peel_taylor_blocked(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t
       if (rc) return rc;
       {
         Span span(h, RTS_K_BLOCK_FIX, s);
-        k_taylor_model<<<bl_grid, 256, 0, s>>>(h->t_X[h->n_iter & 1], src[3 * k + 2], h->d_bl_ant, h->n_bl,
-                                               h->b_model + (size_t)(3 * q) * h->n_bl * 4);
+        k_taylor_model<<<bl_grid, 256, 0, s>>>(h->t_Xf[h->n_iter & 1], (float)src[3 * k + 2], h->d_bl_ant,
+                                               h->n_bl, h->b_model + (size_t)(3 * q) * h->n_bl * 4);
         span.end(1);
       }
     }

@@ -180,18 +180,33 @@ __global__ void __launch_bounds__(256) k_taylor_correct(const float2* __restrict
     for (int e = 0; e < 4; ++e) mom[((size_t)n * n_bl + bl) * 4 + e] = v[n][e];
 }
 
-// P0, P1, P2 of a solved Taylor source (FP64 X = [G H] [n_ant][8]) into slots
-// 3q .. 3q + 2 of the block's model table: P[n][bl][4] (one thread per baseline)
-__global__ void __launch_bounds__(256) k_taylor_model(const double2* __restrict__ X, double S,
+// P0, P1, P2 of a solved Taylor source into slots 3q .. 3q + 2 of the block's
+// model table, P[n][bl][4], in FP32 from the FP32 copy of its iterate Xf =
+// [G H] [n_ant][8] (one thread per baseline; the table is FP32)
+__global__ void __launch_bounds__(256) k_taylor_model(const float2* __restrict__ Xf, float S,
                                                      const int2* __restrict__ bl_ant, int64_t n_bl,
                                                      float2* __restrict__ P) {
   const int64_t bl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (bl >= n_bl) return;
   const int2 ij = bl_ant[bl];
+  float2 Gi[4], Hi[4], Gj[4], Hj[4];
   #pragma unroll
-  for (int n = 0; n < 3; ++n)
-    #pragma unroll
-    for (int e = 0; e < 4; ++e) P[((size_t)n * n_bl + bl) * 4 + e] = taylor_model_entry(X, ij.x, ij.y, S, n, e);
+  for (int e = 0; e < 4; ++e) {
+    Gi[e] = Xf[(size_t)ij.x * 8 + e]; Hi[e] = Xf[(size_t)ij.x * 8 + 4 + e];
+    Gj[e] = Xf[(size_t)ij.y * 8 + e]; Hj[e] = Xf[(size_t)ij.y * 8 + 4 + e];
+  }
+  // (A B^H)[r][c] = sum_k A[r][k] conj(B[c][k])
+  auto ent = [](const float2 (&A)[4], const float2 (&B)[4], int r, int c) {
+    return cadd(cmulc(A[2 * r], B[2 * c]), cmulc(A[2 * r + 1], B[2 * c + 1]));
+  };
+  #pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int r = e >> 1, c = e & 1;
+    const float2 p0 = ent(Gi, Gj, r, c), p1 = cadd(ent(Gi, Hj, r, c), ent(Hi, Gj, r, c)), p2 = ent(Hi, Hj, r, c);
+    P[((size_t)0 * n_bl + bl) * 4 + e] = make_float2(S * p0.x, S * p0.y);
+    P[((size_t)1 * n_bl + bl) * 4 + e] = make_float2(S * p1.x, S * p1.y);
+    P[((size_t)2 * n_bl + bl) * 4 + e] = make_float2(S * p2.x, S * p2.y);
+  }
 }
 
 }  // namespace rts

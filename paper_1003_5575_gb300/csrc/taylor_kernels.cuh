@@ -229,48 +229,53 @@ __device__ inline void mhm_acc(const float2 (&a)[4], const float2 (&b)[4], float
     }
 }
 
-// In-place Cholesky of a 4x4 Hermitian positive-definite matrix (lower
-// triangle used); solves C y^H = b^H for the two rows b of B (y B-shaped):
-// X = B C^-1.  Returns false when C is not positive definite.
-__device__ inline bool chol_solve4(double2 (&C)[4][4], double2 (&B)[2][4]) {
-  double2 L[4][4];
+// One entry of X = b C^-1 (b one row of the right-hand sides, col its column)
+// for a 4x4 Hermitian positive-definite C = [A E; E^H D] (2x2 blocks), by the
+// Schur complement of A:
+//   T = A^-1 E,  Sc = D - E^H T,  x_h = (b_r - b_l T) Sc^-1,  x_g = (b_l - x_h E^H) A^-1,
+// with the 2x2 inverses in closed form.  C is positive definite exactly when
+// A_00 > 0, det A > 0, Sc_00 > 0 and det Sc > 0 (its Cholesky pivots are
+// A_00, det A / A_00, Sc_00, det Sc / Sc_00); returns false otherwise.  Each
+// lane of a warp takes one entry: an FP64 warp instruction costs 64 times an
+// FP32 one on this GPU, and the lanes share the instruction stream.
+__device__ inline bool schur_solve4_entry(const double2 (&C)[4][4], const double2 (&b)[4], int col, double2* x) {
+  // inverse of the Hermitian [a00 a01; conj(a01) a11]
+  auto inv2h = [](double a00, double2 a01, double a11, double2 (&o)[2][2], double* det) {
+    *det = a00 * a11 - (a01.x * a01.x + a01.y * a01.y);
+    const double id = 1.0 / *det;
+    o[0][0] = make_double2(a11 * id, 0.0);
+    o[1][1] = make_double2(a00 * id, 0.0);
+    o[0][1] = make_double2(-a01.x * id, -a01.y * id);
+    o[1][0] = make_double2(-a01.x * id, a01.y * id);
+  };
+  double2 Ai[2][2], Si[2][2], T[2][2], Sc[2][2];
+  double detA, detS;
+  inv2h(C[0][0].x, C[0][1], C[1][1].x, Ai, &detA);
+  if (!(C[0][0].x > 0.0) || !(detA > 0.0)) return false;
   #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    double d = C[j][j].x;
+  for (int r = 0; r < 2; ++r)
     #pragma unroll
-    for (int k = 0; k < j; ++k) d -= L[j][k].x * L[j][k].x + L[j][k].y * L[j][k].y;
-    if (!(d > 0.0)) return false;
-    const double ljj = sqrt(d), inv = 1.0 / ljj;
-    L[j][j] = make_double2(ljj, 0.0);
+    for (int c = 0; c < 2; ++c) T[r][c] = cadd(cmul(Ai[r][0], C[0][2 + c]), cmul(Ai[r][1], C[1][2 + c]));
+  #pragma unroll
+  for (int r = 0; r < 2; ++r)
     #pragma unroll
-    for (int i = j + 1; i < 4; ++i) {
-      double2 s = C[i][j];
-      #pragma unroll
-      for (int k = 0; k < j; ++k) s = csub(s, cmul(L[i][k], cconj(L[j][k])));
-      L[i][j] = make_double2(s.x * inv, s.y * inv);
-    }
+    for (int c = 0; c < 2; ++c)    // (E^H)[r][k] = conj(E[k][r])
+      Sc[r][c] = csub(C[2 + r][2 + c], cadd(cmul(cconj(C[0][2 + r]), T[0][c]), cmul(cconj(C[1][2 + r]), T[1][c])));
+  inv2h(Sc[0][0].x, Sc[0][1], Sc[1][1].x, Si, &detS);
+  if (!(Sc[0][0].x > 0.0) || !(detS > 0.0)) return false;
+  double2 Rh[2], Xh[2], Rg[2];
+  #pragma unroll
+  for (int k = 0; k < 2; ++k) Rh[k] = csub(b[2 + k], cadd(cmul(b[0], T[0][k]), cmul(b[1], T[1][k])));
+  #pragma unroll
+  for (int c = 0; c < 2; ++c) Xh[c] = cadd(cmul(Rh[0], Si[0][c]), cmul(Rh[1], Si[1][c]));
+  if (col >= 2) {
+    *x = col == 2 ? Xh[0] : Xh[1];           // selects, not an indexed (local-memory) read
+    return true;
   }
   #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    double2 y[4];
-    #pragma unroll
-    for (int i = 0; i < 4; ++i) {            // L y = b^H
-      double2 s = cconj(B[r][i]);
-      #pragma unroll
-      for (int k = 0; k < i; ++k) s = csub(s, cmul(L[i][k], y[k]));
-      y[i] = make_double2(s.x / L[i][i].x, s.y / L[i][i].x);
-    }
-    double2 z[4];
-    #pragma unroll
-    for (int i = 3; i >= 0; --i) {           // L^H z = y
-      double2 s = y[i];
-      #pragma unroll
-      for (int k = i + 1; k < 4; ++k) s = csub(s, cmul(cconj(L[k][i]), z[k]));
-      z[i] = make_double2(s.x / L[i][i].x, s.y / L[i][i].x);
-    }
-    #pragma unroll
-    for (int i = 0; i < 4; ++i) B[r][i] = cconj(z[i]);   // x = z^H
-  }
+  for (int k = 0; k < 2; ++k)       // (x_h E^H)[k] = sum_j x_h[j] conj(E[k][j])
+    Rg[k] = csub(b[k], cadd(cmul(Xh[0], cconj(C[k][2])), cmul(Xh[1], cconj(C[k][3]))));
+  *x = col == 0 ? cadd(cmul(Rg[0], Ai[0][0]), cmul(Rg[1], Ai[1][0])) : cadd(cmul(Rg[0], Ai[0][1]), cmul(Rg[1], Ai[1][1]));
   return true;
 }
 
@@ -278,7 +283,6 @@ __device__ inline bool chol_solve4(double2 (&C)[4][4], double2 (&B)[2][4]) {
 __global__ void __launch_bounds__(kAlsThreads) k_als_taylor_sweep(TaylorAlsArgs a) {
   __shared__ double s_red[kAlsThreads / 32][32];
   __shared__ double s_tot[32];
-  __shared__ double2 s_X[8];
   const int p = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // per-thread partials: A (2x4 complex: left M0 G + M1 H, right M1 G + M2 H),
@@ -307,22 +311,24 @@ __global__ void __launch_bounds__(kAlsThreads) k_als_taylor_sweep(TaylorAlsArgs 
     mhm_acc(G, H, K1); mhm_acc(H, G, K1);
     mhm_acc(H, H, K2);
   }
-  // FP64 sums across the CTA: 40 values in two reduce-scatter rounds of 16 + 24
-  double v[16];
+  // sums across the CTA, 40 values: FP32 within each warp (three reduce-scatter
+  // rounds of 16), FP64 across the warps (an FP64 warp instruction costs 64
+  // times an FP32 one here, so the lane sums stay FP32)
+  float v[16];
   #pragma unroll
-  for (int k = 0; k < 8; ++k) { v[k] = (double)Al[k]; v[8 + k] = (double)Ar[k]; }
-  double w0 = warp_reduce_scatter16(v, lane);
+  for (int k = 0; k < 8; ++k) { v[k] = Al[k]; v[8 + k] = Ar[k]; }
+  const float w0 = warp_reduce_scatter16f(v, lane);
   #pragma unroll
-  for (int k = 0; k < 8; ++k) { v[k] = (double)K0[k]; v[8 + k] = (double)K1[k]; }
-  double w1 = warp_reduce_scatter16(v, lane);
+  for (int k = 0; k < 8; ++k) { v[k] = K0[k]; v[8 + k] = K1[k]; }
+  const float w1 = warp_reduce_scatter16f(v, lane);
   #pragma unroll
-  for (int k = 0; k < 8; ++k) { v[k] = (double)K2[k]; v[8 + k] = 0.0; }
-  double w2 = warp_reduce_scatter16(v, lane);
+  for (int k = 0; k < 8; ++k) { v[k] = K2[k]; v[8 + k] = 0.f; }
+  const float w2 = warp_reduce_scatter16f(v, lane);
   __shared__ double s_red2[kAlsThreads / 32][8];
   if ((lane & 1) == 0) {
-    s_red[warp][lane >> 1] = w0;            // 0..15: A left, A right
-    s_red[warp][16 + (lane >> 1)] = w1;     // 16..31: K0, K1
-    if ((lane >> 1) < 8) s_red2[warp][lane >> 1] = w2;   // K2
+    s_red[warp][lane >> 1] = (double)w0;            // 0..15: A left, A right
+    s_red[warp][16 + (lane >> 1)] = (double)w1;     // 16..31: K0, K1
+    if ((lane >> 1) < 8) s_red2[warp][lane >> 1] = (double)w2;   // K2
   }
   __syncthreads();
   __shared__ double s_k2[8];
@@ -338,51 +344,37 @@ __global__ void __launch_bounds__(kAlsThreads) k_als_taylor_sweep(TaylorAlsArgs 
     s_k2[threadIdx.x - 32] = t;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // the normal matrix C (16 lanes, one entry each) and the right-hand sides
+  // B = S [A_l A_r] (8 lanes) in FP64, then lane e < 8 solves for entry e of X
+  __shared__ double2 s_C[16], s_B[8];
+  if (threadIdx.x < 24) {
     auto cm = [&](const double* b, int e) { return make_double2(b[2 * e], b[2 * e + 1]); };
-    const double* k0 = s_tot + 16;
-    const double* k1 = s_tot + 24;
-    const double* k2 = s_k2;
-    const double S = a.S, S2 = S * S;
-    double2 C[4][4];
-    // block (bi, bj) = S^2 (mu[bi+bj] K0 + mu[bi+bj+1] K1 + mu[bi+bj+2] K2)
-    #pragma unroll
-    for (int bi = 0; bi < 2; ++bi)
-      #pragma unroll
-      for (int bj = 0; bj < 2; ++bj) {
-        const double c0 = S2 * a.mu[bi + bj], c1 = S2 * a.mu[bi + bj + 1], c2 = S2 * a.mu[bi + bj + 2];
-        #pragma unroll
-        for (int r = 0; r < 2; ++r)
-          #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int e = 2 * r + c;
-            const double2 x0 = cm(k0, e), x1 = cm(k1, e), x2 = cm(k2, e);
-            C[2 * bi + r][2 * bj + c] = make_double2(c0 * x0.x + c1 * x1.x + c2 * x2.x,
-                                                     c0 * x0.y + c1 * x1.y + c2 * x2.y);
-          }
-      }
-    double2 B[2][4];
-    #pragma unroll
-    for (int r = 0; r < 2; ++r)
-      #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const double2 l = cm(s_tot, 2 * r + c), rr = cm(s_tot + 8, 2 * r + c);
-        B[r][c] = make_double2(S * l.x, S * l.y);
-        B[r][2 + c] = make_double2(S * rr.x, S * rr.y);
-      }
-    const bool ok = chol_solve4(C, B);
-    #pragma unroll
-    for (int r = 0; r < 2; ++r)
-      #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        s_X[2 * r + c] = ok ? B[r][c] : make_double2(NAN, NAN);          // G
-        s_X[4 + 2 * r + c] = ok ? B[r][2 + c] : make_double2(NAN, NAN);  // H
-      }
+    const double S = a.S;
+    const int t = threadIdx.x;
+    if (t < 16) {
+      // block (bi, bj) = S^2 (mu[bi+bj] K0 + mu[bi+bj+1] K1 + mu[bi+bj+2] K2)
+      const int R = t >> 2, Cc = t & 3, bi = R >> 1, bj = Cc >> 1, e = 2 * (R & 1) + (Cc & 1);
+      const double S2 = S * S, c0 = S2 * a.mu[bi + bj], c1 = S2 * a.mu[bi + bj + 1], c2 = S2 * a.mu[bi + bj + 2];
+      const double2 x0 = cm(s_tot + 16, e), x1 = cm(s_tot + 24, e), x2 = cm(s_k2, e);
+      s_C[t] = make_double2(c0 * x0.x + c1 * x1.x + c2 * x2.x, c0 * x0.y + c1 * x1.y + c2 * x2.y);
+    } else {
+      const int j = t - 16, r = j >> 2, c4 = j & 3;     // B[r][c4]: A_l entry 2r + c4, A_r entry 2r + c4 - 2
+      const double2 v = c4 < 2 ? cm(s_tot, 2 * r + c4) : cm(s_tot + 8, 2 * r + c4 - 2);
+      s_B[j] = make_double2(S * v.x, S * v.y);
+    }
   }
   __syncthreads();
   if (threadIdx.x >= 8) return;
   const int e = threadIdx.x;
-  double2 Xn = s_X[e];
+  // lane e: G entry (e >> 1, e & 1) for e < 4, H entry ((e - 4) >> 1, e & 1) for e >= 4
+  const int row = (e & 3) >> 1, col = e < 4 ? (e & 1) : 2 + (e & 1);
+  double2 C[4][4], brow[4];
+  #pragma unroll
+  for (int i = 0; i < 16; ++i) C[i >> 2][i & 3] = s_C[i];
+  #pragma unroll
+  for (int c = 0; c < 4; ++c) brow[c] = s_B[4 * row + c];
+  double2 Xn;
+  if (!schur_solve4_entry(C, brow, col, &Xn)) Xn = make_double2(NAN, NAN);
   double2 Xo;
   if (a.first) Xo = make_double2((e == 0 || e == 3) ? 1.0 : 0.0, 0.0);
   else Xo = a.X_old[(size_t)p * 8 + e];
@@ -424,8 +416,8 @@ __global__ void __launch_bounds__(kAlsThreads) k_als_taylor_sweep(TaylorAlsArgs 
 // B_a B_b + B_b B_a being 2 B_0, 2 B_1, 2 I, 2 I on the diagonal, B_2 at (0, 2)
 // and (1, 2), B_3 at (0, 3) and (1, 3), 0 at (0, 1) and (2, 3).  The sums over
 // all samples carry a common factor (the sample count) that drops out of
-// k = -h^-1 g.  The step is taken when every Cholesky pivot of h exceeds 1e-6
-// of its largest diagonal entry, and only with three channels or more (with
+// k = -h^-1 g (solved by 2x2 blocks).  The step is taken when every Cholesky
+// pivot of h exceeds 1e-6 of its largest diagonal entry, and only with three channels or more (with
 // two, x_c^2 is the same at both and G absorbs the change along K).
 
 constexpr int kRotVals = 18;   // per baseline: Re<rho,F_a> (4), Re<rho,D_a> (4), Re<D_a,D_b> a <= b (10)
@@ -465,8 +457,11 @@ __device__ inline float re_inner(const float2 (&a)[4], const float2 (&b)[4]) {
   return s;
 }
 
-__global__ void __launch_bounds__(256) k_taylor_rot_sums(TaylorRotArgs a) {
-  __shared__ double s_w[8][kRotVals];
+constexpr int kRotThreads = 512;
+constexpr int kRotMaxGrid = 64;    // CTAs: the last one sums at most 4 partials per lane
+
+__global__ void __launch_bounds__(kRotThreads) k_taylor_rot_sums(TaylorRotArgs a) {
+  __shared__ float s_w[kRotThreads / 32][kRotVals];
   __shared__ double s_tot[kRotVals];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -512,19 +507,24 @@ __global__ void __launch_bounds__(256) k_taylor_rot_sums(TaylorRotArgs a) {
       #pragma unroll
       for (int b1 = b0; b1 < 4; ++b1) acc[k++] += re_inner(D[b0], D[b1]);
   }
-  // FP64 sums: warps, then the CTA, then (last CTA) the grid in a fixed order
+  // sums in trees: FP32 within each warp (an FP64 warp instruction costs 64
+  // times an FP32 one here), FP64 over the CTA's 16 warps (16 lanes per value)
+  // and, in the last CTA, over the grid's partials (16 lanes per value, up to
+  // 4 partials each)
   #pragma unroll
   for (int i = 0; i < kRotVals; ++i) {
-    double v = (double)acc[i];
+    float v = acc[i];
     #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) s_w[warp][i] = v;
   }
   __syncthreads();
-  if (tid < kRotVals) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_w[w][tid];
-    a.part[(size_t)blockIdx.x * kRotVals + tid] = v;
+  if (tid < 16 * kRotVals) {                 // warps 0 .. 8, two values each
+    const int i = tid >> 4, w = tid & 15;
+    double v = (double)s_w[w][i];
+    #pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (w == 0) a.part[(size_t)blockIdx.x * kRotVals + i] = v;
   }
   __threadfence();
   __syncthreads();
@@ -532,59 +532,52 @@ __global__ void __launch_bounds__(256) k_taylor_rot_sums(TaylorRotArgs a) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (tid < kRotVals) {
+  if (tid < 16 * kRotVals) {
+    const int i = tid >> 4, w = tid & 15;
     double v = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(a.part + (size_t)b * kRotVals + tid);
-    s_tot[tid] = v;
+    for (unsigned b = w; b < gridDim.x; b += 16) v += __ldcg(a.part + (size_t)b * kRotVals + i);
+    #pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (w == 0) s_tot[i] = v;
   }
   __syncthreads();
   if (tid != 0) return;
   *a.count = 0u;
   const double S = a.S, r0 = s_tot[0], r1 = s_tot[1], r2 = s_tot[2], r3 = s_tot[3];
-  double g[4], h[4][4];
+  const double c4 = 2.0 * S * S * (double)a.mu4, c2 = 2.0 * S;
+  // h = [hA hE; hE^T hD] (2x2 blocks), r = -g
+  const double* dd = s_tot + 8;              // (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3)
+  const double h00 = c4 * dd[0] - c2 * 2.0 * r0, h01 = c4 * dd[1], h11 = c4 * dd[4] - c2 * 2.0 * r1;
+  const double h02 = c4 * dd[2] - c2 * r2, h03 = c4 * dd[3] - c2 * r3;
+  const double h12 = c4 * dd[5] - c2 * r2, h13 = c4 * dd[6] - c2 * r3;
+  const double h22 = c4 * dd[7] - c2 * 2.0 * (r0 + r1), h23 = c4 * dd[8], h33 = c4 * dd[9] - c2 * 2.0 * (r0 + r1);
+  double rv[4];
   #pragma unroll
-  for (int b = 0; b < 4; ++b) g[b] = -2.0 * S * s_tot[4 + b];
-  {
-    int k = 8;
-    for (int b0 = 0; b0 < 4; ++b0)
-      for (int b1 = b0; b1 < 4; ++b1) {
-        h[b0][b1] = 2.0 * S * S * (double)a.mu4 * s_tot[k++];
-        h[b1][b0] = h[b0][b1];
-      }
-  }
-  const double rt[4][4] = {{2 * r0, 0, r2, r3}, {0, 2 * r1, r2, r3}, {r2, r2, 2 * (r0 + r1), 0},
-                           {r3, r3, 0, 2 * (r0 + r1)}};
-  for (int b0 = 0; b0 < 4; ++b0)
-    for (int b1 = 0; b1 < 4; ++b1) h[b0][b1] -= 2.0 * S * rt[b0][b1];
-  double L[4][4] = {{0}}, dmax = 0.0;
-  for (int b = 0; b < 4; ++b) dmax = fmax(dmax, h[b][b]);
-  bool ok = dmax > 0.0;
-  for (int j = 0; j < 4 && ok; ++j) {
-    double d = h[j][j];
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    if (!(d > 1e-6 * dmax)) { ok = false; break; }
-    L[j][j] = sqrt(d);
-    for (int i = j + 1; i < 4; ++i) {
-      double v = h[i][j];
-      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-      L[i][j] = v / L[j][j];
-    }
-  }
-  double kk[4] = {0, 0, 0, 0};
+  for (int b = 0; b < 4; ++b) rv[b] = 2.0 * S * s_tot[4 + b];          // -g_b
+  // Cholesky pivots by the Schur complement of the leading block: h00,
+  // det A / h00, Sc00, det Sc / Sc00, each against 1e-6 of the largest diagonal
+  const double dmax = fmax(fmax(h00, h11), fmax(h22, h33));
+  const double detA = h00 * h11 - h01 * h01, idA = 1.0 / detA;
+  const double A00 = h11 * idA, A01 = -h01 * idA, A11 = h00 * idA;  // A^-1
+  const double T00 = A00 * h02 + A01 * h12, T01 = A00 * h03 + A01 * h13;   // T = A^-1 E
+  const double T10 = A01 * h02 + A11 * h12, T11 = A01 * h03 + A11 * h13;
+  const double S00 = h22 - (h02 * T00 + h12 * T10), S01 = h23 - (h02 * T01 + h12 * T11);
+  const double S11 = h33 - (h03 * T01 + h13 * T11);
+  const double detS = S00 * S11 - S01 * S01;
+  const double tol = 1e-6 * dmax;
+  const bool ok = dmax > 0.0 && h00 > tol && detA > tol * h00 && S00 > tol && detS > tol * S00;
+  double k0 = 0.0, k1 = 0.0, k2 = 0.0, k3 = 0.0;
   if (ok) {
-    double y[4];
-    for (int i = 0; i < 4; ++i) {
-      double v = -g[i];
-      for (int j = 0; j < i; ++j) v -= L[i][j] * y[j];
-      y[i] = v / L[i][i];
-    }
-    for (int i = 3; i >= 0; --i) {
-      double v = y[i];
-      for (int j = i + 1; j < 4; ++j) v -= L[j][i] * kk[j];
-      kk[i] = v / L[i][i];
-    }
+    const double idS = 1.0 / detS;
+    // k_2 = Sc^-1 (r_2 - T^T r_1), k_1 = A^-1 (r_1 - E k_2)
+    const double u0 = rv[2] - (T00 * rv[0] + T10 * rv[1]), u1 = rv[3] - (T01 * rv[0] + T11 * rv[1]);
+    k2 = (S11 * u0 - S01 * u1) * idS;
+    k3 = (S00 * u1 - S01 * u0) * idS;
+    const double w0 = rv[0] - (h02 * k2 + h03 * k3), w1 = rv[1] - (h12 * k2 + h13 * k3);
+    k0 = A00 * w0 + A01 * w1;
+    k1 = A01 * w0 + A11 * w1;
   }
-  for (int i = 0; i < 4; ++i) a.step[i] = kk[i];
+  a.step[0] = k0; a.step[1] = k1; a.step[2] = k2; a.step[3] = k3;
   a.step[4] = ok ? 1.0 : 0.0;
 }
 

@@ -4,8 +4,10 @@ widths) through the C ABI, against the FP64 oracle on its own simulations.
 
 Tolerances (the mixed path's targets): residual <= 1e-5 x rms of the input
 cube's real components; G and H together <= 1e-5 relative per source
-(||dX||_F / ||X||_F, X = [G H]; both sides run the same sweeps from the same
-start).  Status codes are exact.
+(||dX||_F / ||X||_F, X = [G H]; both sides run the same sweeps and slope
+rotation steps from the same start).  Status codes equal the oracle's outside
+a band around the 1e-6 threshold (_parity.rel_tol, "taylor"), and each
+source's last relative change agrees within that band.
 """
 import math
 
@@ -55,11 +57,14 @@ CASES = [
 
 @pytest.mark.parametrize("name,cad", CASES, ids=[c[0] for c in CASES])
 def test_taylor_peel_matches_oracle(name, cad):
+    from _parity import check_status
     V = simulate_linear(cad)
-    R_ref, G_ref, H_ref, st_ref = oracle.peel_taylor(cad.uvw(), cad.freqs(), V, cad.sources(), n_iter=20)
+    R_ref, G_ref, H_ref, st_ref, rel_ref = oracle.peel_taylor(cad.uvw(), cad.freqs(), V, cad.sources(), n_iter=20,
+                                                              with_rel=True)
     p = peeler(cad)
     R, G, H, st = p.cadence_taylor(torch.from_numpy(V.astype(np.complex64)).cuda(), cad.sources())
     torch.cuda.synchronize()
+    rel = p.rel(cad.n_src)
     p.close()
     rms = rms_of(V)
     assert np.abs(R.cpu().numpy() - R_ref).max() <= 1e-5 * rms
@@ -68,7 +73,7 @@ def test_taylor_peel_matches_oracle(name, cad):
         X = np.concatenate([G[k], H[k]], axis=1)
         X_ref = np.concatenate([G_ref[k], H_ref[k]], axis=1)
         assert np.linalg.norm(X - X_ref) <= 1e-5 * np.linalg.norm(X_ref), k
-    np.testing.assert_array_equal(st, st_ref)
+    check_status(name, st, st_ref, rel, rel_ref, "taylor")
 
 
 BLOCKED = [
@@ -85,16 +90,20 @@ def test_blocked_taylor_peel_matches_oracle(name, cad):
     """The blocked Taylor schedule (21 sources per tensor-core pass, in-block
     moments corrected with the closed-form x_c-weighted Dirichlet terms
     D^(0..4)) against the oracle's one-source-at-a-time Taylor peel, statuses
-    included; the pass count shows the blocked schedule ran."""
+    included (outside the band around 1e-6); the pass count shows the blocked
+    schedule ran."""
     from paper_1003_5575_gb300 import _abi
+    from _parity import check_status
     V = simulate_linear(cad)
-    R_ref, G_ref, H_ref, st_ref = oracle.peel_taylor(cad.uvw(), cad.freqs(), V, cad.sources(), n_iter=20)
+    R_ref, G_ref, H_ref, st_ref, rel_ref = oracle.peel_taylor(cad.uvw(), cad.freqs(), V, cad.sources(), n_iter=20,
+                                                              with_rel=True)
     p = peeler(cad)
     _abi.rts_peel_timing(p.h, 1)
     R, G, H, st = p.cadence_taylor(torch.from_numpy(V.astype(np.complex64)).cuda(), cad.sources())
     torch.cuda.synchronize()
     passes = _abi.rts_peel_timing_read(p.h)["block_pass"][2]
     _abi.rts_peel_timing(p.h, 0)
+    rel = p.rel(cad.n_src)
     p.close()
     assert passes == -(-cad.n_src // 21) + 1
     rms = rms_of(V)
@@ -104,7 +113,7 @@ def test_blocked_taylor_peel_matches_oracle(name, cad):
         X = np.concatenate([G[k], H[k]], axis=1)
         X_ref = np.concatenate([G_ref[k], H_ref[k]], axis=1)
         assert np.linalg.norm(X - X_ref) <= 1e-5 * np.linalg.norm(X_ref), k
-    np.testing.assert_array_equal(st, st_ref)
+    check_status(name, st, st_ref, rel, rel_ref, "taylor")
 
 
 def test_taylor_peel_of_constant_gains_matches_constant_gain_peel():
