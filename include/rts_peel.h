@@ -23,7 +23,9 @@
  *              device cubes and averages (d_vis, d_resid, d_avg) start on a
  *              16-byte boundary (the kernels move a polarisation pair per
  *              16-byte access; a misaligned pointer is RTS_EINVAL)
- *   Jones      jones[n_src][n_ant][4] complex, same precision as the cube
+ *   Jones      jones[n_src][n_ant][4] complex, same precision as the cube;
+ *              device Jones arrays (d_jones, d_gain, d_slope) also start
+ *              on a 16-byte boundary (RTS_EINVAL otherwise)
  *   sources    host double [n_src][3] = (l, m, S in Jy), in peel order
  *
  * Ownership: the caller owns every pointer it passes; "d_" pointers are

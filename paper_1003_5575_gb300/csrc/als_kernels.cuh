@@ -65,6 +65,23 @@ __device__ inline double warp_reduce_scatter16(double (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Reduce 16 floats over the 32 lanes of a warp (each level exchanges half of the
+// remaining values with the partner lane); afterwards lane L holds the warp
+// total of value index L >> 1.
+__device__ __forceinline__ float warp_reduce_scatter16f(float (&v)[16], int lane) {
+  #pragma unroll
+  for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+    const bool upper = (lane & o) != 0;
+    #pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = upper ? v[i] : v[i + n / 2];
+      const float keep = upper ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <typename T>   // T = float (mixed) or double (FP64)
 __global__ void __launch_bounds__(kAlsThreads) k_als_sweep(AlsArgs a) {
   using C = typename cplx_of<T>::type;

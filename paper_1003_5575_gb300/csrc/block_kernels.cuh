@@ -303,6 +303,13 @@ __global__ void __launch_bounds__(256) k_block_phases(const PhaseAB* __restrict_
   }
 }
 
+// Layout of a block's closed-form averages D_jk (j < k): by target source k,
+// then baseline, then j, so the terms of source k's correction for a run of
+// consecutive baselines are one contiguous stretch of memory
+__host__ __device__ inline int64_t dir_index(int64_t n_bl, int64_t bl, int j, int k) {
+  return n_bl * (k * (k - 1) / 2) + bl * k + j;
+}
+
 // sin(z) / z by its Taylor series to z^12 (first omitted term z^14/15!, below
 // 5e-10 for |z| <= pi/2)
 __device__ inline float sinc_series(float z) {
@@ -388,7 +395,7 @@ __global__ void __launch_bounds__(256) k_block_dirichlet(const PhaseAB* __restri
   #pragma unroll
   for (int u = 0; u < kU; ++u) {
     const int pr = threadIdx.x + 256 * u;
-    if (pr < n_pairs) Dtab[(size_t)bl * kPairs + pr] = make_float2(dre[u] * inv_t, dim[u] * inv_t);
+    if (pr < n_pairs) Dtab[dir_index(n_bl, bl, pj[u], pk[u])] = make_float2(dre[u] * inv_t, dim[u] * inv_t);
   }
 }
 
@@ -410,14 +417,14 @@ __global__ void __launch_bounds__(256) k_block_model(const double2* __restrict__
 
 __global__ void __launch_bounds__(256) k_block_correct(const float2* __restrict__ Ablk, int q,
                                                       const float2* __restrict__ Mblk,
-                                                      const float2* __restrict__ Dtab, int n_pairs,
+                                                      const float2* __restrict__ Dtab,
                                                       int64_t n_bl, float2* __restrict__ avg_out) {
   const int64_t bl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (bl >= n_bl) return;
   float2 v[4];
   #pragma unroll
   for (int e = 0; e < 4; ++e) v[e] = Ablk[((size_t)q * n_bl + bl) * 4 + e];
-  const float2* D = Dtab + (size_t)bl * n_pairs + q * (q - 1) / 2;
+  const float2* D = Dtab + dir_index(n_bl, bl, 0, q);
   for (int j = 0; j < q; ++j) {
     const float2 d = D[j];
     #pragma unroll

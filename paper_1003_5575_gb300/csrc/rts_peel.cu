@@ -75,7 +75,7 @@ struct rts_peel_t {
   } br;
   PhaseAB* b_ph[kRing] = {};       // [n_bl][n_time][BK] phases of a block
   GeoTrig* b_trig[kRing] = {};     // [n_bl][n_time][BK] trigonometry for D_jk
-  float2* b_dir[kRing] = {};       // [n_bl][BK(BK-1)/2] in-block closed-form averages D_jk
+  float2* b_dir[kRing] = {};       // [BK(BK-1)/2 x n_bl] in-block closed-form averages D_jk (dir_index)
   PhaseAB* b_aph = nullptr;        // [n_time][n_ant][BK] antenna phases of the block being prepared
   float2* b_avg = nullptr;         // [BK][n_bl][4] plain averages of a block
   float2* b_model = nullptr;       // [BK][n_bl][4] model matrices of a block
@@ -86,7 +86,7 @@ struct rts_peel_t {
   int bs_grid = 0, bs_apc = 0;
   size_t bs_smem = 0;
   unsigned* b_sync = nullptr;      // [2] barrier counter, abort flag
-  double* b_part = nullptr;        // [bs_grid][3] per-CTA convergence sums
+  double* b_part = nullptr;        // [BK][n_ant][4] per-antenna convergence sums of the last sweep
   cudaStream_t b_main = nullptr;   // high-priority stream for passes, corrections and solves
   cudaStream_t b_prep = nullptr;   // low-priority geometry stream
   cudaEvent_t b_ev_in = nullptr;   // caller's stream -> main
@@ -374,6 +374,7 @@ int setup_block_solve(rts_peel_t* h) {
   const int64_t want = std::max<int64_t>(h->n_ant, (h->n_bl + kSolveThreads - 1) / kSolveThreads);
   const int G = (int)std::min<int64_t>(n_sm, want);
   const int apc = (h->n_ant + G - 1) / G;
+  if (apc > kSolveMaxApc || h->per_pass > kCorrMaxJ) return RTS_OK;
   const size_t smem = block_solve_smem(h->n_ant, apc);
   cudaFuncAttributes fa;
   RTS_CUDA(h, cudaFuncGetAttributes(&fa, k_block_solve));
@@ -383,7 +384,7 @@ int setup_block_solve(rts_peel_t* h) {
   RTS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_block_solve, kSolveThreads, smem));
   if (occ < 1) return RTS_OK;
   RTS_CUDA(h, cudaMalloc((void**)&h->b_sync, 2 * sizeof(unsigned)));
-  RTS_CUDA(h, cudaMalloc((void**)&h->b_part, (size_t)G * 3 * sizeof(double)));
+  RTS_CUDA(h, cudaMalloc((void**)&h->b_part, (size_t)h->per_pass * h->n_ant * 4 * sizeof(double)));
   h->bs_grid = G;
   h->bs_apc = apc;
   h->bs_smem = smem;
@@ -396,11 +397,11 @@ int setup_block_solve(rts_peel_t* h) {
 int launch_block_solve(rts_peel_t* h, int s0, int nblk, const float2* Dt, void* d_jones, cudaStream_t s) {
   Span span(h, RTS_K_SOLVE, s);
   BlockSolveArgs a;
-  a.Ablk = h->b_avg; a.Dtab = Dt; a.n_pairs = h->per_pass * (h->per_pass - 1) / 2;
+  a.Ablk = h->b_avg; a.Dtab = Dt;
   a.src = h->d_src; a.s0 = s0; a.n_blk = nblk;
   a.bl_ant = h->d_bl_ant; a.n_ant = h->n_ant; a.n_bl = h->n_bl; a.n_iter = h->n_iter;
   a.apc = h->bs_apc;
-  a.avg = static_cast<float2*>(h->d_avg); a.M = h->b_model;
+  a.P = static_cast<float2*>(h->d_avg); a.M = h->b_model;
   a.Jf[0] = h->d_Jf[0]; a.Jf[1] = h->d_Jf[1];
   a.part = h->b_part; a.status = h->d_status; a.rel = h->d_rel;
   a.jones = static_cast<float2*>(d_jones);
@@ -503,7 +504,7 @@ int blocked_begin(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_src
 int blocked_block(rts_peel_t* h) {
   constexpr int R = rts_peel_t::kRing;
   rts_peel_t::BlockRun& br = h->br;
-  const int BK = h->per_pass, n_pairs = BK * (BK - 1) / 2, b = br.b;
+  const int BK = h->per_pass, b = br.b;
   const int n_src = br.n_src, s0 = b * BK, nblk = std::min(BK, n_src - s0);
   const double* h_src = br.src.data();
   cudaStream_t s = h->b_main;
@@ -522,7 +523,7 @@ int blocked_block(rts_peel_t* h) {
       if (q > 0)
         k_block_model<<<bl_grid, 256, 0, s>>>(als_solution(h), h_src[3 * (k - 1) + 2], h->d_bl_ant, h->n_bl,
                                                h->b_model + (size_t)(q - 1) * h->n_bl * 4);
-      k_block_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, Dt, n_pairs, h->n_bl,
+      k_block_correct<<<bl_grid, 256, 0, s>>>(h->b_avg, q, h->b_model, Dt, h->n_bl,
                                               static_cast<float2*>(h->d_avg));
       span.end(q > 0 ? 2 : 1);
     }
@@ -889,6 +890,8 @@ int rts_peel_cadence_taylor(rts_peel_t* h, const void* d_vis, void* d_resid, int
   int rc = validate_sources(h, n_src, h_src);
   if (rc) return rc;
   if (n_src > 0 && (!d_gain || !d_slope)) return fail(h, RTS_EINVAL, "d_gain and d_slope are required");
+  if (n_src > 0 && (misaligned(d_gain) || misaligned(d_slope)))
+    return fail(h, RTS_EINVAL, "d_gain and d_slope must start on a 16-byte boundary");
   if (taylor_blocked(h))
     return peel_taylor_blocked(h, d_vis, d_resid, n_src, h_src, d_gain, d_slope, h_status, as_stream(stream));
   return peel_taylor(h, d_vis, d_resid, n_src, h_src, d_gain, d_slope, h_status, as_stream(stream));
@@ -1059,6 +1062,7 @@ int rts_peel_cadence(rts_peel_t* h, const void* d_vis, void* d_resid, int32_t n_
   int rc = validate_sources(h, n_src, h_src);
   if (rc) return rc;
   if (n_src > 0 && !d_jones) return fail(h, RTS_EINVAL, "d_jones is NULL");
+  if (n_src > 0 && misaligned(d_jones)) return fail(h, RTS_EINVAL, "d_jones must start on a 16-byte boundary");
   return peel_device(h, d_vis, d_resid, n_src, h_src, d_jones, h_status, as_stream(stream));
 }
 
@@ -1074,6 +1078,7 @@ int rts_peel_shard_begin(rts_peel_t* h, const void* d_vis, void* d_resid, int32_
   if (rc) return rc;
   if (n_src < 1) return fail(h, RTS_EINVAL, "a channel-shard cadence needs n_src >= 1");
   if (!d_jones) return fail(h, RTS_EINVAL, "d_jones is NULL");
+  if (misaligned(d_jones)) return fail(h, RTS_EINVAL, "d_jones must start on a 16-byte boundary");
   rc = blocked_begin(h, d_vis, d_resid, n_src, h_src, d_jones, as_stream(stream));
   if (rc) {
     h->br.active = false;

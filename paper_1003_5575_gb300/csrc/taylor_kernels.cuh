@@ -48,23 +48,6 @@ __device__ inline float2 taylor_model_entry(const double2* __restrict__ X, int i
   return make_float2((float)(S * v.x), (float)(S * v.y));
 }
 
-// Reduce 16 floats over the 32 lanes of a warp (each level exchanges half of the
-// remaining values with the partner lane); afterwards lane L holds the warp
-// total of value index L >> 1.
-__device__ inline float warp_reduce_scatter16f(float (&v)[16], int lane) {
-  #pragma unroll
-  for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
-    const bool upper = (lane & o) != 0;
-    #pragma unroll
-    for (int i = 0; i < n / 2; ++i) {
-      const float send = upper ? v[i] : v[i + n / 2];
-      const float keep = upper ? v[i + n / 2] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
-
 template <bool SUB, bool ACC>
 __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_taylor(TaylorStreamArgs ta) {
   const StreamArgs& a = ta.s;

@@ -258,7 +258,7 @@ def test_mixed_adjoint_sweeps_match_oracle(name, cad, grad_kernel):
 
 
 def test_misaligned_cube_rejected():
-    """A cube that does not start on a 16-byte boundary is refused on the host."""
+    """A cube or a Jones array that does not start on a 16-byte boundary is refused on the host."""
     cad = Cadence(4, 16, 2, 2, seed=72)
     p = make_peeler(cad, "mixed")
     buf = torch.zeros(cad.n_vis * 4 + 1, dtype=torch.complex64, device="cuda")
@@ -269,6 +269,11 @@ def test_misaligned_cube_rejected():
         p.grad(v, J, src)
     with pytest.raises(RuntimeError, match="16-byte"):
         p.cadence(v, cad.sources())
+    # a Jones array one complex64 past a 16-byte boundary (never launched on)
+    vis = torch.zeros(p.cube_shape, dtype=torch.complex64, device="cuda")
+    jbuf = torch.zeros(cad.n_src * cad.n_ant * 4 + 1, dtype=torch.complex64, device="cuda")
+    with pytest.raises(RuntimeError, match="16-byte"):
+        p.cadence(vis, cad.sources(), jones=jbuf[1:].view(cad.n_src, cad.n_ant, 4))
     p.close()
 
 
