@@ -71,6 +71,8 @@ constexpr int kTc5Compute = 512;             // 16 compute warps (4 per TMEM lan
 constexpr int kTc5Issuers = 4;               // and 4 warps whose lane 0 issues one accumulator's MMAs
 constexpr int kTc5Threads = kTc5Compute + 32 * kTc5Issuers;
 constexpr int kTc5Src = 64;                  // sources per role
+constexpr int kTc5BaselinesPerCta = 16;     // baselines a CTA peels one after another (not Taylor):
+                                             // its set-up and first operands are paid once for them
 constexpr int kTc5MaxChan = 768;             // NQ <= 48: 5 NQ accumulator columns beside A_s
 constexpr uint32_t kTc5MaxPolls = 1u << 17;  // mbarrier polls (each up to 20 us) before giving up
 constexpr int kTc5T2Row = 17;                // T2 table row stride (float2): conflict-free column reads
@@ -123,7 +125,7 @@ __device__ __forceinline__ float2 tc05_split(float x) {
 }
 
 template <bool SUB, bool ACC, bool TAY = false>
-__global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArgs a, int bk, int* err) {
+__global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArgs a, int bk, int nb, int* err) {
   using namespace tc05;
   const int nq = (a.n_chan + 15) >> 4;
   const int NQ = (nq + 15) & ~15;           // 16, 32 or 48
@@ -157,7 +159,11 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
     return m == 0 ? 1.f : (m == 1 ? u : u * u);
   };
 
-  const int64_t bl = blockIdx.x;
+  // baselines bl0 .. bl0 + nbl - 1, their time steps one after another: step g
+  // is time g % n_time of baseline bl0 + g / n_time
+  const int64_t bl0 = (int64_t)blockIdx.x * nb;
+  const int nbl = TAY ? 1 : (int)min((int64_t)nb, a.n_bl - bl0), n_steps = nbl * a.n_time;
+  auto bl_of = [&](int g) { return bl0 + g / a.n_time; };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qtr = warp & 3, cg = warp >> 2;
   const uint32_t lane_base = (uint32_t)(32 * qtr) << 16;
 
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   if (SUB)
     for (int i = tid; compute && i < kTc5Src * 4; i += kTc5Compute) {
       const int s = i >> 2, e = i & 3;
-      mtab[i] = s < n_sub_slots ? a.M_sub[((size_t)s * a.n_bl + bl) * 4 + e] : make_float2(0.f, 0.f);
+      mtab[i] = s < n_sub_slots ? a.M_sub[((size_t)s * a.n_bl + bl0) * 4 + e] : make_float2(0.f, 0.f);
     }
   if (SUB && TAY) {
     // the Taylor subtraction's A_s coefficients, slot (k, m), channel offset r:
@@ -219,20 +225,20 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   const uint64_t dbs_hi = desc_kmajor(smem_u32(bs_hi), 128, 4096), dbs_lo = desc_kmajor(smem_u32(bs_lo), 128, 4096);
   const uint64_t dba_hi = desc_kmajor(smem_u32(ba_hi), 128, 64 * NQ), dba_lo = desc_kmajor(smem_u32(ba_lo), 128, 64 * NQ);
 
-  // strip of time step t -> buffer t & 1 (thread 0)
-  auto issue_load = [&](int t) {
-    const int b = t & 1;
+  // strip of step g -> buffer g & 1 (thread 0)
+  auto issue_load = [&](int g) {
+    const int b = g & 1, t = g % a.n_time;
     mbar_expect_tx(&mbar[2 + b], strip_bytes);
-    bulk_load(strip0 + (size_t)b * n16 * 8, a.src + ((size_t)t * a.n_bl + bl) * a.n_chan * 2, strip_bytes,
+    bulk_load(strip0 + (size_t)b * n16 * 8, a.src + ((size_t)t * a.n_bl + bl_of(g)) * a.n_chan * 2, strip_bytes,
               &mbar[2 + b]);
   };
-  // the phases of both roles at time step t -> ring slot t & 1 (thread 0): one
-  // bulk copy of bk entries per role, completing on mbarrier 6 + (t & 1)
-  auto issue_ph = [&](int t) {
-    const int b = t & 1;
+  // the phases of both roles at step g -> ring slot g & 1 (thread 0): one bulk
+  // copy of bk entries per role, completing on mbarrier 6 + (g & 1)
+  auto issue_ph = [&](int g) {
+    const int b = g & 1;
     const uint32_t bytes = (uint32_t)bk * sizeof(PhaseAB);
     mbar_expect_tx(&mbar[6 + b], (SUB ? bytes : 0u) + (ACC ? bytes : 0u));
-    const size_t at = ((size_t)bl * a.n_time + t) * bk;
+    const size_t at = ((size_t)bl_of(g) * a.n_time + g % a.n_time) * bk;
     if (SUB) bulk_load(ph + 2 * kTc5Src * b, a.ph_sub + at, bytes, &mbar[6 + b]);
     if (ACC) bulk_load(ph + 2 * kTc5Src * b + kTc5Src, a.ph_acc + at, bytes, &mbar[6 + b]);
   };
@@ -489,6 +495,16 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       ks[u] = tt;
     }
   };
+  // a baseline's averages out, the sums reset for the next (not Taylor: one
+  // baseline per CTA there)
+  auto flush_avg = [&](int64_t blf) {
+    const int k = tid >> 3, i = tid & 7;     // value i = (re, im) of pol i / 2
+    if (k < a.n_acc)
+      reinterpret_cast<float*>(a.avg)[((size_t)k * a.n_bl + blf) * 8 + i] =
+          (float)(((double)ks[0] - (double)kc[0]) * a.inv_n);
+    ks[0] = 0.f;
+    kc[0] = 0.f;
+  };
 
   // the 16 compute warps' own barrier (the MMA-issuing warp is not in it)
   auto csync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(kTc5Compute) : "memory"); };
@@ -511,7 +527,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
     if (lane == 0) {
       uint32_t p_sub = 0, p_avg = 0;
       const uint32_t id_s = idesc_tf32(128, NQ), id_a = idesc_tf32(128, 64);
-      for (int t = 0; t < a.n_time; ++t) {
+      for (int t = 0; t < n_steps; ++t) {
         if (SUB) {
           if (!wait_or_bad(&mbar[4], p_sub)) break;
           p_sub ^= 1;
@@ -569,18 +585,30 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       if (tid == 0 && !s_bad) mbar_arrive(&mbar[4]);
     }
 
-    for (int t = 0; t < a.n_time && !s_bad; ++t) {
+    int tt = 0;                              // the time step of step t
+    int64_t bl = bl0;                        // and its baseline
+    for (int t = 0; t < n_steps && !s_bad; ++t, bl += (++tt == a.n_time), tt = tt == a.n_time ? 0 : tt) {
       const int buf = t & 1;
+      const bool bl_last = !TAY && tt == a.n_time - 1 && t + 1 < n_steps;   // another baseline follows
       float* strip = strip0 + (size_t)buf * n16 * 8;
       // ---- C1 (beside the subtraction MMAs): the next step's strip and
       // phases, the previous step's T2 contraction, T1 and T2 of the averaged
       // sources
-      if (tid == 0 && t + 1 < a.n_time) {
+      if (tid == 0 && t + 1 < n_steps) {
         if (SUB && t >= 1) bulk_wait_read();   // the residual store of step t - 1 has left buffer (t + 1) & 1
         issue_ph(t + 1);
         issue_load(t + 1);
         if ((t + 1) & 1) ++issued1;
         else ++issued0;
+      }
+      // the next baseline's model matrices into mtab (free since the previous
+      // step formed this step's A_s) by asynchronous copies, before this step
+      // forms the next step's A_s in C3
+      if (SUB && bl_last && tid < kTc5Src * 4 && (tid >> 2) < n_sub_slots) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(mtab + tid);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa),
+                     "l"(a.M_sub + ((size_t)(tid >> 2) * a.n_bl + bl + 1) * 4 + (tid & 3)) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
       }
       float2 t1v[12];
       if (ACC) {
@@ -588,6 +616,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
         if (!wait_ph(t)) s_bad = 1;
         csync();                             // parts written; t2a free
         if (t > 0) avg_accumulate();
+        if (!TAY && tt == 0 && t > 0) flush_avg(bl - 1);   // the previous baseline is complete
         aa_compute(t1v, ph_slot(t) + kTc5Src);
         t2_fill(t2a, ph_slot(t) + kTc5Src);
       }
@@ -617,16 +646,17 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       csync();
       if (ACC && tid == 0) mbar_arrive(&mbar[5]);
       if (SUB && tid == 0) {
-        bulk_store(a.dst + ((size_t)t * a.n_bl + bl) * a.n_chan * 2, strip, strip_bytes);
+        bulk_store(a.dst + ((size_t)tt * a.n_bl + bl) * a.n_chan * 2, strip, strip_bytes);
         bulk_commit();
       }
       // ---- C3 (beside the average MMAs): the next step's subtraction tables
       // and A_s hi (its TMEM columns are free of the average)
-      const bool next_sub = SUB && t + 1 < a.n_time;
+      const bool next_sub = SUB && t + 1 < n_steps;
       if (next_sub) {
         if (!wait_ph(t + 1)) s_bad = 1;
         bs_fill(ph_slot(t + 1));
         t2_fill(t2s, ph_slot(t + 1));
+        if (bl_last) asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's model copy
         csync();
         as_store_hi(as_lo);
       }
@@ -665,12 +695,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       csync();
       avg_accumulate();
     }
-    if (ACC && !s_bad && !TAY) {
-      const int k = tid >> 3, i = tid & 7;   // value i = (re, im) of pol i / 2
-      if (k < a.n_acc)
-        reinterpret_cast<float*>(a.avg)[((size_t)k * a.n_bl + bl) * 8 + i] =
-            (float)(((double)ks[0] - (double)kc[0]) * a.inv_n);
-    }
+    if (ACC && !s_bad && !TAY) flush_avg(bl0 + nbl - 1);
     if (ACC && !s_bad && TAY) {
       // the moments M_kn = sum_{m <= n} C(n, m) Q_{k,m,n-m} from the compensated sums
       // (the coefficient table is no longer read: its words hold them)
@@ -691,7 +716,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
           return (double)qs[w] - (double)qs[w + 1];
         };
         const double V = n == 0 ? val(0) : (n == 1 ? val(1) + val(3) : val(2) + 2.0 * val(4) + val(5));
-        reinterpret_cast<float*>(a.avg)[((size_t)s * a.n_bl + bl) * 8 + i] = (float)(V * a.inv_n);
+        reinterpret_cast<float*>(a.avg)[((size_t)s * a.n_bl + bl0) * 8 + i] = (float)(V * a.inv_n);
       }
     }
     if (tid == 0) {

@@ -426,9 +426,11 @@ int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a,
   const unsigned grid = (unsigned)h->n_bl;
   if (h->block_tc05) {
     const size_t tsm = tc05_launch_smem(h);
-    if (sub && acc) k_block_pass_tc05<true, true><<<grid, kTc5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
-    else if (sub) k_block_pass_tc05<true, false><<<grid, kTc5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
-    else k_block_pass_tc05<false, true><<<grid, kTc5Threads, tsm, s>>>(a, h->per_pass, h->d_perr);
+    const int nb = kTc5BaselinesPerCta;
+    const unsigned g5 = (unsigned)((h->n_bl + nb - 1) / nb);
+    if (sub && acc) k_block_pass_tc05<true, true><<<g5, kTc5Threads, tsm, s>>>(a, h->per_pass, nb, h->d_perr);
+    else if (sub) k_block_pass_tc05<true, false><<<g5, kTc5Threads, tsm, s>>>(a, h->per_pass, nb, h->d_perr);
+    else k_block_pass_tc05<false, true><<<g5, kTc5Threads, tsm, s>>>(a, h->per_pass, nb, h->d_perr);
     span.end(1);
     return check_launch(h, "block pass launch");
   }
@@ -778,9 +780,9 @@ int launch_taylor_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a
   Span span(h, RTS_K_BLOCK_PASS, s);
   const unsigned grid = (unsigned)h->n_bl;
   const size_t tsm = tc05_tay_launch_smem(h);
-  if (sub && acc) k_block_pass_tc05<true, true, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, h->d_perr);
-  else if (sub) k_block_pass_tc05<true, false, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, h->d_perr);
-  else k_block_pass_tc05<false, true, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, h->d_perr);
+  if (sub && acc) k_block_pass_tc05<true, true, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, 1, h->d_perr);
+  else if (sub) k_block_pass_tc05<true, false, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, 1, h->d_perr);
+  else k_block_pass_tc05<false, true, true><<<grid, kTc5Threads, tsm, s>>>(a, 32, 1, h->d_perr);
   span.end(1);
   return check_launch(h, "Taylor block pass launch");
 }

@@ -273,16 +273,30 @@ __device__ void solve_correct_rows(const BlockSolveArgs& a, int q, const unsigne
       const float4* Jk1 = JC + ((size_t)kTileAnt + col) * kCorrMaxJ;
       #pragma unroll 2
       for (int j = jl; j < q; j += JL) {
-        float2 M[4];
-        block_model4(JR[j], JR[q + j], Jk0[j], Jk1[j], Sj[j], M);
+        // M_j D = S_j D J_i J_k^H: w_rm = S_j D J_i[r][m], then acc[2r + c] +=
+        // sum_m w_rm conj(J_k[c][m])
+        const float4 i0 = JR[j], i1 = JR[q + j], k0 = Jk0[j], k1 = Jk1[j];
         const float2 d = Dd[j];
-        if (j == q - 1) {
+        const float S = Sj[j];
+        if (j == q - 1) {                      // the model matrix of source q-1, for the pass
+          float2 M[4];
+          block_model4(i0, i1, k0, k1, S, M);
           float4* dm = reinterpret_cast<float4*>(a.M + ((size_t)(q - 1) * a.n_bl + bl) * 4);
           dm[0] = make_float4(M[0].x, M[0].y, M[1].x, M[1].y);
           dm[1] = make_float4(M[2].x, M[2].y, M[3].x, M[3].y);
         }
-        #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[e] = cadd(acc[e], cmul(M[e], d));
+        const float2 sd = make_float2(S * d.x, S * d.y);
+        const float2 w00 = cmul(sd, make_float2(i0.x, i0.y)), w01 = cmul(sd, make_float2(i0.z, i0.w));
+        const float2 w10 = cmul(sd, make_float2(i1.x, i1.y)), w11 = cmul(sd, make_float2(i1.z, i1.w));
+        auto cfma = [](float2 acc2, float2 w, float kx, float ky) {     // acc + w conj(k)
+          acc2.x = fmaf(w.x, kx, fmaf(w.y, ky, acc2.x));
+          acc2.y = fmaf(w.y, kx, fmaf(-w.x, ky, acc2.y));
+          return acc2;
+        };
+        acc[0] = cfma(cfma(acc[0], w00, k0.x, k0.y), w01, k0.z, k0.w);
+        acc[1] = cfma(cfma(acc[1], w00, k1.x, k1.y), w01, k1.z, k1.w);
+        acc[2] = cfma(cfma(acc[2], w10, k0.x, k0.y), w11, k0.z, k0.w);
+        acc[3] = cfma(cfma(acc[3], w10, k1.x, k1.y), w11, k1.z, k1.w);
       }
     }
     float v[8] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y, acc[2].x, acc[2].y, acc[3].x, acc[3].y};
@@ -397,9 +411,9 @@ __device__ void solve_correct(const BlockSolveArgs& a, int q, unsigned char* sme
 static_assert(kSolveWarps == 16 && kSolveThreads == 16 * kTileAnt,
               "a correction pass: at least one row of kTileAnt columns x 16 term lanes");
 
-// at most 64 registers a thread: half of an SM, so the geometry kernels of later
-// blocks (low-priority stream) keep running beside it
-__global__ void __launch_bounds__(kSolveThreads, 2) k_block_solve(BlockSolveArgs a) {
+// at most 96 registers a thread (three quarters of an SM's register file), so a CTA
+// of the geometry kernels of later blocks (low-priority stream) keeps running beside it
+__global__ void __maxnreg__(96) k_block_solve(BlockSolveArgs a) {
   extern __shared__ __align__(16) unsigned char solve_smem[];
   const int n_ant = a.n_ant;
   // the rows and the staged iterate share their space with the correction's tiles

@@ -441,7 +441,8 @@ __device__ inline float re_inner(const float2 (&a)[4], const float2 (&b)[4]) {
 }
 
 constexpr int kRotThreads = 512;
-constexpr int kRotMaxGrid = 64;    // CTAs: the last one sums at most 4 partials per lane
+constexpr int kRotMaxGrid = 256;   // CTAs (one baseline a thread at 512 antennas): the last one
+                                   // sums at most 16 partials per lane
 
 __global__ void __launch_bounds__(kRotThreads) k_taylor_rot_sums(TaylorRotArgs a) {
   __shared__ float s_w[kRotThreads / 32][kRotVals];
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(kRotThreads) k_taylor_rot_sums(TaylorRotArgs a
   // sums in trees: FP32 within each warp (an FP64 warp instruction costs 64
   // times an FP32 one here), FP64 over the CTA's 16 warps (16 lanes per value)
   // and, in the last CTA, over the grid's partials (16 lanes per value, up to
-  // 4 partials each)
+  // 16 partials each)
   #pragma unroll
   for (int i = 0; i < kRotVals; ++i) {
     float v = acc[i];
