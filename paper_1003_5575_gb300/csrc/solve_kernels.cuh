@@ -318,8 +318,18 @@ __device__ void solve_correct_rows(const BlockSolveArgs& a, int q, const unsigne
     if (valid && (JL < 16 || (jl & 1) == 0)) {
       const float* AR = reinterpret_cast<const float*>(st + offA) + ((size_t)rr * kTileAnt + c) * 8 + base;
       float* P = reinterpret_cast<float*>(a.P + bl * 4) + base;
-      #pragma unroll
-      for (int f = 0; f < F; ++f) P[f] = AR[f] - v[f];
+      if (F >= 4) {                            // 16-byte accesses (the floats of a baseline are 32-byte aligned)
+        #pragma unroll
+        for (int f = 0; f < F; f += 4) {
+          const float4 A4 = *reinterpret_cast<const float4*>(AR + f);
+          *reinterpret_cast<float4*>(P + f) = make_float4(A4.x - v[f], A4.y - v[f + 1], A4.z - v[f + 2], A4.w - v[f + 3]);
+        }
+      } else if (F == 2) {
+        const float2 A2 = *reinterpret_cast<const float2*>(AR);
+        *reinterpret_cast<float2*>(P) = make_float2(A2.x - v[0], A2.y - v[1]);
+      } else {
+        P[0] = AR[0] - v[0];
+      }
     }
   }
 }
