@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
   // baselines bl0 .. bl0 + nbl - 1, their time steps one after another: step g
   // is time g % n_time of baseline bl0 + g / n_time
   const int64_t bl0 = (int64_t)blockIdx.x * nb;
-  const int nbl = TAY ? 1 : (int)min((int64_t)nb, a.n_bl - bl0), n_steps = nbl * a.n_time;
+  const int nbl = TAY ? 1 : (int)min((int64_t)nb, a.n_bl - bl0), n_steps = TAY ? a.n_time : nbl * a.n_time;
   auto bl_of = [&](int g) { return bl0 + g / a.n_time; };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, qtr = warp & 3, cg = warp >> 2;
   const uint32_t lane_base = (uint32_t)(32 * qtr) << 16;
@@ -585,9 +585,12 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_block_pass_tc05(BlockPassArg
       if (tid == 0 && !s_bad) mbar_arrive(&mbar[4]);
     }
 
-    int tt = 0;                              // the time step of step t
-    int64_t bl = bl0;                        // and its baseline
-    for (int t = 0; t < n_steps && !s_bad; ++t, bl += (++tt == a.n_time), tt = tt == a.n_time ? 0 : tt) {
+    int tt_run = 0;                          // the time step of step t
+    int64_t bl_run = bl0;                    // and its baseline (Taylor: step t is time t of bl0)
+    for (int t = 0; t < n_steps && !s_bad;
+         ++t, tt_run = (TAY || tt_run + 1 == a.n_time) ? 0 : tt_run + 1, bl_run += (!TAY && tt_run == 0)) {
+      const int tt = TAY ? t : tt_run;
+      const int64_t bl = TAY ? bl0 : bl_run;
       const int buf = t & 1;
       const bool bl_last = !TAY && tt == a.n_time - 1 && t + 1 < n_steps;   // another baseline follows
       float* strip = strip0 + (size_t)buf * n16 * 8;

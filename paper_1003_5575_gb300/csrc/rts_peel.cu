@@ -426,7 +426,8 @@ int launch_block_pass(rts_peel_t* h, bool sub, bool acc, const BlockPassArgs& a,
   const unsigned grid = (unsigned)h->n_bl;
   if (h->block_tc05) {
     const size_t tsm = tc05_launch_smem(h);
-    const int nb = kTc5BaselinesPerCta;
+    // up to kTc5BaselinesPerCta baselines a CTA, keeping at least 8 waves of CTAs
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kTc5BaselinesPerCta, h->n_bl / (8 * h->n_sm)));
     const unsigned g5 = (unsigned)((h->n_bl + nb - 1) / nb);
     if (sub && acc) k_block_pass_tc05<true, true><<<g5, kTc5Threads, tsm, s>>>(a, h->per_pass, nb, h->d_perr);
     else if (sub) k_block_pass_tc05<true, false><<<g5, kTc5Threads, tsm, s>>>(a, h->per_pass, nb, h->d_perr);
