@@ -244,7 +244,7 @@ __device__ __forceinline__ void solve_cp_wait() { asm volatile("cp.async.wait_gr
 
 
 // One chunk's rows of a correction tile (see solve_correct): JL term lanes per
-// baseline (JL >= q where q < 16), kSolveThreads / (kTileAnt JL) rows at a time;
+// baseline (JL >= q where q < 8, else 8), kSolveThreads / (kTileAnt JL) rows at a time;
 // thread (row s, column c, term lane l) sums the terms j = l (mod JL) of its
 // baseline, and the JL lanes are added by a fixed shuffle tree that leaves
 // each lane max(1, 8 / JL) of the 8 floats.  Stage layout: D [R][kTileAnt][q]
@@ -271,7 +271,7 @@ __device__ void solve_correct_rows(const BlockSolveArgs& a, int q, const unsigne
       const float4* JR = reinterpret_cast<const float4*>(st + offJ) + (size_t)rr * 2 * q;
       const float4* Jk0 = JC + (size_t)col * kCorrMaxJ;
       const float4* Jk1 = JC + ((size_t)kTileAnt + col) * kCorrMaxJ;
-      #pragma unroll 2
+      #pragma unroll 4
       for (int j = jl; j < q; j += JL) {
         // M_j D = S_j D J_i J_k^H: w_rm = S_j D J_i[r][m], then acc[2r + c] +=
         // sum_m w_rm conj(J_k[c][m])
@@ -337,8 +337,9 @@ __device__ void solve_correct_rows(const BlockSolveArgs& a, int q, const unsigne
 // Corrected average of source q >= 1 of the block, P_q = A_q - sum_{j<q} M_j D_jq,
 // with M_j = S_j J_i^j J_k^jH recomputed from the solved FP32 Jones matrices.
 // The baselines (i < k) are cut into tiles of kTileAnt x kTileAnt antennas
-// (row group g1 <= column group g2); CTA c takes tiles c, c + G, ...  The
-// Jones matrices of the tile's column antennas for sources 0 .. q-1 are staged
+// (row group g1 <= column group g2); CTA c takes an equal share of all tiles'
+// rows (in tile, row order: parts of at most two tiles).  The Jones matrices
+// of the tile's column antennas for sources 0 .. q-1 are staged
 // in shared memory once per tile; the tile's rows go in chunks of as many rows
 // as a stage holds (all of them for small q), two stages filled by
 // asynchronous copies one chunk ahead (spread over all threads): the row's D values (its
@@ -357,33 +358,41 @@ __device__ void solve_correct(const BlockSolveArgs& a, int q, unsigned char* sme
   // rows per chunk, and the stage layout
   const int R = max(1, min(kTileAnt, (int)(kCorrStageBytes / ((size_t)q * kTileAnt * 8 + (size_t)q * 32 + 1024))));
   const size_t offJ = (size_t)R * kTileAnt * q * sizeof(float2), offA = offJ + (size_t)R * 2 * q * sizeof(float4);
-  for (int t = blockIdx.x; t < n_tiles; t += G) {
+  // this CTA's share of the tiles' rows, in (tile, row) order: at most two tiles
+  const int64_t n_rows_all = (int64_t)n_tiles * kTileAnt;
+  const int64_t gr_end = n_rows_all * (blockIdx.x + 1) / G;
+  for (int64_t gr = n_rows_all * blockIdx.x / G; gr < gr_end;) {
+    const int t = (int)(gr / kTileAnt), rlo = (int)(gr - (int64_t)t * kTileAnt);
+    const int rhi = (int)min((int64_t)kTileAnt, rlo + (gr_end - gr));
+    gr += rhi - rlo;
     int g1 = 0, rest = t;
     while (rest >= ngr - g1) { rest -= ngr - g1; ++g1; }
     const int g2 = g1 + rest;
     const int I0 = g1 * kTileAnt, K0 = g2 * kTileAnt;
     const int nI = min(kTileAnt, n_ant - I0), nK = min(kTileAnt, n_ant - K0);
-    const int n_ch = (nI + R - 1) / R;
+    const int r_hi = min(rhi, nI);             // rows rlo .. r_hi - 1 of the tile
+    if (r_hi <= rlo) continue;                 // CTA-uniform
+    const int n_ch = (r_hi - rlo + R - 1) / R;
     auto issue = [&](int ch) {
       unsigned char* st = ring + (size_t)(ch & 1) * kCorrStageBytes;
-      const int nr = min(R, nI - ch * R);
+      const int nr = min(R, r_hi - rlo - ch * R);
       // D runs of the chunk's rows, spread over all threads: element x of row rr
       for (int idx = tid; idx < nr * kTileAnt * q; idx += kSolveThreads) {
         const int rr = idx / (kTileAnt * q), x = idx - rr * kTileAnt * q;
-        const int i = I0 + ch * R + rr, k0 = max(K0, i + 1), nk = K0 + nK - k0;
+        const int i = I0 + rlo + ch * R + rr, k0 = max(K0, i + 1), nk = K0 + nK - k0;
         if (x < nk * q)
           solve_cp8(reinterpret_cast<float2*>(st) + (size_t)rr * kTileAnt * q + x,
                     a.Dtab + dbase + bl_index(n_ant, i, k0) * q + x);
       }
       // row Jones matrices (x = plane + 2 j) and plain averages (x = half + 2 column)
       for (int idx = tid; idx < nr * 2 * q; idx += kSolveThreads) {
-        const int rr = idx / (2 * q), x = idx - rr * 2 * q, i = I0 + ch * R + rr;
+        const int rr = idx / (2 * q), x = idx - rr * 2 * q, i = I0 + rlo + ch * R + rr;
         solve_cp16(reinterpret_cast<float4*>(st + offJ) + (size_t)rr * 2 * q + (x & 1) * q + (x >> 1),
                    J4 + ((size_t)(a.s0 + (x >> 1)) * n_ant + i) * 2 + (x & 1));
       }
       for (int idx = tid; idx < nr * 2 * kTileAnt; idx += kSolveThreads) {
         const int rr = idx / (2 * kTileAnt), x = idx - rr * 2 * kTileAnt;
-        const int i = I0 + ch * R + rr, k0 = max(K0, i + 1), nk = K0 + nK - k0;
+        const int i = I0 + rlo + ch * R + rr, k0 = max(K0, i + 1), nk = K0 + nK - k0;
         if (x < 2 * nk)
           solve_cp16(reinterpret_cast<float4*>(st + offA) + (size_t)rr * kTileAnt * 2 + x,
                      reinterpret_cast<const float4*>(a.Ablk + ((size_t)q * a.n_bl + bl_index(n_ant, i, k0)) * 4) + x);
@@ -407,9 +416,8 @@ __device__ void solve_correct(const BlockSolveArgs& a, int q, unsigned char* sme
       }
       __syncthreads();
       const unsigned char* st = ring + (size_t)(ch & 1) * kCorrStageBytes;
-      const int r0 = ch * R, nrows = min(R, nI - r0);
-      if (q >= 16) solve_correct_rows<16>(a, q, st, offJ, offA, JC, Sj, I0, K0, nK, r0, nrows);
-      else if (q >= 8) solve_correct_rows<8>(a, q, st, offJ, offA, JC, Sj, I0, K0, nK, r0, nrows);
+      const int r0 = rlo + ch * R, nrows = min(R, r_hi - r0);
+      if (q >= 8) solve_correct_rows<8>(a, q, st, offJ, offA, JC, Sj, I0, K0, nK, r0, nrows);
       else if (q >= 4) solve_correct_rows<4>(a, q, st, offJ, offA, JC, Sj, I0, K0, nK, r0, nrows);
       else if (q >= 2) solve_correct_rows<2>(a, q, st, offJ, offA, JC, Sj, I0, K0, nK, r0, nrows);
       else solve_correct_rows<1>(a, q, st, offJ, offA, JC, Sj, I0, K0, nK, r0, nrows);
