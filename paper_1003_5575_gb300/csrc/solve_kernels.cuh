@@ -573,21 +573,15 @@ __global__ void __maxnreg__(96) k_block_solve(BlockSolveArgs a) {
       }
       __syncthreads();
       // totals: total i = 12 s + u (slot s, value u) on warp i & 3 (the four
-      // sub-partitions), the slot's W warp sums in a fixed order.  Sweeps before
-      // the last in FP32 (two halves; their totals feed an FP32 solve); the last
-      // sweep in FP64 from the lane partials.
+      // sub-partitions), the slot's W warp sums added in FP64 in a fixed order
+      // (the last sweep's warp sums are FP64 from the lane partials on)
       if (tid < 128) {
         for (int i = (tid & 31) * 4 + (tid >> 5); i < 12 * a.apc; i += 128) {
-          const int s = i / 12, u = i - 12 * s, w0 = s * W, half = (W + 1) / 2;
+          const int s = i / 12, u = i - 12 * s, w0 = s * W;
           double tot;
           if (!last) {
-            float h0 = s_wp[w0][u], h1 = 0.f;
-            for (int w = 1; w < half; ++w) h0 += s_wp[w0 + w][u];
-            if (W > 1) {
-              h1 = s_wp[w0 + half][u];
-              for (int w = half + 1; w < W; ++w) h1 += s_wp[w0 + w][u];
-            }
-            tot = h0 + h1;                    // feeds the FP32 solve of this sweep
+            tot = (double)s_wp[w0][u];
+            for (int w = 1; w < W; ++w) tot += (double)s_wp[w0 + w][u];
           } else {
             tot = s_wp64[w0][u];
             for (int w = 1; w < W; ++w) tot += s_wp64[w0 + w][u];

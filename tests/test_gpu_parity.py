@@ -87,6 +87,10 @@ BLOCK_CASES = [
     ("ragged-blocked", Cadence(9, 37, 3, 4, seed=91), 8),           # 37 channels, ragged tiles
     ("max-channels", Cadence(8, 960, 2, 5, freq0_hz=167e6, seed=99), 64),    # largest tensor-core strip
     ("odd-channels", Cadence(12, 203, 3, 9, seed=97), 64),          # ragged 16-channel row tiles
+    ("odd-antennas", Cadence(40, 256, 4, 70, freq0_hz=167e6, seed=105), 64),   # 40 antennas: partial
+    #   32-antenna correction tiles off the diagonal, CTAs whose share of tile rows spans two tiles;
+    #   64 + 6 (256 channels: the oracle moves by 3.5e-8 under a 1e-7 x rms input perturbation, where
+    #   64 channels gave 8.7e-7, too ill-conditioned for the 1e-5 bound)
 ]
 # (pass kernel, solve kernel): FP32 FMA or tensor-core pass; the block's solve
 # chain as one cooperative launch (0) or as one launch per step (1)
