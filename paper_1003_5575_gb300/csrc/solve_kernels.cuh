@@ -7,39 +7,39 @@
 // as separate launches, that chain is n_iter + 2 small kernels per source,
 // each a few microseconds of work behind a launch.  Here one cooperative
 // launch runs the chain of a whole block: the CTAs stay resident and meet at
-// one grid-wide barrier after every sweep, n_iter barriers per source.
+// grid-wide barriers, one after each source's corrected average and one
+// after every sweep.
 //
-// Work split (G CTAs of kSolveThreads threads, G <= number of SMs):
-//   per antenna: antenna p belongs to CTA p % G (slot p / G).  Its row V_pq,
+// Per source q of the block (G CTAs of kSolveThreads threads, G <= SMs):
+//   corrected average (solve_correct): P_q = A_q - sum_{j<q} M_j D_jq for
+//     every baseline, by 32 x 32-antenna tiles.  Every CTA takes an equal
+//     share of the tiles' rows; a tile's column Jones matrices of sources
+//     0 .. q-1 are staged in shared memory, and its rows stream through a
+//     two-stage ring of asynchronous copies (a row's baselines are consecutive,
+//     so its D terms are one contiguous run in the target-major dir_index
+//     layout); M_j D = S_j D J_i J_k^H is recomputed from the solved FP32 Jones
+//     matrices instead of read back from HBM.  The term that needs source q-1
+//     also writes M_{q-1} for the block's pass.  Grid barrier.
+//   rows: antenna p belongs to CTA p % G (slot p / G).  Its row V_pq,
 //     q = 0..n_ant-1 (V_qp = V_pq^H applied while staging, V_pp = 0), is staged
-//     in shared memory once per source, and every sweep stages the FP32
-//     iterate of all antennas.  The CTA's warps are split evenly over its
-//     slots; lane l of the w-th warp of a slot takes the partners
-//     q = l + 32 w (+ 32 W u).  Products and per-lane partial sums are FP32,
-//     a warp's lanes are added in FP32 by a shuffle tree, and the W warps of a
-//     slot in two fixed-order FP32 halves whose sum is FP64 (the normal-
-//     equation accumulation).  The 2x2 solve, the iterate and its averaging
-//     are FP32 in sweeps 1 .. n_iter-1; the last sweep solves from the FP64
-//     totals in FP64 and takes the relative change of its FP64 iterate
-//     against the FP32 previous one in FP64 (the status compares that change
-//     with 1e-6, and the FP32 rounding of a solve would move it by several
-//     per cent near the threshold).
-//   per baseline, in the background: the corrected average of source q is
-//     A_q - sum_{j<q} M_j D_jq.  All terms but the last (j = q-1) only need
-//     sources solved before q-1, so they are summed while source q-1 is being
-//     solved: each CTA owns a contiguous range of baselines, and after it has
-//     arrived at a sweep's barrier it works through a 64-baseline chunk of
-//     that range while the other CTAs finish the sweep (each M_j recomputed
-//     from the solved FP32 Jones matrices, L2-resident, with the arithmetic
-//     that stores it, instead of read back from HBM).  The result P_q goes to
-//     one of two buffers by source parity, and the model matrices of source
-//     q-2 for the block's pass go out in the same chunks.  The last term is
-//     applied while the rows of source q are staged.  The statuses are
-//     reduced from per-antenna norms after the last source, off the chain.
+//     in shared memory from P_q.
+//   n_iter sweeps: every sweep stages the FP32 iterate of all antennas.  The
+//     CTA's warps are split evenly over its slots; lane l of the w-th warp of a
+//     slot takes the partners q = l + 32 w (+ 32 W u).  Products and per-lane
+//     partial sums are FP32, a warp's lanes are added in FP32 by a shuffle tree,
+//     and the W warps of a slot in FP64 (the normal-equation accumulation).  The
+//     2x2 solve, the iterate and its averaging are FP32 in sweeps
+//     1 .. n_iter-1; the last sweep converts the lane partials to FP64, solves
+//     in FP64 and takes the relative change of its FP64 iterate against the
+//     FP32 previous one in FP64 (the status compares that change with 1e-6,
+//     and the FP32 rounding of a solve would move it by several per cent near
+//     the threshold).  Grid barrier after each sweep.
+// After the block's last source: its model matrices, and every source's
+// status from the per-antenna norms of its last sweep (off the chain).
 //
 // FP64 arithmetic runs at 1/64 of the FP32 rate on GB300 and a warp
 // instruction costs the same with 4 or 32 lanes active: the FP64 part of a
-// sweep is two conversions and one addition per total, spread over four warps
+// sweep is a few conversions and additions per total, spread over four warps
 // on the four sub-partitions.
 //
 // Barriers spin on a global counter with a time limit: a CTA whose wait runs
