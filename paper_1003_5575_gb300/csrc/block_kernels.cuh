@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kBlkThreads, 3) k_block_pass(BlockPassArgs a) 
 }
 
 // ---------------------------------------------------------------------------
-// D_jk for every pair j < k of one block, per baseline:  Dtab[bl][k(k-1)/2 + j]
+// D_jk for every pair j < k of one block, per baseline:  Dtab[dir_index(n_bl, bl, j, k)]
 
 // Phase of the band-centre term of the pair: dA + (N-1) dB / 2 modulo one turn,
 // exactly, with dB taken as the signed representative in [-1/2, 1/2).  The
