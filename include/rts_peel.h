@@ -100,9 +100,12 @@ typedef struct rts_peel_config {
                            ceil(n_ant / n_SM) antennas fit in shared memory, about
                            n_ant <= 900 on GB300; otherwise as RTS_SOLVE_LAUNCHES),
                            RTS_SOLVE_LAUNCHES (1: one launch per ALS sweep, per
-                           correction and per model step).  Same arithmetic except
-                           the grouping of the FP32 partial sums of the normal
-                           equations (FP32-rounding-level differences). */
+                           correction and per model step).  The cooperative launch
+                           solves the 2x2 systems of the sweeps before the last in
+                           FP32 and the last in FP64, the per-step launches every
+                           sweep in FP64; both accumulate the normal equations'
+                           cross-thread sums in FP64, and their results agree to
+                           FP32 rounding (statuses outside a band around 1e-6). */
   int32_t grad_kernel;   /* RTS_PREC_MIXED adjoint (rts_peel_grad, rts_peel_offsets):
                            RTS_GRAD_AUTO (0: phasors factorised per 16-channel group into
                            two shared-memory tables, T1[q] T2[r], when the tables of all
