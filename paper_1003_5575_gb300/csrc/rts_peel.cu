@@ -380,6 +380,11 @@ int setup_block_solve(rts_peel_t* h) {
   RTS_CUDA(h, cudaFuncGetAttributes(&fa, k_block_solve));
   if (smem + fa.sharedSizeBytes + 1024 > (size_t)smem_max) return RTS_OK;
   RTS_CUDA(h, cudaFuncSetAttribute(k_block_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the whole unified memory as shared memory: the smallest carveout that holds one
+  // solve CTA leaves no room beside it for the next block's phase and Dirichlet
+  // kernels on the prep stream, which then wait for the solve to end
+  RTS_CUDA(h, cudaFuncSetAttribute(k_block_solve, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared));
   int occ = 0;
   RTS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_block_solve, kSolveThreads, smem));
   if (occ < 1) return RTS_OK;
